@@ -1,0 +1,787 @@
+/*
+ * sph_oracle.c -- plain, slow CPU reference ("oracle") for the SPH hot path of
+ * "The Shamrock code: I - Smoothed Particle Hydrodynamics on GPUs" (arXiv 2503.09713).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is used by the test-suite, by the smoke check and by the
+ * CPU-baseline leg of the benchmark; the product library never calls, links or loads it.  It shares
+ * no code, header, table or helper with the CUDA library.
+ *
+ * Conventions
+ *   - FP64 everywhere; compiled with -ffp-contract=off so that no multiply-add is fused.
+ *   - Every function names the passage of the paper it follows.  Where the paper is silent or
+ *     garbled the reading taken is stated in the comment.
+ *   - Functions that compute a quantity with a plain definition (Morton code, sort, radix tree,
+ *     bounding boxes, neighbour set, root of the density equation) compute that definition
+ *     directly.  Iterations (the smoothing-length update of App. F) follow the paper's steps.
+ *   - OpenMP only parallelises independent per-particle loops; every reduction is a min or max,
+ *     so results do not depend on the thread count.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+/* ====================================================================================== */
+/* Morton codes: App. B, Sect. "Morton codes" (remap to [0,1)^3, (2^beta)^3 integer grid,   */
+/* interleave X0 Y0 Z0 X1 Y1 Z1 ..., X most significant).                                   */
+/* ====================================================================================== */
+
+/* Integer grid coordinate of one axis: X = floor(((x - lo)/(hi - lo)) * 2^bits), clamped to
+ * [0, 2^bits - 1] (the remap excludes 1, so a point on the upper face joins the last cell). */
+uint64_t orc_quantise(double x, double lo, double hi, int bits)
+{
+    double s = (x - lo) / (hi - lo);
+    double g = s * (double)(1ULL << bits); /* power-of-two scale: exact */
+    double top = (double)((1ULL << bits) - 1ULL);
+    if (!(g >= 0.0)) g = 0.0;
+    if (g > top) g = top;
+    return (uint64_t)floor(g);
+}
+
+/* Interleave three bits-wide integers bit by bit, most significant first: X0 Y0 Z0 X1 ... */
+uint64_t orc_interleave(uint64_t X, uint64_t Y, uint64_t Z, int bits)
+{
+    uint64_t m = 0;
+    for (int i = 0; i < bits; i++) {
+        int b = bits - 1 - i;
+        m = (m << 3) | (((X >> b) & 1ULL) << 2) | (((Y >> b) & 1ULL) << 1) | ((Z >> b) & 1ULL);
+    }
+    return m;
+}
+
+/* Inverse of orc_interleave (used only by the round-trip pin). */
+void orc_deinterleave(uint64_t m, int bits, uint64_t *X, uint64_t *Y, uint64_t *Z)
+{
+    uint64_t x = 0, y = 0, z = 0;
+    for (int i = 0; i < bits; i++) {
+        int sh = 3 * (bits - 1 - i);
+        x = (x << 1) | ((m >> (sh + 2)) & 1ULL);
+        y = (y << 1) | ((m >> (sh + 1)) & 1ULL);
+        z = (z << 1) | ((m >> sh) & 1ULL);
+    }
+    *X = x; *Y = y; *Z = z;
+}
+
+void orc_morton(int64_t n, const double *x, const double *y, const double *z,
+                const double *lo, const double *hi, int bits, uint64_t *out)
+{
+    for (int64_t i = 0; i < n; i++)
+        out[i] = orc_interleave(orc_quantise(x[i], lo[0], hi[0], bits),
+                                orc_quantise(y[i], lo[1], hi[1], bits),
+                                orc_quantise(z[i], lo[2], hi[2], bits), bits);
+}
+
+/* Length of the longest common prefix of two nbits-long codes, Eq. delta_ab: clz(a xor b),
+ * counted within the nbits-wide representation. */
+int orc_delta(uint64_t a, uint64_t b, int nbits)
+{
+    uint64_t v = a ^ b;
+    if (v == 0) return nbits;
+    int lz = 0;
+    for (int k = 63; k >= 0; k--) {
+        if ((v >> k) & 1ULL) break;
+        lz++;
+    }
+    return lz - (64 - nbits);
+}
+
+/* ====================================================================================== */
+/* Sort by key (App. C, "Sort by Key"): (code, original index) pairs ordered by code; equal   */
+/* codes keep their original order, so the permutation is unique.                           */
+/* ====================================================================================== */
+typedef struct { uint64_t key; uint32_t idx; } orc_kv;
+
+static int orc_kv_cmp(const void *pa, const void *pb)
+{
+    const orc_kv *a = (const orc_kv *)pa, *b = (const orc_kv *)pb;
+    if (a->key < b->key) return -1;
+    if (a->key > b->key) return 1;
+    return (a->idx < b->idx) ? -1 : (a->idx > b->idx);
+}
+
+void orc_sort_by_key(int64_t n, const uint64_t *keys, uint64_t *sorted, uint32_t *perm)
+{
+    orc_kv *t = (orc_kv *)malloc((size_t)(n > 0 ? n : 1) * sizeof(orc_kv));
+    for (int64_t i = 0; i < n; i++) { t[i].key = keys[i]; t[i].idx = (uint32_t)i; }
+    qsort(t, (size_t)n, sizeof(orc_kv), orc_kv_cmp);
+    for (int64_t i = 0; i < n; i++) { sorted[i] = t[i].key; perm[i] = t[i].idx; }
+    free(t);
+}
+
+/* ====================================================================================== */
+/* Keep mask and reduction: Alg. "Removal mask initialisation and reduction algorithm"      */
+/* (App. C).  Reading: each pass reads the mask of the previous pass and writes a new one    */
+/* (the in-place parallel update of the paper is a race); a neighbour index that runs off    */
+/* either end gives delta = -1.                                                              */
+/* ====================================================================================== */
+void orc_keep_mask(int64_t n, const uint64_t *mu, int nbits, int n_red, uint8_t *xi)
+{
+    if (n <= 0) return;
+    /* duplicates: keep the first of every run of equal codes */
+    for (int64_t i = 0; i < n; i++) xi[i] = (i == 0) ? 1 : (mu[i] != mu[i - 1]);
+    uint8_t *nxt = (uint8_t *)malloc((size_t)n);
+    for (int pass = 0; pass < n_red; pass++) {
+        for (int64_t i = 0; i < n; i++) {
+            if (!xi[i]) { nxt[i] = 0; continue; }
+            int64_t im1 = i - 1;
+            while (im1 >= 0 && !xi[im1]) im1--;
+            int64_t im2 = im1 - 1;
+            while (im2 >= 0 && !xi[im2]) im2--;
+            int64_t ip1 = i + 1;
+            while (ip1 < n && !xi[ip1]) ip1++;
+            int d0 = (ip1 < n) ? orc_delta(mu[i], mu[ip1], nbits) : -1;
+            int dm1 = (im1 >= 0) ? orc_delta(mu[im1], mu[i], nbits) : -1;
+            int dm2 = (im2 >= 0 && im1 >= 0) ? orc_delta(mu[im2], mu[im1], nbits) : -1;
+            nxt[i] = !(d0 < dm1 && dm2 < dm1);
+        }
+        memcpy(xi, nxt, (size_t)n);
+    }
+    free(nxt);
+}
+
+/* Stream compaction (App. C, "Reduction"; Fig. mortonlistbuild): id[j] = index of the j-th kept
+ * code, id[L] = n; mu_leaf[j] = mu[id[j]].  Returns L. */
+int64_t orc_compact(int64_t n, const uint64_t *mu, const uint8_t *xi, int64_t *id, uint64_t *mu_leaf)
+{
+    int64_t L = 0;
+    for (int64_t i = 0; i < n; i++)
+        if (xi[i]) { id[L] = i; mu_leaf[L] = mu[i]; L++; }
+    id[L] = n;
+    return L;
+}
+
+/* ====================================================================================== */
+/* Binary radix tree (App. B, "Binary radix tree" and "Karras algorithm", Table            */
+/* arrays_fig_karras).  Built here by its definition, top-down: the node over leaves          */
+/* [first,last] splits after the last leaf that shares with leaf `first` a prefix longer than */
+/* delta(first,last).  The left child covers [first,g], the right child [g+1,last]; a child   */
+/* over one leaf is that leaf (flag 1), otherwise it is the internal node whose index is the  */
+/* end of its range next to the split (g for the left child, g+1 for the right child); the    */
+/* root is internal node 0.  endrange holds the other end of each internal node's range.     */
+/* ====================================================================================== */
+static void orc_split(const uint64_t *mu, int nbits, int64_t node, int64_t first, int64_t last,
+                      int32_t *lchild, int32_t *rchild, uint8_t *lflag, uint8_t *rflag, int32_t *endrange)
+{
+    int d = orc_delta(mu[first], mu[last], nbits);
+    int64_t g = first;
+    for (int64_t k = first + 1; k < last; k++)
+        if (orc_delta(mu[first], mu[k], nbits) > d) g = k;
+    endrange[node] = (int32_t)((node == first) ? last : first);
+    lchild[node] = (int32_t)g;
+    lflag[node] = (g == first);
+    rchild[node] = (int32_t)(g + 1);
+    rflag[node] = (g + 1 == last);
+    if (g != first) orc_split(mu, nbits, g, first, g, lchild, rchild, lflag, rflag, endrange);
+    if (g + 1 != last) orc_split(mu, nbits, g + 1, g + 1, last, lchild, rchild, lflag, rflag, endrange);
+}
+
+/* mu_leaf: L sorted distinct codes.  Fills L-1 internal nodes. */
+void orc_radix_tree(int64_t L, const uint64_t *mu_leaf, int nbits, int32_t *lchild, int32_t *rchild,
+                    uint8_t *lflag, uint8_t *rflag, int32_t *endrange)
+{
+    if (L < 2) return;
+    orc_split(mu_leaf, nbits, 0, 0, L - 1, lchild, rchild, lflag, rflag, endrange);
+}
+
+/* Tight bounding box and largest smoothing length of every tree cell (App. C, "Compute tree cell
+ * sizes"; the h_max per cell is l_AABB,b of App. D).  Nodes 0..L-2 are internal, node L-1+j is
+ * leaf j.  A cell's particles are the sorted positions id[first] .. id[last+1]-1 of its leaf range.
+ * Positions/h are given in sorted order. */
+void orc_cell_boxes(int64_t L, const int64_t *id, const int32_t *endrange,
+                    const double *x, const double *y, const double *z, const double *h,
+                    double *bmin /*3*(2L-1)*/, double *bmax, double *hmax /*2L-1*/)
+{
+    int64_t nodes = 2 * L - 1;
+    for (int64_t c = 0; c < nodes; c++) {
+        int64_t first, last;
+        if (c < L - 1) {
+            int64_t e = endrange[c];
+            first = c < e ? c : e;
+            last = c < e ? e : c;
+        } else {
+            first = last = c - (L - 1);
+        }
+        double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        double hm = 0.0;
+        for (int64_t p = id[first]; p < id[last + 1]; p++) {
+            double r[3] = {x[p], y[p], z[p]};
+            for (int k = 0; k < 3; k++) {
+                if (r[k] < mn[k]) mn[k] = r[k];
+                if (r[k] > mx[k]) mx[k] = r[k];
+            }
+            if (h[p] > hm) hm = h[p];
+        }
+        for (int k = 0; k < 3; k++) { bmin[3 * c + k] = mn[k]; bmax[3 * c + k] = mx[k]; }
+        hmax[c] = hm;
+    }
+}
+
+/* ====================================================================================== */
+/* M4 cubic spline (Sect. 2.1: B-spline M4, 3-D normalisation).  Reading: Schoenberg M4 as in  */
+/* Monaghan & Lattanzio 1985, f(q) = 1 - 3/2 q^2 + 3/4 q^3 (q<1), (2-q)^3/4 (1<=q<2), 0 after,   */
+/* C_norm = 1/pi, R_kern = 2.  W = C_norm f(q)/h^3 (Eq. rhosphsum), q = r/h.                   */
+/* ====================================================================================== */
+double orc_m4_f(double q)
+{
+    if (q < 1.0) return 1.0 - 1.5 * q * q + 0.75 * q * q * q;
+    if (q < 2.0) { double t = 2.0 - q; return 0.25 * t * t * t; }
+    return 0.0;
+}
+
+double orc_m4_df(double q) /* df/dq */
+{
+    if (q < 1.0) return -3.0 * q + 2.25 * q * q;
+    if (q < 2.0) { double t = 2.0 - q; return -0.75 * t * t; }
+    return 0.0;
+}
+
+double orc_W(double r, double h) { return orc_m4_f(r / h) / (ORC_PI * h * h * h); }
+
+/* dW/dh at fixed r. */
+double orc_dWdh(double r, double h)
+{
+    double q = r / h;
+    return -(3.0 * orc_m4_f(q) + q * orc_m4_df(q)) / (ORC_PI * h * h * h * h);
+}
+
+/* F_ab(h) = rhat . grad_a W_ab(h) = dW/dr (Sect. 2.1 definition of F_ab). */
+double orc_F(double r, double h) { return orc_m4_df(r / h) / (ORC_PI * h * h * h * h); }
+
+/* ====================================================================================== */
+/* Neighbour sets (App. D criteria, App. C neighbour caches).                                */
+/* A pair (a,b), b != a, belongs to the set at radius scale s when                           */
+/*     r_ab^2 < (s * max(hc_a, hc_b))^2                                                       */
+/* with r_ab^2 = (dx*dx + dy*dy) + dz*dz evaluated in that order, dx = x_b - x_a reduced to the */
+/* nearest periodic image (dx > L/2: dx -= L; dx < -L/2: dx += L).  s = R_kern * chi for the  */
+/* cache (App. F tolerance chi), s = R_kern for the force support (object-object criterion).  */
+/* ====================================================================================== */
+typedef struct {
+    int64_t n;
+    int64_t *off; /* n+1 */
+    int32_t *ids; /* off[n] entries, each list ascending in b */
+} orc_nlist;
+
+static double orc_image(double d, double L, int periodic)
+{
+    if (periodic) {
+        if (d > 0.5 * L) d -= L;
+        else if (d < -0.5 * L) d += L;
+    }
+    return d;
+}
+
+static int orc_pair_in(const double *x, const double *y, const double *z, const double *hc,
+                       int64_t a, int64_t b, double s, const double *boxL, int periodic)
+{
+    double dx = orc_image(x[b] - x[a], boxL[0], periodic);
+    double dy = orc_image(y[b] - y[a], boxL[1], periodic);
+    double dz = orc_image(z[b] - z[a], boxL[2], periodic);
+    double r2 = (dx * dx + dy * dy) + dz * dz;
+    double hm = hc[a] > hc[b] ? hc[a] : hc[b];
+    double rad = s * hm;
+    return r2 < rad * rad;
+}
+
+/* Direct O(N^2) evaluation of the definition. */
+static void orc_nlist_brute(int64_t n, const double *x, const double *y, const double *z, const double *hc,
+                            double s, const double *boxL, int periodic, orc_nlist *nl)
+{
+    nl->n = n;
+    nl->off = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int64_t *cnt = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t a = 0; a < n; a++) {
+        int64_t c = 0;
+        for (int64_t b = 0; b < n; b++)
+            if (b != a && orc_pair_in(x, y, z, hc, a, b, s, boxL, periodic)) c++;
+        cnt[a] = c;
+    }
+    nl->off[0] = 0;
+    for (int64_t a = 0; a < n; a++) nl->off[a + 1] = nl->off[a] + cnt[a];
+    nl->ids = (int32_t *)malloc((size_t)(nl->off[n] > 0 ? nl->off[n] : 1) * sizeof(int32_t));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t a = 0; a < n; a++) {
+        int64_t o = nl->off[a];
+        for (int64_t b = 0; b < n; b++)
+            if (b != a && orc_pair_in(x, y, z, hc, a, b, s, boxL, periodic)) nl->ids[o++] = (int32_t)b;
+    }
+    free(cnt);
+}
+
+/* Same set through a uniform grid of cells no smaller than the largest radius: only particles in
+ * the 27 surrounding cells can satisfy the predicate, which is then evaluated exactly as above and
+ * the survivors listed in ascending index order.  Used for sizes beyond brute force; tests check it
+ * against orc_nlist_brute. */
+static int orc_cmp_i32(const void *a, const void *b)
+{
+    int32_t u = *(const int32_t *)a, v = *(const int32_t *)b;
+    return (u > v) - (u < v);
+}
+
+static void orc_nlist_grid(int64_t n, const double *x, const double *y, const double *z, const double *hc,
+                           double s, const double *lo, const double *boxL, int periodic, orc_nlist *nl)
+{
+    double hmax = 0.0;
+    for (int64_t i = 0; i < n; i++) if (hc[i] > hmax) hmax = hc[i];
+    double rmax = s * hmax;
+    int64_t nc[3];
+    for (int k = 0; k < 3; k++) {
+        double c = floor(boxL[k] / rmax);
+        if (c > 256) c = 256;
+        nc[k] = (int64_t)c;
+    }
+    if (nc[0] < 3 || nc[1] < 3 || nc[2] < 3 || n < 2048) {
+        orc_nlist_brute(n, x, y, z, hc, s, boxL, periodic, nl);
+        return;
+    }
+    int64_t ncell = nc[0] * nc[1] * nc[2];
+    int64_t *cell = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *head = (int64_t *)calloc((size_t)(ncell + 1), sizeof(int64_t));
+    int64_t *order = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    const double *pos[3] = {x, y, z};
+    for (int64_t i = 0; i < n; i++) {
+        int64_t ci[3];
+        for (int k = 0; k < 3; k++) {
+            int64_t c = (int64_t)floor((pos[k][i] - lo[k]) / boxL[k] * (double)nc[k]);
+            if (c < 0) c = 0;
+            if (c >= nc[k]) c = nc[k] - 1;
+            ci[k] = c;
+        }
+        cell[i] = (ci[0] * nc[1] + ci[1]) * nc[2] + ci[2];
+        head[cell[i] + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; c++) head[c + 1] += head[c];
+    int64_t *fill = (int64_t *)malloc((size_t)ncell * sizeof(int64_t));
+    memcpy(fill, head, (size_t)ncell * sizeof(int64_t));
+    for (int64_t i = 0; i < n; i++) order[fill[cell[i]]++] = i;
+    free(fill);
+
+    nl->n = n;
+    nl->off = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int64_t *cnt = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+    for (int pass = 0; pass < 2; pass++) {
+        if (pass == 1) {
+            nl->off[0] = 0;
+            for (int64_t a = 0; a < n; a++) nl->off[a + 1] = nl->off[a] + cnt[a];
+            nl->ids = (int32_t *)malloc((size_t)(nl->off[n] > 0 ? nl->off[n] : 1) * sizeof(int32_t));
+        }
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t a = 0; a < n; a++) {
+            int64_t c = cell[a];
+            int64_t cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
+            int64_t o = (pass == 1) ? nl->off[a] : 0;
+            int64_t k = 0;
+            for (int ox = -1; ox <= 1; ox++)
+                for (int oy = -1; oy <= 1; oy++)
+                    for (int oz = -1; oz <= 1; oz++) {
+                        int64_t qx = cx + ox, qy = cy + oy, qz = cz + oz;
+                        if (periodic) {
+                            qx = (qx + nc[0]) % nc[0]; qy = (qy + nc[1]) % nc[1]; qz = (qz + nc[2]) % nc[2];
+                        } else if (qx < 0 || qy < 0 || qz < 0 || qx >= nc[0] || qy >= nc[1] || qz >= nc[2]) {
+                            continue;
+                        }
+                        int64_t q = (qx * nc[1] + qy) * nc[2] + qz;
+                        for (int64_t t = head[q]; t < head[q + 1]; t++) {
+                            int64_t b = order[t];
+                            if (b != a && orc_pair_in(x, y, z, hc, a, b, s, boxL, periodic)) {
+                                if (pass == 1) nl->ids[o + k] = (int32_t)b;
+                                k++;
+                            }
+                        }
+                    }
+            if (pass == 0) cnt[a] = k;
+            else qsort(nl->ids + o, (size_t)k, sizeof(int32_t), orc_cmp_i32);
+        }
+    }
+    free(cnt); free(cell); free(head); free(order);
+}
+
+static void orc_nlist_free(orc_nlist *nl)
+{
+    free(nl->off); free(nl->ids);
+    nl->off = NULL; nl->ids = NULL;
+}
+
+/* Exported neighbour-set builder.  method 0 = brute force, 1 = grid.  Returns the pair count and,
+ * when off/ids are non-NULL, copies the lists out (ids must hold the returned count). */
+static orc_nlist orc_last_list = {0, NULL, NULL};
+
+int64_t orc_neighbours(int64_t n, const double *x, const double *y, const double *z, const double *hc,
+                       double s, const double *lo, const double *hi, int periodic, int method)
+{
+    double boxL[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    orc_nlist_free(&orc_last_list);
+    if (method == 0) orc_nlist_brute(n, x, y, z, hc, s, boxL, periodic, &orc_last_list);
+    else orc_nlist_grid(n, x, y, z, hc, s, lo, boxL, periodic, &orc_last_list);
+    return orc_last_list.off[n];
+}
+
+void orc_neighbours_copy(int64_t *off, int32_t *ids)
+{
+    int64_t n = orc_last_list.n;
+    memcpy(off, orc_last_list.off, (size_t)(n + 1) * sizeof(int64_t));
+    memcpy(ids, orc_last_list.ids, (size_t)orc_last_list.off[n] * sizeof(int32_t));
+}
+
+/* ====================================================================================== */
+/* Parameters of the hydrodynamics (Sect. 2.1, App. F, App. G).                              */
+/* ====================================================================================== */
+typedef struct {
+    double hfact;     /* rho(h) = m (hfact/h)^3, Eq. rhoh */
+    double gamma;     /* adiabatic index: P = (gamma-1) rho u */
+    double alpha_av;  /* alpha^AV in v_sig */
+    double beta_av;   /* beta in v_sig */
+    double alpha_u;   /* beta_u of Lambda_cond (0 switches conductivity off) */
+    double c_cour, c_force; /* CFL safety factors, App. G */
+    double h_tol;     /* epsilon_c of App. F */
+    double h_clamp;   /* lambda of App. F */
+    double cache_tol; /* chi of App. F */
+    double lo[3], hi[3];
+    int periodic;
+    int h_max_iter;
+} orc_params;
+
+static double orc_dist(const double *x, const double *y, const double *z, int64_t a, int64_t b,
+                       const double *boxL, int periodic, double *d /*3, r_a - r_b*/)
+{
+    d[0] = orc_image(x[a] - x[b], boxL[0], periodic);
+    d[1] = orc_image(y[a] - y[b], boxL[1], periodic);
+    d[2] = orc_image(z[a] - z[b], boxL[2], periodic);
+    return sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+}
+
+/* SPH density sum and its h-derivative for particle a at trial h (Eq. SPHmass / rhosphsum), the
+ * sum running over the cached candidates and a itself (r = 0). */
+static void orc_rho_sums(int64_t a, double h, double mass, const orc_nlist *nl,
+                         const double *x, const double *y, const double *z, const double *boxL, int periodic,
+                         double *rho_sum, double *drho_dh)
+{
+    double s0 = mass * orc_W(0.0, h), s1 = mass * orc_dWdh(0.0, h);
+    for (int64_t k = nl->off[a]; k < nl->off[a + 1]; k++) {
+        int64_t b = nl->ids[k];
+        double d[3];
+        double r = orc_dist(x, y, z, a, b, boxL, periodic, d);
+        if (r < 2.0 * h) {
+            s0 += mass * orc_W(r, h);
+            s1 += mass * orc_dWdh(r, h);
+        }
+    }
+    *rho_sum = s0;
+    *drho_dh = s1;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Root of the density equation, by its definition (App. F, Eq. rhoh with Eq. SPHmass):       */
+/* h_a solves  sum_b m W(r_ab, h_a) = m (hfact/h_a)^3.  h^3 * sum_b W is non-decreasing in h   */
+/* (f is non-increasing in q), so the root is unique and bisection on                          */
+/*      phi(h) = sum_b f(r_ab/h)/pi - hfact^3                                                 */
+/* brackets it.  Candidates: every b within R_kern * h_hi (brute force or grid).              */
+/* ---------------------------------------------------------------------------------------- */
+static double orc_phi(int64_t a, double h, const orc_nlist *nl, const double *x, const double *y,
+                      const double *z, const double *boxL, int periodic, double hfact)
+{
+    double s = orc_m4_f(0.0) / ORC_PI;
+    for (int64_t k = nl->off[a]; k < nl->off[a + 1]; k++) {
+        double d[3];
+        double r = orc_dist(x, y, z, a, nl->ids[k], boxL, periodic, d);
+        s += orc_m4_f(r / h) / ORC_PI;
+    }
+    return s - hfact * hfact * hfact;
+}
+
+/* h_hi: an upper bracket for every particle (phi(h_hi) > 0 is checked; returns the number of
+ * particles whose bracket failed, which are left at NaN). */
+int64_t orc_density_root(int64_t n, const double *x, const double *y, const double *z,
+                         double hfact, double h_hi, const double *lo, const double *hi, int periodic,
+                         int method, double *h_out)
+{
+    double boxL[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    double *hc = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    for (int64_t i = 0; i < n; i++) hc[i] = h_hi;
+    orc_nlist nl;
+    if (method == 0) orc_nlist_brute(n, x, y, z, hc, 2.0, boxL, periodic, &nl);
+    else orc_nlist_grid(n, x, y, z, hc, 2.0, lo, boxL, periodic, &nl);
+    int64_t bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad)
+    for (int64_t a = 0; a < n; a++) {
+        double hl = 0.0, hh = h_hi;
+        if (!(orc_phi(a, hh, &nl, x, y, z, boxL, periodic, hfact) > 0.0)) { h_out[a] = NAN; bad++; continue; }
+        /* lower bracket: h below half the nearest distance sees only the self term, phi < 0 */
+        for (int it = 0; it < 200; it++) {
+            double hm = 0.5 * (hl + hh);
+            if (hm <= hl || hm >= hh) break;
+            if (hl > 0.0 && (hh - hl) <= 1e-16 * hh) break;
+            if (orc_phi(a, hm, &nl, x, y, z, boxL, periodic, hfact) > 0.0) hh = hm;
+            else hl = hm;
+        }
+        h_out[a] = 0.5 * (hl + hh);
+    }
+    orc_nlist_free(&nl);
+    free(hc);
+    return bad;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Smoothing-length update, Alg. "Smoothing length update" (App. F), in the paper's order:     */
+/*   outer loop: build the candidate lists at R_kern * chi * max(h_a^n, h_b^n) (the ghost /     */
+/*     cache tolerance), inner Newton-Raphson loop on delta rho = rho_a - rho(h_a):            */
+/*       d(delta rho) = sum_b m dW/dh + 3 rho(h_a)/h_a          (reading: the analytic         */
+/*                                                               derivative, rho(h) of Eq. rhoh) */
+/*       h <- h - delta rho / d(delta rho), clamped to [h/lambda, h*lambda]                     */
+/*       eps_a = |h_new - h| / h_a^n; h_new > chi h_a^n -> h_new = chi h_a^n, eps_a = -1           */
+/*   until max eps <= eps_c; restart the outer loop while some eps = -1, with h^n := current h  */
+/*   (reading of "restart with the updated smoothing length").                                  */
+/* Epilogue: rho_a = rho(h_a) (Eq. rhoh), Omega_a = 1 - (dh/drho) sum_b m dW/dh with             */
+/* dh/drho = -h/(3 rho) (Eq. sphomega), evaluated at the final h.                                */
+/* Returns total inner iterations (>= 0) or -1 when h_max_iter was exceeded.  outer_out: the    */
+/* number of outer passes.                                                                      */
+/* ---------------------------------------------------------------------------------------- */
+int orc_density_algF(int64_t n, double mass, const orc_params *p, const double *x, const double *y,
+                     const double *z, double *h, double *rho, double *omega, int method, int *outer_out)
+{
+    double boxL[3] = {p->hi[0] - p->lo[0], p->hi[1] - p->lo[1], p->hi[2] - p->lo[2]};
+    double *hn = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *eps = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *hnew = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    int total = 0, outer = 0, failed = 0;
+    for (int64_t a = 0; a < n; a++) eps[a] = -1.0;
+    double mineps = -1.0;
+    while (mineps == -1.0 && n > 0) {
+        outer++;
+        for (int64_t a = 0; a < n; a++) hn[a] = h[a];
+        orc_nlist nl;
+        if (method == 0) orc_nlist_brute(n, x, y, z, hn, 2.0 * p->cache_tol, boxL, p->periodic, &nl);
+        else orc_nlist_grid(n, x, y, z, hn, 2.0 * p->cache_tol, p->lo, boxL, p->periodic, &nl);
+        double maxeps = INFINITY;
+        while (maxeps > p->h_tol) {
+            if (total >= p->h_max_iter) { failed = 1; break; }
+            total++;
+#pragma omp parallel for schedule(dynamic, 64)
+            for (int64_t a = 0; a < n; a++) {
+                double ha = h[a];
+                double rs, ds;
+                orc_rho_sums(a, ha, mass, &nl, x, y, z, boxL, p->periodic, &rs, &ds);
+                double rho_h = mass * pow(p->hfact / ha, 3.0);
+                double drho = rs - rho_h;
+                double ddrho = ds + 3.0 * rho_h / ha;
+                double hnw = ha - drho / ddrho;
+                if (hnw > ha * p->h_clamp) hnw = ha * p->h_clamp;
+                else if (hnw < ha / p->h_clamp) hnw = ha / p->h_clamp;
+                double e = fabs(hnw - ha) / hn[a];
+                if (hnw > hn[a] * p->cache_tol) { hnw = hn[a] * p->cache_tol; e = -1.0; }
+                hnew[a] = hnw;
+                eps[a] = e;
+            }
+            maxeps = -INFINITY;
+            mineps = INFINITY;
+            for (int64_t a = 0; a < n; a++) {
+                h[a] = hnew[a];
+                if (eps[a] > maxeps) maxeps = eps[a];
+                if (eps[a] < mineps) mineps = eps[a];
+            }
+        }
+        if (!failed) {
+            mineps = INFINITY;
+            for (int64_t a = 0; a < n; a++) if (eps[a] < mineps) mineps = eps[a];
+        }
+        if (failed) { orc_nlist_free(&nl); break; }
+        if (mineps != -1.0) {
+#pragma omp parallel for schedule(dynamic, 64)
+            for (int64_t a = 0; a < n; a++) {
+                double rs, ds;
+                orc_rho_sums(a, h[a], mass, &nl, x, y, z, boxL, p->periodic, &rs, &ds);
+                double rho_h = mass * pow(p->hfact / h[a], 3.0);
+                rho[a] = rho_h;
+                omega[a] = 1.0 + h[a] / (3.0 * rho_h) * ds;
+            }
+        }
+        orc_nlist_free(&nl);
+    }
+    free(hn); free(eps); free(hnew);
+    if (outer_out) *outer_out = outer;
+    return failed ? -1 : total;
+}
+
+/* Density and Omega at given smoothing lengths (no iteration): rho_sum_a (Eq. SPHmass) and
+ * Omega_a (Eq. sphomega with rho = rho(h_a)).  Used by pins on h-independent quantities. */
+void orc_density_at(int64_t n, double mass, double hfact, const double *x, const double *y, const double *z,
+                    const double *h, const double *lo, const double *hi, int periodic, int method,
+                    double *rho_sum, double *omega)
+{
+    double boxL[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    orc_nlist nl;
+    if (method == 0) orc_nlist_brute(n, x, y, z, h, 2.0, boxL, periodic, &nl);
+    else orc_nlist_grid(n, x, y, z, h, 2.0, lo, boxL, periodic, &nl);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t a = 0; a < n; a++) {
+        double rs, ds;
+        orc_rho_sums(a, h[a], mass, &nl, x, y, z, boxL, periodic, &rs, &ds);
+        double rho_h = mass * pow(hfact / h[a], 3.0);
+        rho_sum[a] = rs;
+        omega[a] = 1.0 + h[a] / (3.0 * rho_h) * ds;
+    }
+    orc_nlist_free(&nl);
+}
+
+/* ====================================================================================== */
+/* Derivatives (Sect. 2.1, Eqs. sphvel, sphuint, q^a_ab, v_sig, Lambda_cond, F_ab).          */
+/* Readings:                                                                                */
+/*   - dv_a/dt carries a minus sign: a_a = -sum_b m [(P_a+q^a)/(rho_a^2 Omega_a) grad_a W(h_a) */
+/*     + (P_b+q^b)/(rho_b^2 Omega_b) grad_a W(h_b)]; the printed form has none, which would make */
+/*     pressure attractive and break energy conservation.                                     */
+/*   - q^a_ab sits inside the sum of Eq. sphuint: du_a/dt = sum_b m (P_a+q^a_ab)/(rho_a^2      */
+/*     Omega_a) v_ab . grad_a W_ab(h_a) + Lambda_cond.                                         */
+/*   - grad_a W_ab(h) = rhat_ab F_ab(h), rhat_ab = (r_a - r_b)/|r_a - r_b|.                     */
+/*   - pairs interact when r_ab < R_kern max(h_a, h_b) (object-object criterion, App. D).      */
+/*   - v_sig^dt_a = max_b (alpha c_s,a + beta max(0, -v_ab . rhat_ab)), alpha c_s,a without     */
+/*     neighbours (the paper does not define v_sig^dt).                                       */
+/*   - rho_a = rho(h_a) (Eq. rhoh), P_a = (gamma-1) rho_a u_a, c_s,a = sqrt(gamma P_a/rho_a).   */
+/* Inputs are per-particle h, Omega (rho follows from h); outputs ax,ay,az,du,vsig.           */
+/* ====================================================================================== */
+void orc_forces(int64_t n, double mass, const orc_params *p, const double *x, const double *y,
+                const double *z, const double *vx, const double *vy, const double *vz, const double *u,
+                const double *h, const double *omega, int method,
+                double *ax, double *ay, double *az, double *du, double *vsig)
+{
+    double boxL[3] = {p->hi[0] - p->lo[0], p->hi[1] - p->lo[1], p->hi[2] - p->lo[2]};
+    double *rho = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *P = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *cs = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    for (int64_t a = 0; a < n; a++) {
+        rho[a] = mass * pow(p->hfact / h[a], 3.0);
+        P[a] = (p->gamma - 1.0) * rho[a] * u[a];
+        cs[a] = sqrt(p->gamma * P[a] / rho[a]);
+    }
+    orc_nlist nl;
+    if (method == 0) orc_nlist_brute(n, x, y, z, h, 2.0, boxL, p->periodic, &nl);
+    else orc_nlist_grid(n, x, y, z, h, 2.0, p->lo, boxL, p->periodic, &nl);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t a = 0; a < n; a++) {
+        double acc[3] = {0.0, 0.0, 0.0}, dua = 0.0;
+        double vs = p->alpha_av * cs[a];
+        for (int64_t k = nl.off[a]; k < nl.off[a + 1]; k++) {
+            int64_t b = nl.ids[k];
+            double d[3];
+            double r = orc_dist(x, y, z, a, b, boxL, p->periodic, d);
+            double rhat[3] = {d[0] / r, d[1] / r, d[2] / r};
+            double vab[3] = {vx[a] - vx[b], vy[a] - vy[b], vz[a] - vz[b]};
+            double vdotr = vab[0] * rhat[0] + vab[1] * rhat[1] + vab[2] * rhat[2];
+            double Fa = orc_F(r, h[a]);
+            double Fb = orc_F(r, h[b]);
+            double qa = 0.0, qb = 0.0;
+            if (vdotr < 0.0) {
+                double vsa = p->alpha_av * cs[a] + p->beta_av * fabs(vdotr);
+                double vsb = p->alpha_av * cs[b] + p->beta_av * fabs(vdotr);
+                qa = -0.5 * rho[a] * vsa * vdotr;
+                qb = -0.5 * rho[b] * vsb * vdotr;
+            }
+            double Aa = (P[a] + qa) / (rho[a] * rho[a] * omega[a]);
+            double Ab = (P[b] + qb) / (rho[b] * rho[b] * omega[b]);
+            double sc = mass * (Aa * Fa + Ab * Fb);
+            for (int c = 0; c < 3; c++) acc[c] -= sc * rhat[c];
+            dua += mass * Aa * vdotr * Fa;
+            if (p->alpha_u != 0.0) {
+                double vsu = sqrt(fabs(P[a] - P[b]) / (0.5 * (rho[a] + rho[b])));
+                dua += mass * p->alpha_u * vsu * (u[a] - u[b]) * 0.5 *
+                       (Fa / (omega[a] * rho[a]) + Fb / (omega[b] * rho[b]));
+            }
+            double vsdt = p->alpha_av * cs[a] + p->beta_av * (vdotr < 0.0 ? -vdotr : 0.0);
+            if (vsdt > vs) vs = vsdt;
+        }
+        ax[a] = acc[0]; ay[a] = acc[1]; az[a] = acc[2];
+        du[a] = dua;
+        vsig[a] = vs;
+    }
+    orc_nlist_free(&nl);
+    free(rho); free(P); free(cs);
+}
+
+/* CFL time step (App. G, "Choice of the timestep"): min_a min(C_cour h_a / v_sig,a, C_force sqrt(h_a/|a_a|)). */
+double orc_cfl(int64_t n, const orc_params *p, const double *h, const double *vsig,
+               const double *ax, const double *ay, const double *az)
+{
+    double dt = INFINITY;
+    for (int64_t a = 0; a < n; a++) {
+        double t1 = p->c_cour * h[a] / vsig[a];
+        double am = sqrt((ax[a] * ax[a] + ay[a] * ay[a]) + az[a] * az[a]);
+        double t2 = am > 0.0 ? p->c_force * sqrt(h[a] / am) : INFINITY;
+        double t = t1 < t2 ? t1 : t2;
+        if (t < dt) dt = t;
+    }
+    return dt;
+}
+
+/* Periodic wrap of one coordinate into [lo, hi): x - L*floor((x-lo)/L); a result equal to hi
+ * (rounding of a tiny negative offset) is set to lo. */
+static double orc_wrap(double x, double lo, double hi)
+{
+    double L = hi - lo;
+    double w = x - L * floor((x - lo) / L);
+    if (w >= hi) w = lo;
+    if (w < lo) w = lo;
+    return w;
+}
+
+/* ====================================================================================== */
+/* One kick-drift-kick step (App. G, "Leapfrog integration"):                                */
+/*   v^{n+1/2} = v^n + dt/2 a^n;  r^{n+1} = r^n + dt v^{n+1/2} (wrapped);  v* = v^{n+1/2} + dt/2 a^n */
+/*   u is advanced the same way with du/dt (reading);                                           */
+/*   h, rho, Omega from Alg. F at r^{n+1};  a^{n+1}, du^{n+1} from (r^{n+1}, v*, u*);             */
+/*   v^{n+1} = v* + dt/2 (a^{n+1} - a^n), likewise u.                                            */
+/* State arrays are updated in place (original particle order).  Returns the CFL time step for  */
+/* the next step, or a negative value if the h iteration failed.  dv_ratio (optional) receives   */
+/* max_i |dv_i| / sqrt(<|v|^2>) for the correction dv_i = dt/2 (a^{n+1}_i - a^n_i) (Eq. deltavi;   */
+/* reading of Eq. cvleapfrog, whose printed ratio is always >= 1).                              */
+/* ====================================================================================== */
+double orc_step(int64_t n, double mass, const orc_params *p, double dt,
+                double *x, double *y, double *z, double *vx, double *vy, double *vz, double *u, double *h,
+                double *ax, double *ay, double *az, double *du, double *rho, double *omega, double *vsig,
+                int method, int *iters, double *dv_ratio)
+{
+    size_t sz = (size_t)(n > 0 ? n : 1) * sizeof(double);
+    double *a0x = (double *)malloc(sz), *a0y = (double *)malloc(sz), *a0z = (double *)malloc(sz),
+           *du0 = (double *)malloc(sz);
+    for (int64_t a = 0; a < n; a++) {
+        a0x[a] = ax[a]; a0y[a] = ay[a]; a0z[a] = az[a]; du0[a] = du[a];
+        double hvx = vx[a] + 0.5 * dt * ax[a], hvy = vy[a] + 0.5 * dt * ay[a], hvz = vz[a] + 0.5 * dt * az[a];
+        double hu = u[a] + 0.5 * dt * du[a];
+        x[a] = orc_wrap(x[a] + dt * hvx, p->lo[0], p->hi[0]);
+        y[a] = orc_wrap(y[a] + dt * hvy, p->lo[1], p->hi[1]);
+        z[a] = orc_wrap(z[a] + dt * hvz, p->lo[2], p->hi[2]);
+        vx[a] = hvx + 0.5 * dt * ax[a];
+        vy[a] = hvy + 0.5 * dt * ay[a];
+        vz[a] = hvz + 0.5 * dt * az[a];
+        u[a] = hu + 0.5 * dt * du[a];
+    }
+    int outer = 0;
+    int it = orc_density_algF(n, mass, p, x, y, z, h, rho, omega, method, &outer);
+    if (iters) *iters = it;
+    if (it < 0) { free(a0x); free(a0y); free(a0z); free(du0); return -1.0; }
+    orc_forces(n, mass, p, x, y, z, vx, vy, vz, u, h, omega, method, ax, ay, az, du, vsig);
+    double dvmax = 0.0, v2 = 0.0;
+    for (int64_t a = 0; a < n; a++) {
+        double dvx = 0.5 * dt * (ax[a] - a0x[a]), dvy = 0.5 * dt * (ay[a] - a0y[a]), dvz = 0.5 * dt * (az[a] - a0z[a]);
+        vx[a] += dvx; vy[a] += dvy; vz[a] += dvz;
+        u[a] += 0.5 * dt * (du[a] - du0[a]);
+        double dv = sqrt((dvx * dvx + dvy * dvy) + dvz * dvz);
+        if (dv > dvmax) dvmax = dv;
+        v2 += (vx[a] * vx[a] + vy[a] * vy[a]) + vz[a] * vz[a];
+    }
+    if (dv_ratio) *dv_ratio = (v2 > 0.0) ? dvmax / sqrt(v2 / (double)n) : 0.0;
+    free(a0x); free(a0y); free(a0z); free(du0);
+    return orc_cfl(n, p, h, vsig, ax, ay, az);
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

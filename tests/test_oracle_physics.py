@@ -1,0 +1,289 @@
+"""Pins of the oracle's kernel, neighbour, density, force and step functions (Sect. 2.1, App. D-G)
+against closed forms, continuum limits, lattice counts and conservation laws."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_09713_gb300 import workloads as WL
+
+
+# ---------------------------------------------------------------- kernel (Sect. 2.1)
+def test_m4_normalisation_by_quadrature():
+    """int W dV = 1 in 3-D (C_norm of Sect. 2.1), by Simpson quadrature of 4 pi r^2 W."""
+    h = 0.7
+    r = np.linspace(0.0, 2.0 * h, 20001)
+    w = np.array([4.0 * math.pi * ri * ri * O.W(ri, h) for ri in r])
+    dr = r[1] - r[0]
+    integ = dr / 3.0 * (w[0] + w[-1] + 4.0 * w[1:-1:2].sum() + 2.0 * w[2:-1:2].sum())
+    assert abs(integ - 1.0) < 1e-10
+
+
+def test_m4_support_and_continuity():
+    assert O.m4_f(2.0) == 0.0 and O.m4_df(2.0) == 0.0 and O.m4_f(3.0) == 0.0
+    for q in (1.0, 2.0):
+        e = 1e-9
+        assert abs(O.m4_f(q - e) - O.m4_f(q + e)) < 1e-8
+        assert abs(O.m4_df(q - e) - O.m4_df(q + e)) < 1e-8
+    assert O.m4_f(0.0) == 1.0
+
+
+@pytest.mark.parametrize("q", [0.1, 0.5, 0.9, 1.2, 1.7, 1.95])
+def test_kernel_derivatives_finite_difference(q):
+    """F = dW/dr and dW/dh against central differences of W."""
+    h = 0.37
+    r = q * h
+    e = 1e-6
+    fd_r = (O.W(r + e * h, h) - O.W(r - e * h, h)) / (2 * e * h)
+    fd_h = (O.W(r, h * (1 + e)) - O.W(r, h * (1 - e))) / (2 * e * h)
+    assert abs(O.F(r, h) - fd_r) < 1e-6 * abs(O.W(0, h) / h)
+    assert abs(O.dWdh(r, h) - fd_h) < 1e-6 * abs(O.W(0, h) / h)
+
+
+# ---------------------------------------------------------------- neighbours (App. C-D)
+def test_lattice_neighbour_count_closed_form():
+    """Perfect cubic lattice, radius 2h with h = 1.19967 dx: the points with |k|^2 < (2h/dx)^2 = 5.757
+    are the shells |k|^2 = 1..5 with 6+12+8+6+24 = 56 points (integer lattice count)."""
+    s = WL.perfect_lattice(10)
+    hc = np.full(s["n"], 1.19967 * s["dx"])
+    off, ids = O.neighbours(s["x"], s["y"], s["z"], hc, 2.0)
+    assert np.all(np.diff(off) == 56)
+    shells = {}
+    for k in range(-3, 4):
+        for j in range(-3, 4):
+            for i in range(-3, 4):
+                d2 = i * i + j * j + k * k
+                if 0 < d2 < (2 * 1.19967) ** 2:
+                    shells[d2] = shells.get(d2, 0) + 1
+    assert sum(shells.values()) == 56
+
+
+def test_grid_equals_brute_force():
+    rng = np.random.default_rng(5)
+    n = 3000
+    x, y, z = rng.uniform(0, 1, size=(3, n))
+    hc = rng.uniform(0.02, 0.05, size=n)
+    for per in (1, 0):
+        o1, i1 = O.neighbours(x, y, z, hc, 2.2, periodic=per, method=0)
+        o2, i2 = O.neighbours(x, y, z, hc, 2.2, periodic=per, method=1)
+        assert np.array_equal(o1, o2) and np.array_equal(i1, i2)
+
+
+def test_neighbour_symmetry_and_minimum_image():
+    rng = np.random.default_rng(6)
+    n = 800
+    x, y, z = rng.uniform(0, 1, size=(3, n))
+    hc = rng.uniform(0.03, 0.08, size=n)
+    off, ids = O.neighbours(x, y, z, hc, 2.0)
+    pairs = {(a, int(b)) for a in range(n) for b in ids[off[a]:off[a + 1]]}
+    assert all((b, a) in pairs for a, b in pairs)
+    # a pair across the periodic face is found, and not in the open box
+    x2 = np.array([0.01, 0.99]); y2 = np.array([0.5, 0.5]); z2 = np.array([0.5, 0.5]); h2 = np.array([0.02, 0.02])
+    o, i = O.neighbours(x2, y2, z2, h2, 2.0, periodic=1)
+    assert list(np.diff(o)) == [1, 1]
+    o, i = O.neighbours(x2, y2, z2, h2, 2.0, periodic=0)
+    assert list(np.diff(o)) == [0, 0]
+
+
+# ---------------------------------------------------------------- density (App. F)
+def test_lattice_density_continuum_limit():
+    """On a perfect lattice the SPH sum tends to the continuum value rho_0 = m/dx^3 as h/dx grows;
+    the root of rho_sum(h) = m (hfact/h)^3 then tends to h = hfact dx (Eq. rhoh)."""
+    s = WL.perfect_lattice(10)
+    h = O.density_root(s["x"], s["y"], s["z"], 1.2, 2.0 * s["dx"])
+    assert np.allclose(h, h[0], rtol=1e-13, atol=0)
+    assert abs(h[0] / s["dx"] - 1.2) < 1e-3
+    s = WL.perfect_lattice(16)             # support 2h < half the box for every h below
+    rho0 = s["mass"] / s["dx"] ** 3
+    # lattice sums oscillate around the continuum value with an amplitude that decays with h/dx;
+    # a wrong C_norm or spline coefficient is off by O(1)
+    for hs, tol in ((1.0, 2e-3), (1.2, 2e-3), (1.5, 2e-3), (2.0, 2e-4), (3.0, 1e-4)):
+        rs, _ = O.density_at(s["x"], s["y"], s["z"], np.full(s["n"], hs * s["dx"]), s["mass"], 1.2)
+        assert abs(rs[0] / rho0 - 1.0) < tol
+
+
+def test_root_satisfies_density_equation_jittered():
+    """Invariant h_a (rho_sum,a / m)^(1/3) = hfact at the root, and Alg. F agrees with the root to its
+    tolerance."""
+    s = WL.lattice(12, sigma_v=0.0, jitter=0.2, seed=3)
+    hroot = O.density_root(s["x"], s["y"], s["z"], 1.2, 2.5 * s["dx"])
+    rs, _ = O.density_at(s["x"], s["y"], s["z"], hroot, s["mass"], 1.2)
+    inv = hroot * np.cbrt(rs / s["mass"])
+    assert np.max(np.abs(inv - 1.2)) < 1e-12
+    P = O.Params()
+    h, rho, om, it, outer = O.density_algF(s["x"], s["y"], s["z"], s["h"], s["mass"], P)
+    assert np.max(np.abs(h / hroot - 1.0)) < 1e-9
+    assert np.allclose(rho, s["mass"] * (1.2 / h) ** 3, rtol=1e-14)
+    assert it >= 1 and outer >= 1
+
+
+def test_algF_outer_restart_when_h_leaves_cache():
+    """Start far from the root: h must exceed chi h^n, which triggers the outer restart of Alg. F."""
+    s = WL.lattice(10, sigma_v=0.0, jitter=0.1, seed=4)
+    P = O.Params()
+    h, rho, om, it, outer = O.density_algF(s["x"], s["y"], s["z"], 0.5 * s["h"], s["mass"], P)
+    assert outer >= 2
+    hroot = O.density_root(s["x"], s["y"], s["z"], 1.2, 2.5 * s["dx"])
+    assert np.max(np.abs(h / hroot - 1.0)) < 1e-9
+
+
+def test_omega_equals_finite_difference_of_rho_sum():
+    """Eq. sphomega: Omega = 1 - (dh/drho) d(rho_sum)/dh with dh/drho = -h/(3 rho); check against a
+    central difference of the oracle's rho_sum(h)."""
+    s = WL.lattice(8, sigma_v=0.0, jitter=0.2, seed=8)
+    h = O.density_root(s["x"], s["y"], s["z"], 1.2, 2.5 * s["dx"])
+    _, om = O.density_at(s["x"], s["y"], s["z"], h, s["mass"], 1.2)
+    e = 1e-6
+    rp, _ = O.density_at(s["x"], s["y"], s["z"], h * (1 + e), s["mass"], 1.2)
+    rm, _ = O.density_at(s["x"], s["y"], s["z"], h * (1 - e), s["mass"], 1.2)
+    drdh = (rp - rm) / (2 * e * h)
+    rho = s["mass"] * (1.2 / h) ** 3
+    assert np.max(np.abs(om - (1.0 + h / (3 * rho) * drdh))) < 1e-7
+
+
+# ---------------------------------------------------------------- forces (Sect. 2.1)
+def _converged(s, P=None):
+    P = P or O.Params()
+    h, rho, om, _, _ = O.density_algF(s["x"], s["y"], s["z"], s["h"], s["mass"], P)
+    return h, rho, om
+
+
+def test_lattice_is_in_equilibrium():
+    s = WL.perfect_lattice(8)
+    P = O.Params()
+    h, rho, om = _converged(s, P)
+    ax, ay, az, du, vs = O.forces(s["x"], s["y"], s["z"], s["vx"], s["vy"], s["vz"], s["u"], h, om, s["mass"], P)
+    scale = (P.gamma - 1) / s["dx"]
+    assert np.max(np.abs(np.stack([ax, ay, az]))) < 1e-10 * scale
+    assert np.max(np.abs(du)) < 1e-12
+    cs = math.sqrt(P.gamma * (P.gamma - 1) * 1.0)
+    assert np.allclose(vs, cs, rtol=1e-14)
+
+
+def _random_state(seed, n_side=8, sigma=0.3):
+    s = WL.lattice(n_side, sigma_v=sigma, jitter=0.15, seed=seed)
+    rng = np.random.default_rng(seed + 100)
+    s["u"] = 1.0 + 0.5 * rng.uniform(size=s["n"])
+    return s
+
+
+@pytest.mark.parametrize("alpha_u", [0.0, 1.0])
+def test_momentum_and_energy_conservation_of_pair_forces(alpha_u):
+    """sum_a m a_a = 0 (antisymmetric pair terms) and sum_a m (v_a . a_a + du_a/dt) = 0 (the energy
+    equation pairs with the momentum equation; conductivity is antisymmetric in (a,b))."""
+    s = _random_state(11)
+    P = O.Params(alpha_u=alpha_u)
+    h, rho, om = _converged(s, P)
+    ax, ay, az, du, vs = O.forces(s["x"], s["y"], s["z"], s["vx"], s["vy"], s["vz"], s["u"], h, om, s["mass"], P)
+    m = s["mass"]
+    amag = np.abs(np.stack([ax, ay, az])).max()
+    assert np.max(np.abs([np.sum(m * ax), np.sum(m * ay), np.sum(m * az)])) < 1e-13 * amag
+    e_rate = np.sum(m * (s["vx"] * ax + s["vy"] * ay + s["vz"] * az + du))
+    scale = np.sum(m * (np.abs(s["vx"] * ax) + np.abs(s["vy"] * ay) + np.abs(s["vz"] * az) + np.abs(du)))
+    assert abs(e_rate) < 1e-12 * scale
+
+
+def test_galilean_invariance():
+    s = _random_state(12)
+    P = O.Params()
+    h, rho, om = _converged(s, P)
+    base = O.forces(s["x"], s["y"], s["z"], s["vx"], s["vy"], s["vz"], s["u"], h, om, s["mass"], P)
+    shifted = O.forces(s["x"], s["y"], s["z"], s["vx"] + 3.0, s["vy"] - 1.5, s["vz"] + 0.25, s["u"], h, om,
+                       s["mass"], P)
+    for a, b in zip(base[:4], shifted[:4]):
+        assert np.max(np.abs(a - b)) < 1e-9 * np.max(np.abs(a))
+
+
+def test_pressure_gradient_closed_form():
+    """u = u0 (1 + e sin 2 pi x) on a uniform lattice, v = 0: a_x -> -(gamma-1) u0 e 2 pi cos 2 pi x
+    (a = -grad P / rho with P = (gamma-1) rho u).  The sign pins the minus of Eq. sphvel."""
+    s = WL.perfect_lattice(24)
+    P = O.Params(alpha_u=0.0)
+    eps = 0.01
+    u = 1.0 + eps * np.sin(2 * np.pi * s["x"])
+    h, rho, om = _converged(s, P)
+    ax, ay, az, du, vs = O.forces(s["x"], s["y"], s["z"], s["vx"], s["vy"], s["vz"], u, h, om, s["mass"], P)
+    expect = -(P.gamma - 1) * eps * 2 * np.pi * np.cos(2 * np.pi * s["x"])
+    amp = np.max(np.abs(expect))
+    assert np.max(np.abs(ax - expect)) < 0.02 * amp
+    assert np.max(np.abs(ay)) < 1e-9 * amp and np.max(np.abs(az)) < 1e-9 * amp
+
+
+def test_adiabatic_compression_closed_form():
+    """v_x = e sin 2 pi x, uniform u, no dissipation: du/dt -> -(P/rho) div v = -(gamma-1) u e 2 pi cos 2 pi x."""
+    s = WL.perfect_lattice(24)
+    P = O.Params(alpha_av=0.0, beta_av=0.0, alpha_u=0.0)
+    eps = 0.01
+    vx = eps * np.sin(2 * np.pi * s["x"])
+    h, rho, om = _converged(s, P)
+    ax, ay, az, du, vs = O.forces(s["x"], s["y"], s["z"], vx, s["vy"], s["vz"], s["u"], h, om, s["mass"], P)
+    expect = -(P.gamma - 1) * 1.0 * eps * 2 * np.pi * np.cos(2 * np.pi * s["x"])
+    assert np.max(np.abs(du - expect)) < 0.02 * np.max(np.abs(expect))
+
+
+def test_artificial_viscosity_dissipates_and_conduction_flows_downhill():
+    s = _random_state(13)
+    P0 = O.Params(alpha_u=0.0)
+    h, rho, om = _converged(s, P0)
+    args = (s["x"], s["y"], s["z"], s["vx"], s["vy"], s["vz"], s["u"], h, om, s["mass"])
+    no_av = O.forces(*args, O.Params(alpha_av=0.0, beta_av=0.0, alpha_u=0.0))
+    av = O.forces(*args, P0)
+    assert np.sum(av[3] - no_av[3]) > 0            # shock heating is positive overall
+    # conduction only: hot particle between cold ones loses energy
+    s2 = WL.perfect_lattice(8)
+    u = np.ones(s2["n"]); u[0] = 2.0
+    hc, rhoc, omc = _converged(s2, P0)
+    args2 = (s2["x"], s2["y"], s2["z"], s2["vx"], s2["vy"], s2["vz"], u, hc, omc, s2["mass"])
+    with_c = O.forces(*args2, O.Params(alpha_av=0.0, beta_av=0.0, alpha_u=1.0))
+    without = O.forces(*args2, O.Params(alpha_av=0.0, beta_av=0.0, alpha_u=0.0))
+    dcond = with_c[3] - without[3]
+    assert dcond[0] < 0 and np.all(dcond[1:] >= -1e-15) and abs(np.sum(dcond)) < 1e-12 * abs(dcond[0])
+
+
+# ---------------------------------------------------------------- step (App. G)
+def _setup_step(s, P):
+    h, rho, om = _converged(s, P)
+    st = {k: s[k].copy() for k in ("x", "y", "z", "vx", "vy", "vz", "u")}
+    st["h"] = h
+    ax, ay, az, du, vs = O.forces(st["x"], st["y"], st["z"], st["vx"], st["vy"], st["vz"], st["u"], h, om,
+                                  s["mass"], P)
+    st.update(ax=ax, ay=ay, az=az, du=du, rho=rho, omega=om, vsig=vs)
+    return st, O.cfl(h, vs, ax, ay, az, P)
+
+
+def test_uniform_advection_is_exact():
+    """Perfect lattice moving at uniform v: a = 0 so KDK drifts the positions exactly (Galilean
+    invariance, Sect. 4.2)."""
+    s = WL.perfect_lattice(8)
+    s["vx"][:] = 1.0
+    P = O.Params()
+    st, dt = _setup_step(s, P)
+    x0 = st["x"].copy()
+    dtn, it, _ = O.step(st, s["mass"], P, dt)
+    expect = np.mod(x0 + dt * 1.0, 1.0)
+    assert np.max(np.abs(st["x"] - expect)) < 1e-15
+    assert np.max(np.abs(st["vx"] - 1.0)) < 1e-12
+
+
+def test_energy_conserved_across_steps():
+    """Total energy sum m (v^2/2 + u) is conserved by the semi-discrete equations; the KDK step leaves
+    a local error that falls at least as dt^3 and stays below 1e-6 relative at the CFL factor of the
+    paper's Sedov runs (0.1, Sect. 4.4); momentum is conserved to rounding."""
+    s = WL.lattice(10, sigma_v=0.1, jitter=0.05, seed=21)
+    P = O.Params()
+    m = s["mass"]
+
+    def energy(st):
+        return np.sum(m * (0.5 * (st["vx"] ** 2 + st["vy"] ** 2 + st["vz"] ** 2) + st["u"]))
+    errs = []
+    for fac in (1.0, 0.5, 0.1 / 0.3):
+        st, dt = _setup_step(s, P)
+        e0 = energy(st)
+        O.step(st, m, P, dt * fac)
+        errs.append(abs(energy(st) - e0) / e0)
+        mom = np.array([np.sum(m * st[k]) for k in ("vx", "vy", "vz")])
+        mom0 = np.array([np.sum(m * s[k]) for k in ("vx", "vy", "vz")])
+        assert np.max(np.abs(mom - mom0)) < 1e-14
+    assert errs[0] / errs[1] > 6.0
+    assert errs[2] < 1e-6
