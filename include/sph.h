@@ -1,0 +1,209 @@
+/*
+ * sph.h -- C ABI of the GB300 (sm_103a) SPH hot path: Morton-code radix tree with per-cell bounding
+ * boxes, tree-walk neighbour cache, smoothing-length / density iteration (M4, Newton-Raphson on h)
+ * and the pairwise momentum / energy loop with artificial viscosity and conductivity, advanced by a
+ * kick-drift-kick leapfrog.  Method: "The Shamrock code: I - Smoothed Particle Hydrodynamics on
+ * GPUs" (arXiv 2503.09713), Sect. 2.1 and Apps. B-G.
+ *
+ * General rules
+ *  - Every function returns SPH_OK (0) or a negative sph_status; no exception or abort crosses
+ *    the ABI.  sph_last_error(ctx) returns a message for the last failure of that context.
+ *  - Pointers in sph_state are DEVICE pointers (except for sph_step_host), owned by the caller;
+ *    the library never frees them.  All scratch memory (tree, neighbour cache, flags) belongs to
+ *    the context and is freed by sph_destroy.
+ *  - All device work is issued on the context's CUDA stream.  Functions that return host scalars
+ *    (leaf count, pair count, iteration count, time steps) synchronise that stream.
+ *  - Particle arrays are structure-of-arrays, float64, length state->n.  sph_build_tree (and
+ *    therefore sph_step) reorders every non-NULL per-particle array of the state into Morton order
+ *    in place and applies the same permutation to state->id, so id[i] is the original index of the
+ *    particle now stored at i.
+ *  - Equal-mass particles (state->mass).  The box [box_lo, box_hi) is periodic when periodic = 1;
+ *    positions must lie inside it.  The interaction radius 2*cache_tol*h of every particle must
+ *    stay below a quarter of the smallest box side.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_ctx sph_ctx;
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_INVALID_ARG = -1,     /* NULL pointer, n out of range, bad parameter */
+    SPH_ERR_OOM = -2,             /* device allocation failed */
+    SPH_ERR_CAPACITY = -3,        /* a fixed-capacity buffer overflowed and could not grow */
+    SPH_ERR_CACHE_STALE = -4,     /* some h exceeded cache_tol * h^n: rebuild the cache (App. F) */
+    SPH_ERR_H_NOT_CONVERGED = -5, /* Newton iteration on h hit h_max_iter */
+    SPH_ERR_TIMEOUT = -6,         /* a bounded device-side wait ran out (no hang, results invalid) */
+    SPH_ERR_CUDA = -7,            /* a CUDA runtime call failed */
+    SPH_ERR_ORDER = -8,           /* call made before the stage it depends on */
+    SPH_ERR_NONFINITE = -9        /* a NaN/Inf appeared in positions or smoothing lengths */
+} sph_status;
+
+enum { SPH_KERNEL_M4 = 0 };
+enum { SPH_FP64 = 0, SPH_MIXED = 1 };
+
+/* Solver parameters (Sect. 2.1, App. F, App. G).  sph_default_params fills the paper's values. */
+typedef struct {
+    int kernel;           /* SPH_KERNEL_M4 (cubic spline, R_kern = 2) */
+    int precision;        /* SPH_FP64: all pair arithmetic in FP64.  SPH_MIXED: FP64 positions, h
+                             iteration and integration; FP32 pair sums on cell-relative offsets with
+                             Kahan-compensated accumulation */
+    double hfact;         /* rho(h) = m (hfact/h)^3 (Eq. rhoh); 1.2 */
+    double gamma;         /* P = (gamma-1) rho u; 5/3 */
+    double alpha_av;      /* alpha^AV of v_sig; 1 */
+    double beta_av;       /* beta of v_sig; 2 */
+    double alpha_u;       /* beta_u of Lambda_cond; 1 (0 switches conductivity off) */
+    double c_cour;        /* CFL factors (App. G); 0.3 */
+    double c_force;       /* 0.25 */
+    double h_tol;         /* epsilon_c of App. F; 1e-6 */
+    double h_clamp;       /* lambda of App. F; 1.2 */
+    double cache_tol;     /* chi of App. F (cache / ghost tolerance); 1.1 */
+    int h_max_iter;       /* Newton iterations per particle before SPH_ERR_H_NOT_CONVERGED; 64 */
+    int reduction_level;  /* n_red reduction passes of App. C; 3 */
+    int periodic;         /* 1: periodic box */
+    int max_outer;        /* cache rebuilds inside sph_step before SPH_ERR_CACHE_STALE; 8 */
+    double box_lo[3];
+    double box_hi[3];
+} sph_params;
+
+/* Particle state.  Arrays: float64[n] (id: uint32[n]).  Inputs/outputs per function below. */
+typedef struct {
+    int64_t n;
+    double mass;
+    double *x, *y, *z;        /* positions */
+    double *vx, *vy, *vz;     /* velocities */
+    double *u;                /* specific internal energy */
+    double *h;                /* smoothing length */
+    double *ax, *ay, *az;     /* acceleration dv/dt */
+    double *du;               /* du/dt */
+    double *rho, *omega;      /* density rho(h) and grad-h term Omega (outputs of density) */
+    double *vsig;             /* signal speed v_sig^dt (output of forces) */
+    uint32_t *id;             /* original particle index (permuted with the particles) */
+} sph_state;
+
+/* Host view of the tree for sph_export_tree.  The caller allocates every non-NULL array with the
+ * sizes returned by sph_tree_sizes: n particles, L leaves, L-1 internal nodes, 2L-1 nodes.  Node c
+ * < L-1 is internal node c; node L-1+j is leaf j (App. C tree traversal numbering). */
+typedef struct {
+    uint64_t *mu;          /* [n]   sorted Morton codes (63-bit, 21 bits per axis, x most significant) */
+    uint32_t *perm;        /* [n]   sort permutation epsilon of the last build (index before the build) */
+    int64_t *leaf_first;   /* [L+1] id_i of Fig. mortonlistbuild: first sorted particle of leaf i; [L] = n */
+    uint64_t *mu_leaf;     /* [L]   leaf Morton codes */
+    int32_t *lchild, *rchild;       /* [L-1] Table arrays_fig_karras */
+    uint8_t *lflag, *rflag;         /* [L-1] 1 = child is a leaf */
+    int32_t *endrange;              /* [L-1] */
+    double *bmin, *bmax;            /* [3*(2L-1)] tight per-node box, node-major (x,y,z) */
+    double *hmax;                   /* [2L-1] largest h in the node */
+} sph_tree_view;
+
+/* Per-call statistics (host copy, filled by the library after each stage). */
+typedef struct {
+    int64_t n, n_leaves, n_groups, n_pairs, cache_slots;
+    int density_iters_max;   /* largest per-particle Newton count in the last density call */
+    int outer_passes;        /* cache builds in the last sph_step (1 = no restart) */
+    int n_red;
+    double dt_next;
+    double dv_ratio;         /* max |dv_i| / sqrt(<|v|^2>) of the last corrector (Eq. deltavi) */
+    int64_t kernel_launches; /* kernels launched by this context since sph_create */
+    int64_t density_pair_evals; /* neighbour evaluations of the last density call (all Newton passes) */
+    int64_t density_inrange; /* of those, evaluations with r < 2 h_a */
+    int64_t force_pairs;     /* pairs inside 2 max(h_a, h_b) in the last force call */
+    double stage_ms[8];      /* with sph_set_timing(ctx, 1): accumulated device time per stage since the
+                                last sph_reset_timing: predictor, tree, neighbours, density, force
+                                preparation, force loop, corrector, unused */
+} sph_stats;
+
+/* Fill *p with the paper's defaults and a periodic unit box.  Never fails. */
+void sph_default_params(sph_params *p);
+
+/* Create a context for up to n_cap particles on the current CUDA device.  neigh_cap: initial
+ * capacity of the neighbour cache in entries (0: 96 * n_cap); it grows on demand outside graph
+ * capture.  stream: a cudaStream_t (NULL = the legacy default stream).  On success *out owns all
+ * scratch memory. Errors: INVALID_ARG, OOM, CUDA. */
+int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stream, sph_ctx **out);
+
+/* Free every buffer of the context (synchronises its stream).  NULL is accepted. */
+int sph_destroy(sph_ctx *ctx);
+
+/* Replace the solver parameters (same capacity).  Invalidates the tree and cache. */
+int sph_set_params(sph_ctx *ctx, const sph_params *p);
+
+/* A1-A6 (App. B-C): Morton codes of the positions, stable radix sort by code, reorder of every
+ * non-NULL state array (and id) into Morton order, duplicate mask + reduction_level reduction
+ * passes (Alg. mortonmask), compaction into leaves, Karras radix tree (Table arrays_fig_karras),
+ * bottom-up tight box and h_max of every node.  Input: positions, h.  Output: state reordered;
+ * the tree is kept in the context.  Errors: INVALID_ARG (n > n_cap), NONFINITE, TIMEOUT, CUDA. */
+int sph_build_tree(sph_ctx *ctx, sph_state *s);
+
+/* A7 (App. C two-stage neighbour cache, App. D criteria): stage 1 walks the tree once per group of
+ * 32 consecutive particles with the group-group criterion at radius 2*cache_tol*max(h); stage 2
+ * keeps, for every particle a, each b != a with |r_ab|^2 < (2*cache_tol*max(h_a,h_b))^2 (nearest
+ * periodic image, FP64 decision).  h = state->h is recorded as h^n.  *n_pairs (may be NULL)
+ * receives the number of cached pairs.  Requires sph_build_tree.  Errors: ORDER, CAPACITY, OOM, CUDA. */
+int sph_find_neighbours(sph_ctx *ctx, const sph_state *s, int64_t *n_pairs);
+
+/* A8 (App. F): per particle, Newton-Raphson on rho_sum(h) - m (hfact/h)^3 over the cached
+ * neighbours, step clamped to [h/lambda, h*lambda], until |dh|/h^n < h_tol; then rho = rho(h)
+ * (Eq. rhoh) and Omega (Eq. sphomega) at the final h.  Input: positions, h.  Output: h, rho, omega.
+ * *iters (may be NULL): largest per-particle iteration count.  If some h would exceed
+ * cache_tol*h^n it is clamped there and SPH_ERR_CACHE_STALE is returned: rebuild the cache
+ * (sph_find_neighbours, after sph_build_tree or not) and call again.  Errors: ORDER, CACHE_STALE,
+ * H_NOT_CONVERGED, CUDA. */
+int sph_compute_density_h(sph_ctx *ctx, sph_state *s, int *iters);
+
+/* A9 (Sect. 2.1, Eqs. sphvel, sphuint): accelerations, du/dt (artificial viscosity and
+ * conductivity) and v_sig^dt for every particle, from positions, v, u, h, omega.  Also stores the
+ * CFL time step (App. G) in the stats.  Requires a neighbour cache built from h values with
+ * h <= cache_tol*h^n.  Output: ax, ay, az, du, vsig.  Errors: ORDER, CUDA. */
+int sph_compute_forces(sph_ctx *ctx, sph_state *s);
+
+/* A0-A10 (App. G): one global kick-drift-kick step: predictor, tree build, neighbour cache,
+ * density/h (rebuilding the cache while h leaves its tolerance, App. F outer loop), forces,
+ * corrector, CFL.  dt <= 0 uses the CFL step computed by the previous sph_compute_forces /
+ * sph_step.  Requires accelerations and du of the current state (a first sph_compute_density_h +
+ * sph_compute_forces on the initial state).  *dt_used / *dt_next may be NULL.  The state is
+ * reordered into Morton order (see sph_build_tree).  Errors: ORDER, CACHE_STALE (more than
+ * max_outer rebuilds), H_NOT_CONVERGED, CAPACITY, TIMEOUT, CUDA. */
+int sph_step(sph_ctx *ctx, sph_state *s, double dt, double *dt_used, double *dt_next);
+
+/* Same as sph_step with every pointer of *host_state in HOST memory (pinned or pageable): copies
+ * the state to context-owned device buffers, runs the step, copies it back (Morton order).  Used
+ * for end-to-end timing.  Errors: as sph_step. */
+int sph_step_host(sph_ctx *ctx, sph_state *host_state, double dt, double *dt_used, double *dt_next);
+
+/* Sizes of the current tree: *n particles, *n_leaves L. */
+int sph_tree_sizes(sph_ctx *ctx, int64_t *n, int64_t *n_leaves);
+
+/* Copy the current tree to caller-allocated host arrays (NULL entries are skipped). */
+int sph_export_tree(sph_ctx *ctx, sph_tree_view *view);
+
+/* Copy the neighbour cache as CSR to host arrays: off[n+1] (int64) and ids[n_pairs] (indices in
+ * the current, Morton, order; each list in the cache's walk order). */
+int sph_export_neighbours(sph_ctx *ctx, int64_t *off, uint32_t *ids);
+
+/* Statistics of the last calls. */
+int sph_get_stats(sph_ctx *ctx, sph_stats *st);
+
+/* Enable (1) or disable (0) per-stage CUDA-event timing.  With timing on, every stage waits for its
+ * own completion, so stage boundaries serialise with the host; kernel durations are unaffected. */
+int sph_set_timing(sph_ctx *ctx, int enable);
+
+/* Zero the accumulated stage times. */
+int sph_reset_timing(sph_ctx *ctx);
+
+/* Message of the last error of ctx (never NULL; "" when none). */
+const char *sph_last_error(sph_ctx *ctx);
+
+/* Static description of a status code. */
+const char *sph_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_GB300_H */

@@ -107,6 +107,8 @@ def _setup(lib):
         "orc_cfl": (_d, [_i64, P, _p, _p, _p, _p, _p]),
         "orc_step": (_d, [_i64, _d, P, _d] + [_p] * 15 + [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_d)]),
         "orc_num_threads": (_i32, []),
+        "orc_subset_forces": (_i64, [_i64, _d, P] + [_p] * 7 + [_d, _i64, _p] + [_p] * 7),
+        "orc_subset_neighbours": (_i64, [_i64, _p, _p, _p, _p, _d, _p, _p, _i32, _i64, _p, _p, _p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -347,3 +349,34 @@ def step(state: dict, mass, params: Params, dt, method=None):
     if dtn < 0:
         raise RuntimeError("oracle h iteration exceeded h_max_iter")
     return dtn, it.value, dvr.value
+
+
+# ---- sampled evaluation for full-size inputs ----
+def subset_forces(x, y, z, vx, vy, vz, u, mass, params: Params, idx, h_hi):
+    """Root h, Omega and (ax, ay, az, du, vsig) of the particles idx, by brute force over all n.
+    Returns a dict of arrays aligned with idx."""
+    arrs = [_f64(a) for a in (x, y, z, vx, vy, vz, u)]
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    m = len(idx)
+    outs = [np.zeros(m) for _ in range(7)]
+    p = params.c()
+    bad = _load().orc_subset_forces(len(arrs[0]), float(mass), ctypes.byref(p), *[_ptr(a) for a in arrs],
+                                    float(h_hi), m, _ptr(idx), *[_ptr(o) for o in outs])
+    if bad:
+        raise ValueError(f"{bad} roots not bracketed below h_hi={h_hi}")
+    return dict(zip(("h", "omega", "ax", "ay", "az", "du", "vsig"), outs))
+
+
+def subset_neighbours(x, y, z, hc, s, idx, lo=(0, 0, 0), hi=(1, 1, 1), periodic=1):
+    """Neighbour lists (definition of ``neighbours``) of the particles idx only."""
+    x, y, z, hc = _f64(x), _f64(y), _f64(z), _f64(hc)
+    lo, hi = _box(lo, hi)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    lib = _load()
+    args = (len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(hc), float(s), _ptr(lo), _ptr(hi), int(periodic), len(idx),
+            _ptr(idx))
+    tot = lib.orc_subset_neighbours(*args, None, None)
+    off = np.zeros(len(idx) + 1, np.int64)
+    ids = np.zeros(max(tot, 1), np.int32)
+    lib.orc_subset_neighbours(*args, _ptr(off), _ptr(ids))
+    return off, ids[:tot].copy()

@@ -785,3 +785,144 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ====================================================================================== */
+/* Sampled evaluation for large inputs: the same definitions, for a list of particles only.   */
+/* Candidates are found by brute force over all n; smoothing lengths are the roots of the      */
+/* density equation (orc_density_root), Omega follows Eq. sphomega at those roots, and the      */
+/* derivatives follow orc_forces term by term.                                                  */
+/* ====================================================================================== */
+
+/* Brute-force candidate list of particle a: every b != a within radius rad (nearest image). */
+static int64_t orc_candidates(int64_t n, const double *x, const double *y, const double *z, int64_t a, double rad,
+                              const double *boxL, int periodic, int64_t **out)
+{
+    int64_t cap = 256, k = 0;
+    int64_t *l = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+    for (int64_t b = 0; b < n; b++) {
+        if (b == a) continue;
+        double d[3];
+        double r = orc_dist(x, y, z, a, b, boxL, periodic, d);
+        if (r < rad) {
+            if (k == cap) { cap *= 2; l = (int64_t *)realloc(l, (size_t)cap * sizeof(int64_t)); }
+            l[k++] = b;
+        }
+    }
+    *out = l;
+    return k;
+}
+
+/* Root h (bisection of phi as in orc_density_root) and Omega of one particle from its candidate list. */
+static void orc_one_root(int64_t a, const int64_t *cand, int64_t nc, const double *x, const double *y, const double *z,
+                         double mass, double hfact, double h_hi, const double *boxL, int periodic,
+                         double *h_out, double *om_out)
+{
+    orc_nlist one;
+    int64_t *off = (int64_t *)malloc((size_t)(a + 2) * sizeof(int64_t));
+    int32_t *ids = (int32_t *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(int32_t));
+    for (int64_t i = 0; i <= a; i++) off[i] = 0;
+    off[a + 1] = nc;
+    for (int64_t k = 0; k < nc; k++) ids[k] = (int32_t)cand[k];
+    one.n = a + 1; one.off = off; one.ids = ids;
+    double hl = 0.0, hh = h_hi;
+    for (int it = 0; it < 200; it++) {
+        double hm = 0.5 * (hl + hh);
+        if (hm <= hl || hm >= hh) break;
+        if (hl > 0.0 && (hh - hl) <= 1e-16 * hh) break;
+        if (orc_phi(a, hm, &one, x, y, z, boxL, periodic, hfact) > 0.0) hh = hm;
+        else hl = hm;
+    }
+    double h = 0.5 * (hl + hh);
+    if (!(orc_phi(a, h_hi, &one, x, y, z, boxL, periodic, hfact) > 0.0)) h = NAN;
+    double rs, ds;
+    orc_rho_sums(a, h, mass, &one, x, y, z, boxL, periodic, &rs, &ds);
+    double rho_h = mass * pow(hfact / h, 3.0);
+    *h_out = h;
+    *om_out = 1.0 + h / (3.0 * rho_h) * ds;
+    free(off); free(ids);
+}
+
+/* For m sampled particles idx[]: root h, Omega, and (ax, ay, az, du, vsig) from the definitions.
+ * h_hi must exceed every smoothing length involved.  Returns the number of particles whose root
+ * could not be bracketed (0 on success). */
+int64_t orc_subset_forces(int64_t n, double mass, const orc_params *p, const double *x, const double *y,
+                          const double *z, const double *vx, const double *vy, const double *vz, const double *u,
+                          double h_hi, int64_t m, const int64_t *idx, double *h_o, double *om_o,
+                          double *ax, double *ay, double *az, double *du, double *vs_o)
+{
+    double boxL[3] = {p->hi[0] - p->lo[0], p->hi[1] - p->lo[1], p->hi[2] - p->lo[2]};
+    int64_t bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
+    for (int64_t s = 0; s < m; s++) {
+        int64_t a = idx[s];
+        int64_t *cand;
+        int64_t nc = orc_candidates(n, x, y, z, a, 2.0 * h_hi, boxL, p->periodic, &cand);
+        double ha, oma;
+        orc_one_root(a, cand, nc, x, y, z, mass, p->hfact, h_hi, boxL, p->periodic, &ha, &oma);
+        double rho_a = mass * pow(p->hfact / ha, 3.0);
+        double P_a = (p->gamma - 1.0) * rho_a * u[a];
+        double c_a = sqrt(p->gamma * P_a / rho_a);
+        double acc[3] = {0.0, 0.0, 0.0}, dua = 0.0, vs = p->alpha_av * c_a;
+        if (!(ha == ha)) bad++;
+        for (int64_t k = 0; k < nc; k++) {
+            int64_t b = cand[k];
+            int64_t *cb;
+            int64_t nb = orc_candidates(n, x, y, z, b, 2.0 * h_hi, boxL, p->periodic, &cb);
+            double hb, omb;
+            orc_one_root(b, cb, nb, x, y, z, mass, p->hfact, h_hi, boxL, p->periodic, &hb, &omb);
+            free(cb);
+            if (!(hb == hb)) { bad++; continue; }
+            double d[3];
+            double r = orc_dist(x, y, z, a, b, boxL, p->periodic, d);
+            double hm = ha > hb ? ha : hb;
+            if (!(r < 2.0 * hm)) continue;
+            double rho_b = mass * pow(p->hfact / hb, 3.0);
+            double P_b = (p->gamma - 1.0) * rho_b * u[b];
+            double c_b = sqrt(p->gamma * P_b / rho_b);
+            double rhat[3] = {d[0] / r, d[1] / r, d[2] / r};
+            double vdotr = (vx[a] - vx[b]) * rhat[0] + (vy[a] - vy[b]) * rhat[1] + (vz[a] - vz[b]) * rhat[2];
+            double Fa = orc_F(r, ha), Fb = orc_F(r, hb);
+            double qa = 0.0, qb = 0.0;
+            if (vdotr < 0.0) {
+                qa = -0.5 * rho_a * (p->alpha_av * c_a + p->beta_av * fabs(vdotr)) * vdotr;
+                qb = -0.5 * rho_b * (p->alpha_av * c_b + p->beta_av * fabs(vdotr)) * vdotr;
+            }
+            double Aa = (P_a + qa) / (rho_a * rho_a * oma);
+            double Ab = (P_b + qb) / (rho_b * rho_b * omb);
+            double sc = mass * (Aa * Fa + Ab * Fb);
+            for (int c = 0; c < 3; c++) acc[c] -= sc * rhat[c];
+            dua += mass * Aa * vdotr * Fa;
+            if (p->alpha_u != 0.0) {
+                double vsu = sqrt(fabs(P_a - P_b) / (0.5 * (rho_a + rho_b)));
+                dua += mass * p->alpha_u * vsu * (u[a] - u[b]) * 0.5 * (Fa / (oma * rho_a) + Fb / (omb * rho_b));
+            }
+            double vsdt = p->alpha_av * c_a + p->beta_av * (vdotr < 0.0 ? -vdotr : 0.0);
+            if (vsdt > vs) vs = vsdt;
+        }
+        free(cand);
+        h_o[s] = ha; om_o[s] = oma;
+        ax[s] = acc[0]; ay[s] = acc[1]; az[s] = acc[2]; du[s] = dua; vs_o[s] = vs;
+    }
+    return bad;
+}
+
+/* Neighbour set (definition of orc_neighbours) of m sampled particles; off[m+1], ids sized by the
+ * caller from a first call with ids == NULL (returns the total). */
+int64_t orc_subset_neighbours(int64_t n, const double *x, const double *y, const double *z, const double *hc,
+                              double s, const double *lo, const double *hi, int periodic, int64_t m,
+                              const int64_t *idx, int64_t *off, int32_t *ids)
+{
+    double boxL[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    int64_t tot = 0;
+    if (off) off[0] = 0;
+    for (int64_t k = 0; k < m; k++) {
+        int64_t a = idx[k];
+        for (int64_t b = 0; b < n; b++)
+            if (b != a && orc_pair_in(x, y, z, hc, a, b, s, boxL, periodic)) {
+                if (ids) ids[tot] = (int32_t)b;
+                tot++;
+            }
+        if (off) off[k + 1] = tot;
+    }
+    return tot;
+}

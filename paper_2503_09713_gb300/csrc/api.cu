@@ -1,0 +1,477 @@
+// C ABI of the SPH library: context, allocation, stage entry points and the time step (App. G).
+#include <cstdarg>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+int64_t scan_scratch_elems(int64_t n);
+
+int fail(sph_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->last_error = buf;
+    }
+    return code;
+}
+
+int cuda_fail(sph_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, SPH_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+int stage_begin(sph_ctx *c, int k) {
+    (void)k;
+    if (!c->timing) return SPH_OK;
+    SPH_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    return SPH_OK;
+}
+
+int stage_end(sph_ctx *c, int k) {
+    if (!c->timing) return SPH_OK;
+    SPH_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+    SPH_CUDA(c, cudaEventSynchronize(c->ev[1]));
+    float ms = 0.f;
+    SPH_CUDA(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    c->stats.stage_ms[k] += ms;
+    return SPH_OK;
+}
+
+int read_scalars(sph_ctx *c) {
+    SPH_CUDA(c, cudaMemcpyAsync(c->hscal, c->dscal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SPH_OK;
+}
+
+}  // namespace sph
+
+using namespace sph;
+
+namespace {
+
+template <typename T>
+int alloc(sph_ctx *c, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, SPH_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    return SPH_OK;
+}
+
+void free_all(sph_ctx *c) {
+    void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->digit_hist, c->lookback, c->tile_ctr,
+                    c->mask[0], c->mask[1], c->scan_tmp, c->leaf_first, c->mu_leaf, c->lchild, c->rchild,
+                    c->endrange, c->lflag, c->rflag, c->child, c->node_parent, c->leaf_parent, c->visit, c->nodes,
+                    c->gather_tmp, c->id_tmp, c->rel, c->h32, c->h_base, c->gbox, c->cand, c->cand_cnt, c->nb_cnt,
+                    c->grp_slots, c->grp_off, c->nb_ids, c->frec, c->m_v, c->m_t, c->m_r, c->a_new, c->block_part,
+                    c->hs_fields, c->hs_id, c->dscal};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->hscal) cudaFreeHost(c->hscal);
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
+}
+
+int check_params(sph_ctx *c, const sph_params *p) {
+    if (!p) return fail(c, SPH_ERR_INVALID_ARG, "params is NULL");
+    if (p->kernel != SPH_KERNEL_M4) return fail(c, SPH_ERR_INVALID_ARG, "only the M4 kernel is built");
+    if (p->precision != SPH_FP64 && p->precision != SPH_MIXED)
+        return fail(c, SPH_ERR_INVALID_ARG, "precision must be SPH_FP64 or SPH_MIXED");
+    if (!(p->hfact > 0) || !(p->gamma > 1) || !(p->h_tol > 0) || !(p->h_clamp > 1) || !(p->cache_tol >= 1) ||
+        !(p->c_cour > 0) || !(p->c_force > 0) || p->alpha_av < 0 || p->beta_av < 0 || p->alpha_u < 0)
+        return fail(c, SPH_ERR_INVALID_ARG, "parameter out of range");
+    if (p->h_max_iter < 1 || p->reduction_level < 0 || p->reduction_level > 16 || p->max_outer < 1)
+        return fail(c, SPH_ERR_INVALID_ARG, "iteration limits out of range");
+    for (int k = 0; k < 3; k++)
+        if (!(p->box_hi[k] > p->box_lo[k])) return fail(c, SPH_ERR_INVALID_ARG, "empty box along axis %d", k);
+    return SPH_OK;
+}
+
+int check_state(sph_ctx *c, const sph_state *s, bool need_vel) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    if (!s) return fail(c, SPH_ERR_INVALID_ARG, "state is NULL");
+    if (s->n < 1 || s->n > c->n_cap)
+        return fail(c, SPH_ERR_INVALID_ARG, "n = %lld outside [1, %lld]", (long long)s->n, (long long)c->n_cap);
+    if (!(s->mass > 0)) return fail(c, SPH_ERR_INVALID_ARG, "mass must be positive");
+    if (!s->x || !s->y || !s->z || !s->h) return fail(c, SPH_ERR_INVALID_ARG, "x, y, z and h are required");
+    if (need_vel && (!s->vx || !s->vy || !s->vz || !s->u || !s->ax || !s->ay || !s->az || !s->du || !s->rho ||
+                     !s->omega || !s->vsig))
+        return fail(c, SPH_ERR_INVALID_ARG, "v, u, a, du, rho, omega and vsig are required");
+    if (c->tree_valid && s->n != c->n && need_vel) return fail(c, SPH_ERR_ORDER, "n changed since the tree build");
+    return SPH_OK;
+}
+
+int finish_forces(sph_ctx *c) {
+    int r = read_scalars(c);
+    if (r) return r;
+    double dt;
+    unsigned long long b = c->hscal->dt_min_bits;
+    std::memcpy(&dt, &b, sizeof dt);
+    c->dt_next = dt;
+    c->stats.dt_next = dt;
+    c->stats.force_pairs = (int64_t)c->hscal->inrange_pairs;
+    if (c->hscal->flags & kErrTimeout) return fail(c, SPH_ERR_TIMEOUT, "device wait ran out");
+    return SPH_OK;
+}
+
+// Density with the outer loop of App. F: while some h leaves cache_tol * h^n, refresh the cell
+// h_max and rebuild the cache around the current h, then iterate again.
+int density_with_restarts(sph_ctx *c, sph_state *s, int *iters, int max_outer) {
+    int passes = 1;
+    for (;;) {
+        bool stale = false;
+        int r;
+        if ((r = stage_begin(c, kStDensity)) || (r = density_run(c, s, iters, &stale)) ||
+            (r = stage_end(c, kStDensity)))
+            return r;
+        if (!stale) break;
+        if (passes >= max_outer)
+            return fail(c, SPH_ERR_CACHE_STALE, "h left the cache tolerance after %d cache builds", passes);
+        if ((r = stage_begin(c, kStNeigh)) || (r = tree_boxes(c, s)) || (r = neighbours_build(c, s)) ||
+            (r = stage_end(c, kStNeigh)))
+            return r;
+        ++passes;
+    }
+    c->stats.outer_passes = passes;
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sph_default_params(sph_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->kernel = SPH_KERNEL_M4;
+    p->precision = SPH_FP64;
+    p->hfact = 1.2;
+    p->gamma = 5.0 / 3.0;
+    p->alpha_av = 1.0;
+    p->beta_av = 2.0;
+    p->alpha_u = 1.0;
+    p->c_cour = 0.3;
+    p->c_force = 0.25;
+    p->h_tol = 1e-6;
+    p->h_clamp = 1.2;
+    p->cache_tol = 1.1;
+    p->h_max_iter = 64;
+    p->reduction_level = 3;
+    p->periodic = 1;
+    p->max_outer = 8;
+    for (int k = 0; k < 3; k++) {
+        p->box_lo[k] = 0.0;
+        p->box_hi[k] = 1.0;
+    }
+}
+
+int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stream, sph_ctx **out) {
+    if (!out) return SPH_ERR_INVALID_ARG;
+    *out = nullptr;
+    sph_ctx *c = new (std::nothrow) sph_ctx();
+    if (!c) return SPH_ERR_OOM;
+    int r = check_params(c, p);
+    if (r) { delete c; return r; }
+    if (n_cap < 1 || n_cap > (int64_t)1 << 30) { delete c; return SPH_ERR_INVALID_ARG; }
+    c->p = *p;
+    c->stream = (cudaStream_t)stream;
+    c->n_cap = n_cap;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SPH_ERR_CUDA;
+    }
+    const int64_t N = n_cap;
+    const int64_t G = (N + 31) / 32;
+    const int64_t tiles = (N + 4095) / 4096;
+    const int64_t chunks = (N + 2047) / 2048;
+    c->sort_tiles = tiles;
+    c->cand_cap = 256;
+    c->nb_cap = neigh_cap > 0 ? neigh_cap : 96 * N;
+    const int64_t scan_elems = 2 * (chunks + 1) + scan_scratch_elems(chunks) + scan_scratch_elems(G + 1) + 64;
+    if ((r = alloc(c, &c->keys[0], N)) || (r = alloc(c, &c->keys[1], N)) || (r = alloc(c, &c->vals[0], N)) ||
+        (r = alloc(c, &c->vals[1], N)) || (r = alloc(c, &c->digit_hist, 8 * 256)) ||
+        (r = alloc(c, &c->lookback, (size_t)8 * tiles * 256)) || (r = alloc(c, &c->tile_ctr, 8)) ||
+        (r = alloc(c, &c->mask[0], N)) || (r = alloc(c, &c->mask[1], N)) || (r = alloc(c, &c->scan_tmp, scan_elems)) ||
+        (r = alloc(c, &c->leaf_first, N + 1)) || (r = alloc(c, &c->mu_leaf, N)) || (r = alloc(c, &c->lchild, N)) ||
+        (r = alloc(c, &c->rchild, N)) || (r = alloc(c, &c->endrange, N)) || (r = alloc(c, &c->lflag, N)) ||
+        (r = alloc(c, &c->rflag, N)) || (r = alloc(c, &c->child, 2 * N)) || (r = alloc(c, &c->node_parent, N)) ||
+        (r = alloc(c, &c->leaf_parent, N)) || (r = alloc(c, &c->visit, N)) || (r = alloc(c, &c->nodes, 2 * N)) ||
+        (r = alloc(c, &c->gather_tmp, (size_t)15 * N)) || (r = alloc(c, &c->id_tmp, N)) ||
+        (r = alloc(c, &c->rel, N)) || (r = alloc(c, &c->h32, N)) || (r = alloc(c, &c->h_base, N)) ||
+        (r = alloc(c, &c->gbox, G)) || (r = alloc(c, &c->cand, (size_t)G * c->cand_cap)) ||
+        (r = alloc(c, &c->cand_cnt, G)) || (r = alloc(c, &c->nb_cnt, N)) || (r = alloc(c, &c->grp_slots, G + 1)) ||
+        (r = alloc(c, &c->grp_off, G + 1)) || (r = alloc(c, &c->nb_ids, c->nb_cap)) ||
+        (r = alloc(c, (char **)&c->frec, (size_t)128 * N)) || (r = alloc(c, &c->m_v, N)) ||
+        (r = alloc(c, &c->m_t, N)) || (r = alloc(c, &c->m_r, N)) || (r = alloc(c, &c->a_new, (size_t)4 * N)) ||
+        (r = alloc(c, &c->block_part, (size_t)(N / 256 + 2))) || (r = alloc(c, &c->dscal, 1))) {
+        free_all(c);
+        delete c;
+        return r;
+    }
+    if (cudaMallocHost((void **)&c->hscal, sizeof(DevScalars)) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return SPH_ERR_OOM;
+    }
+    std::memset(c->hscal, 0, sizeof(DevScalars));
+    if (cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return SPH_ERR_CUDA;
+    }
+    if (cudaMemsetAsync(c->dscal, 0, sizeof(DevScalars), c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return SPH_ERR_CUDA;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+int sph_destroy(sph_ctx *c) {
+    if (!c) return SPH_OK;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return SPH_OK;
+}
+
+int sph_set_params(sph_ctx *c, const sph_params *p) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    int r = check_params(c, p);
+    if (r) return r;
+    c->p = *p;
+    c->tree_valid = c->cache_valid = c->density_valid = c->forces_valid = false;
+    c->dt_next = -1.0;
+    return SPH_OK;
+}
+
+int sph_build_tree(sph_ctx *c, sph_state *s) {
+    int r = check_state(c, s, false);
+    if (r) return r;
+    c->n = s->n;
+    c->density_valid = c->forces_valid = false;
+    return tree_build(c, s, true);
+}
+
+int sph_find_neighbours(sph_ctx *c, const sph_state *s, int64_t *n_pairs) {
+    int r = check_state(c, s, false);
+    if (r) return r;
+    if (!c->tree_valid || s->n != c->n) return fail(c, SPH_ERR_ORDER, "sph_find_neighbours needs sph_build_tree");
+    r = tree_boxes(c, s);   // h_max of the cells from the current h
+    if (r) return r;
+    r = neighbours_build(c, s);
+    if (r) return r;
+    if (n_pairs) *n_pairs = c->n_pairs;
+    return SPH_OK;
+}
+
+int sph_compute_density_h(sph_ctx *c, sph_state *s, int *iters) {
+    int r = check_state(c, s, false);
+    if (r) return r;
+    if (!s->rho || !s->omega) return fail(c, SPH_ERR_INVALID_ARG, "rho and omega are required");
+    if (!c->cache_valid || s->n != c->n) return fail(c, SPH_ERR_ORDER, "density needs sph_find_neighbours");
+    bool stale = false;
+    r = density_run(c, s, iters, &stale);
+    if (r) return r;
+    if (stale) return fail(c, SPH_ERR_CACHE_STALE, "some h exceeded cache_tol * h^n; rebuild the cache");
+    return SPH_OK;
+}
+
+int sph_compute_forces(sph_ctx *c, sph_state *s) {
+    int r = check_state(c, s, true);
+    if (r) return r;
+    if (!c->cache_valid || s->n != c->n) return fail(c, SPH_ERR_ORDER, "forces need sph_find_neighbours");
+    r = forces_run(c, s, s->ax, s->ay, s->az, s->du);
+    if (r) return r;
+    r = finish_forces(c);
+    if (r) return r;
+    c->forces_valid = true;
+    return SPH_OK;
+}
+
+int sph_step(sph_ctx *c, sph_state *s, double dt, double *dt_used, double *dt_next) {
+    int r = check_state(c, s, true);
+    if (r) return r;
+    if (!(dt > 0)) {
+        if (!(c->dt_next > 0)) return fail(c, SPH_ERR_ORDER, "dt <= 0 needs a previous force evaluation");
+        dt = c->dt_next;
+    }
+    c->n = s->n;
+    // A0 predictor
+    if ((r = stage_begin(c, kStPredict)) || (r = integrate_predict(c, s, dt)) || (r = stage_end(c, kStPredict)))
+        return r;
+    // A1-A6 tree (reorders the state; outputs are recomputed below)
+    if ((r = stage_begin(c, kStTree)) || (r = tree_build(c, s, false)) || (r = stage_end(c, kStTree))) return r;
+    // A7 cache at h^n
+    if ((r = stage_begin(c, kStNeigh)) || (r = neighbours_build(c, s)) || (r = stage_end(c, kStNeigh))) return r;
+    // A8 density / h with the outer restart
+    int iters = 0;
+    if ((r = density_with_restarts(c, s, &iters, c->p.max_outer))) return r;
+    // A9 forces into a_new
+    const int64_t st = c->n_cap;
+    if ((r = forces_run(c, s, c->a_new, c->a_new + st, c->a_new + 2 * st, c->a_new + 3 * st))) return r;
+    // A10 corrector
+    if ((r = stage_begin(c, kStCorrect)) || (r = integrate_correct(c, s, dt)) || (r = stage_end(c, kStCorrect)))
+        return r;
+    if ((r = finish_forces(c))) return r;
+    double dvm;
+    unsigned long long b = c->hscal->dv_max_bits;
+    std::memcpy(&dvm, &b, sizeof dvm);
+    const double v2 = c->hscal->v2_sum;
+    c->stats.dv_ratio = v2 > 0 ? dvm / std::sqrt(v2 / (double)s->n) : 0.0;
+    c->forces_valid = true;
+    if (dt_used) *dt_used = dt;
+    if (dt_next) *dt_next = c->dt_next;
+    return SPH_OK;
+}
+
+int sph_step_host(sph_ctx *c, sph_state *hs, double dt, double *dt_used, double *dt_next) {
+    int r = check_state(c, hs, true);
+    if (r) return r;
+    const int64_t n = hs->n;
+    const int64_t N = c->n_cap;
+    if (!c->hs_fields) {
+        if ((r = alloc(c, &c->hs_fields, (size_t)15 * N))) return r;
+        if ((r = alloc(c, &c->hs_id, N))) return r;
+    }
+    double **hf[15] = {&hs->x, &hs->y, &hs->z, &hs->vx, &hs->vy, &hs->vz, &hs->u, &hs->h,
+                       &hs->ax, &hs->ay, &hs->az, &hs->du, &hs->rho, &hs->omega, &hs->vsig};
+    sph_state ds = *hs;
+    double **df[15] = {&ds.x, &ds.y, &ds.z, &ds.vx, &ds.vy, &ds.vz, &ds.u, &ds.h,
+                       &ds.ax, &ds.ay, &ds.az, &ds.du, &ds.rho, &ds.omega, &ds.vsig};
+    // inputs of the step: positions, velocities, u, h, a, du
+    for (int f = 0; f < 15; f++) {
+        *df[f] = c->hs_fields + (size_t)f * N;
+        if (f < 12)
+            SPH_CUDA(c, cudaMemcpyAsync(*df[f], *hf[f], (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    }
+    ds.id = hs->id ? c->hs_id : nullptr;
+    if (hs->id)
+        SPH_CUDA(c, cudaMemcpyAsync(ds.id, hs->id, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+    r = sph_step(c, &ds, dt, dt_used, dt_next);
+    if (r) return r;
+    for (int f = 0; f < 15; f++)
+        SPH_CUDA(c, cudaMemcpyAsync(*hf[f], *df[f], (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (hs->id)
+        SPH_CUDA(c, cudaMemcpyAsync(hs->id, ds.id, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SPH_OK;
+}
+
+int sph_tree_sizes(sph_ctx *c, int64_t *n, int64_t *n_leaves) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    if (!c->tree_valid) return fail(c, SPH_ERR_ORDER, "no tree");
+    if (n) *n = c->n;
+    if (n_leaves) *n_leaves = c->n_leaves;
+    return SPH_OK;
+}
+
+int sph_export_tree(sph_ctx *c, sph_tree_view *v) {
+    if (!c || !v) return SPH_ERR_INVALID_ARG;
+    if (!c->tree_valid) return fail(c, SPH_ERR_ORDER, "no tree");
+    const int64_t n = c->n, L = c->n_leaves, nin = L - 1, nodes = 2 * L - 1;
+    auto cp = [&](void *dst, const void *src, size_t bytes) -> int {
+        if (!dst || bytes == 0) return SPH_OK;
+        SPH_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+        return SPH_OK;
+    };
+    int r;
+    if ((r = cp(v->mu, c->mu, n * 8)) || (r = cp(v->perm, c->perm, n * 4)) ||
+        (r = cp(v->leaf_first, c->leaf_first, (L + 1) * 8)) || (r = cp(v->mu_leaf, c->mu_leaf, L * 8)) ||
+        (r = cp(v->lchild, c->lchild, nin * 4)) || (r = cp(v->rchild, c->rchild, nin * 4)) ||
+        (r = cp(v->lflag, c->lflag, nin)) || (r = cp(v->rflag, c->rflag, nin)) ||
+        (r = cp(v->endrange, c->endrange, nin * 4)))
+        return r;
+    if (v->bmin || v->bmax || v->hmax) {
+        std::vector<Node> nd((size_t)nodes);
+        SPH_CUDA(c, cudaMemcpyAsync(nd.data(), c->nodes, nodes * sizeof(Node), cudaMemcpyDeviceToHost, c->stream));
+        SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int64_t i = 0; i < nodes; i++) {
+            for (int k = 0; k < 3; k++) {
+                if (v->bmin) v->bmin[3 * i + k] = nd[i].lo[k];
+                if (v->bmax) v->bmax[3 * i + k] = nd[i].hi[k];
+            }
+            if (v->hmax) v->hmax[i] = nd[i].hmax;
+        }
+    }
+    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SPH_OK;
+}
+
+int sph_export_neighbours(sph_ctx *c, int64_t *off, uint32_t *ids) {
+    if (!c || !off) return SPH_ERR_INVALID_ARG;
+    if (!c->cache_valid) return fail(c, SPH_ERR_ORDER, "no neighbour cache");
+    const int64_t n = c->n, G = c->n_groups;
+    std::vector<uint32_t> cnt((size_t)n);
+    std::vector<int64_t> goff((size_t)G + 1);
+    std::vector<uint32_t> raw((size_t)std::max<int64_t>(c->total_slots, 1));
+    SPH_CUDA(c, cudaMemcpyAsync(cnt.data(), c->nb_cnt, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    SPH_CUDA(c, cudaMemcpyAsync(goff.data(), c->grp_off, (G + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (c->total_slots > 0)
+        SPH_CUDA(c, cudaMemcpyAsync(raw.data(), c->nb_ids, c->total_slots * 4, cudaMemcpyDeviceToHost, c->stream));
+    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+    off[0] = 0;
+    for (int64_t a = 0; a < n; a++) off[a + 1] = off[a] + cnt[a];
+    if (ids) {
+        for (int64_t a = 0; a < n; a++) {
+            const int64_t base = goff[a >> 5] + (a & 31);
+            for (uint32_t k = 0; k < cnt[a]; k++) ids[off[a] + k] = raw[base + (int64_t)k * 32];
+        }
+    }
+    return SPH_OK;
+}
+
+int sph_get_stats(sph_ctx *c, sph_stats *st) {
+    if (!c || !st) return SPH_ERR_INVALID_ARG;
+    c->stats.kernel_launches = c->launches;
+    *st = c->stats;
+    return SPH_OK;
+}
+
+int sph_set_timing(sph_ctx *c, int enable) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    c->timing = enable != 0;
+    return SPH_OK;
+}
+
+int sph_reset_timing(sph_ctx *c) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    for (double &v : c->stats.stage_ms) v = 0.0;
+    return SPH_OK;
+}
+
+const char *sph_last_error(sph_ctx *c) { return c ? c->last_error.c_str() : "no context"; }
+
+const char *sph_error_string(int s) {
+    switch (s) {
+        case SPH_OK: return "ok";
+        case SPH_ERR_INVALID_ARG: return "invalid argument";
+        case SPH_ERR_OOM: return "device out of memory";
+        case SPH_ERR_CAPACITY: return "capacity exceeded";
+        case SPH_ERR_CACHE_STALE: return "neighbour cache stale: h exceeded cache_tol * h^n";
+        case SPH_ERR_H_NOT_CONVERGED: return "smoothing-length iteration did not converge";
+        case SPH_ERR_TIMEOUT: return "bounded device wait ran out";
+        case SPH_ERR_CUDA: return "CUDA error";
+        case SPH_ERR_ORDER: return "call order: a required stage has not run";
+        case SPH_ERR_NONFINITE: return "non-finite position or smoothing length";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+// Smoothing-length / density iteration (App. F, Alg. smoothinglenghtupdate) and Omega (Eq. sphomega).
+//
+// Each particle's equation  rho_sum(h_a) = m (hfact/h_a)^3  involves only its own h_a, so a thread
+// iterates Newton-Raphson on its own particle until |dh|/h^n <= eps_c (the paper iterates all
+// particles until the largest eps is below eps_c; once a particle meets the criterion its further
+// updates are below eps_c^2).  Steps are clamped to [h/lambda, h*lambda]; an h above chi*h^n is
+// clamped there and flagged so the host rebuilds the cache (outer loop of Alg. F).  After
+// convergence rho = rho(h) (Eq. rhoh) and Omega = 1 + h/(3 rho) sum_b m dW/dh at the final h.
+// FP64 path: all pair arithmetic in FP64.  Mixed path: pair sums in FP32 (Kahan) on cell-relative
+// offsets; Newton update, h, rho and Omega in FP64.
+#include <cstddef>
+
+#include "physics.cuh"
+
+namespace sph {
+
+struct DensParams {
+    double mass, hfact, h_tol, h_clamp, chi;
+    int max_iter;
+    PairGeo geo;
+};
+
+// Sums over the neighbours of a at smoothing length h:  sf = sum f(q),  sg = sum (3 f + q f')
+// (self term included: f(0) = 1, 3 f(0) = 3).
+template <bool kMixed>
+__device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt, const uint32_t *__restrict__ ids,
+                                             const double *__restrict__ x, const double *__restrict__ y,
+                                             const double *__restrict__ z, const float4 *__restrict__ rel,
+                                             const PairGeo &geo, double &sf, double &sg, uint32_t &nin) {
+    const double hinv = 1.0 / ha;
+    if (!kMixed) {
+        const double xa = x[a], ya = y[a], za = z[a];
+        const double hinv2 = hinv * hinv;
+        double f0 = 1.0, g0 = 3.0;
+        for (uint32_t k = 0; k < cnt; k++) {
+            const uint32_t b = ids[(int64_t)k * 32];
+            const double dx = min_image(x[b] - xa, geo.L[0], geo.halfL[0], geo.periodic);
+            const double dy = min_image(y[b] - ya, geo.L[1], geo.halfL[1], geo.periodic);
+            const double dz = min_image(z[b] - za, geo.L[2], geo.halfL[2], geo.periodic);
+            const double q2 = (dx * dx + dy * dy + dz * dz) * hinv2;
+            if (q2 < 4.0) {
+                ++nin;
+                const double q = sqrt(q2);
+                double f, df;
+                m4(q, f, df);
+                f0 += f;
+                g0 += 3.0 * f + q * df;
+            }
+        }
+        sf = f0;
+        sg = g0;
+    } else {
+        const float4 A = rel[a];
+        const float hi = (float)hinv;
+        const float hi2 = hi * hi;
+        float s0 = 1.f, c0 = 0.f, s1 = 3.f, c1 = 0.f;
+        for (uint32_t k = 0; k < cnt; k++) {
+            const uint32_t b = ids[(int64_t)k * 32];
+            float dx, dy, dz;
+            rel_sep(A, rel[b], geo, dx, dy, dz);
+            const float q2 = (dx * dx + dy * dy + dz * dz) * hi2;
+            if (q2 < 4.f) {
+                ++nin;
+                const float q = sqrtf(q2);
+                float f, df;
+                m4(q, f, df);
+                kahan_add(s0, c0, f);
+                kahan_add(s1, c1, 3.f * f + q * df);
+            }
+        }
+        sf = kahan_value(s0, c0);
+        sg = kahan_value(s1, c1);
+    }
+}
+
+template <bool kMixed>
+__global__ void __launch_bounds__(128) k_density(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                                                 const double *__restrict__ z, const float4 *__restrict__ rel,
+                                                 double *__restrict__ h, const double *__restrict__ h_base,
+                                                 const uint32_t *__restrict__ nb_cnt, const int64_t *__restrict__ grp_off,
+                                                 const uint32_t *__restrict__ nb_ids, DensParams dp,
+                                                 double *__restrict__ rho, double *__restrict__ omega, DevScalars *sc) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    const int lane = (int)(a & 31);
+    const int64_t g = a >> 5;
+    const uint32_t cnt = nb_cnt[a];
+    const uint32_t *ids = nb_ids + grp_off[g] + lane;
+    double ha = h[a];
+    const double hn = h_base[a];
+    const double m = dp.mass;
+    const double hf3 = dp.hfact * dp.hfact * dp.hfact;
+    int it = 0;
+    uint32_t nin = 0;
+    bool stale = false, conv = false;
+    while (it < dp.max_iter) {
+        ++it;
+        double sf, sg;
+        density_sums<kMixed>(a, ha, cnt, ids, x, y, z, rel, dp.geo, sf, sg, nin);
+        const double hinv = 1.0 / ha;
+        const double hinv3 = hinv * hinv * hinv;
+        const double rho_sum = m * sf * hinv3 * kInvPi;
+        const double dsum = -m * sg * hinv3 * hinv * kInvPi;   // sum_b m dW/dh
+        const double rho_h = m * hf3 * hinv3;
+        double hnew = ha - (rho_sum - rho_h) / (dsum + 3.0 * rho_h * hinv);
+        if (hnew > ha * dp.h_clamp) hnew = ha * dp.h_clamp;
+        else if (hnew < ha / dp.h_clamp) hnew = ha / dp.h_clamp;
+        const double eps = fabs(hnew - ha) / hn;
+        if (hnew > hn * dp.chi) {
+            hnew = hn * dp.chi;
+            stale = true;
+        }
+        ha = hnew;
+        if (stale) break;
+        if (eps <= dp.h_tol) {
+            conv = true;
+            break;
+        }
+    }
+    h[a] = ha;
+    if (stale) atomicOr(&sc->flags, kErrStale);
+    else if (!conv) atomicOr(&sc->flags, kErrNotConverged);
+    // epilogue at the final h
+    double sf, sg;
+    density_sums<kMixed>(a, ha, cnt, ids, x, y, z, rel, dp.geo, sf, sg, nin);
+    const double hinv = 1.0 / ha;
+    const double hinv3 = hinv * hinv * hinv;
+    const double rho_h = m * hf3 * hinv3;
+    const double dsum = -m * sg * hinv3 * hinv * kInvPi;
+    rho[a] = rho_h;
+    omega[a] = 1.0 + ha / (3.0 * rho_h) * dsum;
+    atomicMax(&sc->max_iters, (uint32_t)it);
+    atomicAdd(&sc->pair_evals, (unsigned long long)cnt * (unsigned long long)(it + 1));
+    atomicAdd(&sc->dens_inrange, (unsigned long long)nin);
+}
+
+int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
+    if (!c->cache_valid) return fail(c, SPH_ERR_ORDER, "density before sph_find_neighbours");
+    const int64_t n = s->n;
+    DensParams dp;
+    dp.mass = s->mass;
+    dp.hfact = c->p.hfact;
+    dp.h_tol = c->p.h_tol;
+    dp.h_clamp = c->p.h_clamp;
+    dp.chi = c->p.cache_tol;
+    dp.max_iter = c->p.h_max_iter;
+    dp.geo = make_pair_geo(c->p);
+    SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
+    SPH_CUDA(c, cudaMemsetAsync(&c->dscal->max_iters, 0, sizeof(uint32_t), c->stream));
+    SPH_CUDA(c, cudaMemsetAsync(&c->dscal->pair_evals, 0, 2 * sizeof(unsigned long long), c->stream));
+    if (c->p.precision == SPH_MIXED)
+        k_density<true><<<grid_for(n, 128), 128, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+                                                                 c->nb_cnt, c->grp_off, c->nb_ids, dp, s->rho,
+                                                                 s->omega, c->dscal);
+    else
+        k_density<false><<<grid_for(n, 128), 128, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+                                                                  c->nb_cnt, c->grp_off, c->nb_ids, dp, s->rho,
+                                                                  s->omega, c->dscal);
+    SPH_LAUNCH_CHECK(c, "k_density");
+    static_assert(offsetof(DevScalars, flags) == offsetof(DevScalars, max_iters) + sizeof(uint32_t), "layout");
+    SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->max_iters, &c->dscal->max_iters, 2 * sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, c->stream));
+    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+    SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->pair_evals, &c->dscal->pair_evals, 2 * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, c->stream));
+    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->stats.density_pair_evals = (int64_t)c->hscal->pair_evals;
+    c->stats.density_inrange = (int64_t)c->hscal->dens_inrange;
+    const uint32_t fl = c->hscal->flags;
+    const int it = (int)c->hscal->max_iters;
+    if (iters) *iters = it;
+    c->stats.density_iters_max = it;
+    *stale = (fl & kErrStale) != 0;
+    if (fl & kErrNotConverged) return fail(c, SPH_ERR_H_NOT_CONVERGED, "h iteration exceeded %d", c->p.h_max_iter);
+    c->density_valid = !*stale;
+    return SPH_OK;
+}
+
+}  // namespace sph

@@ -1,0 +1,271 @@
+// Pair force loop (Sect. 2.1, Eqs. sphvel, sphuint, q^a_ab, v_sig, Lambda_cond, F_ab) and the CFL
+// time step (App. G).
+//
+//   a_a    = - sum_b m [ (P_a + q^a_ab)/(rho_a^2 Omega_a) F_ab(h_a) + (P_b + q^b_ab)/(rho_b^2 Omega_b) F_ab(h_b) ] rhat_ab
+//   du_a/dt=   sum_b m (P_a + q^a_ab)/(rho_a^2 Omega_a) (v_ab . rhat_ab) F_ab(h_a)
+//            + sum_b m alpha_u v_sig^u (u_a - u_b) 1/2 [F_ab(h_a)/(Omega_a rho_a) + F_ab(h_b)/(Omega_b rho_b)]
+//   q^a_ab = -1/2 rho_a (alpha c_s,a + beta |v_ab.rhat|) (v_ab.rhat)  when v_ab.rhat < 0, else 0
+//   v_sig^dt_a = max_b (alpha c_s,a + beta max(0, -v_ab.rhat)),  alpha c_s,a without neighbours
+// over pairs with r_ab < 2 max(h_a, h_b).  Per-particle factors (P/(rho^2 Omega), 1/(rho Omega), c_s,
+// P, rho, 1/h) are computed once per particle by a preparation kernel.  The mixed path evaluates
+// each pair in FP32 from cell-relative offsets and accumulates with Kahan compensation.
+#include "physics.cuh"
+
+namespace sph {
+
+struct ForceParams {
+    double mass, gamma, alpha_av, beta_av, alpha_u, c_cour, c_force;
+    PairGeo geo;
+};
+
+// Per-particle FP64 record of the force loop: 128 bytes, read as 8 double2.
+struct __align__(16) FRec {
+    double x, y, z, h;
+    double vx, vy, vz, u;
+    double pre, qf, cs, P;
+    double rho, hinv, pad0, pad1;
+};
+
+__global__ void k_force_prep(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                             const double *__restrict__ z, const double *__restrict__ vx,
+                             const double *__restrict__ vy, const double *__restrict__ vz,
+                             const double *__restrict__ u, const double *__restrict__ h,
+                             const double *__restrict__ rho, const double *__restrict__ omega, ForceParams fp,
+                             int mixed, FRec *__restrict__ rec, float4 *__restrict__ m_v, float4 *__restrict__ m_t,
+                             float4 *__restrict__ m_r) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double r = rho[i], om = omega[i], ui = u[i], hi = h[i];
+    const double P = (fp.gamma - 1.0) * r * ui;
+    const double cs = sqrt(fp.gamma * P / r);
+    const double pre = P / (r * r * om);
+    const double qf = 1.0 / (r * om);
+    const double hinv = 1.0 / hi;
+    if (mixed) {
+        m_v[i] = make_float4((float)vx[i], (float)vy[i], (float)vz[i], (float)hinv);
+        m_t[i] = make_float4((float)pre, (float)qf, (float)cs, (float)P);
+        m_r[i] = make_float4((float)r, (float)ui, 0.f, 0.f);
+    } else {
+        FRec f;
+        f.x = x[i]; f.y = y[i]; f.z = z[i]; f.h = hi;
+        f.vx = vx[i]; f.vy = vy[i]; f.vz = vz[i]; f.u = ui;
+        f.pre = pre; f.qf = qf; f.cs = cs; f.P = P;
+        f.rho = r; f.hinv = hinv; f.pad0 = 0.0; f.pad1 = 0.0;
+        rec[i] = f;
+    }
+}
+
+__device__ __forceinline__ void load_rec(const FRec *p, FRec &o) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 t;
+    t = __ldg(q + 0); o.x = t.x; o.y = t.y;
+    t = __ldg(q + 1); o.z = t.x; o.h = t.y;
+    t = __ldg(q + 2); o.vx = t.x; o.vy = t.y;
+    t = __ldg(q + 3); o.vz = t.x; o.u = t.y;
+    t = __ldg(q + 4); o.pre = t.x; o.qf = t.y;
+    t = __ldg(q + 5); o.cs = t.x; o.P = t.y;
+    t = __ldg(q + 6); o.rho = t.x; o.hinv = t.y;
+}
+
+struct ForceOut {
+    double *ax, *ay, *az, *du, *vsig;
+};
+
+// CFL candidate of one particle (App. G): min(C_cour h / v_sig, C_force sqrt(h/|a|)).
+__device__ __forceinline__ double dt_candidate(double h, double vs, double ax, double ay, double az,
+                                               const ForceParams &fp) {
+    const double t1 = fp.c_cour * h / vs;
+    const double am = sqrt(ax * ax + ay * ay + az * az);
+    const double t2 = am > 0.0 ? fp.c_force * sqrt(h / am) : INFINITY;
+    return fmin(t1, t2);
+}
+
+// Warp minimum of the CFL candidates and warp sum of the in-range pair counts (all 32 lanes
+// participate), then one atomic each per warp; positive doubles order like their bit patterns.
+__device__ __forceinline__ void dt_reduce(double t, unsigned long long npair, DevScalars *sc) {
+    for (int o = 16; o > 0; o >>= 1) {
+        t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
+        npair += __shfl_xor_sync(0xffffffffu, npair, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (t > 0.0 && t < INFINITY) atomicMin(&sc->dt_min_bits, dbits(t));
+        atomicAdd(&sc->inrange_pairs, npair);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__restrict__ rec,
+                                                     const uint32_t *__restrict__ nb_cnt,
+                                                     const int64_t *__restrict__ grp_off,
+                                                     const uint32_t *__restrict__ nb_ids, ForceParams fp, ForceOut out,
+                                                     DevScalars *sc) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double tdt = INFINITY;
+    unsigned long long npair = 0;
+    if (a < n) {
+    const int lane = (int)(a & 31);
+    const uint32_t cnt = nb_cnt[a];
+    const uint32_t *ids = nb_ids + grp_off[a >> 5] + lane;
+    FRec A;
+    load_rec(&rec[a], A);
+    const double m = fp.mass;
+    const PairGeo &geo = fp.geo;
+    double axs = 0.0, ays = 0.0, azs = 0.0, dus = 0.0;
+    double vs = fp.alpha_av * A.cs;
+    const double Fa_n = A.hinv * A.hinv * A.hinv * A.hinv * kInvPi;
+    for (uint32_t k = 0; k < cnt; k++) {
+        const uint32_t b = ids[(int64_t)k * 32];
+        FRec B;
+        load_rec(&rec[b], B);
+        const double dx = min_image(A.x - B.x, geo.L[0], geo.halfL[0], geo.periodic);
+        const double dy = min_image(A.y - B.y, geo.L[1], geo.halfL[1], geo.periodic);
+        const double dz = min_image(A.z - B.z, geo.L[2], geo.halfL[2], geo.periodic);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        const double hm = A.h > B.h ? A.h : B.h;
+        const double rad = __dmul_rn(2.0, hm);
+        if (!(r2 < __dmul_rn(rad, rad))) continue;
+        ++npair;
+        const double r = sqrt(r2);
+        const double rinv = 1.0 / r;
+        double f, dfa, dfb;
+        m4(r * A.hinv, f, dfa);
+        m4(r * B.hinv, f, dfb);
+        const double Fa = dfa * Fa_n;
+        const double Fb = dfb * (B.hinv * B.hinv * B.hinv * B.hinv * kInvPi);
+        const double vdotr = ((A.vx - B.vx) * dx + (A.vy - B.vy) * dy + (A.vz - B.vz) * dz) * rinv;
+        double Aa = A.pre, Ab = B.pre;
+        if (vdotr < 0.0) {
+            const double w = fp.beta_av * vdotr;   // = -beta |v.rhat|
+            Aa += -0.5 * (fp.alpha_av * A.cs - w) * vdotr * A.qf;
+            Ab += -0.5 * (fp.alpha_av * B.cs - w) * vdotr * B.qf;
+            vs = fmax(vs, fp.alpha_av * A.cs - w);
+        }
+        const double sc_ = m * (Aa * Fa + Ab * Fb) * rinv;
+        axs -= sc_ * dx;
+        ays -= sc_ * dy;
+        azs -= sc_ * dz;
+        dus += m * Aa * vdotr * Fa;
+        if (fp.alpha_u != 0.0) {
+            const double vsu = sqrt(fabs(A.P - B.P) / (0.5 * (A.rho + B.rho)));
+            dus += m * fp.alpha_u * vsu * (A.u - B.u) * 0.5 * (Fa * A.qf + Fb * B.qf);
+        }
+    }
+    out.ax[a] = axs;
+    out.ay[a] = ays;
+    out.az[a] = azs;
+    out.du[a] = dus;
+    out.vsig[a] = vs;
+    tdt = dt_candidate(A.h, vs, axs, ays, azs, fp);
+    }
+    dt_reduce(tdt, npair, sc);
+}
+
+__global__ void __launch_bounds__(128) k_forces_mixed(int64_t n, const float4 *__restrict__ rel,
+                                                      const float4 *__restrict__ m_v, const float4 *__restrict__ m_t,
+                                                      const float4 *__restrict__ m_r, const double *__restrict__ h,
+                                                      const uint32_t *__restrict__ nb_cnt,
+                                                      const int64_t *__restrict__ grp_off,
+                                                      const uint32_t *__restrict__ nb_ids, ForceParams fp,
+                                                      ForceOut out, DevScalars *sc) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double tdt = INFINITY;
+    unsigned long long npair = 0;
+    if (a < n) {
+    const int lane = (int)(a & 31);
+    const uint32_t cnt = nb_cnt[a];
+    const uint32_t *ids = nb_ids + grp_off[a >> 5] + lane;
+    const float4 PA = rel[a], VA = m_v[a], TA = m_t[a], RA = m_r[a];
+    const float mass = (float)fp.mass, alpha = (float)fp.alpha_av, beta = (float)fp.beta_av,
+                au = (float)fp.alpha_u;
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f, su = 0.f, cu = 0.f;
+    float vs = alpha * TA.z;
+    const float hia = VA.w;
+    const float Fa_n = hia * hia * hia * hia * kInvPiF;
+    for (uint32_t k = 0; k < cnt; k++) {
+        const uint32_t b = ids[(int64_t)k * 32];
+        const float4 PB = rel[b];
+        const float4 VB = m_v[b];
+        float dx, dy, dz;
+        rel_sep(PA, PB, fp.geo, dx, dy, dz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float him = fminf(hia, VB.w);
+        if (!(r2 * him * him < 4.f)) continue;
+        ++npair;
+        const float4 TB = m_t[b];
+        const float4 RB = m_r[b];
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        float f, dfa, dfb;
+        m4(r * hia, f, dfa);
+        m4(r * VB.w, f, dfb);
+        const float Fa = dfa * Fa_n;
+        const float hib = VB.w;
+        const float Fb = dfb * (hib * hib * hib * hib * kInvPiF);
+        const float vdotr = ((VA.x - VB.x) * dx + (VA.y - VB.y) * dy + (VA.z - VB.z) * dz) * rinv;
+        float Aa = TA.x, Ab = TB.x;
+        if (vdotr < 0.f) {
+            const float w = beta * vdotr;
+            Aa += -0.5f * (alpha * TA.z - w) * vdotr * TA.y;
+            Ab += -0.5f * (alpha * TB.z - w) * vdotr * TB.y;
+            vs = fmaxf(vs, alpha * TA.z - w);
+        }
+        const float sc_ = mass * (Aa * Fa + Ab * Fb) * rinv;
+        kahan_add(sx, cx, -sc_ * dx);
+        kahan_add(sy, cy, -sc_ * dy);
+        kahan_add(sz, cz, -sc_ * dz);
+        float dut = mass * Aa * vdotr * Fa;
+        if (au != 0.f) {
+            const float vsu = sqrtf(fabsf(TA.w - TB.w) / (0.5f * (RA.x + RB.x)));
+            dut += mass * au * vsu * (RA.y - RB.y) * 0.5f * (Fa * TA.y + Fb * TB.y);
+        }
+        kahan_add(su, cu, dut);
+    }
+    const double axs = kahan_value(sx, cx), ays = kahan_value(sy, cy), azs = kahan_value(sz, cz);
+    out.ax[a] = axs;
+    out.ay[a] = ays;
+    out.az[a] = azs;
+    out.du[a] = kahan_value(su, cu);
+    out.vsig[a] = (double)vs;
+    tdt = dt_candidate(h[a], (double)vs, axs, ays, azs, fp);
+    }
+    dt_reduce(tdt, npair, sc);
+}
+
+__global__ void k_reset_dt(DevScalars *sc) {
+    sc->dt_min_bits = 0x7ff0000000000000ULL;
+    sc->inrange_pairs = 0ULL;
+}
+
+int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, double *du) {
+    if (!c->cache_valid) return fail(c, SPH_ERR_ORDER, "forces before sph_find_neighbours");
+    const int64_t n = s->n;
+    ForceParams fp;
+    fp.mass = s->mass;
+    fp.gamma = c->p.gamma;
+    fp.alpha_av = c->p.alpha_av;
+    fp.beta_av = c->p.beta_av;
+    fp.alpha_u = c->p.alpha_u;
+    fp.c_cour = c->p.c_cour;
+    fp.c_force = c->p.c_force;
+    fp.geo = make_pair_geo(c->p);
+    const int mixed = c->p.precision == SPH_MIXED;
+    int r;
+    if ((r = stage_begin(c, kStForcePrep))) return r;
+    k_force_prep<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->h,
+                                                           s->rho, s->omega, fp, mixed, (FRec *)c->frec, c->m_v,
+                                                           c->m_t, c->m_r);
+    SPH_LAUNCH_CHECK(c, "k_force_prep");
+    k_reset_dt<<<1, 1, 0, c->stream>>>(c->dscal);
+    SPH_LAUNCH_CHECK(c, "k_reset_dt");
+    if ((r = stage_end(c, kStForcePrep)) || (r = stage_begin(c, kStForces))) return r;
+    ForceOut out{ax, ay, az, du, s->vsig};
+    if (mixed)
+        k_forces_mixed<<<grid_for(n, 128), 128, 0, c->stream>>>(n, c->rel, c->m_v, c->m_t, c->m_r, s->h,
+                                                                c->nb_cnt, c->grp_off, c->nb_ids, fp, out, c->dscal);
+    else
+        k_forces_fp64<<<grid_for(n, 128), 128, 0, c->stream>>>(n, (const FRec *)c->frec, c->nb_cnt, c->grp_off,
+                                                               c->nb_ids, fp, out, c->dscal);
+    SPH_LAUNCH_CHECK(c, "k_forces");
+    return stage_end(c, kStForces);
+}
+
+}  // namespace sph

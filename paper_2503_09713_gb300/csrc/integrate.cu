@@ -1,0 +1,132 @@
+// Kick-drift-kick leapfrog (App. G, "Leapfrog integration"):
+//   predictor:  v^{n+1/2} = v^n + dt/2 a^n;  r^{n+1} = r^n + dt v^{n+1/2} (wrapped);  v* = v^{n+1/2} + dt/2 a^n
+//               (u advanced the same way with du/dt)
+//   corrector:  v^{n+1} = v* + dt/2 (a^{n+1} - a^n), likewise u; the correction dv_i (Eq. deltavi) is
+//               reduced to max|dv_i| and sum |v_i|^2 for the check of Eq. cvleapfrog.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+struct IntParams {
+    double dt;
+    double lo[3], hi[3];
+    int periodic;
+};
+
+// x - L floor((x-lo)/L); a result equal to hi (rounding of a tiny negative offset) becomes lo.
+__device__ __forceinline__ double wrap(double x, double lo, double hi) {
+    const double L = hi - lo;
+    double w = x - L * floor((x - lo) / L);
+    if (w >= hi) w = lo;
+    if (w < lo) w = lo;
+    return w;
+}
+
+__global__ void k_predict(int64_t n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
+                          double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
+                          double *__restrict__ u, const double *__restrict__ ax, const double *__restrict__ ay,
+                          const double *__restrict__ az, const double *__restrict__ du, IntParams ip) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double hdt = 0.5 * ip.dt;
+    const double kx = hdt * ax[i], ky = hdt * ay[i], kz = hdt * az[i], ku = hdt * du[i];
+    const double hvx = vx[i] + kx, hvy = vy[i] + ky, hvz = vz[i] + kz;
+    double px = x[i] + ip.dt * hvx, py = y[i] + ip.dt * hvy, pz = z[i] + ip.dt * hvz;
+    if (ip.periodic) {
+        px = wrap(px, ip.lo[0], ip.hi[0]);
+        py = wrap(py, ip.lo[1], ip.hi[1]);
+        pz = wrap(pz, ip.lo[2], ip.hi[2]);
+    }
+    x[i] = px;
+    y[i] = py;
+    z[i] = pz;
+    vx[i] = hvx + kx;
+    vy[i] = hvy + ky;
+    vz[i] = hvz + kz;
+    u[i] = (u[i] + ku) + ku;
+}
+
+__global__ void k_correct(int64_t n, double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
+                          double *__restrict__ u, double *__restrict__ ax, double *__restrict__ ay,
+                          double *__restrict__ az, double *__restrict__ du, const double *__restrict__ anew,
+                          int64_t stride, double dt, DevScalars *sc, double *__restrict__ block_part) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double dv = 0.0, v2 = 0.0;
+    if (i < n) {
+        const double hdt = 0.5 * dt;
+        const double nax = anew[i], nay = anew[stride + i], naz = anew[2 * stride + i], ndu = anew[3 * stride + i];
+        const double dvx = hdt * (nax - ax[i]), dvy = hdt * (nay - ay[i]), dvz = hdt * (naz - az[i]);
+        const double wx = vx[i] + dvx, wy = vy[i] + dvy, wz = vz[i] + dvz;
+        vx[i] = wx;
+        vy[i] = wy;
+        vz[i] = wz;
+        u[i] = u[i] + hdt * (ndu - du[i]);
+        ax[i] = nax;
+        ay[i] = nay;
+        az[i] = naz;
+        du[i] = ndu;
+        dv = sqrt(dvx * dvx + dvy * dvy + dvz * dvz);
+        v2 = wx * wx + wy * wy + wz * wz;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dv = fmax(dv, __shfl_xor_sync(0xffffffffu, dv, o));
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+    }
+    __shared__ double part[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        part[warp] = v2;
+        if (dv > 0.0) atomicMax(&sc->dv_max_bits, dbits(dv));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += part[w];
+        block_part[blockIdx.x] = s;
+    }
+}
+
+// Deterministic sum of the per-block partials (one block).
+__global__ void k_sum_parts(const double *__restrict__ part, int64_t m, double *out) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s += part[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+__global__ void k_reset_dv(DevScalars *sc) { sc->dv_max_bits = 0ULL; }
+
+int integrate_predict(sph_ctx *c, sph_state *s, double dt) {
+    IntParams ip;
+    ip.dt = dt;
+    for (int k = 0; k < 3; k++) {
+        ip.lo[k] = c->p.box_lo[k];
+        ip.hi[k] = c->p.box_hi[k];
+    }
+    ip.periodic = c->p.periodic;
+    k_predict<<<grid_for(s->n, 256), 256, 0, c->stream>>>(s->n, s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->ax,
+                                                           s->ay, s->az, s->du, ip);
+    SPH_LAUNCH_CHECK(c, "k_predict");
+    return SPH_OK;
+}
+
+int integrate_correct(sph_ctx *c, sph_state *s, double dt) {
+    const int64_t n = s->n;
+    const unsigned blocks = grid_for(n, 256);
+    k_reset_dv<<<1, 1, 0, c->stream>>>(c->dscal);
+    SPH_LAUNCH_CHECK(c, "k_reset_dv");
+    k_correct<<<blocks, 256, 0, c->stream>>>(n, s->vx, s->vy, s->vz, s->u, s->ax, s->ay, s->az, s->du, c->a_new,
+                                             c->n_cap, dt, c->dscal, c->block_part);
+    SPH_LAUNCH_CHECK(c, "k_correct");
+    k_sum_parts<<<1, 256, 0, c->stream>>>(c->block_part, blocks, &c->dscal->v2_sum);
+    SPH_LAUNCH_CHECK(c, "k_sum_parts");
+    return SPH_OK;
+}
+
+}  // namespace sph

@@ -1,0 +1,228 @@
+// Internal declarations shared by the CUDA translation units of the SPH library.
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <cuda_runtime.h>
+
+#include "../../include/sph.h"
+
+namespace sph {
+
+constexpr int kMortonBits = 21;          // bits per axis; 63-bit codes (App. B)
+constexpr int kCodeBits = 3 * kMortonBits;
+constexpr int kGroup = 32;               // particles per neighbour-search group (one warp)
+constexpr int kCellBits = 10;            // cell grid of the FP32 relative coordinates: 2^10 per axis
+constexpr int kStackDepth = 66;          // tree-walk stack (tree depth <= 63 for distinct 63-bit codes)
+constexpr double kPi = 3.14159265358979323846;
+
+// Device error word bits (ctx->d_flags[0]).
+enum : uint32_t {
+    kErrTimeout = 1u << 0,      // a bounded spin ran out
+    kErrCandOverflow = 1u << 1, // stage-1 candidate list overflow (host grows and retries)
+    kErrStack = 1u << 2,        // walk stack overflow
+    kErrNonFinite = 1u << 3,    // NaN/Inf position or h
+    kErrNotConverged = 1u << 4, // Newton iteration hit h_max_iter
+    kErrStale = 1u << 5,        // an h was clamped at cache_tol * h^n
+};
+
+// One tree node: tight box and largest smoothing length; 64 bytes, two 32-byte sectors.
+struct __align__(16) Node {
+    double lo[3];
+    double hmax;
+    double hi[3];
+    double pad;
+};
+
+// Device scalars written by kernels and read back by the host in one copy.
+struct DevScalars {
+    unsigned long long dt_min_bits;   // CFL min over particles (positive double as bits)
+    unsigned long long dv_max_bits;   // max |dv| (positive double as bits)
+    int64_t n_leaves;
+    int64_t total_slots;              // neighbour-cache entries incl. padding
+    int64_t n_pairs;                  // real pairs
+    uint32_t max_iters;
+    uint32_t flags;
+    unsigned long long pair_evals;    // density: neighbour evaluations summed over Newton passes
+    unsigned long long dens_inrange;  // density: evaluations with q < 2
+    unsigned long long inrange_pairs; // forces: pairs inside 2 max(h_a, h_b)
+    double v2_sum;                    // sum |v|^2 after the corrector
+};
+
+struct Buffer {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive prefix and sets total
+// to the block sum (same value in every thread).
+template <int kThreads>
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t &total) {
+    __shared__ int64_t warp_off[kThreads / 32];
+    __shared__ int64_t s_total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_off[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = (lane < kThreads / 32) ? warp_off[lane] : 0;
+        int64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < kThreads / 32) warp_off[lane] = wi - w;
+        if (lane == kThreads / 32 - 1) s_total = wi;
+    }
+    __syncthreads();
+    const int64_t r = warp_off[warp] + incl - v;
+    total = s_total;
+    __syncthreads();
+    return r;
+}
+
+}  // namespace sph
+
+struct sph_ctx {
+    sph_params p;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    int64_t n_cap = 0;
+    int64_t n = 0;
+    std::string last_error;
+
+    // ---- tree ----
+    uint64_t *keys[2] = {nullptr, nullptr};
+    uint32_t *vals[2] = {nullptr, nullptr};
+    uint32_t *digit_hist = nullptr;    // [8][256] global digit counts
+    uint32_t *lookback = nullptr;      // [8][tiles][256] decoupled look-back words
+    uint32_t *tile_ctr = nullptr;      // [8]
+    int64_t sort_tiles = 0;
+    uint64_t *mu = nullptr;            // sorted codes (points into keys[x])
+    uint32_t *perm = nullptr;          // sort permutation (points into vals[x])
+    uint8_t *mask[2] = {nullptr, nullptr};
+    int64_t *scan_tmp = nullptr;       // block sums for scans
+    int64_t *leaf_first = nullptr;     // [n_cap + 1]
+    uint64_t *mu_leaf = nullptr;       // [n_cap]
+    int32_t *lchild = nullptr, *rchild = nullptr, *endrange = nullptr;  // [n_cap]
+    uint8_t *lflag = nullptr, *rflag = nullptr;
+    int32_t *child = nullptr;          // [2 n_cap] absolute node ids of both children
+    int32_t *node_parent = nullptr;    // [n_cap] parent of internal node (-1 root)
+    int32_t *leaf_parent = nullptr;    // [n_cap] parent of leaf
+    uint32_t *visit = nullptr;         // [n_cap]
+    sph::Node *nodes = nullptr;        // [2 n_cap]
+    int64_t n_leaves = 0;
+    bool tree_valid = false;
+
+    // ---- reorder scratch and per-particle derived arrays ----
+    double *gather_tmp = nullptr;      // [16][n_cap]
+    uint32_t *id_tmp = nullptr;
+    float4 *rel = nullptr;             // [n_cap] FP32 cell offsets + packed cell index
+    float *h32 = nullptr;              // [n_cap]
+    double *h_base = nullptr;          // [n_cap] h^n of the cache
+
+    // ---- neighbour cache ----
+    int64_t n_groups = 0;
+    sph::Node *gbox = nullptr;         // [groups] group boxes
+    uint32_t *cand = nullptr;          // [groups * cand_cap] candidate leaves
+    uint32_t *cand_cnt = nullptr;      // [groups]
+    int cand_cap = 0;
+    uint32_t *nb_cnt = nullptr;        // [n_cap] per-particle neighbour count
+    int64_t *grp_slots = nullptr;      // [groups + 1] -> exclusive scan = group offsets
+    int64_t *grp_off = nullptr;        // [groups + 1]
+    uint32_t *nb_ids = nullptr;        // cache entries, group-interleaved: off_g + k*32 + lane
+    int64_t nb_cap = 0;
+    int64_t n_pairs = 0, total_slots = 0;
+    bool cache_valid = false;
+
+    // ---- physics scratch ----
+    void *frec = nullptr;              // [n_cap] 128-byte FP64 records of the force loop
+    float4 *m_v = nullptr;             // [n_cap] mixed: vx, vy, vz, 1/h
+    float4 *m_t = nullptr;             // [n_cap] mixed: P/(rho^2 Omega), 1/(rho Omega), c_s, P
+    float4 *m_r = nullptr;             // [n_cap] mixed: rho, u
+    double *a_new = nullptr;           // [4][n_cap] ax, ay, az, du of the force pass inside sph_step
+    double *block_part = nullptr;      // per-block partial sums
+    bool density_valid = false;
+    bool forces_valid = false;
+
+    // ---- host-state staging for sph_step_host ----
+    double *hs_fields = nullptr;       // [16][n_cap]
+    uint32_t *hs_id = nullptr;
+
+    // ---- scalars / flags ----
+    sph::DevScalars *dscal = nullptr;
+    sph::DevScalars *hscal = nullptr;  // pinned host mirror
+    double dt_next = -1.0;
+    sph_stats stats{};
+    int64_t launches = 0;              // kernels launched by this context
+    bool timing = false;               // per-stage CUDA-event timing (sph_set_timing)
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace sph {
+
+// ---------------------------------------------------------------- launch helpers (host)
+int fail(sph_ctx *c, int code, const char *fmt, ...);
+int cuda_fail(sph_ctx *c, cudaError_t e, const char *where);
+inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+#define SPH_CUDA(ctx, call)                                        \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return sph::cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+#define SPH_LAUNCH_CHECK(ctx, name)                                \
+    do {                                                           \
+        ++(ctx)->launches;                                         \
+        cudaError_t e_ = cudaGetLastError();                       \
+        if (e_ != cudaSuccess) return sph::cuda_fail((ctx), e_, name); \
+    } while (0)
+
+// ---------------------------------------------------------------- stage entry points (host)
+int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs);
+int tree_boxes(sph_ctx *c, const sph_state *s);   // A6 again with the current h
+int neighbours_build(sph_ctx *c, const sph_state *s);
+int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale);
+int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, double *du);
+int integrate_predict(sph_ctx *c, sph_state *s, double dt);
+int integrate_correct(sph_ctx *c, sph_state *s, double dt);
+int read_scalars(sph_ctx *c);
+// Per-stage timing: stage_begin/stage_end bracket the launches of one stage on the context stream;
+// with timing on, stage_end waits for the stage and adds its duration to stats.stage_ms[k].
+enum Stage { kStPredict = 0, kStTree, kStNeigh, kStDensity, kStForcePrep, kStForces, kStCorrect, kStCount };
+int stage_begin(sph_ctx *c, int k);
+int stage_end(sph_ctx *c, int k);
+int exclusive_scan_i64(sph_ctx *c, const int64_t *in, int64_t *out, int64_t n);  // out[n] = total
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ double min_image(double d, double L, double halfL, int periodic) {
+    if (periodic) {
+        if (d > halfL) d -= L;
+        else if (d < -halfL) d += L;
+    }
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double v) {
+    return (unsigned long long)__double_as_longlong(v);
+}
+
+__device__ __forceinline__ double warp_min_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+}  // namespace sph

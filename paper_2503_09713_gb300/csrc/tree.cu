@@ -1,0 +1,571 @@
+// Tree build (App. B-C): Morton codes, stable radix sort by key (onesweep, decoupled look-back),
+// reorder of the particle arrays, duplicate mask + reduction passes (Alg. mortonmask), compaction
+// into leaves, Karras radix tree (Table arrays_fig_karras) and bottom-up tight boxes + h_max.
+#include <cuda/atomic>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// ====================================================================================== Morton
+// 21 bits per axis spread to every third bit (bit i -> bit 3i).
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {
+    v &= 0x1fffffULL;
+    v = (v | (v << 32)) & 0x1f00000000ffffULL;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+    v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+    v = (v | (v << 2)) & 0x1249249249249249ULL;
+    return v;
+}
+
+// App. B "Morton codes": remap to [0,1) by (x-lo)/(hi-lo), integer grid of 2^21 per axis,
+// interleave X0 Y0 Z0 X1 ... with x most significant.
+__device__ __forceinline__ uint64_t quantise(double x, double lo, double span) {
+    double s = (x - lo) / span;
+    double g = s * 2097152.0;  // 2^21, exact scale
+    const double top = 2097151.0;
+    if (!(g >= 0.0)) g = 0.0;
+    if (g > top) g = top;
+    return (uint64_t)floor(g);
+}
+
+struct Box3 {
+    double lo[3], span[3];
+};
+
+__global__ void k_morton(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                         const double *__restrict__ z, const double *__restrict__ h, Box3 b,
+                         uint64_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t *flags) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double px = x[i], py = y[i], pz = z[i], ph = h[i];
+    if (!isfinite(px) || !isfinite(py) || !isfinite(pz) || !isfinite(ph) || !(ph > 0.0))
+        atomicOr(flags, kErrNonFinite);
+    const uint64_t X = quantise(px, b.lo[0], b.span[0]);
+    const uint64_t Y = quantise(py, b.lo[1], b.span[1]);
+    const uint64_t Z = quantise(pz, b.lo[2], b.span[2]);
+    keys[i] = (spread3(X) << 2) | (spread3(Y) << 1) | spread3(Z);
+    vals[i] = (uint32_t)i;
+}
+
+// ====================================================================================== radix sort
+// LSD radix sort of (63-bit key, u32 value) pairs, 8 passes of 8-bit digits.  One kernel per pass
+// ranks a 4096-key tile in shared memory (warp multi-split with match.any, stable), obtains the
+// tile's global digit offsets by decoupled look-back over earlier tiles, and writes each digit run
+// contiguously.
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsItems = 16;
+constexpr int kRsTile = kRsThreads * kRsItems;
+constexpr int kRsWarpKeys = 32 * kRsItems;
+constexpr uint32_t kLbAgg = 1u << 30;
+constexpr uint32_t kLbInc = 2u << 30;
+constexpr uint32_t kLbMask = (1u << 30) - 1;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__global__ void __launch_bounds__(256) k_digit_hist(const uint64_t *__restrict__ keys, int64_t n,
+                                                     uint32_t *__restrict__ hist) {
+    __shared__ uint32_t sh[8 * 256];
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t k = keys[i];
+#pragma unroll
+        for (int p = 0; p < 8; p++) atomicAdd(&sh[p * 256 + ((k >> (8 * p)) & 255)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// In place: hist[p][d] -> exclusive prefix over d.  One block of 256 threads per pass.
+__global__ void k_digit_scan(uint32_t *hist) {
+    uint32_t *h = hist + blockIdx.x * 256;
+    int64_t tot;
+    const int64_t ex = block_exclusive_scan<256>((int64_t)h[threadIdx.x], tot);
+    h[threadIdx.x] = (uint32_t)ex;
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_onesweep(const uint64_t *__restrict__ kin,
+                                                         const uint32_t *__restrict__ vin,
+                                                         uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                         int64_t n, int shift, const uint32_t *__restrict__ digit_off,
+                                                         uint32_t *lookback, uint32_t *tile_ctr, uint32_t *flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);                 // [kRsTile]
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sk + kRsTile);             // [kRsTile]
+    uint32_t *whist = sv + kRsTile;                                        // [kRsWarps][256]
+    uint32_t *tstart = whist + kRsWarps * 256;                             // [256]
+    uint32_t *gbase = tstart + 256;                                        // [256]
+    uint32_t *stile = gbase + 256;                                         // [1]
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < kRsWarps * 256; i += kRsThreads) whist[i] = 0;
+    if (tid == 0) stile[0] = atomicAdd(tile_ctr, 1u);
+    __syncthreads();
+    const int64_t tile = stile[0];
+    const int64_t base = tile * kRsTile;
+    const int64_t wbase = base + (int64_t)warp * kRsWarpKeys;
+
+    uint64_t k[kRsItems];
+    uint32_t v[kRsItems];
+    uint32_t rank[kRsItems];
+#pragma unroll
+    for (int i = 0; i < kRsItems; i++) {
+        const int64_t idx = wbase + i * 32 + lane;
+        if (idx < n) {
+            k[i] = kin[idx];
+            v[i] = vin[idx];
+        } else {
+            k[i] = 0;
+            v[i] = 0;
+        }
+    }
+    uint32_t *mh = whist + warp * 256;
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int i = 0; i < kRsItems; i++) {
+        const bool valid = (wbase + i * 32 + lane) < n;
+        const uint32_t d = valid ? (uint32_t)((k[i] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = 31 - __clz((int)peers);
+        const uint32_t before = valid ? mh[d] : 0u;
+        __syncwarp();
+        if (valid && lane == leader) mh[d] = before + (uint32_t)__popc(peers);
+        __syncwarp();
+        rank[i] = before + (uint32_t)__popc(peers & lt);
+    }
+    __syncthreads();
+
+    // per digit (thread tid = digit): exclusive prefix over warps and tile total
+    const int d = tid;
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; w++) {
+        const uint32_t cnt = whist[w * 256 + d];
+        whist[w * 256 + d] = run;
+        run += cnt;
+    }
+    const uint32_t total = run;
+    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> mine(lookback[tile * 256 + d]);
+    mine.store((tile == 0 ? kLbInc : kLbAgg) | total, cuda::memory_order_relaxed);
+
+    int64_t tot_unused;
+    const uint32_t ts = (uint32_t)block_exclusive_scan<kRsThreads>((int64_t)total, tot_unused);
+    tstart[d] = ts;
+
+    uint32_t excl = 0;
+    if (tile > 0) {
+        int64_t j = tile - 1;
+        uint32_t spins = 0;
+        while (j >= 0) {
+            cuda::atomic_ref<uint32_t, cuda::thread_scope_device> other(lookback[j * 256 + d]);
+            const uint32_t w = other.load(cuda::memory_order_relaxed);
+            const uint32_t fl = w & ~kLbMask;
+            if (fl == 0u) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(flags, kErrTimeout);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            excl += w & kLbMask;
+            if (fl == kLbInc) break;
+            --j;
+        }
+        mine.store(kLbInc | (excl + total), cuda::memory_order_relaxed);
+    }
+    gbase[d] = digit_off[d] + excl;
+    __syncthreads();
+
+#pragma unroll
+    for (int i = 0; i < kRsItems; i++) {
+        if ((wbase + i * 32 + lane) < n) {
+            const uint32_t dd = (uint32_t)((k[i] >> shift) & 255u);
+            const uint32_t pos = tstart[dd] + mh[dd] + rank[i];
+            sk[pos] = k[i];
+            sv[pos] = v[i];
+        }
+    }
+    __syncthreads();
+    const int64_t rem = n - base;
+    const int tile_n = rem < kRsTile ? (int)rem : kRsTile;
+    for (int j = tid; j < tile_n; j += kRsThreads) {
+        const uint64_t key = sk[j];
+        const uint32_t dd = (uint32_t)((key >> shift) & 255u);
+        const uint32_t o = gbase[dd] + ((uint32_t)j - tstart[dd]);
+        if (o < (uint64_t)n) {   // always true unless a look-back wait ran out (flagged)
+            kout[o] = key;
+            vout[o] = sv[j];
+        }
+    }
+}
+
+static size_t onesweep_smem() {
+    return (size_t)kRsTile * 8 + (size_t)kRsTile * 4 + (size_t)kRsWarps * 256 * 4 + 256 * 4 * 2 + 16;
+}
+
+static int radix_sort(sph_ctx *c, int64_t n) {
+    // keys[0], vals[0] hold the input; after 8 passes the result is back in keys[0], vals[0]
+    const int64_t tiles = (n + kRsTile - 1) / kRsTile;
+    SPH_CUDA(c, cudaMemsetAsync(c->digit_hist, 0, 8 * 256 * sizeof(uint32_t), c->stream));
+    SPH_CUDA(c, cudaMemsetAsync(c->lookback, 0, (size_t)8 * tiles * 256 * sizeof(uint32_t), c->stream));
+    SPH_CUDA(c, cudaMemsetAsync(c->tile_ctr, 0, 8 * sizeof(uint32_t), c->stream));
+    unsigned hb = (unsigned)std::min<int64_t>(grid_for(n, 256), (int64_t)c->num_sms * 8);
+    if (hb == 0) hb = 1;
+    k_digit_hist<<<hb, 256, 0, c->stream>>>(c->keys[0], n, c->digit_hist);
+    SPH_LAUNCH_CHECK(c, "k_digit_hist");
+    k_digit_scan<<<8, 256, 0, c->stream>>>(c->digit_hist);
+    SPH_LAUNCH_CHECK(c, "k_digit_scan");
+    const size_t sm = onesweep_smem();
+    static bool attr_set = false;
+    if (!attr_set) {
+        SPH_CUDA(c, cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr_set = true;
+    }
+    for (int p = 0; p < 8; p++) {
+        const int src = p & 1, dst = src ^ 1;
+        k_onesweep<<<(unsigned)tiles, kRsThreads, sm, c->stream>>>(
+            c->keys[src], c->vals[src], c->keys[dst], c->vals[dst], n, 8 * p, c->digit_hist + 256 * p,
+            c->lookback + (size_t)p * tiles * 256, c->tile_ctr + p, &c->dscal->flags);
+        SPH_LAUNCH_CHECK(c, "k_onesweep");
+    }
+    return SPH_OK;
+}
+
+// ====================================================================================== reorder
+struct GatherArgs {
+    const double *src[16];
+    double *dst[16];
+    int nf;
+    const uint32_t *id_src;
+    uint32_t *id_dst;
+};
+
+__global__ void k_gather(int64_t n, const uint32_t *__restrict__ perm, GatherArgs g) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t p = perm[i];
+    if (p >= (uint64_t)n) p = 0;   // only after a flagged sort failure
+    for (int f = 0; f < g.nf; f++) g.dst[f][i] = g.src[f][p];
+    if (g.id_dst) g.id_dst[i] = g.id_src ? g.id_src[p] : p;
+}
+
+// FP32 cell-relative coordinates: cell index on a 2^10 grid per axis and the FP32 offset from the
+// cell corner; packed cell index in .w (x<<20 | y<<10 | z).
+__global__ void k_rel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                      const double *__restrict__ z, Box3 b, float4 *__restrict__ rel) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double p[3] = {x[i], y[i], z[i]};
+    uint32_t ci[3];
+    float off[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const double cell = b.span[k] * (1.0 / 1024.0);
+        double g = floor((p[k] - b.lo[k]) / cell);
+        if (!(g >= 0.0)) g = 0.0;
+        if (g > 1023.0) g = 1023.0;
+        ci[k] = (uint32_t)g;
+        off[k] = (float)(p[k] - (b.lo[k] + g * cell));
+    }
+    rel[i] = make_float4(off[0], off[1], off[2], __uint_as_float((ci[0] << 20) | (ci[1] << 10) | ci[2]));
+}
+
+// ====================================================================================== mask
+__global__ void k_mask_init(int64_t n, const uint64_t *__restrict__ mu, uint8_t *__restrict__ xi) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    xi[i] = (i == 0) ? 1 : (mu[i] != mu[i - 1]);
+}
+
+// One reduction pass of Alg. mortonmask: code i (kept) is removed when
+// delta(mu_{i-2}, mu_{i-1}) < delta(mu_{i-1}, mu_i) > delta(mu_i, mu_{i+1}) over kept codes; a
+// missing neighbour gives delta = -1.  Reads the previous mask, writes a new one.
+__device__ __forceinline__ int dlt(uint64_t a, uint64_t b) { return __clzll((long long)(a ^ b)); }
+
+__global__ void k_reduce_pass(int64_t n, const uint64_t *__restrict__ mu, const uint8_t *__restrict__ in,
+                              uint8_t *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (!in[i]) {
+        out[i] = 0;
+        return;
+    }
+    int64_t im1 = i - 1;
+    while (im1 >= 0 && !in[im1]) --im1;
+    int64_t im2 = im1 - 1;
+    while (im2 >= 0 && !in[im2]) --im2;
+    int64_t ip1 = i + 1;
+    while (ip1 < n && !in[ip1]) ++ip1;
+    const uint64_t mi = mu[i];
+    const int d0 = (ip1 < n) ? dlt(mi, mu[ip1]) : -1;
+    const int dm1 = (im1 >= 0) ? dlt(mu[im1], mi) : -1;
+    const int dm2 = (im2 >= 0) ? dlt(mu[im2], mu[im1]) : -1;
+    out[i] = !(d0 < dm1 && dm2 < dm1);
+}
+
+// ====================================================================================== compaction
+constexpr int kCpThreads = 256;
+constexpr int kCpItems = 8;
+constexpr int kCpChunk = kCpThreads * kCpItems;
+
+__global__ void k_flag_sums(int64_t n, const uint8_t *__restrict__ xi, int64_t *__restrict__ bsum) {
+    const int64_t base = (int64_t)blockIdx.x * kCpChunk + (int64_t)threadIdx.x * kCpItems;
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kCpItems; k++)
+        if (base + k < n) s += xi[base + k];
+    int64_t tot;
+    block_exclusive_scan<kCpThreads>(s, tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_compact(int64_t n, const uint8_t *__restrict__ xi, const uint64_t *__restrict__ mu,
+                          const int64_t *__restrict__ boff, int64_t *__restrict__ leaf_first,
+                          uint64_t *__restrict__ mu_leaf, DevScalars *sc) {
+    const int64_t base = (int64_t)blockIdx.x * kCpChunk + (int64_t)threadIdx.x * kCpItems;
+    uint8_t f[kCpItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kCpItems; k++) {
+        f[k] = (base + k < n) ? xi[base + k] : 0;
+        s += f[k];
+    }
+    int64_t tot;
+    const int64_t ex = block_exclusive_scan<kCpThreads>(s, tot);
+    int64_t pos = boff[blockIdx.x] + ex;
+#pragma unroll
+    for (int k = 0; k < kCpItems; k++) {
+        if (f[k]) {
+            leaf_first[pos] = base + k;
+            mu_leaf[pos] = mu[base + k];
+            ++pos;
+        }
+        if (base + k == n - 1) {
+            leaf_first[pos] = n;
+            sc->n_leaves = pos;
+        }
+    }
+}
+
+// ====================================================================================== Karras
+// Karras (2012) parallel construction over L sorted distinct codes: internal node i covers the
+// range between i and endrange[i]; children at the split gamma (App. B, "Karras algorithm").
+__device__ __forceinline__ int kdelta(const uint64_t *mu, int64_t L, int64_t i, int64_t j) {
+    if (j < 0 || j >= L) return -1;
+    return __clzll((long long)(mu[i] ^ mu[j]));
+}
+
+__global__ void k_karras(int64_t L, const uint64_t *__restrict__ mu, int32_t *__restrict__ lchild,
+                         int32_t *__restrict__ rchild, uint8_t *__restrict__ lflag, uint8_t *__restrict__ rflag,
+                         int32_t *__restrict__ endrange, int32_t *__restrict__ child,
+                         int32_t *__restrict__ node_parent, int32_t *__restrict__ leaf_parent) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L - 1) return;
+    const int dir = (kdelta(mu, L, i, i + 1) - kdelta(mu, L, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = kdelta(mu, L, i, i - dir);
+    int64_t lmax = 2;
+    while (kdelta(mu, L, i, i + lmax * dir) > dmin) lmax *= 2;
+    int64_t l = 0;
+    for (int64_t t = lmax / 2; t >= 1; t /= 2)
+        if (kdelta(mu, L, i, i + (l + t) * dir) > dmin) l += t;
+    const int64_t j = i + l * dir;
+    const int dnode = kdelta(mu, L, i, j);
+    int64_t s = 0;
+    int64_t t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (kdelta(mu, L, i, i + (s + t) * dir) > dnode) s += t;
+    } while (t > 1);
+    const int64_t gamma = i + s * dir + (dir < 0 ? -1 : 0);
+    const int64_t first = i < j ? i : j, last = i < j ? j : i;
+    const bool lf = (first == gamma), rf = (last == gamma + 1);
+    lchild[i] = (int32_t)gamma;
+    rchild[i] = (int32_t)(gamma + 1);
+    lflag[i] = lf;
+    rflag[i] = rf;
+    endrange[i] = (int32_t)j;
+    const int64_t nin = L - 1;
+    child[2 * i] = (int32_t)(lf ? nin + gamma : gamma);
+    child[2 * i + 1] = (int32_t)(rf ? nin + gamma + 1 : gamma + 1);
+    if (lf) leaf_parent[gamma] = (int32_t)i;
+    else node_parent[gamma] = (int32_t)i;
+    if (rf) leaf_parent[gamma + 1] = (int32_t)i;
+    else node_parent[gamma + 1] = (int32_t)i;
+    if (i == 0) node_parent[0] = -1;
+}
+
+// ====================================================================================== boxes
+// Leaf boxes from their particles, then a climb: the second child to arrive at a node merges both
+// children (min/max are exact, so the result does not depend on the arrival order).
+__device__ __forceinline__ void load_node(const Node *nd, Node &o) {
+    const double2 *p = reinterpret_cast<const double2 *>(nd);
+    double2 a = __ldcg(p), b = __ldcg(p + 1), cc = __ldcg(p + 2), dd = __ldcg(p + 3);
+    o.lo[0] = a.x; o.lo[1] = a.y; o.lo[2] = b.x; o.hmax = b.y;
+    o.hi[0] = cc.x; o.hi[1] = cc.y; o.hi[2] = dd.x; o.pad = dd.y;
+}
+
+__global__ void k_boxes(int64_t L, const int64_t *__restrict__ leaf_first, const double *__restrict__ x,
+                        const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h,
+                        const int32_t *__restrict__ child, const int32_t *__restrict__ node_parent,
+                        const int32_t *__restrict__ leaf_parent, uint32_t *visit, Node *nodes) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= L) return;
+    Node b;
+    for (int k = 0; k < 3; k++) { b.lo[k] = INFINITY; b.hi[k] = -INFINITY; }
+    b.hmax = 0.0;
+    b.pad = 0.0;
+    for (int64_t p = leaf_first[j]; p < leaf_first[j + 1]; p++) {
+        const double r[3] = {x[p], y[p], z[p]};
+        for (int k = 0; k < 3; k++) {
+            b.lo[k] = fmin(b.lo[k], r[k]);
+            b.hi[k] = fmax(b.hi[k], r[k]);
+        }
+        b.hmax = fmax(b.hmax, h[p]);
+    }
+    const int64_t nin = L - 1;
+    nodes[nin + j] = b;
+    if (L == 1) return;
+    int64_t node = leaf_parent[j];
+    while (node >= 0) {
+        __threadfence();
+        const uint32_t old = atomicAdd(&visit[node], 1u);
+        if (old == 0) return;
+        __threadfence();
+        Node l, r;
+        load_node(&nodes[child[2 * node]], l);
+        load_node(&nodes[child[2 * node + 1]], r);
+        Node m;
+        for (int k = 0; k < 3; k++) {
+            m.lo[k] = fmin(l.lo[k], r.lo[k]);
+            m.hi[k] = fmax(l.hi[k], r.hi[k]);
+        }
+        m.hmax = fmax(l.hmax, r.hmax);
+        m.pad = 0.0;
+        nodes[node] = m;
+        node = node_parent[node];
+    }
+}
+
+static Box3 make_box(const sph_params &p) {
+    Box3 b;
+    for (int k = 0; k < 3; k++) {
+        b.lo[k] = p.box_lo[k];
+        b.span[k] = p.box_hi[k] - p.box_lo[k];
+    }
+    return b;
+}
+
+static int boxes(sph_ctx *c, const sph_state *s) {
+    const int64_t L = c->n_leaves;
+    if (L > 1) SPH_CUDA(c, cudaMemsetAsync(c->visit, 0, (size_t)(L - 1) * sizeof(uint32_t), c->stream));
+    k_boxes<<<grid_for(L, 128), 128, 0, c->stream>>>(L, c->leaf_first, s->x, s->y, s->z, s->h, c->child,
+                                                     c->node_parent, c->leaf_parent, c->visit, c->nodes);
+    SPH_LAUNCH_CHECK(c, "k_boxes");
+    return SPH_OK;
+}
+
+int tree_boxes(sph_ctx *c, const sph_state *s) { return boxes(c, s); }
+
+int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
+    const int64_t n = s->n;
+    const Box3 bx = make_box(c->p);
+    c->tree_valid = false;
+    c->cache_valid = false;
+    SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
+
+    // A1 Morton codes
+    k_morton<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, s->h, bx, c->keys[0], c->vals[0],
+                                                      &c->dscal->flags);
+    SPH_LAUNCH_CHECK(c, "k_morton");
+    // A2 sort
+    int r = radix_sort(c, n);
+    if (r) return r;
+    c->mu = c->keys[0];
+    c->perm = c->vals[0];
+
+    // reorder the particle arrays
+    GatherArgs g{};
+    double *fields[15] = {s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->h, s->ax, s->ay, s->az, s->du,
+                          s->rho, s->omega, s->vsig};
+    const int nf_all = gather_outputs ? 15 : 12;
+    int nf = 0;
+    for (int f = 0; f < nf_all; f++) {
+        if (!fields[f]) continue;
+        g.src[nf] = fields[f];
+        g.dst[nf] = c->gather_tmp + (size_t)nf * c->n_cap;
+        nf++;
+    }
+    g.nf = nf;
+    g.id_src = s->id;
+    g.id_dst = s->id ? c->id_tmp : nullptr;
+    k_gather<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->perm, g);
+    SPH_LAUNCH_CHECK(c, "k_gather");
+    for (int f = 0; f < nf; f++)
+        SPH_CUDA(c, cudaMemcpyAsync(const_cast<double *>(g.src[f]), g.dst[f], (size_t)n * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    if (s->id)
+        SPH_CUDA(c, cudaMemcpyAsync(s->id, c->id_tmp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                                    c->stream));
+    k_rel<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, bx, c->rel);
+    SPH_LAUNCH_CHECK(c, "k_rel");
+
+    // A3 mask + reduction
+    k_mask_init<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->mu, c->mask[0]);
+    SPH_LAUNCH_CHECK(c, "k_mask_init");
+    int cur = 0;
+    for (int pass = 0; pass < c->p.reduction_level; pass++) {
+        k_reduce_pass<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->mu, c->mask[cur], c->mask[cur ^ 1]);
+        SPH_LAUNCH_CHECK(c, "k_reduce_pass");
+        cur ^= 1;
+    }
+    // A4 scan + compaction
+    const int64_t nb = (n + kCpChunk - 1) / kCpChunk;
+    int64_t *bsum = c->scan_tmp;                       // [nb]
+    int64_t *boff = c->scan_tmp + nb + 1;              // [nb + 1]
+    int64_t *rest = c->scan_tmp + 2 * (nb + 1);
+    k_flag_sums<<<(unsigned)nb, kCpThreads, 0, c->stream>>>(n, c->mask[cur], bsum);
+    SPH_LAUNCH_CHECK(c, "k_flag_sums");
+    {
+        int64_t *save = c->scan_tmp;
+        c->scan_tmp = rest;
+        r = exclusive_scan_i64(c, bsum, boff, nb);
+        c->scan_tmp = save;
+        if (r) return r;
+    }
+    k_compact<<<(unsigned)nb, kCpThreads, 0, c->stream>>>(n, c->mask[cur], c->mu, boff, c->leaf_first, c->mu_leaf,
+                                                         c->dscal);
+    SPH_LAUNCH_CHECK(c, "k_compact");
+    SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->n_leaves, &c->dscal->n_leaves, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                c->stream));
+    SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->flags, &c->dscal->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                c->stream));
+    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->hscal->flags & kErrNonFinite) return fail(c, SPH_ERR_NONFINITE, "non-finite position or h <= 0");
+    if (c->hscal->flags & kErrTimeout) return fail(c, SPH_ERR_TIMEOUT, "radix sort look-back wait ran out");
+    const int64_t L = c->hscal->n_leaves;
+    if (L < 1 || L > n) return fail(c, SPH_ERR_CUDA, "bad leaf count %lld", (long long)L);
+    c->n_leaves = L;
+
+    // A5 Karras
+    if (L > 1) {
+        k_karras<<<grid_for(L - 1, 256), 256, 0, c->stream>>>(L, c->mu_leaf, c->lchild, c->rchild, c->lflag,
+                                                               c->rflag, c->endrange, c->child, c->node_parent,
+                                                               c->leaf_parent);
+        SPH_LAUNCH_CHECK(c, "k_karras");
+    }
+    // A6 boxes + h_max
+    r = boxes(c, s);
+    if (r) return r;
+    c->tree_valid = true;
+    c->stats.n = n;
+    c->stats.n_leaves = L;
+    c->stats.n_red = c->p.reduction_level;
+    return SPH_OK;
+}
+
+}  // namespace sph

@@ -1,0 +1,327 @@
+"""Python binding of the C ABI in ``include/sph.h`` (ctypes; argument marshalling only).
+
+Every computation runs in ``libsph_gb300.so``.  The module refuses to work without it: there is no
+CPU fallback.  Device memory comes from PyTorch tensors (``DeviceState``); the library receives their
+raw pointers and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsph_gb300.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "sph.h")
+
+SPH_OK = 0
+SPH_ERR_INVALID_ARG = -1
+SPH_ERR_OOM = -2
+SPH_ERR_CAPACITY = -3
+SPH_ERR_CACHE_STALE = -4
+SPH_ERR_H_NOT_CONVERGED = -5
+SPH_ERR_TIMEOUT = -6
+SPH_ERR_CUDA = -7
+SPH_ERR_ORDER = -8
+SPH_ERR_NONFINITE = -9
+SPH_KERNEL_M4 = 0
+SPH_FP64 = 0
+SPH_MIXED = 1
+
+FIELDS = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du", "rho", "omega", "vsig")
+
+_d = ctypes.c_double
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_p = ctypes.c_void_p
+
+
+class sph_params(ctypes.Structure):
+    _fields_ = [("kernel", _i), ("precision", _i), ("hfact", _d), ("gamma", _d), ("alpha_av", _d),
+                ("beta_av", _d), ("alpha_u", _d), ("c_cour", _d), ("c_force", _d), ("h_tol", _d),
+                ("h_clamp", _d), ("cache_tol", _d), ("h_max_iter", _i), ("reduction_level", _i),
+                ("periodic", _i), ("max_outer", _i), ("box_lo", _d * 3), ("box_hi", _d * 3)]
+
+
+class sph_state(ctypes.Structure):
+    _fields_ = [("n", _i64), ("mass", _d)] + [(f, _p) for f in FIELDS] + [("id", _p)]
+
+
+class sph_tree_view(ctypes.Structure):
+    _fields_ = [(f, _p) for f in ("mu", "perm", "leaf_first", "mu_leaf", "lchild", "rchild", "lflag", "rflag",
+                                  "endrange", "bmin", "bmax", "hmax")]
+
+
+class sph_stats(ctypes.Structure):
+    _fields_ = [("n", _i64), ("n_leaves", _i64), ("n_groups", _i64), ("n_pairs", _i64), ("cache_slots", _i64),
+                ("density_iters_max", _i), ("outer_passes", _i), ("n_red", _i), ("dt_next", _d), ("dv_ratio", _d),
+                ("kernel_launches", _i64), ("density_pair_evals", _i64), ("density_inrange", _i64), ("force_pairs", _i64), ("stage_ms", _d * 8)]
+
+STAGES = ("predict", "tree", "neighbours", "density", "force_prep", "forces", "correct")
+
+
+class SPHError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load the CUDA library (built by ``__graft_entry__.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(the SPH path has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "sph_default_params": (None, [P(sph_params)]),
+        "sph_create": (_i, [P(sph_params), _i64, _i64, _p, P(_p)]),
+        "sph_destroy": (_i, [_p]),
+        "sph_set_params": (_i, [_p, P(sph_params)]),
+        "sph_build_tree": (_i, [_p, P(sph_state)]),
+        "sph_find_neighbours": (_i, [_p, P(sph_state), P(_i64)]),
+        "sph_compute_density_h": (_i, [_p, P(sph_state), P(_i)]),
+        "sph_compute_forces": (_i, [_p, P(sph_state)]),
+        "sph_step": (_i, [_p, P(sph_state), _d, P(_d), P(_d)]),
+        "sph_step_host": (_i, [_p, P(sph_state), _d, P(_d), P(_d)]),
+        "sph_tree_sizes": (_i, [_p, P(_i64), P(_i64)]),
+        "sph_export_tree": (_i, [_p, P(sph_tree_view)]),
+        "sph_export_neighbours": (_i, [_p, _p, _p]),
+        "sph_get_stats": (_i, [_p, P(sph_stats)]),
+        "sph_set_timing": (_i, [_p, _i]),
+        "sph_reset_timing": (_i, [_p]),
+        "sph_last_error": (ctypes.c_char_p, [_p]),
+        "sph_error_string": (ctypes.c_char_p, [_i]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions() -> list:
+    """Names of the functions declared in include/sph.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(sph_\w+)\s*\(", txt, flags=re.M)))
+
+
+def default_params(**kw) -> sph_params:
+    p = sph_params()
+    load().sph_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k in ("box_lo", "box_hi"):
+            setattr(p, k, (_d * 3)(*v))
+        else:
+            setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------- thin wrappers with the ABI names
+def _check(ctx, code):
+    if code != SPH_OK:
+        lib = load()
+        msg = lib.sph_last_error(ctx).decode() if ctx else ""
+        raise SPHError(code, f"{lib.sph_error_string(code).decode()}: {msg}")
+
+
+def sph_create(params: sph_params, n_cap: int, neigh_cap: int = 0, stream: int | None = None):
+    ctx = _p()
+    code = load().sph_create(ctypes.byref(params), int(n_cap), int(neigh_cap), _p(stream or 0), ctypes.byref(ctx))
+    _check(None, code)
+    return ctx
+
+
+def sph_destroy(ctx):
+    load().sph_destroy(ctx)
+
+
+def sph_build_tree(ctx, st: sph_state):
+    _check(ctx, load().sph_build_tree(ctx, ctypes.byref(st)))
+
+
+def sph_find_neighbours(ctx, st: sph_state) -> int:
+    n = _i64()
+    _check(ctx, load().sph_find_neighbours(ctx, ctypes.byref(st), ctypes.byref(n)))
+    return n.value
+
+
+def sph_compute_density_h(ctx, st: sph_state) -> int:
+    it = _i()
+    _check(ctx, load().sph_compute_density_h(ctx, ctypes.byref(st), ctypes.byref(it)))
+    return it.value
+
+
+def sph_compute_forces(ctx, st: sph_state):
+    _check(ctx, load().sph_compute_forces(ctx, ctypes.byref(st)))
+
+
+def sph_step(ctx, st: sph_state, dt: float = 0.0):
+    used, nxt = _d(), _d()
+    _check(ctx, load().sph_step(ctx, ctypes.byref(st), float(dt), ctypes.byref(used), ctypes.byref(nxt)))
+    return used.value, nxt.value
+
+
+def sph_step_host(ctx, st: sph_state, dt: float = 0.0):
+    used, nxt = _d(), _d()
+    _check(ctx, load().sph_step_host(ctx, ctypes.byref(st), float(dt), ctypes.byref(used), ctypes.byref(nxt)))
+    return used.value, nxt.value
+
+
+def sph_get_stats(ctx) -> dict:
+    s = sph_stats()
+    _check(ctx, load().sph_get_stats(ctx, ctypes.byref(s)))
+    out = {f: getattr(s, f) for f, _ in sph_stats._fields_}
+    out["stage_ms"] = {k: s.stage_ms[i] for i, k in enumerate(STAGES)}
+    return out
+
+
+def sph_set_timing(ctx, on: bool):
+    _check(ctx, load().sph_set_timing(ctx, 1 if on else 0))
+
+
+def sph_reset_timing(ctx):
+    _check(ctx, load().sph_reset_timing(ctx))
+
+
+def sph_export_tree(ctx) -> dict:
+    lib = load()
+    n, L = _i64(), _i64()
+    _check(ctx, lib.sph_tree_sizes(ctx, ctypes.byref(n), ctypes.byref(L)))
+    n, L = n.value, L.value
+    nin, nodes = max(L - 1, 0), 2 * L - 1
+    out = {"mu": np.zeros(n, np.uint64), "perm": np.zeros(n, np.uint32), "leaf_first": np.zeros(L + 1, np.int64),
+           "mu_leaf": np.zeros(L, np.uint64), "lchild": np.zeros(nin, np.int32), "rchild": np.zeros(nin, np.int32),
+           "lflag": np.zeros(nin, np.uint8), "rflag": np.zeros(nin, np.uint8), "endrange": np.zeros(nin, np.int32),
+           "bmin": np.zeros((nodes, 3)), "bmax": np.zeros((nodes, 3)), "hmax": np.zeros(nodes)}
+    v = sph_tree_view(**{k: (a.ctypes.data if a.size else None) for k, a in out.items()})
+    _check(ctx, lib.sph_export_tree(ctx, ctypes.byref(v)))
+    return out
+
+
+def sph_export_neighbours(ctx, n: int, n_pairs: int):
+    off = np.zeros(n + 1, np.int64)
+    ids = np.zeros(max(n_pairs, 1), np.uint32)
+    _check(ctx, load().sph_export_neighbours(ctx, off.ctypes.data, ids.ctypes.data))
+    return off, ids[:off[-1]].copy()
+
+
+# ---------------------------------------------------------------- device state (PyTorch memory)
+class DeviceState:
+    """Particle arrays as float64 CUDA tensors (id: int32 holding the uint32 original index)."""
+
+    def __init__(self, n: int, mass: float, device: str = "cuda"):
+        import torch
+        self.n = int(n)
+        self.mass = float(mass)
+        self.t = {f: torch.zeros(self.n, dtype=torch.float64, device=device) for f in FIELDS}
+        self.t["id"] = torch.arange(self.n, dtype=torch.int32, device=device)
+
+    @classmethod
+    def from_numpy(cls, d: dict, device: str = "cuda"):
+        import torch
+        s = cls(len(d["x"]), d["mass"], device)
+        for f in FIELDS:
+            if f in d:
+                s.t[f].copy_(torch.from_numpy(np.ascontiguousarray(d[f], dtype=np.float64)))
+        return s
+
+    def to_numpy(self) -> dict:
+        out = {f: self.t[f].cpu().numpy() for f in FIELDS}
+        out["id"] = self.t["id"].cpu().numpy().view(np.uint32)
+        out["mass"] = self.mass
+        return out
+
+    def c(self) -> sph_state:
+        return sph_state(self.n, self.mass, *[self.t[f].data_ptr() for f in FIELDS], self.t["id"].data_ptr())
+
+
+def host_state(d: dict) -> tuple:
+    """sph_state over host numpy arrays (kept alive by the returned dict) for sph_step_host."""
+    arrs = {f: np.ascontiguousarray(d[f], dtype=np.float64) for f in FIELDS}
+    arrs["id"] = np.ascontiguousarray(d.get("id", np.arange(len(arrs["x"]))), dtype=np.uint32)
+    st = sph_state(len(arrs["x"]), float(d["mass"]), *[arrs[f].ctypes.data for f in FIELDS], arrs["id"].ctypes.data)
+    return st, arrs
+
+
+class Solver:
+    """Owns one context; methods mirror the ABI on a DeviceState."""
+
+    def __init__(self, params: sph_params, n_cap: int, neigh_cap: int = 0, stream: int | None = None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.ctx = sph_create(params, n_cap, neigh_cap, stream)
+
+    def close(self):
+        if self.ctx:
+            sph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_tree(self, s: DeviceState):
+        st = s.c()
+        sph_build_tree(self.ctx, st)
+
+    def find_neighbours(self, s: DeviceState) -> int:
+        return sph_find_neighbours(self.ctx, s.c())
+
+    def compute_density_h(self, s: DeviceState) -> int:
+        return sph_compute_density_h(self.ctx, s.c())
+
+    def compute_forces(self, s: DeviceState):
+        sph_compute_forces(self.ctx, s.c())
+
+    def step(self, s: DeviceState, dt: float = 0.0):
+        return sph_step(self.ctx, s.c(), dt)
+
+    def converge(self, s: DeviceState, max_outer: int = 16) -> int:
+        """Initial ("white") step: tree, cache and density until h stays inside the cache tolerance,
+        then forces (sets a, du and the first CFL step)."""
+        self.build_tree(s)
+        total = 0
+        for _ in range(max_outer):
+            self.find_neighbours(s)
+            try:
+                total += self.compute_density_h(s)
+                break
+            except SPHError as e:
+                if e.code != SPH_ERR_CACHE_STALE:
+                    raise
+        else:
+            raise SPHError(SPH_ERR_CACHE_STALE, "initial h did not settle")
+        self.compute_forces(s)
+        return total
+
+    def stats(self) -> dict:
+        return sph_get_stats(self.ctx)
+
+    def set_timing(self, on: bool):
+        sph_set_timing(self.ctx, on)
+
+    def reset_timing(self):
+        sph_reset_timing(self.ctx)
+
+    def step_host(self, host_st, dt: float = 0.0):
+        return sph_step_host(self.ctx, host_st, dt)
+
+    def export_tree(self) -> dict:
+        return sph_export_tree(self.ctx)
+
+    def export_neighbours(self, n: int) -> tuple:
+        st = self.stats()
+        return sph_export_neighbours(self.ctx, n, st["n_pairs"])

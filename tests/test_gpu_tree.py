@@ -1,0 +1,106 @@
+"""GPU tree build (App. B-C) against the oracle: bit-exact Morton codes, sort permutation, leaves,
+Karras tables, tight boxes and h_max; the paper's worked examples through the GPU path."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import random_positions, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _build(x, y, z, h, n_red):
+    require_gpu()
+    from paper_2503_09713_gb300 import sph
+    n = len(x)
+    d = {"x": x, "y": y, "z": z, "h": h, "mass": 1.0 / n}
+    s = sph.DeviceState.from_numpy(d)
+    solver = sph.Solver(sph.default_params(reduction_level=n_red), n)
+    solver.build_tree(s)
+    t = solver.export_tree()
+    out = s.to_numpy()
+    solver.close()
+    return t, out
+
+
+def _check_against_oracle(x, y, z, h, n_red):
+    t, out = _build(x, y, z, h, n_red)
+    m = O.morton(x, y, z)
+    mu, perm = O.sort_by_key(m)
+    assert np.array_equal(t["mu"], mu)
+    assert np.array_equal(t["perm"], perm)
+    assert np.array_equal(out["id"], perm)
+    xs, ys, zs, hs = x[perm], y[perm], z[perm], h[perm]
+    assert np.array_equal(out["x"], xs) and np.array_equal(out["h"], hs)
+    xi = O.keep_mask(mu, 63, n_red)
+    idv, ml = O.compact(mu, xi)
+    assert np.array_equal(t["leaf_first"], idv)
+    assert np.array_equal(t["mu_leaf"], ml)
+    tr = O.radix_tree(ml, 63)
+    for k in ("lchild", "rchild", "lflag", "rflag", "endrange"):
+        assert np.array_equal(t[k], getattr(tr, k)), k
+    bmin, bmax, hmax = O.cell_boxes(idv, tr.endrange, xs, ys, zs, hs)
+    assert np.array_equal(t["bmin"], bmin) and np.array_equal(t["bmax"], bmax) and np.array_equal(t["hmax"], hmax)
+    return len(ml)
+
+
+@pytest.mark.parametrize("kind,n,n_red", [("uniform", 5000, 0), ("uniform", 5000, 3), ("cluster", 9001, 4),
+                                          ("dups", 4099, 2), ("uniform", 70001, 3)])
+def test_tree_bit_exact(kind, n, n_red):
+    x, y, z = random_positions(n, 11 + n_red, kind)
+    h = np.random.default_rng(5).uniform(0.01, 0.02, size=n)
+    L = _check_against_oracle(x, y, z, h, n_red)
+    assert 1 <= L <= n
+
+
+def test_tree_lattice_reduction_levels():
+    from paper_2503_09713_gb300 import workloads
+    w = workloads.lattice(24, sigma_v=0.0, seed=99)
+    counts = [_check_against_oracle(w["x"], w["y"], w["z"], w["h"], lv) for lv in range(0, 6)]
+    assert counts[0] == 24 ** 3 and all(a > b for a, b in zip(counts, counts[1:]))
+
+
+def test_tree_edge_sizes():
+    for n in (1, 2, 3, 33):
+        x, y, z = random_positions(n, n, "uniform")
+        _check_against_oracle(x, y, z, np.full(n, 0.05), 3)
+    # all particles on one point: a single leaf
+    n = 100
+    x = np.full(n, 0.3); y = np.full(n, 0.6); z = np.full(n, 0.9)
+    t, _ = _build(x, y, z, np.full(n, 0.05), 2)
+    assert list(t["leaf_first"]) == [0, n]
+
+
+def test_karras_table_through_gpu(golden):
+    """Positions whose 63-bit codes start with the 6-bit codes of the Karras table example."""
+    g = golden("karras_table.json")
+    X, Y, Z = [], [], []
+    for c in g["codes_6bit"]:
+        v = int(c, 2)
+        X.append(((v >> 5) & 1) * 2 + ((v >> 2) & 1))
+        Y.append(((v >> 4) & 1) * 2 + ((v >> 1) & 1))
+        Z.append(((v >> 3) & 1) * 2 + (v & 1))
+    x = np.array(X) / 4 + 1 / 8
+    y = np.array(Y) / 4 + 1 / 8
+    z = np.array(Z) / 4 + 1 / 8
+    t, _ = _build(x, y, z, np.full(12, 0.01), 0)
+    assert [int(m >> np.uint64(57)) for m in t["mu_leaf"]] == [int(c, 2) for c in g["codes_6bit"]]
+    assert list(t["lchild"]) == g["left_child_id"]
+    assert list(t["rchild"]) == g["right_child_id"]
+    assert list(t["lflag"]) == g["left_child_flag"]
+    assert list(t["rflag"]) == g["right_child_flag"]
+    assert list(t["endrange"]) == g["endrange"]
+
+
+def test_mortonlistbuild_through_gpu(golden):
+    g = golden("mortonlistbuild.json")
+    codes = [int(c, 2) for c in g["m"]]
+    x = np.array([(c >> 2) & 1 for c in codes]) * 0.5
+    y = np.array([(c >> 1) & 1 for c in codes]) * 0.5
+    z = np.array([c & 1 for c in codes]) * 0.5
+    t, out = _build(x, y, z, np.full(7, 0.01), 0)
+    assert [int(m >> np.uint64(60)) for m in t["mu"]] == [int(c, 2) for c in g["mu"]]
+    assert list(t["leaf_first"]) == g["id"]
+    assert [int(m >> np.uint64(60)) for m in t["mu_leaf"]] == [int(c, 2) for c in g["mu_leaf"]]
+    m = np.array(codes)
+    assert np.array_equal(m[t["perm"]], np.array([int(c, 2) for c in g["mu"]]))
