@@ -155,8 +155,9 @@ def test_step_vs_oracle(precision):
     ax, ay, az, du, vs = O.forces(w["x"], w["y"], w["z"], w["vx"], w["vy"], w["vz"], w["u"], h, om, w["mass"], P)
     dt = O.cfl(h, vs, ax, ay, az, P)
     ref = {k: w[k].copy() for k in ("x", "y", "z", "vx", "vy", "vz", "u")}
-    ref.update(h=h.copy(), ax=ax, ay=ay, az=az, du=du, rho=rho, omega=om, vsig=vs)
-    dtn_ref, it, dvr = O.step(ref, w["mass"], P, dt)
+    ref.update({k: v.copy() for k, v in (("h", h), ("ax", ax), ("ay", ay), ("az", az), ("du", du), ("rho", rho),
+                                          ("omega", om), ("vsig", vs))})
+    dtn_ref, it, dvr = O.step(ref, w["mass"], P, dt)     # in place on ref; h, a, ... keep the step-n values
 
     d = dict(w)
     d.update(h=h, rho=rho, omega=om, ax=ax, ay=ay, az=az, du=du, vsig=vs)
