@@ -197,6 +197,28 @@ int sph_set_timing(sph_ctx *ctx, int enable);
 /* Zero the accumulated stage times. */
 int sph_reset_timing(sph_ctx *ctx);
 
+/* Morton codes and stable sort without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc/cudaFree -- an application whose device
+ * memory is owned by another allocator (a framework's caching allocator or a fixed arena already
+ * holding the free memory, where a fresh cudaMalloc fails or fragments it), or a latency-bound caller
+ * that cannot accept the device synchronisation cudaFree implies.
+ * Computes the same codes and permutation as sph_build_tree (A1-A2): codes_out[i] = i-th smallest
+ * 63-bit Morton code of the positions in [box_lo, box_hi), perm_out[i] = its original index, ties in
+ * original order.  x, y, z: DEVICE float64[n]; box_lo, box_hi: HOST double[3]; codes_out (uint64[n])
+ * and perm_out (uint32[n]): DEVICE, caller-owned, must not alias the inputs.  Work is issued on
+ * `stream` (a cudaStream_t, NULL = legacy default) and the call returns after it has finished.
+ * Limit: n <= 262144 (SPH_ERR_CAPACITY beyond; SPH_ERR_INVALID_ARG for NULL pointers or an empty
+ * box).  Scratch: a fixed 3.5 MiB device array inside the library, one per GPU, created by the CUDA
+ * runtime when the library's device code is loaded on that GPU and held until the process exits;
+ * its device address is looked up on the first call made on each device, so make that first call
+ * outside any stream capture.  Every call on a
+ * device shares that array and leaves its last contents there (the parts that must start at zero
+ * are cleared by each call); calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.  Errors: CAPACITY, INVALID_ARG,
+ * TIMEOUT (a bounded look-back wait ran out), CUDA. */
+int sph_sort_morton_noalloc(int64_t n, const double *x, const double *y, const double *z, const double *box_lo,
+                            const double *box_hi, uint64_t *codes_out, uint32_t *perm_out, void *stream);
+
 /* Message of the last error of ctx (never NULL; "" when none). */
 const char *sph_last_error(sph_ctx *ctx);
 

@@ -2,6 +2,7 @@
 // reorder of the particle arrays, duplicate mask + reduction passes (Alg. mortonmask), compaction
 // into leaves, Karras radix tree (Table arrays_fig_karras) and bottom-up tight boxes + h_max.
 #include <cuda/atomic>
+#include <mutex>
 
 #include "sph_internal.cuh"
 
@@ -569,3 +570,117 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
 }
 
 }  // namespace sph
+
+// ====================================================================================== no-alloc sort
+// Morton codes + stable radix sort for callers that must not allocate device memory.  Some callers
+// cannot call cudaMalloc/cudaFree: an application whose device memory is owned by another allocator
+// (a framework's caching allocator or a fixed arena that already holds the free memory, so a fresh
+// cudaMalloc fails or fragments it), or a latency-bound caller that cannot accept the implicit
+// device synchronisation cudaFree performs.  This variant keeps all its scratch (one ping-pong side
+// of the sort, histograms, look-back words, counters) in one file-scope device array of fixed size.
+namespace sph {
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 262144;                       // largest n accepted (64^3 particles)
+constexpr int64_t kNoAllocTiles = kNoAllocMaxN / kRsTile;      // 64 sort tiles
+
+struct NoAllocScratch {
+    uint64_t keys[kNoAllocMaxN];                  // ping-pong side of the sort (2 MiB)
+    uint32_t vals[kNoAllocMaxN];                  // (1 MiB)
+    uint32_t lookback[8 * kNoAllocTiles * 256];   // decoupled look-back words (512 KiB)
+    uint32_t hist[8 * 256];                       // digit histograms -> offsets
+    uint32_t tile_ctr[8];
+    uint32_t flags;
+};
+
+// Shared by every call on a device: it keeps the last call's contents.  3.5 MiB per device, held by
+// every GPU that loads the library until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+NoAllocScratch *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+__global__ void k_morton_codes(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                               const double *__restrict__ z, Box3 b, uint64_t *__restrict__ keys,
+                               uint32_t *__restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t X = quantise(x[i], b.lo[0], b.span[0]);
+    const uint64_t Y = quantise(y[i], b.lo[1], b.span[1]);
+    const uint64_t Z = quantise(z[i], b.lo[2], b.span[2]);
+    keys[i] = (spread3(X) << 2) | (spread3(Y) << 1) | spread3(Z);
+    vals[i] = (uint32_t)i;
+}
+
+// Device address of the scratch array on the current device.  The symbol name is only a host-side
+// stand-in; the address comes from cudaGetSymbolAddress, once per device, with that device current.
+int noalloc_scratch(NoAllocScratch **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SPH_ERR_CUDA; }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return SPH_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return SPH_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<NoAllocScratch *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return SPH_OK;
+}
+
+}  // namespace
+}  // namespace sph
+
+extern "C" int sph_sort_morton_noalloc(int64_t n, const double *x, const double *y, const double *z,
+                                       const double *box_lo, const double *box_hi, uint64_t *codes_out,
+                                       uint32_t *perm_out, void *stream) {
+    using namespace sph;
+    if (n < 1 || n > kNoAllocMaxN) return SPH_ERR_CAPACITY;
+    if (!x || !y || !z || !box_lo || !box_hi || !codes_out || !perm_out) return SPH_ERR_INVALID_ARG;
+    Box3 b;
+    for (int k = 0; k < 3; k++) {
+        if (!(box_hi[k] > box_lo[k])) return SPH_ERR_INVALID_ARG;
+        b.lo[k] = box_lo[k];
+        b.span[k] = box_hi[k] - box_lo[k];
+    }
+    NoAllocScratch *sc = nullptr;
+    int r = noalloc_scratch(&sc);
+    if (r) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t tiles = (n + kRsTile - 1) / kRsTile;
+    const size_t sm = onesweep_smem();
+    // what must start at zero: histograms, look-back words, tile counters, the error word
+    if (cudaMemsetAsync(sc->hist, 0, sizeof(sc->hist), st) != cudaSuccess ||
+        cudaMemsetAsync(sc->lookback, 0, sizeof(sc->lookback), st) != cudaSuccess ||
+        cudaMemsetAsync(sc->tile_ctr, 0, sizeof(sc->tile_ctr) + sizeof(sc->flags), st) != cudaSuccess ||
+        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+        cudaGetLastError();
+        return SPH_ERR_CUDA;
+    }
+    // codes start in the caller's output; 8 passes alternate output -> scratch -> output, so the
+    // last (odd) pass writes the result into the output
+    k_morton_codes<<<grid_for(n, 256), 256, 0, st>>>(n, x, y, z, b, codes_out, perm_out);
+    unsigned hb = (unsigned)grid_for(n, 256);
+    k_digit_hist<<<hb, 256, 0, st>>>(codes_out, n, sc->hist);
+    k_digit_scan<<<8, 256, 0, st>>>(sc->hist);
+    for (int p = 0; p < 8; p++) {
+        const bool even = (p & 1) == 0;
+        k_onesweep<<<(unsigned)tiles, kRsThreads, sm, st>>>(
+            even ? codes_out : sc->keys, even ? perm_out : sc->vals, even ? sc->keys : codes_out,
+            even ? sc->vals : perm_out, n, 8 * p, sc->hist + 256 * p, sc->lookback + (size_t)p * tiles * 256,
+            sc->tile_ctr + p, &sc->flags);
+    }
+    if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
+    uint32_t flags = 0;
+    if (cudaMemcpyAsync(&flags, &sc->flags, sizeof flags, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return SPH_ERR_CUDA;
+    }
+    return (flags & kErrTimeout) ? SPH_ERR_TIMEOUT : SPH_OK;
+}
+

@@ -98,6 +98,7 @@ def load():
         "sph_get_stats": (_i, [_p, P(sph_stats)]),
         "sph_set_timing": (_i, [_p, _i]),
         "sph_reset_timing": (_i, [_p]),
+        "sph_sort_morton_noalloc": (_i, [_i64, _p, _p, _p, P(_d * 3), P(_d * 3), _p, _p, _p]),
         "sph_last_error": (ctypes.c_char_p, [_p]),
         "sph_error_string": (ctypes.c_char_p, [_i]),
     }
@@ -191,6 +192,16 @@ def sph_set_timing(ctx, on: bool):
 
 def sph_reset_timing(ctx):
     _check(ctx, load().sph_reset_timing(ctx))
+
+
+def sph_sort_morton_noalloc(n: int, x_ptr: int, y_ptr: int, z_ptr: int, box_lo, box_hi, codes_ptr: int,
+                            perm_ptr: int, stream: int | None = None) -> None:
+    """Morton codes + stable sort into caller buffers, without device allocation (see sph.h)."""
+    lo, hi = (_d * 3)(*box_lo), (_d * 3)(*box_hi)
+    code = load().sph_sort_morton_noalloc(int(n), _p(x_ptr), _p(y_ptr), _p(z_ptr), ctypes.byref(lo),
+                                          ctypes.byref(hi), _p(codes_ptr), _p(perm_ptr), _p(stream or 0))
+    if code != SPH_OK:
+        raise SPHError(code, load().sph_error_string(code).decode())
 
 
 def sph_export_tree(ctx) -> dict:
