@@ -42,6 +42,8 @@ WORKLOADS = {
     "uniform32": ("uniform", 32, "uniform periodic box 32^3 = 32,768 particles, jitter 0.01 dx, sigma_v 0.01, u 1"),
     "uniform256": ("uniform", 256, "uniform periodic box 256^3 = 16,777,216 particles, sigma_v 0.1, u 1"),
     "sedov512": ("sedov", 512, "Sedov blast 512^3 = 134,217,728 particles"),
+    "sedov96": ("sedov", 96, "Sedov blast 96^3 = 884,736 particles (profiling size: inputs above L2, "
+                             "a few GB on the device)"),
 }
 
 
@@ -216,6 +218,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
+                    help="run one precision only (profiling); the headline needs both")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -263,6 +267,12 @@ def main():
     w = make_workload(args.workload, rank)
     n = w["n"]
     clocks = ClockSampler(local)
+    if args.only == "mixed":
+        r = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, clocks)
+        print(json.dumps({"workload": args.workload, "precision": "mixed", "ms_per_step": r["ms_per_step"],
+                          "particles_per_s": n / (r["ms_per_step"] * 1e-3), "stage_ms": r["stage_ms"]}))
+        r["solver"].close()
+        return
     r64 = run_precision(torch, sph, w, 0, args.steps, max(args.warmup, 3), dist, True, clocks)
     ms = r64["ms_per_step"]
     if dist:
@@ -300,7 +310,7 @@ def main():
             "clocks": r64["clocks"], "gpu_launches": int(round(r64["launches_per_step"] * args.steps)),
             "roofline": roofline}
 
-    if not args.no_mixed:
+    if not args.no_mixed and args.only != "fp64":
         r32 = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, None)
         ms32 = r32["ms_per_step"]
         line["mixed"] = {"value": n * world / (ms32 * 1e-3), "unit": "particles/s", "ms_per_step": ms32,
