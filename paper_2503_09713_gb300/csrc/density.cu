@@ -29,14 +29,22 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                                              const PairGeo &geo, double &sf, double &sg, uint32_t &nin) {
     const double hinv = 1.0 / ha;
     if (!kMixed) {
+        // FP32 pre-test on the cell-relative offsets skips the candidates that are clearly outside
+        // 2h; the others are evaluated in FP64 with the image shift taken from the cell indices.
         const double xa = x[a], ya = y[a], za = z[a];
         const double hinv2 = hinv * hinv;
+        const float4 A = rel[a];
+        const float lim = 4.f * kPreBand / ((float)hinv2);
         double f0 = 1.0, g0 = 3.0;
         for (uint32_t k = 0; k < cnt; k++) {
             const uint32_t b = ids[(int64_t)k * 32];
-            const double dx = min_image(x[b] - xa, geo.L[0], geo.halfL[0], geo.periodic);
-            const double dy = min_image(y[b] - ya, geo.L[1], geo.halfL[1], geo.periodic);
-            const double dz = min_image(z[b] - za, geo.L[2], geo.halfL[2], geo.periodic);
+            float fx, fy, fz;
+            int sx, sy, sz;
+            rel_sep_shift(A, rel[b], geo, fx, fy, fz, sx, sy, sz);
+            if (fx * fx + fy * fy + fz * fz > lim) continue;
+            const double dx = image_diff(xa, x[b], sx, geo.L[0]);
+            const double dy = image_diff(ya, y[b], sy, geo.L[1]);
+            const double dz = image_diff(za, z[b], sz, geo.L[2]);
             const double q2 = (dx * dx + dy * dy + dz * dz) * hinv2;
             if (q2 < 4.0) {
                 ++nin;

@@ -19,11 +19,12 @@ struct ForceParams {
 };
 
 // Per-particle FP64 record of the force loop: 128 bytes, read as 8 double2.
+// pre = P/(rho^2 Omega), qf = 1/(rho Omega), fn = 1/(pi h^4), acs = alpha_AV c_s.
 struct __align__(16) FRec {
     double x, y, z, h;
     double vx, vy, vz, u;
-    double pre, qf, cs, P;
-    double rho, hinv, pad0, pad1;
+    double pre, qf, acs, P;
+    double rho, hinv, fn, pad;
 };
 
 __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
@@ -32,7 +33,7 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
                              const double *__restrict__ u, const double *__restrict__ h,
                              const double *__restrict__ rho, const double *__restrict__ omega, ForceParams fp,
                              int mixed, FRec *__restrict__ rec, float4 *__restrict__ m_v, float4 *__restrict__ m_t,
-                             float4 *__restrict__ m_r) {
+                             float4 *__restrict__ m_r, float *__restrict__ h32) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double r = rho[i], om = omega[i], ui = u[i], hi = h[i];
@@ -49,9 +50,10 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
         FRec f;
         f.x = x[i]; f.y = y[i]; f.z = z[i]; f.h = hi;
         f.vx = vx[i]; f.vy = vy[i]; f.vz = vz[i]; f.u = ui;
-        f.pre = pre; f.qf = qf; f.cs = cs; f.P = P;
-        f.rho = r; f.hinv = hinv; f.pad0 = 0.0; f.pad1 = 0.0;
+        f.pre = pre; f.qf = qf; f.acs = fp.alpha_av * cs; f.P = P;
+        f.rho = r; f.hinv = hinv; f.fn = hinv * hinv * hinv * hinv * kInvPi; f.pad = 0.0;
         rec[i] = f;
+        h32[i] = (float)hi;
     }
 }
 
@@ -63,8 +65,9 @@ __device__ __forceinline__ void load_rec(const FRec *p, FRec &o) {
     t = __ldg(q + 2); o.vx = t.x; o.vy = t.y;
     t = __ldg(q + 3); o.vz = t.x; o.u = t.y;
     t = __ldg(q + 4); o.pre = t.x; o.qf = t.y;
-    t = __ldg(q + 5); o.cs = t.x; o.P = t.y;
+    t = __ldg(q + 5); o.acs = t.x; o.P = t.y;
     t = __ldg(q + 6); o.rho = t.x; o.hinv = t.y;
+    t = __ldg(q + 7); o.fn = t.x; o.pad = t.y;
 }
 
 struct ForceOut {
@@ -93,7 +96,11 @@ __device__ __forceinline__ void dt_reduce(double t, unsigned long long npair, De
     }
 }
 
+// FP64 pair loop.  A candidate is first tested in FP32 on the cell-relative offsets against the
+// current h (kPreBand margin); the survivors are decided and evaluated in FP64 with the nearest
+// image from the cell indices.  The mass factor is applied once per particle.
 __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__restrict__ rec,
+                                                     const float4 *__restrict__ rel, const float *__restrict__ h32,
                                                      const uint32_t *__restrict__ nb_cnt,
                                                      const int64_t *__restrict__ grp_off,
                                                      const uint32_t *__restrict__ nb_ids, ForceParams fp, ForceOut out,
@@ -107,48 +114,61 @@ __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__re
     const uint32_t *ids = nb_ids + grp_off[a >> 5] + lane;
     FRec A;
     load_rec(&rec[a], A);
-    const double m = fp.mass;
+    const float4 PA = rel[a];
+    const float hA = h32[a];
     const PairGeo &geo = fp.geo;
     double axs = 0.0, ays = 0.0, azs = 0.0, dus = 0.0;
-    double vs = fp.alpha_av * A.cs;
-    const double Fa_n = A.hinv * A.hinv * A.hinv * A.hinv * kInvPi;
+    double vs = A.acs;
     for (uint32_t k = 0; k < cnt; k++) {
         const uint32_t b = ids[(int64_t)k * 32];
+        float fx, fy, fz;
+        int sx, sy, sz;
+        rel_sep_shift(PA, rel[b], geo, fx, fy, fz, sx, sy, sz);
+        const float hmf = fmaxf(hA, h32[b]);
+        if (fx * fx + fy * fy + fz * fz > 4.f * kPreBand * hmf * hmf) continue;
         FRec B;
         load_rec(&rec[b], B);
-        const double dx = min_image(A.x - B.x, geo.L[0], geo.halfL[0], geo.periodic);
-        const double dy = min_image(A.y - B.y, geo.L[1], geo.halfL[1], geo.periodic);
-        const double dz = min_image(A.z - B.z, geo.L[2], geo.halfL[2], geo.periodic);
+        const double dx = image_diff(A.x, B.x, sx, geo.L[0]);
+        const double dy = image_diff(A.y, B.y, sy, geo.L[1]);
+        const double dz = image_diff(A.z, B.z, sz, geo.L[2]);
         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
         const double hm = A.h > B.h ? A.h : B.h;
         const double rad = __dmul_rn(2.0, hm);
         if (!(r2 < __dmul_rn(rad, rad))) continue;
         ++npair;
-        const double r = sqrt(r2);
-        const double rinv = 1.0 / r;
+        const double rinv = rsqrt(r2);
+        const double r = r2 * rinv;
         double f, dfa, dfb;
         m4(r * A.hinv, f, dfa);
         m4(r * B.hinv, f, dfb);
-        const double Fa = dfa * Fa_n;
-        const double Fb = dfb * (B.hinv * B.hinv * B.hinv * B.hinv * kInvPi);
+        const double Fa = dfa * A.fn;
+        const double Fb = dfb * B.fn;
         const double vdotr = ((A.vx - B.vx) * dx + (A.vy - B.vy) * dy + (A.vz - B.vz) * dz) * rinv;
         double Aa = A.pre, Ab = B.pre;
         if (vdotr < 0.0) {
             const double w = fp.beta_av * vdotr;   // = -beta |v.rhat|
-            Aa += -0.5 * (fp.alpha_av * A.cs - w) * vdotr * A.qf;
-            Ab += -0.5 * (fp.alpha_av * B.cs - w) * vdotr * B.qf;
-            vs = fmax(vs, fp.alpha_av * A.cs - w);
+            Aa -= 0.5 * (A.acs - w) * vdotr * A.qf;
+            Ab -= 0.5 * (B.acs - w) * vdotr * B.qf;
+            vs = fmax(vs, A.acs - w);
         }
-        const double sc_ = m * (Aa * Fa + Ab * Fb) * rinv;
+        const double sc_ = (Aa * Fa + Ab * Fb) * rinv;
         axs -= sc_ * dx;
         ays -= sc_ * dy;
         azs -= sc_ * dz;
-        dus += m * Aa * vdotr * Fa;
+        dus += Aa * vdotr * Fa;
         if (fp.alpha_u != 0.0) {
-            const double vsu = sqrt(fabs(A.P - B.P) / (0.5 * (A.rho + B.rho)));
-            dus += m * fp.alpha_u * vsu * (A.u - B.u) * 0.5 * (Fa * A.qf + Fb * B.qf);
+            const double t = 2.0 * fabs(A.P - B.P);   // v_sig^u = sqrt(t / (rho_a + rho_b))
+            if (t > 0.0) {
+                const double vsu = t * rsqrt(t * (A.rho + B.rho));
+                dus += fp.alpha_u * vsu * (A.u - B.u) * 0.5 * (Fa * A.qf + Fb * B.qf);
+            }
         }
     }
+    const double m = fp.mass;
+    axs *= m;
+    ays *= m;
+    azs *= m;
+    dus *= m;
     out.ax[a] = axs;
     out.ay[a] = ays;
     out.az[a] = azs;
@@ -252,7 +272,7 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     if ((r = stage_begin(c, kStForcePrep))) return r;
     k_force_prep<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->h,
                                                            s->rho, s->omega, fp, mixed, (FRec *)c->frec, c->m_v,
-                                                           c->m_t, c->m_r);
+                                                           c->m_t, c->m_r, c->h32);
     SPH_LAUNCH_CHECK(c, "k_force_prep");
     k_reset_dt<<<1, 1, 0, c->stream>>>(c->dscal);
     SPH_LAUNCH_CHECK(c, "k_reset_dt");
@@ -262,8 +282,8 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
         k_forces_mixed<<<grid_for(n, 128), 128, 0, c->stream>>>(n, c->rel, c->m_v, c->m_t, c->m_r, s->h,
                                                                 c->nb_cnt, c->grp_off, c->nb_ids, fp, out, c->dscal);
     else
-        k_forces_fp64<<<grid_for(n, 128), 128, 0, c->stream>>>(n, (const FRec *)c->frec, c->nb_cnt, c->grp_off,
-                                                               c->nb_ids, fp, out, c->dscal);
+        k_forces_fp64<<<grid_for(n, 128), 128, 0, c->stream>>>(n, (const FRec *)c->frec, c->rel, c->h32, c->nb_cnt,
+                                                               c->grp_off, c->nb_ids, fp, out, c->dscal);
     SPH_LAUNCH_CHECK(c, "k_forces");
     return stage_end(c, kStForces);
 }

@@ -63,10 +63,22 @@ __device__ __forceinline__ void load_node_ro(const Node *nd, Node &o) {
     o.hi[0] = c.x; o.hi[1] = c.y; o.hi[2] = d.x; o.pad = d.y;
 }
 
+// Candidates are stored as particle-index ranges [x, y): consecutive leaves found by the walk are
+// merged into one range (leaves are contiguous runs of the Morton order).
+__device__ __forceinline__ void push_leaf(uint2 *out, int cap, int &count, uint32_t first, uint32_t last) {
+    if (count > 0 && count <= cap && out[count - 1].y == first) {
+        out[count - 1].y = last;
+        return;
+    }
+    if (count < cap) out[count] = make_uint2(first, last);
+    ++count;
+}
+
 __global__ void __launch_bounds__(128) k_walk(int64_t G, int64_t L, const Node *__restrict__ gbox,
                                              const Node *__restrict__ nodes, const int32_t *__restrict__ child,
-                                             double s, Geo geo, uint32_t *__restrict__ cand,
-                                             uint32_t *__restrict__ cand_cnt, int cap, uint32_t *flags) {
+                                             const int64_t *__restrict__ leaf_first, double s, Geo geo,
+                                             uint2 *__restrict__ cand, uint32_t *__restrict__ cand_cnt, int cap,
+                                             uint32_t *flags) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
     Node q;
@@ -86,7 +98,7 @@ __global__ void __launch_bounds__(128) k_walk(int64_t G, int64_t L, const Node *
             if (q.lo[k] - geo.lo[k] - rmax <= 0.0) sh[k][nsh[k]++] = geo.L[k];
         }
     }
-    uint32_t *out = cand + (size_t)g * cap;
+    uint2 *out = cand + (size_t)g * cap;
     int count = 0;
     int32_t stack[kStackDepth];
     const int64_t nin = L - 1;
@@ -107,8 +119,8 @@ __global__ void __launch_bounds__(128) k_walk(int64_t G, int64_t L, const Node *
                                      (qlo[2] <= nd.hi[2] + r) && (nd.lo[2] - r <= qhi[2]);
                     if (!hit) continue;
                     if (c >= nin) {
-                        if (count < cap) out[count] = (uint32_t)(c - nin);
-                        ++count;
+                        const int64_t j = c - nin;
+                        push_leaf(out, cap, count, (uint32_t)leaf_first[j], (uint32_t)leaf_first[j + 1]);
                     } else {
                         if (sp + 2 > kStackDepth) {
                             atomicOr(flags, kErrStack);
@@ -126,19 +138,25 @@ __global__ void __launch_bounds__(128) k_walk(int64_t G, int64_t L, const Node *
         return;
     }
     if (nsh[0] * nsh[1] * nsh[2] > 1) {
-        // merge the image lists: sort ascending and drop repeats (only the nearest image is used later)
+        // several images: sort the ranges by start and merge overlapping or touching ones, so every
+        // particle appears once (the nearest image is chosen later)
         for (int i = 1; i < count; i++) {
-            const uint32_t v = out[i];
+            const uint2 v = out[i];
             int j = i - 1;
-            while (j >= 0 && out[j] > v) {
+            while (j >= 0 && out[j].x > v.x) {
                 out[j + 1] = out[j];
                 --j;
             }
             out[j + 1] = v;
         }
         int m = 0;
-        for (int i = 0; i < count; i++)
-            if (m == 0 || out[i] != out[m - 1]) out[m++] = out[i];
+        for (int i = 0; i < count; i++) {
+            if (m > 0 && out[i].x <= out[m - 1].y) {
+                out[m - 1].y = max(out[m - 1].y, out[i].y);
+            } else {
+                out[m++] = out[i];
+            }
+        }
         count = m;
     }
     cand_cnt[g] = (uint32_t)count;
@@ -149,16 +167,12 @@ __device__ __forceinline__ int wrap_cell(int d, int periodic) {
     return periodic ? (((d + 512) & 1023) - 512) : d;
 }
 
-// FP32 squared distance between a and b from cell-relative coordinates (direction irrelevant).
-__device__ __forceinline__ float rel_r2(const float4 A, const float4 B, const Geo &geo) {
-    const uint32_t pa = __float_as_uint(A.w), pb = __float_as_uint(B.w);
-    const int dix = wrap_cell((int)((pb >> 20) & 1023u) - (int)((pa >> 20) & 1023u), geo.periodic);
-    const int diy = wrap_cell((int)((pb >> 10) & 1023u) - (int)((pa >> 10) & 1023u), geo.periodic);
-    const int diz = wrap_cell((int)(pb & 1023u) - (int)(pa & 1023u), geo.periodic);
-    const float dx = fmaf((float)dix, geo.cell[0], B.x - A.x);
-    const float dy = fmaf((float)diy, geo.cell[1], B.y - A.y);
-    const float dz = fmaf((float)diz, geo.cell[2], B.z - A.z);
-    return dx * dx + dy * dy + dz * dz;
+// Cell index components of a packed relative coordinate.
+__device__ __forceinline__ void unpack_cell(const float4 P, int &cx, int &cy, int &cz) {
+    const uint32_t p = __float_as_uint(P.w);
+    cx = (int)((p >> 20) & 1023u);
+    cy = (int)((p >> 10) & 1023u);
+    cz = (int)(p & 1023u);
 }
 
 // The definition, in FP64 and in the order of the oracle: r^2 = (dx*dx + dy*dy) + dz*dz < (s*max h)^2.
@@ -176,61 +190,94 @@ __device__ __forceinline__ bool exact_pair(int64_t a, int64_t b, const double *_
 }
 
 constexpr int kS2Warps = 4;
-constexpr float kBand = 1.0f / 1024.0f;
+constexpr float kBandLo = 1.0f - 1.0f / 1024.0f;
+constexpr float kBandHi = 1.0f + 1.0f / 1024.0f;
 
+// One warp per group.  Every particle (the group's and the candidates') is expressed in FP32
+// relative to the cell of the group's first particle, with the periodic wrap done once per
+// particle on the integer cell index; a test is then three differences, r^2 and one compare.
+// A true neighbour b of a group particle a lies within ext + s*h_max of that cell (ext: group box
+// extent, h_max: largest h in the tree), so its wrapped coordinate is its nearest image whenever
+// ext + s*h_max is below half a box; the kernel asks for a quarter box (checked per group,
+// warp-uniform) and otherwise wraps every separation on its own.
 template <bool kFill>
 __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
-    int64_t n, int64_t G, const int64_t *__restrict__ leaf_first, const uint32_t *__restrict__ cand,
-    const uint32_t *__restrict__ cand_cnt, int cap, const float4 *__restrict__ rel, const float *__restrict__ h32,
+    int64_t n, int64_t G, const uint2 *__restrict__ cand, const uint32_t *__restrict__ cand_cnt, int cap,
+    const Node *__restrict__ gbox, const Node *__restrict__ nodes, const float4 *__restrict__ rel,
+    const float *__restrict__ h32,
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-    const double *__restrict__ h, double s, Geo geo, uint32_t *__restrict__ nb_cnt, int64_t *__restrict__ grp_slots,
-    const int64_t *__restrict__ grp_off, uint32_t *__restrict__ nb_ids, DevScalars *sc) {
-    __shared__ float4 s_rel[kS2Warps][32];
-    __shared__ float s_h[kS2Warps][32];
+    const double *__restrict__ h, double s, float quarter_box, Geo geo, uint32_t *__restrict__ nb_cnt,
+    int64_t *__restrict__ grp_slots, const int64_t *__restrict__ grp_off, uint32_t *__restrict__ nb_ids,
+    DevScalars *sc) {
+    __shared__ float4 s_pos[kS2Warps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t g = (int64_t)blockIdx.x * kS2Warps + warp;
     if (g >= G) return;
     const int64_t a = g * 32 + lane;
     const bool va = a < n;
-    const float4 A = va ? rel[a] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float hA = va ? h32[a] : 0.f;
     const float s32 = (float)s;
-    const uint32_t *cl = cand + (size_t)g * cap;
+    const float4 Araw = rel[va ? a : g * 32];
+    int rcx, rcy, rcz;
+    unpack_cell(rel[g * 32], rcx, rcy, rcz);
+    // group-relative FP32 coordinates of a particle from its packed cell and offset
+    auto grel = [&](const float4 P, float &px, float &py, float &pz) {
+        int cx, cy, cz;
+        unpack_cell(P, cx, cy, cz);
+        px = fmaf((float)wrap_cell(cx - rcx, geo.periodic), geo.cell[0], P.x);
+        py = fmaf((float)wrap_cell(cy - rcy, geo.periodic), geo.cell[1], P.y);
+        pz = fmaf((float)wrap_cell(cz - rcz, geo.periodic), geo.cell[2], P.z);
+    };
+    float ax, ay, az;
+    grel(Araw, ax, ay, az);
+    const float hA = va ? h32[a] : 0.f;
+    const float tA = (s32 * hA) * (s32 * hA);
+    const Node q = gbox[g];
+    const double hroot = nodes[0].hmax;
+    const float ext = (float)fmax(fmax(q.hi[0] - q.lo[0], q.hi[1] - q.lo[1]), q.hi[2] - q.lo[2]);
+    const bool compact = ext + (float)(s * hroot) < quarter_box;   // warp-uniform
+    const uint2 *cl = cand + (size_t)g * cap;
     const int ncand = (int)min(cand_cnt[g], (uint32_t)cap);
     uint32_t cnt = 0;
     const int64_t off = kFill ? grp_off[g] + lane : 0;
     const uint32_t slots = kFill ? (uint32_t)((grp_off[g + 1] - grp_off[g]) / 32) : 0u;
-    int ci = 0;
-    while (ci < ncand) {
-        uint32_t j = cl[ci++];
-        const int64_t s0 = leaf_first[j];
-        int64_t e0 = leaf_first[j + 1];
-        while (ci < ncand && cl[ci] == j + 1) {
-            ++j;
-            e0 = leaf_first[j + 1];
-            ++ci;
-        }
-        for (int64_t base = s0; base < e0; base += 32) {
+    for (int ci = 0; ci < ncand; ci++) {
+        const uint2 rg = cl[ci];
+        for (int64_t base = rg.x; base < rg.y; base += 32) {
             const int64_t b = base + lane;
-            if (b < e0) {
-                s_rel[warp][lane] = rel[b];
-                s_h[warp][lane] = h32[b];
+            if (b < rg.y) {
+                const float4 P = rel[b];
+                const float hb = h32[b];
+                float px, py, pz;
+                if (compact) grel(P, px, py, pz);
+                else { px = P.x; py = P.y; pz = P.z; }
+                s_pos[warp][lane] = make_float4(px, py, pz, compact ? (s32 * hb) * (s32 * hb) : P.w);
             }
             __syncwarp();
-            const int m = (e0 - base) < 32 ? (int)(e0 - base) : 32;
+            const int m = (rg.y - base) < 32 ? (int)(rg.y - base) : 32;
             if (va) {
                 for (int jj = 0; jj < m; jj++) {
+                    const float4 B = s_pos[warp][jj];
+                    float r2, thr;
+                    if (compact) {
+                        const float dx = B.x - ax, dy = B.y - ay, dz = B.z - az;
+                        r2 = dx * dx + dy * dy + dz * dz;
+                        thr = fmaxf(tA, B.w);
+                    } else {
+                        const int64_t bj = base + jj;
+                        int ca[3], cb[3];
+                        unpack_cell(Araw, ca[0], ca[1], ca[2]);
+                        unpack_cell(B, cb[0], cb[1], cb[2]);
+                        const float dx = fmaf((float)wrap_cell(cb[0] - ca[0], geo.periodic), geo.cell[0], B.x - Araw.x);
+                        const float dy = fmaf((float)wrap_cell(cb[1] - ca[1], geo.periodic), geo.cell[1], B.y - Araw.y);
+                        const float dz = fmaf((float)wrap_cell(cb[2] - ca[2], geo.periodic), geo.cell[2], B.z - Araw.z);
+                        r2 = dx * dx + dy * dy + dz * dz;
+                        const float hm = fmaxf(hA, h32[bj]);
+                        thr = (s32 * hm) * (s32 * hm);
+                    }
+                    if (r2 > thr * kBandHi) continue;
                     const int64_t bi = base + jj;
                     if (bi == a) continue;
-                    const float4 B = s_rel[warp][jj];
-                    const float hm = fmaxf(hA, s_h[warp][jj]);
-                    const float t = s32 * hm;
-                    const float thr = t * t;
-                    const float r2 = rel_r2(A, B, geo);
-                    bool in;
-                    if (r2 < thr * (1.0f - kBand)) in = true;
-                    else if (r2 > thr * (1.0f + kBand)) in = false;
-                    else in = exact_pair(a, bi, x, y, z, h, s, geo);
+                    const bool in = (r2 < thr * kBandLo) || exact_pair(a, bi, x, y, z, h, s, geo);
                     if (in) {
                         if (kFill && cnt < slots) nb_ids[off + (int64_t)cnt * 32] = (uint32_t)bi;
                         ++cnt;
@@ -279,8 +326,8 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
 
     for (int attempt = 0;; attempt++) {
         SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
-        k_walk<<<grid_for(G, 128), 128, 0, c->stream>>>(G, L, c->gbox, c->nodes, c->child, sc, geo, c->cand,
-                                                        c->cand_cnt, c->cand_cap, &c->dscal->flags);
+        k_walk<<<grid_for(G, 128), 128, 0, c->stream>>>(G, L, c->gbox, c->nodes, c->child, c->leaf_first, sc, geo,
+                                                        c->cand, c->cand_cnt, c->cand_cap, &c->dscal->flags);
         SPH_LAUNCH_CHECK(c, "k_walk");
         SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->flags, &c->dscal->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                     c->stream));
@@ -291,8 +338,8 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         if (attempt >= 6) return fail(c, SPH_ERR_CAPACITY, "candidate leaf list overflow (cap %d)", c->cand_cap);
         // grow the candidate capacity (x2) and retry
         const int newcap = c->cand_cap * 2;
-        uint32_t *nc = nullptr;
-        if (cudaMalloc(&nc, (size_t)G * newcap * sizeof(uint32_t)) != cudaSuccess) {
+        uint2 *nc = nullptr;
+        if (cudaMalloc(&nc, (size_t)G * newcap * sizeof(uint2)) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, SPH_ERR_OOM, "candidate list of %lld x %d", (long long)G, newcap);
         }
@@ -303,8 +350,9 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
 
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->n_pairs, 0, sizeof(int64_t), c->stream));
     const unsigned blocks = grid_for(G, kS2Warps);
-    k_stage2<false><<<blocks, kS2Warps * 32, 0, c->stream>>>(n, G, c->leaf_first, c->cand, c->cand_cnt, c->cand_cap,
-                                                             c->rel, c->h32, s->x, s->y, s->z, s->h, sc, geo,
+    const float qbox = (float)(0.25 * fmin(fmin(geo.L[0], geo.L[1]), geo.L[2]));
+    k_stage2<false><<<blocks, kS2Warps * 32, 0, c->stream>>>(n, G, c->cand, c->cand_cnt, c->cand_cap, c->gbox,
+                                                             c->nodes, c->rel, c->h32, s->x, s->y, s->z, s->h, sc, qbox, geo,
                                                              c->nb_cnt, c->grp_slots, nullptr, nullptr, c->dscal);
     SPH_LAUNCH_CHECK(c, "k_stage2<count>");
     int r = exclusive_scan_i64(c, c->grp_slots, c->grp_off, G);
@@ -326,8 +374,8 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         }
         c->nb_cap = newcap;
     }
-    k_stage2<true><<<blocks, kS2Warps * 32, 0, c->stream>>>(n, G, c->leaf_first, c->cand, c->cand_cnt, c->cand_cap,
-                                                            c->rel, c->h32, s->x, s->y, s->z, s->h, sc, geo,
+    k_stage2<true><<<blocks, kS2Warps * 32, 0, c->stream>>>(n, G, c->cand, c->cand_cnt, c->cand_cap, c->gbox,
+                                                            c->nodes, c->rel, c->h32, s->x, s->y, s->z, s->h, sc, qbox, geo,
                                                             nullptr, nullptr, c->grp_off, c->nb_ids, c->dscal);
     SPH_LAUNCH_CHECK(c, "k_stage2<fill>");
     c->total_slots = total;

@@ -69,4 +69,39 @@ __device__ __forceinline__ void rel_sep(const float4 A, const float4 B, const Pa
     dz = fmaf((float)diz, geo.cell[2], A.z - B.z);
 }
 
+// Same separation, plus the periodic image shift (in box lengths, -1/0/+1 per axis) that turns the
+// FP64 difference r_a - r_b into the nearest image: the cell-index difference is wrapped into
+// [-512, 511]; a wrap of +-1024 cells is an image shift of -+1 box.
+__device__ __forceinline__ void rel_sep_shift(const float4 A, const float4 B, const PairGeo &geo, float &dx,
+                                              float &dy, float &dz, int &sx, int &sy, int &sz) {
+    const uint32_t pa = __float_as_uint(A.w), pb = __float_as_uint(B.w);
+    const int rx = (int)((pa >> 20) & 1023u) - (int)((pb >> 20) & 1023u);
+    const int ry = (int)((pa >> 10) & 1023u) - (int)((pb >> 10) & 1023u);
+    const int rz = (int)(pa & 1023u) - (int)(pb & 1023u);
+    int wx = rx, wy = ry, wz = rz;
+    if (geo.periodic) {
+        wx = ((rx + 512) & 1023) - 512;
+        wy = ((ry + 512) & 1023) - 512;
+        wz = ((rz + 512) & 1023) - 512;
+    }
+    sx = (wx - rx) / 1024;
+    sy = (wy - ry) / 1024;
+    sz = (wz - rz) / 1024;
+    dx = fmaf((float)wx, geo.cell[0], A.x - B.x);
+    dy = fmaf((float)wy, geo.cell[1], A.y - B.y);
+    dz = fmaf((float)wz, geo.cell[2], A.z - B.z);
+}
+
+// FP64 nearest-image difference a - b given the shift from rel_sep_shift (the shift is zero for all
+// but boundary-crossing pairs; adding -L gives the same rounding as subtracting L).
+__device__ __forceinline__ double image_diff(double a, double b, int s, double L) {
+    double d = a - b;
+    if (s != 0) d += (double)s * L;
+    return d;
+}
+
+// Relative band of the FP32 pre-test: FP32 separations carry relative errors below 1e-6, so a pair
+// whose FP32 q^2 exceeds the limit by more than 2^-10 is certainly outside in FP64 as well.
+constexpr float kPreBand = 1.0f + 1.0f / 1024.0f;
+
 }  // namespace sph

@@ -132,7 +132,7 @@ struct sph_ctx {
     // ---- neighbour cache ----
     int64_t n_groups = 0;
     sph::Node *gbox = nullptr;         // [groups] group boxes
-    uint32_t *cand = nullptr;          // [groups * cand_cap] candidate leaves
+    uint2 *cand = nullptr;             // [groups * cand_cap] candidate particle ranges [x, y)
     uint32_t *cand_cnt = nullptr;      // [groups]
     int cand_cap = 0;
     uint32_t *nb_cnt = nullptr;        // [n_cap] per-particle neighbour count
