@@ -165,7 +165,9 @@ int sph_compute_forces(sph_ctx *ctx, sph_state *s);
 
 /* A0-A10 (App. G): one global kick-drift-kick step: predictor, tree build, neighbour cache,
  * density/h (rebuilding the cache while h leaves its tolerance, App. F outer loop), forces,
- * corrector, CFL.  dt <= 0 uses the CFL step computed by the previous sph_compute_forces /
+ * corrector, CFL.  The h iteration starts from h + dt dh/dt, with dh/dt = -h/(3 rho Omega) sum_b m
+ * v_ab . grad_a W_ab(h_a) from this context's last force evaluation (clamped to a factor h_clamp);
+ * without one it starts from h.  dt <= 0 uses the CFL step computed by the previous sph_compute_forces /
  * sph_step.  Requires accelerations and du of the current state (a first sph_compute_density_h +
  * sph_compute_forces on the initial state).  *dt_used / *dt_next may be NULL.  The state is
  * reordered into Morton order (see sph_build_tree).  Errors: ORDER, CACHE_STALE (more than

@@ -73,7 +73,7 @@ void free_all(sph_ctx *c) {
                     c->mask[0], c->mask[1], c->scan_tmp, c->leaf_first, c->mu_leaf, c->lchild, c->rchild,
                     c->endrange, c->lflag, c->rflag, c->child, c->node_parent, c->leaf_parent, c->visit, c->nodes,
                     c->gather_tmp, c->id_tmp, c->rel, c->h32, c->h_base, c->gbox, c->cand, c->cand_cnt, c->nb_cnt,
-                    c->grp_slots, c->grp_off, c->nb_ids, c->frec, c->m_v, c->m_t, c->m_r, c->a_new, c->block_part,
+                    c->grp_slots, c->grp_off, c->nb_ids, c->frec, c->m_v, c->m_t, c->m_r, c->a_new, c->dhdt, c->block_part,
                     c->hs_fields, c->hs_id, c->dscal};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -208,13 +208,13 @@ int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stre
         (r = alloc(c, &c->rchild, N)) || (r = alloc(c, &c->endrange, N)) || (r = alloc(c, &c->lflag, N)) ||
         (r = alloc(c, &c->rflag, N)) || (r = alloc(c, &c->child, 2 * N)) || (r = alloc(c, &c->node_parent, N)) ||
         (r = alloc(c, &c->leaf_parent, N)) || (r = alloc(c, &c->visit, N)) || (r = alloc(c, &c->nodes, 2 * N)) ||
-        (r = alloc(c, &c->gather_tmp, (size_t)15 * N)) || (r = alloc(c, &c->id_tmp, N)) ||
+        (r = alloc(c, &c->gather_tmp, (size_t)16 * N)) || (r = alloc(c, &c->id_tmp, N)) ||
         (r = alloc(c, &c->rel, N)) || (r = alloc(c, &c->h32, N)) || (r = alloc(c, &c->h_base, N)) ||
         (r = alloc(c, &c->gbox, G)) || (r = alloc(c, &c->cand, (size_t)G * c->cand_cap)) ||
         (r = alloc(c, &c->cand_cnt, G)) || (r = alloc(c, &c->nb_cnt, N)) || (r = alloc(c, &c->grp_slots, G + 1)) ||
         (r = alloc(c, &c->grp_off, G + 1)) || (r = alloc(c, &c->nb_ids, c->nb_cap)) ||
         (r = alloc(c, (char **)&c->frec, (size_t)128 * N)) || (r = alloc(c, &c->m_v, N)) ||
-        (r = alloc(c, &c->m_t, N)) || (r = alloc(c, &c->m_r, N)) || (r = alloc(c, &c->a_new, (size_t)4 * N)) ||
+        (r = alloc(c, &c->m_t, N)) || (r = alloc(c, &c->m_r, N)) || (r = alloc(c, &c->a_new, (size_t)4 * N)) || (r = alloc(c, &c->dhdt, N)) ||
         (r = alloc(c, &c->block_part, (size_t)(N / 256 + 2))) || (r = alloc(c, &c->dscal, 1))) {
         free_all(c);
         delete c;
@@ -257,6 +257,7 @@ int sph_set_params(sph_ctx *c, const sph_params *p) {
     if (r) return r;
     c->p = *p;
     c->tree_valid = c->cache_valid = c->density_valid = c->forces_valid = false;
+    c->dhdt_valid = false;
     c->dt_next = -1.0;
     return SPH_OK;
 }
@@ -302,6 +303,7 @@ int sph_compute_forces(sph_ctx *c, sph_state *s) {
     r = finish_forces(c);
     if (r) return r;
     c->forces_valid = true;
+    c->dhdt_valid = true;
     return SPH_OK;
 }
 
@@ -314,7 +316,8 @@ int sph_step(sph_ctx *c, sph_state *s, double dt, double *dt_used, double *dt_ne
     }
     c->n = s->n;
     // A0 predictor
-    if ((r = stage_begin(c, kStPredict)) || (r = integrate_predict(c, s, dt)) || (r = stage_end(c, kStPredict)))
+    if ((r = stage_begin(c, kStPredict)) || (r = integrate_predict(c, s, dt, c->dhdt_valid ? c->dhdt : nullptr)) ||
+        (r = stage_end(c, kStPredict)))
         return r;
     // A1-A6 tree (reorders the state; outputs are recomputed below)
     if ((r = stage_begin(c, kStTree)) || (r = tree_build(c, s, false)) || (r = stage_end(c, kStTree))) return r;
@@ -336,6 +339,7 @@ int sph_step(sph_ctx *c, sph_state *s, double dt, double *dt_used, double *dt_ne
     const double v2 = c->hscal->v2_sum;
     c->stats.dv_ratio = v2 > 0 ? dvm / std::sqrt(v2 / (double)s->n) : 0.0;
     c->forces_valid = true;
+    c->dhdt_valid = true;
     if (dt_used) *dt_used = dt;
     if (dt_next) *dt_next = c->dt_next;
     return SPH_OK;

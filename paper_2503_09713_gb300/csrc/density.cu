@@ -58,14 +58,14 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         sf = f0;
         sg = g0;
     } else {
+        // FP32 path: four neighbours per iteration so that four independent gathers are in flight
         const float4 A = rel[a];
         const float hi = (float)hinv;
         const float hi2 = hi * hi;
         float s0 = 1.f, c0 = 0.f, s1 = 3.f, c1 = 0.f;
-        for (uint32_t k = 0; k < cnt; k++) {
-            const uint32_t b = ids[(int64_t)k * 32];
+        auto acc = [&](const float4 B) {
             float dx, dy, dz;
-            rel_sep(A, rel[b], geo, dx, dy, dz);
+            rel_sep(A, B, geo, dx, dy, dz);
             const float q2 = (dx * dx + dy * dy + dz * dz) * hi2;
             if (q2 < 4.f) {
                 ++nin;
@@ -75,7 +75,18 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 kahan_add(s0, c0, f);
                 kahan_add(s1, c1, 3.f * f + q * df);
             }
+        };
+        uint32_t k = 0;
+        for (; k + 4 <= cnt; k += 4) {
+            const uint32_t b0 = ids[(int64_t)k * 32], b1 = ids[(int64_t)(k + 1) * 32];
+            const uint32_t b2 = ids[(int64_t)(k + 2) * 32], b3 = ids[(int64_t)(k + 3) * 32];
+            const float4 B0 = rel[b0], B1 = rel[b1], B2 = rel[b2], B3 = rel[b3];
+            acc(B0);
+            acc(B1);
+            acc(B2);
+            acc(B3);
         }
+        for (; k < cnt; k++) acc(rel[ids[(int64_t)k * 32]]);
         sf = kahan_value(s0, c0);
         sg = kahan_value(s1, c1);
     }

@@ -72,6 +72,8 @@ __device__ __forceinline__ void load_rec(const FRec *p, FRec &o) {
 
 struct ForceOut {
     double *ax, *ay, *az, *du, *vsig;
+    double *dhdt;   // dh/dt = -h/(3 rho Omega) sum_b m v_ab . grad_a W_ab(h_a)  (Eq. rhoh with the SPH
+                    // continuity equation); only the initial guess of the next h iteration uses it
 };
 
 // CFL candidate of one particle (App. G): min(C_cour h / v_sig, C_force sqrt(h/|a|)).
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__re
     const float4 PA = rel[a];
     const float hA = h32[a];
     const PairGeo &geo = fp.geo;
-    double axs = 0.0, ays = 0.0, azs = 0.0, dus = 0.0;
+    double axs = 0.0, ays = 0.0, azs = 0.0, dus = 0.0, divs = 0.0;
     double vs = A.acs;
     for (uint32_t k = 0; k < cnt; k++) {
         const uint32_t b = ids[(int64_t)k * 32];
@@ -156,6 +158,7 @@ __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__re
         ays -= sc_ * dy;
         azs -= sc_ * dz;
         dus += Aa * vdotr * Fa;
+        divs += vdotr * Fa;
         if (fp.alpha_u != 0.0) {
             const double t = 2.0 * fabs(A.P - B.P);   // v_sig^u = sqrt(t / (rho_a + rho_b))
             if (t > 0.0) {
@@ -174,6 +177,7 @@ __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__re
     out.az[a] = azs;
     out.du[a] = dus;
     out.vsig[a] = vs;
+    out.dhdt[a] = -A.h * A.qf * (1.0 / 3.0) * m * divs;
     tdt = dt_candidate(A.h, vs, axs, ays, azs, fp);
     }
     dt_reduce(tdt, npair, sc);
@@ -196,19 +200,17 @@ __global__ void __launch_bounds__(128) k_forces_mixed(int64_t n, const float4 *_
     const float4 PA = rel[a], VA = m_v[a], TA = m_t[a], RA = m_r[a];
     const float mass = (float)fp.mass, alpha = (float)fp.alpha_av, beta = (float)fp.beta_av,
                 au = (float)fp.alpha_u;
-    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f, su = 0.f, cu = 0.f;
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f, su = 0.f, cu = 0.f, sdiv = 0.f;
     float vs = alpha * TA.z;
     const float hia = VA.w;
     const float Fa_n = hia * hia * hia * hia * kInvPiF;
-    for (uint32_t k = 0; k < cnt; k++) {
-        const uint32_t b = ids[(int64_t)k * 32];
-        const float4 PB = rel[b];
-        const float4 VB = m_v[b];
+    // one pair; B's position and velocity are already loaded
+    auto pair = [&](uint32_t b, const float4 PB, const float4 VB) {
         float dx, dy, dz;
         rel_sep(PA, PB, fp.geo, dx, dy, dz);
         const float r2 = dx * dx + dy * dy + dz * dz;
         const float him = fminf(hia, VB.w);
-        if (!(r2 * him * him < 4.f)) continue;
+        if (!(r2 * him * him < 4.f)) return;
         ++npair;
         const float4 TB = m_t[b];
         const float4 RB = m_r[b];
@@ -233,11 +235,25 @@ __global__ void __launch_bounds__(128) k_forces_mixed(int64_t n, const float4 *_
         kahan_add(sy, cy, -sc_ * dy);
         kahan_add(sz, cz, -sc_ * dz);
         float dut = mass * Aa * vdotr * Fa;
+        sdiv += vdotr * Fa;
         if (au != 0.f) {
             const float vsu = sqrtf(fabsf(TA.w - TB.w) / (0.5f * (RA.x + RB.x)));
             dut += mass * au * vsu * (RA.y - RB.y) * 0.5f * (Fa * TA.y + Fb * TB.y);
         }
         kahan_add(su, cu, dut);
+    };
+    // two neighbours per iteration: their gathers are issued together
+    uint32_t k = 0;
+    for (; k + 2 <= cnt; k += 2) {
+        const uint32_t b0 = ids[(int64_t)k * 32], b1 = ids[(int64_t)(k + 1) * 32];
+        const float4 P0 = rel[b0], P1 = rel[b1];
+        const float4 V0 = m_v[b0], V1 = m_v[b1];
+        pair(b0, P0, V0);
+        pair(b1, P1, V1);
+    }
+    if (k < cnt) {
+        const uint32_t b = ids[(int64_t)k * 32];
+        pair(b, rel[b], m_v[b]);
     }
     const double axs = kahan_value(sx, cx), ays = kahan_value(sy, cy), azs = kahan_value(sz, cz);
     out.ax[a] = axs;
@@ -245,6 +261,7 @@ __global__ void __launch_bounds__(128) k_forces_mixed(int64_t n, const float4 *_
     out.az[a] = azs;
     out.du[a] = kahan_value(su, cu);
     out.vsig[a] = (double)vs;
+    out.dhdt[a] = -h[a] * (double)TA.y * (1.0 / 3.0) * fp.mass * (double)sdiv;
     tdt = dt_candidate(h[a], (double)vs, axs, ays, azs, fp);
     }
     dt_reduce(tdt, npair, sc);
@@ -277,7 +294,7 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     k_reset_dt<<<1, 1, 0, c->stream>>>(c->dscal);
     SPH_LAUNCH_CHECK(c, "k_reset_dt");
     if ((r = stage_end(c, kStForcePrep)) || (r = stage_begin(c, kStForces))) return r;
-    ForceOut out{ax, ay, az, du, s->vsig};
+    ForceOut out{ax, ay, az, du, s->vsig, c->dhdt};
     if (mixed)
         k_forces_mixed<<<grid_for(n, 128), 128, 0, c->stream>>>(n, c->rel, c->m_v, c->m_t, c->m_r, s->h,
                                                                 c->nb_cnt, c->grp_off, c->nb_ids, fp, out, c->dscal);

@@ -1,6 +1,7 @@
 // Kick-drift-kick leapfrog (App. G, "Leapfrog integration"):
 //   predictor:  v^{n+1/2} = v^n + dt/2 a^n;  r^{n+1} = r^n + dt v^{n+1/2} (wrapped);  v* = v^{n+1/2} + dt/2 a^n
-//               (u advanced the same way with du/dt)
+//               (u advanced the same way with du/dt); h is moved to h + dt dh/dt (clamped to a factor
+//               lambda) as the starting guess of the h iteration, dh/dt from the last force pass
 //   corrector:  v^{n+1} = v* + dt/2 (a^{n+1} - a^n), likewise u; the correction dv_i (Eq. deltavi) is
 //               reduced to max|dv_i| and sum |v_i|^2 for the check of Eq. cvleapfrog.
 #include "sph_internal.cuh"
@@ -9,6 +10,7 @@ namespace sph {
 
 struct IntParams {
     double dt;
+    double h_clamp;
     double lo[3], hi[3];
     int periodic;
 };
@@ -25,7 +27,8 @@ __device__ __forceinline__ double wrap(double x, double lo, double hi) {
 __global__ void k_predict(int64_t n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                           double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                           double *__restrict__ u, const double *__restrict__ ax, const double *__restrict__ ay,
-                          const double *__restrict__ az, const double *__restrict__ du, IntParams ip) {
+                          const double *__restrict__ az, const double *__restrict__ du, double *__restrict__ h,
+                          const double *__restrict__ dhdt, IntParams ip) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double hdt = 0.5 * ip.dt;
@@ -44,6 +47,12 @@ __global__ void k_predict(int64_t n, double *__restrict__ x, double *__restrict_
     vy[i] = hvy + ky;
     vz[i] = hvz + kz;
     u[i] = (u[i] + ku) + ku;
+    if (dhdt) {
+        const double h0 = h[i];
+        double hp = h0 + ip.dt * dhdt[i];
+        hp = fmin(fmax(hp, h0 / ip.h_clamp), h0 * ip.h_clamp);
+        h[i] = hp;
+    }
 }
 
 __global__ void k_correct(int64_t n, double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
@@ -102,16 +111,17 @@ __global__ void k_sum_parts(const double *__restrict__ part, int64_t m, double *
 
 __global__ void k_reset_dv(DevScalars *sc) { sc->dv_max_bits = 0ULL; }
 
-int integrate_predict(sph_ctx *c, sph_state *s, double dt) {
+int integrate_predict(sph_ctx *c, sph_state *s, double dt, const double *dhdt) {
     IntParams ip;
     ip.dt = dt;
+    ip.h_clamp = c->p.h_clamp;
     for (int k = 0; k < 3; k++) {
         ip.lo[k] = c->p.box_lo[k];
         ip.hi[k] = c->p.box_hi[k];
     }
     ip.periodic = c->p.periodic;
     k_predict<<<grid_for(s->n, 256), 256, 0, c->stream>>>(s->n, s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->ax,
-                                                           s->ay, s->az, s->du, ip);
+                                                           s->ay, s->az, s->du, s->h, dhdt, ip);
     SPH_LAUNCH_CHECK(c, "k_predict");
     return SPH_OK;
 }

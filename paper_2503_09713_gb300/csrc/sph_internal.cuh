@@ -149,6 +149,8 @@ struct sph_ctx {
     float4 *m_t = nullptr;             // [n_cap] mixed: P/(rho^2 Omega), 1/(rho Omega), c_s, P
     float4 *m_r = nullptr;             // [n_cap] mixed: rho, u
     double *a_new = nullptr;           // [4][n_cap] ax, ay, az, du of the force pass inside sph_step
+    double *dhdt = nullptr;            // [n_cap] dh/dt from the last force pass (Morton order of the state)
+    bool dhdt_valid = false;
     double *block_part = nullptr;      // per-block partial sums
     bool density_valid = false;
     bool forces_valid = false;
@@ -193,7 +195,7 @@ int tree_boxes(sph_ctx *c, const sph_state *s);   // A6 again with the current h
 int neighbours_build(sph_ctx *c, const sph_state *s);
 int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale);
 int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, double *du);
-int integrate_predict(sph_ctx *c, sph_state *s, double dt);
+int integrate_predict(sph_ctx *c, sph_state *s, double dt, const double *dhdt);
 int integrate_correct(sph_ctx *c, sph_state *s, double dt);
 int read_scalars(sph_ctx *c);
 // Per-stage timing: stage_begin/stage_end bracket the launches of one stage on the context stream;

@@ -501,6 +501,11 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
         g.dst[nf] = c->gather_tmp + (size_t)nf * c->n_cap;
         nf++;
     }
+    if (c->dhdt_valid) {   // dh/dt of the last force pass travels with its particles
+        g.src[nf] = c->dhdt;
+        g.dst[nf] = c->gather_tmp + (size_t)nf * c->n_cap;
+        nf++;
+    }
     g.nf = nf;
     g.id_src = s->id;
     g.id_dst = s->id ? c->id_tmp : nullptr;
