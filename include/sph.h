@@ -105,6 +105,7 @@ typedef struct {
 /* Per-call statistics (host copy, filled by the library after each stage). */
 typedef struct {
     int64_t n, n_leaves, n_groups, n_pairs, cache_slots;
+    int64_t cand_chunks;     /* 32-candidate chunks tested by stage 2 of the last cache build */
     int density_iters_max;   /* largest per-particle Newton count in the last density call */
     int outer_passes;        /* cache builds in the last sph_step (1 = no restart) */
     int n_red;

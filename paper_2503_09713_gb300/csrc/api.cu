@@ -71,8 +71,8 @@ int alloc(sph_ctx *c, T **p, size_t count) {
 void free_all(sph_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->digit_hist, c->lookback, c->tile_ctr,
                     c->mask[0], c->mask[1], c->scan_tmp, c->leaf_first, c->mu_leaf, c->lchild, c->rchild,
-                    c->endrange, c->lflag, c->rflag, c->child, c->node_parent, c->leaf_parent, c->visit, c->nodes,
-                    c->gather_tmp, c->id_tmp, c->rel, c->h32, c->h_base, c->gbox, c->cand, c->cand_cnt, c->nb_cnt,
+                    c->endrange, c->lflag, c->rflag, c->child, c->node_parent, c->leaf_parent, c->visit, c->nodes, c->nodesf,
+                    c->gather_tmp, c->id_tmp, c->rel, c->h32, c->h_base, c->gbox, c->gboxf, c->grp_chunks, c->chunk_off, c->masks, c->cand, c->cand_cnt, c->nb_cnt,
                     c->grp_slots, c->grp_off, c->nb_ids, c->frec, c->m_v, c->m_t, c->m_r, c->a_new, c->dhdt, c->block_part,
                     c->hs_fields, c->hs_id, c->dscal};
     for (void *p : ptrs)
@@ -199,6 +199,7 @@ int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stre
     c->sort_tiles = tiles;
     c->cand_cap = 256;
     c->nb_cap = neigh_cap > 0 ? neigh_cap : 96 * N;
+    c->masks_cap = G * 40 * 32;
     const int64_t scan_elems = 2 * (chunks + 1) + scan_scratch_elems(chunks) + scan_scratch_elems(G + 1) + 64;
     if ((r = alloc(c, &c->keys[0], N)) || (r = alloc(c, &c->keys[1], N)) || (r = alloc(c, &c->vals[0], N)) ||
         (r = alloc(c, &c->vals[1], N)) || (r = alloc(c, &c->digit_hist, 8 * 256)) ||
@@ -207,10 +208,11 @@ int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stre
         (r = alloc(c, &c->leaf_first, N + 1)) || (r = alloc(c, &c->mu_leaf, N)) || (r = alloc(c, &c->lchild, N)) ||
         (r = alloc(c, &c->rchild, N)) || (r = alloc(c, &c->endrange, N)) || (r = alloc(c, &c->lflag, N)) ||
         (r = alloc(c, &c->rflag, N)) || (r = alloc(c, &c->child, 2 * N)) || (r = alloc(c, &c->node_parent, N)) ||
-        (r = alloc(c, &c->leaf_parent, N)) || (r = alloc(c, &c->visit, N)) || (r = alloc(c, &c->nodes, 2 * N)) ||
+        (r = alloc(c, &c->leaf_parent, N)) || (r = alloc(c, &c->visit, N)) || (r = alloc(c, &c->nodes, 2 * N)) || (r = alloc(c, &c->nodesf, 2 * N)) ||
         (r = alloc(c, &c->gather_tmp, (size_t)16 * N)) || (r = alloc(c, &c->id_tmp, N)) ||
         (r = alloc(c, &c->rel, N)) || (r = alloc(c, &c->h32, N)) || (r = alloc(c, &c->h_base, N)) ||
-        (r = alloc(c, &c->gbox, G)) || (r = alloc(c, &c->cand, (size_t)G * c->cand_cap)) ||
+        (r = alloc(c, &c->gbox, G)) || (r = alloc(c, &c->gboxf, G)) || (r = alloc(c, &c->grp_chunks, G + 1)) ||
+        (r = alloc(c, &c->chunk_off, G + 1)) || (r = alloc(c, &c->cand, (size_t)G * c->cand_cap)) || (r = alloc(c, &c->masks, (size_t)G * 40 * 32)) ||
         (r = alloc(c, &c->cand_cnt, G)) || (r = alloc(c, &c->nb_cnt, N)) || (r = alloc(c, &c->grp_slots, G + 1)) ||
         (r = alloc(c, &c->grp_off, G + 1)) || (r = alloc(c, &c->nb_ids, c->nb_cap)) ||
         (r = alloc(c, (char **)&c->frec, (size_t)128 * N)) || (r = alloc(c, &c->m_v, N)) ||

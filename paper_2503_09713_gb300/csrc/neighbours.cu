@@ -2,13 +2,16 @@
 //
 // Stage 1: every group of 32 consecutive (Morton-ordered) particles walks the radix tree once with
 // the group-group criterion  AABB_g  intersects  AABB_c (+) s*max(h_max,g, h_max,c),  s = R_kern*chi,
-// shifting the group box by the periodic images it can reach; the surviving leaves are the group's
-// candidates.  Stage 2: one warp per group, lane = particle a, tests every particle of the candidate
-// leaves against  |r_ab|^2 < (s*max(h_a,h_b))^2  (App. D object-object criterion with the cache
-// tolerance of App. F).  The test runs on FP32 cell-relative offsets with a +-2^-10 relative band;
-// pairs inside the band are decided in FP64 exactly as the definition states, so the kept set is
-// the FP64 set.  A count pass, a scan over groups and a fill pass write the cache in a
-// group-interleaved layout: particle a = 32g + lane owns entries off_g + 32k + lane, k < count_a.
+// shifting the group box by the periodic images it can reach.  The walk runs on FP32 copies of the
+// boxes rounded outwards, so it keeps every cell the FP64 test keeps.  Leaves found one after the
+// other are merged into particle ranges (leaves are contiguous runs of the Morton order).
+// Stage 2: one warp per group, lane = particle a, tests the candidates of the ranges, 32 at a time
+// from shared memory, against  |r_ab|^2 < (s*max(h_a,h_b))^2  (object-object criterion with the cache
+// tolerance of App. F).  The test runs in FP32 on coordinates relative to the group; pairs within a
+// relative 2^-10 of the radius are decided in FP64 exactly as the definition states, so the kept set
+// is the FP64 set.  The count pass stores, per 32-candidate chunk and lane, the bit mask of kept
+// candidates; after a scan over groups the fill pass only expands those masks.  Layout of the cache:
+// particle a = 32g + lane owns entries off_g + 32k + lane, k < count_a.
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -16,6 +19,7 @@ namespace sph {
 struct Geo {
     double lo[3], L[3], halfL[3];
     float cell[3];   // box side / 1024 in FP32
+    float Lf[3];     // box side in FP32
     int periodic;
 };
 
@@ -26,6 +30,7 @@ static Geo make_geo(const sph_params &p) {
         g.L[k] = p.box_hi[k] - p.box_lo[k];
         g.halfL[k] = 0.5 * g.L[k];
         g.cell[k] = (float)(g.L[k] / 1024.0);
+        g.Lf[k] = (float)g.L[k];
     }
     g.periodic = p.periodic;
     return g;
@@ -33,7 +38,8 @@ static Geo make_geo(const sph_params &p) {
 
 // ------------------------------------------------------------------ group boxes (warp per group)
 __global__ void k_group_boxes(int64_t n, int64_t G, const double *__restrict__ x, const double *__restrict__ y,
-                              const double *__restrict__ z, const double *__restrict__ h, Node *__restrict__ gbox) {
+                              const double *__restrict__ z, const double *__restrict__ h, Node *__restrict__ gbox,
+                              NodeF *__restrict__ gboxf) {
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (g >= G) return;
@@ -52,19 +58,21 @@ __global__ void k_group_boxes(int64_t n, int64_t G, const double *__restrict__ x
         b.hmax = hm;
         b.pad = 0.0;
         gbox[g] = b;
+        gboxf[g] = to_float_outward(b);
     }
 }
 
 // ------------------------------------------------------------------ stage 1: tree walk per group
-__device__ __forceinline__ void load_node_ro(const Node *nd, Node &o) {
-    const double2 *p = reinterpret_cast<const double2 *>(nd);
-    double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
-    o.lo[0] = a.x; o.lo[1] = a.y; o.lo[2] = b.x; o.hmax = b.y;
-    o.hi[0] = c.x; o.hi[1] = c.y; o.hi[2] = d.x; o.pad = d.y;
+__device__ __forceinline__ NodeF load_nodef(const NodeF *p) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    const float4 a = __ldg(q), b = __ldg(q + 1);
+    NodeF o;
+    o.lo[0] = a.x; o.lo[1] = a.y; o.lo[2] = a.z; o.hmax = a.w;
+    o.hi[0] = b.x; o.hi[1] = b.y; o.hi[2] = b.z; o.pad = b.w;
+    return o;
 }
 
-// Candidates are stored as particle-index ranges [x, y): consecutive leaves found by the walk are
-// merged into one range (leaves are contiguous runs of the Morton order).
+// Candidates are particle-index ranges [x, y); a leaf that continues the previous range extends it.
 __device__ __forceinline__ void push_leaf(uint2 *out, int cap, int &count, uint32_t first, uint32_t last) {
     if (count > 0 && count <= cap && out[count - 1].y == first) {
         out[count - 1].y = last;
@@ -74,28 +82,31 @@ __device__ __forceinline__ void push_leaf(uint2 *out, int cap, int &count, uint3
     ++count;
 }
 
-__global__ void __launch_bounds__(128) k_walk(int64_t G, int64_t L, const Node *__restrict__ gbox,
-                                             const Node *__restrict__ nodes, const int32_t *__restrict__ child,
-                                             const int64_t *__restrict__ leaf_first, double s, Geo geo,
+// Upward-rounded s * max(h1, h2) with a relative margin that covers the FP32 products.
+__device__ __forceinline__ float walk_radius(float s, float h1, float h2) {
+    return __fmul_ru(__fmul_ru(s, fmaxf(h1, h2)), 1.0f + 1.0f / 65536.0f);
+}
+
+__global__ void __launch_bounds__(128) k_walk(int64_t G, int64_t L, const NodeF *__restrict__ gboxf,
+                                             const NodeF *__restrict__ nodesf, const int32_t *__restrict__ child,
+                                             const int64_t *__restrict__ leaf_first, float s, Geo geo,
                                              uint2 *__restrict__ cand, uint32_t *__restrict__ cand_cnt, int cap,
-                                             uint32_t *flags) {
+                                             int64_t *__restrict__ grp_chunks, uint32_t *flags) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
-    Node q;
-    load_node_ro(&gbox[g], q);
-    Node root;
-    load_node_ro(&nodes[0], root);
-    const double margin = 1.0 + 1e-9;
-    const double rmax = s * fmax(q.hmax, root.hmax) * margin;
-    // periodic images of the group box that can reach the box
+    const NodeF q = load_nodef(&gboxf[g]);
+    const NodeF root = load_nodef(&nodesf[0]);
+    const float rmax = walk_radius(s, q.hmax, root.hmax);
+    // periodic images of the group box that can reach the box (offsets added with outward rounding)
     int nsh[3];
-    double sh[3][3];
+    float sh[3][3];
     for (int k = 0; k < 3; k++) {
         nsh[k] = 1;
-        sh[k][0] = 0.0;
+        sh[k][0] = 0.f;
         if (geo.periodic) {
-            if (q.hi[k] - geo.lo[k] + rmax >= geo.L[k]) sh[k][nsh[k]++] = -geo.L[k];
-            if (q.lo[k] - geo.lo[k] - rmax <= 0.0) sh[k][nsh[k]++] = geo.L[k];
+            const float lo = (float)geo.lo[k];
+            if (__fadd_ru(__fadd_ru(q.hi[k], -lo), rmax) >= geo.Lf[k] * (1.0f - 1e-6f)) sh[k][nsh[k]++] = -geo.Lf[k];
+            if (__fadd_rd(__fadd_rd(q.lo[k], -lo), -rmax) <= geo.Lf[k] * 1e-6f) sh[k][nsh[k]++] = geo.Lf[k];
         }
     }
     uint2 *out = cand + (size_t)g * cap;
@@ -105,18 +116,19 @@ __global__ void __launch_bounds__(128) k_walk(int64_t G, int64_t L, const Node *
     for (int ix = 0; ix < nsh[0]; ix++)
         for (int iy = 0; iy < nsh[1]; iy++)
             for (int iz = 0; iz < nsh[2]; iz++) {
-                const double qlo[3] = {q.lo[0] + sh[0][ix], q.lo[1] + sh[1][iy], q.lo[2] + sh[2][iz]};
-                const double qhi[3] = {q.hi[0] + sh[0][ix], q.hi[1] + sh[1][iy], q.hi[2] + sh[2][iz]};
+                const float qlo[3] = {__fadd_rd(q.lo[0], sh[0][ix]), __fadd_rd(q.lo[1], sh[1][iy]),
+                                      __fadd_rd(q.lo[2], sh[2][iz])};
+                const float qhi[3] = {__fadd_ru(q.hi[0], sh[0][ix]), __fadd_ru(q.hi[1], sh[1][iy]),
+                                      __fadd_ru(q.hi[2], sh[2][iz])};
                 int sp = 0;
                 stack[sp++] = 0;
                 while (sp > 0) {
                     const int32_t c = stack[--sp];
-                    Node nd;
-                    load_node_ro(&nodes[c], nd);
-                    const double r = s * fmax(q.hmax, nd.hmax) * margin;
-                    const bool hit = (qlo[0] <= nd.hi[0] + r) && (nd.lo[0] - r <= qhi[0]) &&
-                                     (qlo[1] <= nd.hi[1] + r) && (nd.lo[1] - r <= qhi[1]) &&
-                                     (qlo[2] <= nd.hi[2] + r) && (nd.lo[2] - r <= qhi[2]);
+                    const NodeF nd = load_nodef(&nodesf[c]);
+                    const float r = walk_radius(s, q.hmax, nd.hmax);
+                    const bool hit = (qlo[0] <= __fadd_ru(nd.hi[0], r)) && (__fadd_rd(nd.lo[0], -r) <= qhi[0]) &&
+                                     (qlo[1] <= __fadd_ru(nd.hi[1], r)) && (__fadd_rd(nd.lo[1], -r) <= qhi[1]) &&
+                                     (qlo[2] <= __fadd_ru(nd.hi[2], r)) && (__fadd_rd(nd.lo[2], -r) <= qhi[2]);
                     if (!hit) continue;
                     if (c >= nin) {
                         const int64_t j = c - nin;
@@ -135,6 +147,7 @@ __global__ void __launch_bounds__(128) k_walk(int64_t G, int64_t L, const Node *
     if (count > cap) {
         atomicOr(flags, kErrCandOverflow);
         cand_cnt[g] = (uint32_t)count;
+        grp_chunks[g] = 0;
         return;
     }
     if (nsh[0] * nsh[1] * nsh[2] > 1) {
@@ -159,7 +172,10 @@ __global__ void __launch_bounds__(128) k_walk(int64_t G, int64_t L, const Node *
         }
         count = m;
     }
+    int64_t chunks = 0;
+    for (int i = 0; i < count; i++) chunks += (out[i].y - out[i].x + 31) / 32;
     cand_cnt[g] = (uint32_t)count;
+    grp_chunks[g] = chunks;
 }
 
 // ------------------------------------------------------------------ stage 2: per-particle filter
@@ -167,7 +183,6 @@ __device__ __forceinline__ int wrap_cell(int d, int periodic) {
     return periodic ? (((d + 512) & 1023) - 512) : d;
 }
 
-// Cell index components of a packed relative coordinate.
 __device__ __forceinline__ void unpack_cell(const float4 P, int &cx, int &cy, int &cz) {
     const uint32_t p = __float_as_uint(P.w);
     cx = (int)((p >> 20) & 1023u);
@@ -193,23 +208,21 @@ constexpr int kS2Warps = 4;
 constexpr float kBandLo = 1.0f - 1.0f / 1024.0f;
 constexpr float kBandHi = 1.0f + 1.0f / 1024.0f;
 
-// One warp per group.  Every particle (the group's and the candidates') is expressed in FP32
-// relative to the cell of the group's first particle, with the periodic wrap done once per
-// particle on the integer cell index; a test is then three differences, r^2 and one compare.
-// A true neighbour b of a group particle a lies within ext + s*h_max of that cell (ext: group box
-// extent, h_max: largest h in the tree), so its wrapped coordinate is its nearest image whenever
-// ext + s*h_max is below half a box; the kernel asks for a quarter box (checked per group,
-// warp-uniform) and otherwise wraps every separation on its own.
-template <bool kFill>
-__global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
+// Count pass.  Every particle (the group's and the candidates') is expressed in FP32 relative to the
+// cell of the group's first particle, the periodic wrap done once per particle on the integer cell
+// index, so a test is three differences, r^2 and compares.  A true neighbour b of a group particle
+// lies within ext + s*h_max of that cell (ext: group extent, h_max: largest h in the tree), so its
+// wrapped coordinate is its nearest image whenever ext + s*h_max is below half a box; the kernel
+// asks for a quarter box (warp-uniform), otherwise every separation is wrapped on its own.
+__global__ void __launch_bounds__(kS2Warps * 32) k_stage2_count(
     int64_t n, int64_t G, const uint2 *__restrict__ cand, const uint32_t *__restrict__ cand_cnt, int cap,
-    const Node *__restrict__ gbox, const Node *__restrict__ nodes, const float4 *__restrict__ rel,
-    const float *__restrict__ h32,
-    const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-    const double *__restrict__ h, double s, float quarter_box, Geo geo, uint32_t *__restrict__ nb_cnt,
-    int64_t *__restrict__ grp_slots, const int64_t *__restrict__ grp_off, uint32_t *__restrict__ nb_ids,
-    DevScalars *sc) {
+    const int64_t *__restrict__ chunk_off, const Node *__restrict__ gbox, const Node *__restrict__ nodes,
+    const float4 *__restrict__ rel, const float *__restrict__ h32, const double *__restrict__ x,
+    const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h, double s,
+    float quarter_box, Geo geo, uint32_t *__restrict__ masks, uint32_t *__restrict__ nb_cnt,
+    int64_t *__restrict__ grp_slots, DevScalars *sc) {
     __shared__ float4 s_pos[kS2Warps][32];
+    __shared__ float s_h[kS2Warps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t g = (int64_t)blockIdx.x * kS2Warps + warp;
     if (g >= G) return;
@@ -219,7 +232,6 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
     const float4 Araw = rel[va ? a : g * 32];
     int rcx, rcy, rcz;
     unpack_cell(rel[g * 32], rcx, rcy, rcz);
-    // group-relative FP32 coordinates of a particle from its packed cell and offset
     auto grel = [&](const float4 P, float &px, float &py, float &pz) {
         int cx, cy, cz;
         unpack_cell(P, cx, cy, cz);
@@ -235,68 +247,115 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
     const double hroot = nodes[0].hmax;
     const float ext = (float)fmax(fmax(q.hi[0] - q.lo[0], q.hi[1] - q.lo[1]), q.hi[2] - q.lo[2]);
     const bool compact = ext + (float)(s * hroot) < quarter_box;   // warp-uniform
+    int ca[3];
+    unpack_cell(Araw, ca[0], ca[1], ca[2]);
     const uint2 *cl = cand + (size_t)g * cap;
     const int ncand = (int)min(cand_cnt[g], (uint32_t)cap);
+    uint32_t *gm = masks + (size_t)chunk_off[g] * 32 + lane;
     uint32_t cnt = 0;
-    const int64_t off = kFill ? grp_off[g] + lane : 0;
-    const uint32_t slots = kFill ? (uint32_t)((grp_off[g + 1] - grp_off[g]) / 32) : 0u;
+    int64_t chunk = 0;
     for (int ci = 0; ci < ncand; ci++) {
         const uint2 rg = cl[ci];
-        for (int64_t base = rg.x; base < rg.y; base += 32) {
+        for (int64_t base = rg.x; base < rg.y; base += 32, ++chunk) {
             const int64_t b = base + lane;
+            float4 P = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+            float hb = 0.f;
             if (b < rg.y) {
-                const float4 P = rel[b];
-                const float hb = h32[b];
-                float px, py, pz;
-                if (compact) grel(P, px, py, pz);
-                else { px = P.x; py = P.y; pz = P.z; }
-                s_pos[warp][lane] = make_float4(px, py, pz, compact ? (s32 * hb) * (s32 * hb) : P.w);
-            }
-            __syncwarp();
-            const int m = (rg.y - base) < 32 ? (int)(rg.y - base) : 32;
-            if (va) {
-                for (int jj = 0; jj < m; jj++) {
-                    const float4 B = s_pos[warp][jj];
-                    float r2, thr;
-                    if (compact) {
-                        const float dx = B.x - ax, dy = B.y - ay, dz = B.z - az;
-                        r2 = dx * dx + dy * dy + dz * dz;
-                        thr = fmaxf(tA, B.w);
-                    } else {
-                        const int64_t bj = base + jj;
-                        int ca[3], cb[3];
-                        unpack_cell(Araw, ca[0], ca[1], ca[2]);
-                        unpack_cell(B, cb[0], cb[1], cb[2]);
-                        const float dx = fmaf((float)wrap_cell(cb[0] - ca[0], geo.periodic), geo.cell[0], B.x - Araw.x);
-                        const float dy = fmaf((float)wrap_cell(cb[1] - ca[1], geo.periodic), geo.cell[1], B.y - Araw.y);
-                        const float dz = fmaf((float)wrap_cell(cb[2] - ca[2], geo.periodic), geo.cell[2], B.z - Araw.z);
-                        r2 = dx * dx + dy * dy + dz * dz;
-                        const float hm = fmaxf(hA, h32[bj]);
-                        thr = (s32 * hm) * (s32 * hm);
-                    }
-                    if (r2 > thr * kBandHi) continue;
-                    const int64_t bi = base + jj;
-                    if (bi == a) continue;
-                    const bool in = (r2 < thr * kBandLo) || exact_pair(a, bi, x, y, z, h, s, geo);
-                    if (in) {
-                        if (kFill && cnt < slots) nb_ids[off + (int64_t)cnt * 32] = (uint32_t)bi;
-                        ++cnt;
-                    }
+                P = rel[b];
+                hb = h32[b];
+                if (compact) {
+                    float px, py, pz;
+                    grel(P, px, py, pz);
+                    P = make_float4(px, py, pz, (s32 * hb) * (s32 * hb));
                 }
             }
+            s_pos[warp][lane] = P;
+            s_h[warp][lane] = hb;
+            __syncwarp();
+            uint32_t hi_mask = 0, lo_mask = 0;
+            if (compact) {
+#pragma unroll 8
+                for (int jj = 0; jj < 32; jj++) {
+                    const float4 B = s_pos[warp][jj];
+                    const float dx = B.x - ax, dy = B.y - ay, dz = B.z - az;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const float thr = fmaxf(tA, B.w);
+                    hi_mask |= (uint32_t)(r2 <= thr * kBandHi) << jj;
+                    lo_mask |= (uint32_t)(r2 < thr * kBandLo) << jj;
+                }
+            } else {
+                const int m = (rg.y - base) < 32 ? (int)(rg.y - base) : 32;
+                for (int jj = 0; jj < m; jj++) {
+                    const float4 B = s_pos[warp][jj];
+                    int cb[3];
+                    unpack_cell(B, cb[0], cb[1], cb[2]);
+                    const float dx = fmaf((float)wrap_cell(cb[0] - ca[0], geo.periodic), geo.cell[0], B.x - Araw.x);
+                    const float dy = fmaf((float)wrap_cell(cb[1] - ca[1], geo.periodic), geo.cell[1], B.y - Araw.y);
+                    const float dz = fmaf((float)wrap_cell(cb[2] - ca[2], geo.periodic), geo.cell[2], B.z - Araw.z);
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const float hm = fmaxf(hA, s_h[warp][jj]);
+                    const float thr = va ? (s32 * hm) * (s32 * hm) : -1.f;
+                    hi_mask |= (uint32_t)(r2 <= thr * kBandHi) << jj;
+                    lo_mask |= (uint32_t)(r2 < thr * kBandLo) << jj;
+                }
+            }
+            if (!va) hi_mask = lo_mask = 0;   // lanes past n keep nothing
+            // the particle itself is not its own neighbour
+            if (a >= base && a < base + 32) {
+                hi_mask &= ~(1u << (uint32_t)(a - base));
+                lo_mask &= ~(1u << (uint32_t)(a - base));
+            }
+            // candidates inside the band: decide in FP64
+            uint32_t band = hi_mask & ~lo_mask;
+            while (band) {
+                const int jj = __ffs(band) - 1;
+                band &= band - 1;
+                if (!exact_pair(a, base + jj, x, y, z, h, s, geo)) hi_mask &= ~(1u << jj);
+            }
+            gm[(size_t)chunk * 32] = hi_mask;
+            cnt += __popc(hi_mask);
             __syncwarp();
         }
     }
-    if (!kFill) {
-        if (va) nb_cnt[a] = cnt;
-        uint32_t mx = cnt, sum = cnt;
-        for (int o = 16; o > 0; o >>= 1) {
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        }
-        if (lane == 0) {
-            grp_slots[g] = (int64_t)mx * 32;
-            atomicAdd((unsigned long long *)&sc->n_pairs, (unsigned long long)sum);
+    if (va) nb_cnt[a] = cnt;
+    uint32_t mx = cnt, sum = cnt;
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    if (lane == 0) {
+        grp_slots[g] = (int64_t)mx * 32;
+        atomicAdd((unsigned long long *)&sc->n_pairs, (unsigned long long)sum);
+    }
+}
+
+// Fill pass: expand the masks of the count pass into the cache, in candidate order.
+__global__ void __launch_bounds__(128) k_stage2_fill(int64_t G, const uint2 *__restrict__ cand,
+                                                     const uint32_t *__restrict__ cand_cnt, int cap,
+                                                     const int64_t *__restrict__ chunk_off,
+                                                     const uint32_t *__restrict__ masks,
+                                                     const int64_t *__restrict__ grp_off,
+                                                     uint32_t *__restrict__ nb_ids) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (g >= G) return;
+    const uint2 *cl = cand + (size_t)g * cap;
+    const int ncand = (int)min(cand_cnt[g], (uint32_t)cap);
+    const uint32_t *gm = masks + (size_t)chunk_off[g] * 32 + lane;
+    const int64_t off = grp_off[g] + lane;
+    const uint32_t slots = (uint32_t)((grp_off[g + 1] - grp_off[g]) / 32);
+    uint32_t cnt = 0;
+    int64_t chunk = 0;
+    for (int ci = 0; ci < ncand; ci++) {
+        const uint2 rg = cl[ci];
+        for (int64_t base = rg.x; base < rg.y; base += 32, ++chunk) {
+            uint32_t m = gm[(size_t)chunk * 32];
+            while (m) {
+                const int jj = __ffs(m) - 1;
+                m &= m - 1;
+                if (cnt < slots) nb_ids[off + (int64_t)cnt * 32] = (uint32_t)(base + jj);
+                ++cnt;
+            }
         }
     }
 }
@@ -307,6 +366,21 @@ __global__ void k_h32(int64_t n, const double *__restrict__ h, float *__restrict
     const double v = h[i];
     h32[i] = (float)v;
     hb[i] = v;
+}
+
+template <typename T>
+static int ensure(sph_ctx *c, T **p, int64_t &cap, int64_t need, const char *what) {
+    if (need <= cap) return SPH_OK;
+    const int64_t newcap = need + need / 4 + 1024;
+    SPH_CUDA(c, cudaFree(*p));
+    *p = nullptr;
+    if (cudaMalloc((void **)p, (size_t)newcap * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        cap = 0;
+        return fail(c, SPH_ERR_OOM, "%s of %lld entries", what, (long long)newcap);
+    }
+    cap = newcap;
+    return SPH_OK;
 }
 
 int neighbours_build(sph_ctx *c, const sph_state *s) {
@@ -321,22 +395,27 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
 
     k_h32<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->h, c->h32, c->h_base);
     SPH_LAUNCH_CHECK(c, "k_h32");
-    k_group_boxes<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(n, G, s->x, s->y, s->z, s->h, c->gbox);
+    k_group_boxes<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(n, G, s->x, s->y, s->z, s->h, c->gbox, c->gboxf);
     SPH_LAUNCH_CHECK(c, "k_group_boxes");
 
+    // stage 1, growing the candidate capacity while a list overflows
     for (int attempt = 0;; attempt++) {
         SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
-        k_walk<<<grid_for(G, 128), 128, 0, c->stream>>>(G, L, c->gbox, c->nodes, c->child, c->leaf_first, sc, geo,
-                                                        c->cand, c->cand_cnt, c->cand_cap, &c->dscal->flags);
+        k_walk<<<grid_for(G, 128), 128, 0, c->stream>>>(G, L, c->gboxf, c->nodesf, c->child, c->leaf_first,
+                                                        (float)sc, geo, c->cand, c->cand_cnt, c->cand_cap,
+                                                        c->grp_chunks, &c->dscal->flags);
         SPH_LAUNCH_CHECK(c, "k_walk");
+        int r = exclusive_scan_i64(c, c->grp_chunks, c->chunk_off, G);
+        if (r) return r;
         SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->flags, &c->dscal->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                     c->stream));
+        SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->total_chunks, &c->chunk_off[G], sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, c->stream));
         SPH_CUDA(c, cudaStreamSynchronize(c->stream));
         const uint32_t fl = c->hscal->flags;
         if (fl & kErrStack) return fail(c, SPH_ERR_CAPACITY, "tree walk stack overflow");
         if (!(fl & kErrCandOverflow)) break;
-        if (attempt >= 6) return fail(c, SPH_ERR_CAPACITY, "candidate leaf list overflow (cap %d)", c->cand_cap);
-        // grow the candidate capacity (x2) and retry
+        if (attempt >= 6) return fail(c, SPH_ERR_CAPACITY, "candidate range list overflow (cap %d)", c->cand_cap);
         const int newcap = c->cand_cap * 2;
         uint2 *nc = nullptr;
         if (cudaMalloc(&nc, (size_t)G * newcap * sizeof(uint2)) != cudaSuccess) {
@@ -347,15 +426,20 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         c->cand = nc;
         c->cand_cap = newcap;
     }
+    const int64_t chunks = c->hscal->total_chunks;
+    int r = ensure(c, &c->masks, c->masks_cap, chunks * 32, "candidate masks");
+    if (r) return r;
 
+    // stage 2: count (and masks), scan, fill
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->n_pairs, 0, sizeof(int64_t), c->stream));
     const unsigned blocks = grid_for(G, kS2Warps);
     const float qbox = (float)(0.25 * fmin(fmin(geo.L[0], geo.L[1]), geo.L[2]));
-    k_stage2<false><<<blocks, kS2Warps * 32, 0, c->stream>>>(n, G, c->cand, c->cand_cnt, c->cand_cap, c->gbox,
-                                                             c->nodes, c->rel, c->h32, s->x, s->y, s->z, s->h, sc, qbox, geo,
-                                                             c->nb_cnt, c->grp_slots, nullptr, nullptr, c->dscal);
-    SPH_LAUNCH_CHECK(c, "k_stage2<count>");
-    int r = exclusive_scan_i64(c, c->grp_slots, c->grp_off, G);
+    k_stage2_count<<<blocks, kS2Warps * 32, 0, c->stream>>>(n, G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off,
+                                                            c->gbox, c->nodes, c->rel, c->h32, s->x, s->y, s->z,
+                                                            s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->grp_slots,
+                                                            c->dscal);
+    SPH_LAUNCH_CHECK(c, "k_stage2_count");
+    r = exclusive_scan_i64(c, c->grp_slots, c->grp_off, G);
     if (r) return r;
     SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->total_slots, &c->grp_off[G], sizeof(int64_t), cudaMemcpyDeviceToHost,
                                 c->stream));
@@ -363,26 +447,17 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
                                 c->stream));
     SPH_CUDA(c, cudaStreamSynchronize(c->stream));
     const int64_t total = c->hscal->total_slots;
-    if (total > c->nb_cap) {
-        const int64_t newcap = total + total / 4 + 1024;
-        SPH_CUDA(c, cudaFree(c->nb_ids));
-        c->nb_ids = nullptr;
-        if (cudaMalloc(&c->nb_ids, (size_t)newcap * sizeof(uint32_t)) != cudaSuccess) {
-            cudaGetLastError();
-            c->nb_cap = 0;
-            return fail(c, SPH_ERR_OOM, "neighbour cache of %lld entries", (long long)newcap);
-        }
-        c->nb_cap = newcap;
-    }
-    k_stage2<true><<<blocks, kS2Warps * 32, 0, c->stream>>>(n, G, c->cand, c->cand_cnt, c->cand_cap, c->gbox,
-                                                            c->nodes, c->rel, c->h32, s->x, s->y, s->z, s->h, sc, qbox, geo,
-                                                            nullptr, nullptr, c->grp_off, c->nb_ids, c->dscal);
-    SPH_LAUNCH_CHECK(c, "k_stage2<fill>");
+    r = ensure(c, &c->nb_ids, c->nb_cap, total, "neighbour cache");
+    if (r) return r;
+    k_stage2_fill<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off,
+                                                                c->masks, c->grp_off, c->nb_ids);
+    SPH_LAUNCH_CHECK(c, "k_stage2_fill");
     c->total_slots = total;
     c->n_pairs = c->hscal->n_pairs;
     c->stats.n_pairs = c->n_pairs;
     c->stats.cache_slots = total;
     c->stats.n_groups = G;
+    c->stats.cand_chunks = chunks;
     c->cache_valid = true;
     return SPH_OK;
 }

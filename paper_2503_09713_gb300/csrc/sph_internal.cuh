@@ -35,12 +35,32 @@ struct __align__(16) Node {
     double pad;
 };
 
+// FP32 copy of a node with the box rounded outwards and h_max rounded up (tree walk): 32 bytes.
+struct __align__(16) NodeF {
+    float lo[3];
+    float hmax;
+    float hi[3];
+    float pad;
+};
+
+__device__ __forceinline__ NodeF to_float_outward(const Node &b) {
+    NodeF f;
+    for (int k = 0; k < 3; k++) {
+        f.lo[k] = __double2float_rd(b.lo[k]);
+        f.hi[k] = __double2float_ru(b.hi[k]);
+    }
+    f.hmax = __double2float_ru(b.hmax);
+    f.pad = 0.f;
+    return f;
+}
+
 // Device scalars written by kernels and read back by the host in one copy.
 struct DevScalars {
     unsigned long long dt_min_bits;   // CFL min over particles (positive double as bits)
     unsigned long long dv_max_bits;   // max |dv| (positive double as bits)
     int64_t n_leaves;
     int64_t total_slots;              // neighbour-cache entries incl. padding
+    int64_t total_chunks;             // 32-candidate chunks of stage 2
     int64_t n_pairs;                  // real pairs
     uint32_t max_iters;
     uint32_t flags;
@@ -119,6 +139,7 @@ struct sph_ctx {
     int32_t *leaf_parent = nullptr;    // [n_cap] parent of leaf
     uint32_t *visit = nullptr;         // [n_cap]
     sph::Node *nodes = nullptr;        // [2 n_cap]
+    sph::NodeF *nodesf = nullptr;      // [2 n_cap] FP32 outward copy for the walk
     int64_t n_leaves = 0;
     bool tree_valid = false;
 
@@ -132,6 +153,11 @@ struct sph_ctx {
     // ---- neighbour cache ----
     int64_t n_groups = 0;
     sph::Node *gbox = nullptr;         // [groups] group boxes
+    sph::NodeF *gboxf = nullptr;       // [groups] FP32 outward copy
+    int64_t *grp_chunks = nullptr;     // [groups + 1] candidate chunks per group -> scan
+    int64_t *chunk_off = nullptr;      // [groups + 1]
+    uint32_t *masks = nullptr;         // [chunks * 32] stage-2 hit masks
+    int64_t masks_cap = 0;
     uint2 *cand = nullptr;             // [groups * cand_cap] candidate particle ranges [x, y)
     uint32_t *cand_cnt = nullptr;      // [groups]
     int cand_cap = 0;

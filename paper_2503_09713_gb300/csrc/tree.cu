@@ -413,7 +413,7 @@ __device__ __forceinline__ void load_node(const Node *nd, Node &o) {
 __global__ void k_boxes(int64_t L, const int64_t *__restrict__ leaf_first, const double *__restrict__ x,
                         const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h,
                         const int32_t *__restrict__ child, const int32_t *__restrict__ node_parent,
-                        const int32_t *__restrict__ leaf_parent, uint32_t *visit, Node *nodes) {
+                        const int32_t *__restrict__ leaf_parent, uint32_t *visit, Node *nodes, NodeF *nodesf) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= L) return;
     Node b;
@@ -430,6 +430,7 @@ __global__ void k_boxes(int64_t L, const int64_t *__restrict__ leaf_first, const
     }
     const int64_t nin = L - 1;
     nodes[nin + j] = b;
+    nodesf[nin + j] = to_float_outward(b);
     if (L == 1) return;
     int64_t node = leaf_parent[j];
     while (node >= 0) {
@@ -448,6 +449,7 @@ __global__ void k_boxes(int64_t L, const int64_t *__restrict__ leaf_first, const
         m.hmax = fmax(l.hmax, r.hmax);
         m.pad = 0.0;
         nodes[node] = m;
+        nodesf[node] = to_float_outward(m);
         node = node_parent[node];
     }
 }
@@ -465,7 +467,8 @@ static int boxes(sph_ctx *c, const sph_state *s) {
     const int64_t L = c->n_leaves;
     if (L > 1) SPH_CUDA(c, cudaMemsetAsync(c->visit, 0, (size_t)(L - 1) * sizeof(uint32_t), c->stream));
     k_boxes<<<grid_for(L, 128), 128, 0, c->stream>>>(L, c->leaf_first, s->x, s->y, s->z, s->h, c->child,
-                                                     c->node_parent, c->leaf_parent, c->visit, c->nodes);
+                                                     c->node_parent, c->leaf_parent, c->visit, c->nodes,
+                                                     c->nodesf);
     SPH_LAUNCH_CHECK(c, "k_boxes");
     return SPH_OK;
 }

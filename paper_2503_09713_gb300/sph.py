@@ -56,6 +56,7 @@ class sph_tree_view(ctypes.Structure):
 
 class sph_stats(ctypes.Structure):
     _fields_ = [("n", _i64), ("n_leaves", _i64), ("n_groups", _i64), ("n_pairs", _i64), ("cache_slots", _i64),
+                ("cand_chunks", _i64),
                 ("density_iters_max", _i), ("outer_passes", _i), ("n_red", _i), ("dt_next", _d), ("dv_ratio", _d),
                 ("kernel_launches", _i64), ("density_pair_evals", _i64), ("density_inrange", _i64), ("force_pairs", _i64), ("stage_ms", _d * 8)]
 
