@@ -307,7 +307,8 @@ def main():
                        "l2": "inputs larger than L2 (state 0.3 GB, neighbour cache 0.8 GB per replica)",
                        "leaves": st["n_leaves"], "cache_pairs": st["n_pairs"],
                        "density_iters_max": st["density_iters_max"],
-                       "density_passes_avg": st["density_pair_evals"] / max(st["n_pairs"], 1)},
+                       "density_passes_avg": st["density_pair_evals"] / max(st["n_pairs"], 1),
+                       "cache_slots": st["cache_slots"], "stage2_chunks": st["cand_chunks"]},
             "clocks": r64["clocks"], "gpu_launches": int(round(r64["launches_per_step"] * args.steps)),
             "roofline": roofline}
 

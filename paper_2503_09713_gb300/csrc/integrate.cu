@@ -16,9 +16,15 @@ struct IntParams {
 };
 
 // x - L floor((x-lo)/L); a result equal to hi (rounding of a tiny negative offset) becomes lo.
+// A particle moves less than a box length per step, so the floor is -1, 0 or 1: taken by compares
+// (the same values as the quotient form), with the quotient form kept for anything further out.
 __device__ __forceinline__ double wrap(double x, double lo, double hi) {
     const double L = hi - lo;
-    double w = x - L * floor((x - lo) / L);
+    double w;
+    if (x >= lo && x < hi) return x;
+    if (x >= hi && x < hi + L) w = x - L;
+    else if (x < lo && x >= lo - L) w = x + L;
+    else w = x - L * floor((x - lo) / L);
     if (w >= hi) w = lo;
     if (w < lo) w = lo;
     return w;

@@ -243,6 +243,7 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2_count(
     grel(Araw, ax, ay, az);
     const float hA = va ? h32[a] : 0.f;
     const float tA = (s32 * hA) * (s32 * hA);
+    const float tAhi = tA * kBandHi;
     const Node q = gbox[g];
     const double hroot = nodes[0].hmax;
     const float ext = (float)fmax(fmax(q.hi[0] - q.lo[0], q.hi[1] - q.lo[1]), q.hi[2] - q.lo[2]);
@@ -266,22 +267,21 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2_count(
                 if (compact) {
                     float px, py, pz;
                     grel(P, px, py, pz);
-                    P = make_float4(px, py, pz, (s32 * hb) * (s32 * hb));
+                    P = make_float4(px, py, pz, (s32 * hb) * (s32 * hb) * kBandHi);
                 }
             }
             s_pos[warp][lane] = P;
             s_h[warp][lane] = hb;
             __syncwarp();
-            uint32_t hi_mask = 0, lo_mask = 0;
+            // candidates within the upper band edge: r^2 <= (s max(h_a, h_b))^2 (1 + 2^-10)
+            uint32_t hit = 0;
             if (compact) {
-#pragma unroll 8
+#pragma unroll
                 for (int jj = 0; jj < 32; jj++) {
                     const float4 B = s_pos[warp][jj];
                     const float dx = B.x - ax, dy = B.y - ay, dz = B.z - az;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    const float thr = fmaxf(tA, B.w);
-                    hi_mask |= (uint32_t)(r2 <= thr * kBandHi) << jj;
-                    lo_mask |= (uint32_t)(r2 < thr * kBandLo) << jj;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    if (r2 <= fmaxf(tAhi, B.w)) hit |= 1u << jj;
                 }
             } else {
                 const int m = (rg.y - base) < 32 ? (int)(rg.y - base) : 32;
@@ -292,28 +292,38 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2_count(
                     const float dx = fmaf((float)wrap_cell(cb[0] - ca[0], geo.periodic), geo.cell[0], B.x - Araw.x);
                     const float dy = fmaf((float)wrap_cell(cb[1] - ca[1], geo.periodic), geo.cell[1], B.y - Araw.y);
                     const float dz = fmaf((float)wrap_cell(cb[2] - ca[2], geo.periodic), geo.cell[2], B.z - Araw.z);
-                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     const float hm = fmaxf(hA, s_h[warp][jj]);
-                    const float thr = va ? (s32 * hm) * (s32 * hm) : -1.f;
-                    hi_mask |= (uint32_t)(r2 <= thr * kBandHi) << jj;
-                    lo_mask |= (uint32_t)(r2 < thr * kBandLo) << jj;
+                    if (r2 <= (s32 * hm) * (s32 * hm) * kBandHi) hit |= 1u << jj;
                 }
             }
-            if (!va) hi_mask = lo_mask = 0;   // lanes past n keep nothing
-            // the particle itself is not its own neighbour
-            if (a >= base && a < base + 32) {
-                hi_mask &= ~(1u << (uint32_t)(a - base));
-                lo_mask &= ~(1u << (uint32_t)(a - base));
+            if (!va) hit = 0;   // lanes past n keep nothing
+            if (a >= base && a < base + 32) hit &= ~(1u << (uint32_t)(a - base));   // not its own neighbour
+            // the hits: inside the lower band edge they are neighbours; in the band, FP64 decides
+            uint32_t todo = hit;
+            while (todo) {
+                const int jj = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const float hm = fmaxf(hA, s_h[warp][jj]);
+                const float t = (s32 * hm) * (s32 * hm);
+                float r2;
+                if (compact) {
+                    const float4 B = s_pos[warp][jj];
+                    const float dx = B.x - ax, dy = B.y - ay, dz = B.z - az;
+                    r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                } else {
+                    const float4 B = s_pos[warp][jj];
+                    int cb[3];
+                    unpack_cell(B, cb[0], cb[1], cb[2]);
+                    const float dx = fmaf((float)wrap_cell(cb[0] - ca[0], geo.periodic), geo.cell[0], B.x - Araw.x);
+                    const float dy = fmaf((float)wrap_cell(cb[1] - ca[1], geo.periodic), geo.cell[1], B.y - Araw.y);
+                    const float dz = fmaf((float)wrap_cell(cb[2] - ca[2], geo.periodic), geo.cell[2], B.z - Araw.z);
+                    r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                }
+                if (!(r2 < t * kBandLo) && !exact_pair(a, base + jj, x, y, z, h, s, geo)) hit &= ~(1u << jj);
             }
-            // candidates inside the band: decide in FP64
-            uint32_t band = hi_mask & ~lo_mask;
-            while (band) {
-                const int jj = __ffs(band) - 1;
-                band &= band - 1;
-                if (!exact_pair(a, base + jj, x, y, z, h, s, geo)) hi_mask &= ~(1u << jj);
-            }
-            gm[(size_t)chunk * 32] = hi_mask;
-            cnt += __popc(hi_mask);
+            gm[(size_t)chunk * 32] = hit;
+            cnt += __popc(hit);
             __syncwarp();
         }
     }

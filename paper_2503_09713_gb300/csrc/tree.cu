@@ -2,6 +2,7 @@
 // reorder of the particle arrays, duplicate mask + reduction passes (Alg. mortonmask), compaction
 // into leaves, Karras radix tree (Table arrays_fig_karras) and bottom-up tight boxes + h_max.
 #include <cuda/atomic>
+#include <cmath>
 #include <mutex>
 
 #include "sph_internal.cuh"
@@ -21,9 +22,10 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v) {
 }
 
 // App. B "Morton codes": remap to [0,1) by (x-lo)/(hi-lo), integer grid of 2^21 per axis,
-// interleave X0 Y0 Z0 X1 ... with x most significant.
-__device__ __forceinline__ uint64_t quantise(double x, double lo, double span) {
-    double s = (x - lo) / span;
+// interleave X0 Y0 Z0 X1 ... with x most significant.  inv_span is 1/span when span is a power of
+// two (then the product equals the quotient bit for bit) and 0 otherwise (divide).
+__device__ __forceinline__ uint64_t quantise(double x, double lo, double span, double inv_span) {
+    double s = inv_span != 0.0 ? (x - lo) * inv_span : (x - lo) / span;
     double g = s * 2097152.0;  // 2^21, exact scale
     const double top = 2097151.0;
     if (!(g >= 0.0)) g = 0.0;
@@ -33,6 +35,7 @@ __device__ __forceinline__ uint64_t quantise(double x, double lo, double span) {
 
 struct Box3 {
     double lo[3], span[3];
+    double inv_span[3];   // exact reciprocal when span is a power of two, else 0
 };
 
 __global__ void k_morton(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
@@ -43,9 +46,9 @@ __global__ void k_morton(int64_t n, const double *__restrict__ x, const double *
     const double px = x[i], py = y[i], pz = z[i], ph = h[i];
     if (!isfinite(px) || !isfinite(py) || !isfinite(pz) || !isfinite(ph) || !(ph > 0.0))
         atomicOr(flags, kErrNonFinite);
-    const uint64_t X = quantise(px, b.lo[0], b.span[0]);
-    const uint64_t Y = quantise(py, b.lo[1], b.span[1]);
-    const uint64_t Z = quantise(pz, b.lo[2], b.span[2]);
+    const uint64_t X = quantise(px, b.lo[0], b.span[0], b.inv_span[0]);
+    const uint64_t Y = quantise(py, b.lo[1], b.span[1], b.inv_span[1]);
+    const uint64_t Z = quantise(pz, b.lo[2], b.span[2], b.inv_span[2]);
     keys[i] = (spread3(X) << 2) | (spread3(Y) << 1) | spread3(Z);
     vals[i] = (uint32_t)i;
 }
@@ -267,7 +270,7 @@ __global__ void k_rel(int64_t n, const double *__restrict__ x, const double *__r
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         const double cell = b.span[k] * (1.0 / 1024.0);
-        double g = floor((p[k] - b.lo[k]) / cell);
+        double g = floor(b.inv_span[k] != 0.0 ? (p[k] - b.lo[k]) * (1024.0 * b.inv_span[k]) : (p[k] - b.lo[k]) / cell);
         if (!(g >= 0.0)) g = 0.0;
         if (g > 1023.0) g = 1023.0;
         ci[k] = (uint32_t)g;
@@ -454,11 +457,18 @@ __global__ void k_boxes(int64_t L, const int64_t *__restrict__ leaf_first, const
     }
 }
 
+static double pow2_reciprocal(double v) {
+    int e = 0;
+    const double m = std::frexp(v, &e);
+    return (m == 0.5) ? std::ldexp(1.0, 1 - e) : 0.0;
+}
+
 static Box3 make_box(const sph_params &p) {
     Box3 b;
     for (int k = 0; k < 3; k++) {
         b.lo[k] = p.box_lo[k];
         b.span[k] = p.box_hi[k] - p.box_lo[k];
+        b.inv_span[k] = pow2_reciprocal(b.span[k]);
     }
     return b;
 }
@@ -614,9 +624,9 @@ __global__ void k_morton_codes(int64_t n, const double *__restrict__ x, const do
                                uint32_t *__restrict__ vals) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint64_t X = quantise(x[i], b.lo[0], b.span[0]);
-    const uint64_t Y = quantise(y[i], b.lo[1], b.span[1]);
-    const uint64_t Z = quantise(z[i], b.lo[2], b.span[2]);
+    const uint64_t X = quantise(x[i], b.lo[0], b.span[0], b.inv_span[0]);
+    const uint64_t Y = quantise(y[i], b.lo[1], b.span[1], b.inv_span[1]);
+    const uint64_t Z = quantise(z[i], b.lo[2], b.span[2], b.inv_span[2]);
     keys[i] = (spread3(X) << 2) | (spread3(Y) << 1) | spread3(Z);
     vals[i] = (uint32_t)i;
 }
@@ -654,6 +664,7 @@ extern "C" int sph_sort_morton_noalloc(int64_t n, const double *x, const double 
         if (!(box_hi[k] > box_lo[k])) return SPH_ERR_INVALID_ARG;
         b.lo[k] = box_lo[k];
         b.span[k] = box_hi[k] - box_lo[k];
+        b.inv_span[k] = pow2_reciprocal(b.span[k]);
     }
     NoAllocScratch *sc = nullptr;
     int r = noalloc_scratch(&sc);

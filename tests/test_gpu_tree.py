@@ -9,13 +9,13 @@ from gpu_common import random_positions, require_gpu
 pytestmark = pytest.mark.gpu
 
 
-def _build(x, y, z, h, n_red):
+def _build(x, y, z, h, n_red, lo=(0, 0, 0), hi=(1, 1, 1)):
     require_gpu()
     from paper_2503_09713_gb300 import sph
     n = len(x)
     d = {"x": x, "y": y, "z": z, "h": h, "mass": 1.0 / n}
     s = sph.DeviceState.from_numpy(d)
-    solver = sph.Solver(sph.default_params(reduction_level=n_red), n)
+    solver = sph.Solver(sph.default_params(reduction_level=n_red, box_lo=lo, box_hi=hi), n)
     solver.build_tree(s)
     t = solver.export_tree()
     out = s.to_numpy()
@@ -23,9 +23,9 @@ def _build(x, y, z, h, n_red):
     return t, out
 
 
-def _check_against_oracle(x, y, z, h, n_red):
-    t, out = _build(x, y, z, h, n_red)
-    m = O.morton(x, y, z)
+def _check_against_oracle(x, y, z, h, n_red, lo=(0, 0, 0), hi=(1, 1, 1)):
+    t, out = _build(x, y, z, h, n_red, lo, hi)
+    m = O.morton(x, y, z, lo, hi)
     mu, perm = O.sort_by_key(m)
     assert np.array_equal(t["mu"], mu)
     assert np.array_equal(t["perm"], perm)
@@ -51,6 +51,15 @@ def test_tree_bit_exact(kind, n, n_red):
     h = np.random.default_rng(5).uniform(0.01, 0.02, size=n)
     L = _check_against_oracle(x, y, z, h, n_red)
     assert 1 <= L <= n
+
+
+@pytest.mark.parametrize("lo,hi", [((-0.6, -0.6, -0.6), (0.6, 0.6, 0.6)), ((-1.0, 0.0, 2.0), (1.0, 4.0, 2.5))])
+def test_tree_other_boxes(lo, hi):
+    """Boxes whose sides are not 1: span 1.2 (quotient path) and spans 2, 4, 0.5 (power-of-two path)."""
+    x, y, z = random_positions(6000, 21, "uniform")
+    lo, hi = np.array(lo), np.array(hi)
+    x, y, z = [lo[k] + (hi[k] - lo[k]) * p for k, p in enumerate((x, y, z))]
+    _check_against_oracle(x, y, z, np.full(6000, 0.05), 2, tuple(lo), tuple(hi))
 
 
 def test_tree_lattice_reduction_levels():
