@@ -12,6 +12,8 @@
 // is the FP64 set.  The count pass stores, per 32-candidate chunk and lane, the bit mask of kept
 // candidates; after a scan over groups the fill pass only expands those masks.  Layout of the cache:
 // particle a = 32g + lane owns entries off_g + 32k + lane, k < count_a.
+#include <cuda/atomic>
+
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -208,23 +210,35 @@ constexpr int kS2Warps = 4;
 constexpr float kBandLo = 1.0f - 1.0f / 1024.0f;
 constexpr float kBandHi = 1.0f + 1.0f / 1024.0f;
 
-// Count pass.  Every particle (the group's and the candidates') is expressed in FP32 relative to the
-// cell of the group's first particle, the periodic wrap done once per particle on the integer cell
-// index, so a test is three differences, r^2 and compares.  A true neighbour b of a group particle
-// lies within ext + s*h_max of that cell (ext: group extent, h_max: largest h in the tree), so its
-// wrapped coordinate is its nearest image whenever ext + s*h_max is below half a box; the kernel
-// asks for a quarter box (warp-uniform), otherwise every separation is wrapped on its own.
-__global__ void __launch_bounds__(kS2Warps * 32) k_stage2_count(
+constexpr unsigned long long kGrpAgg = 1ULL << 62;
+constexpr unsigned long long kGrpInc = 2ULL << 62;
+constexpr unsigned long long kGrpVal = (1ULL << 62) - 1;
+constexpr uint32_t kGrpSpinLimit = 1u << 22;
+
+// Stage 2 in one pass.  Groups are taken in launch order from a ticket.  For its group a warp
+// (1) tests the candidates and keeps, per 32-candidate chunk and lane, the bit mask of kept
+// candidates; (2) obtains the group's offset in the cache by decoupled look-back over the
+// preceding groups (the group needs 32 x its largest count entries); (3) expands its masks, which
+// are still in L2, into the cache.  Tests run in FP32 relative to the cell of the group's first
+// particle, the periodic wrap done once per particle on the integer cell index.  A true neighbour
+// b of a group particle lies within ext + s*h_max of that cell (ext: group extent, h_max: largest h
+// in the tree), so its wrapped coordinate is its nearest image whenever ext + s*h_max is below half
+// a box; the kernel asks for a quarter box (warp-uniform), otherwise every separation is wrapped on
+// its own.  Pairs within a relative 2^-10 of the radius are decided in FP64 (exact_pair).
+__global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
     int64_t n, int64_t G, const uint2 *__restrict__ cand, const uint32_t *__restrict__ cand_cnt, int cap,
     const int64_t *__restrict__ chunk_off, const Node *__restrict__ gbox, const Node *__restrict__ nodes,
     const float4 *__restrict__ rel, const float *__restrict__ h32, const double *__restrict__ x,
     const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h, double s,
     float quarter_box, Geo geo, uint32_t *__restrict__ masks, uint32_t *__restrict__ nb_cnt,
-    int64_t *__restrict__ grp_slots, DevScalars *sc) {
+    unsigned long long *lookback, uint32_t *ticket, int64_t *__restrict__ grp_off, uint32_t *__restrict__ nb_ids,
+    int64_t nb_cap, DevScalars *sc) {
     __shared__ float4 s_pos[kS2Warps][32];
-    __shared__ float s_h[kS2Warps][32];
+    __shared__ float2 s_t[kS2Warps][32];   // (s h_b)^2 (1 - 2^-10), h_b
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * kS2Warps + warp;
+    int64_t g = 0;
+    if (lane == 0) g = atomicAdd(ticket, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
     if (g >= G) return;
     const int64_t a = g * 32 + lane;
     const bool va = a < n;
@@ -239,11 +253,24 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2_count(
         py = fmaf((float)wrap_cell(cy - rcy, geo.periodic), geo.cell[1], P.y);
         pz = fmaf((float)wrap_cell(cz - rcz, geo.periodic), geo.cell[2], P.z);
     };
+    auto sep2 = [&](const float4 B, bool compact_path, float axr, float ayr, float azr, const int *ca) {
+        float dx, dy, dz;
+        if (compact_path) {
+            dx = B.x - axr; dy = B.y - ayr; dz = B.z - azr;
+        } else {
+            int cb[3];
+            unpack_cell(B, cb[0], cb[1], cb[2]);
+            dx = fmaf((float)wrap_cell(cb[0] - ca[0], geo.periodic), geo.cell[0], B.x - Araw.x);
+            dy = fmaf((float)wrap_cell(cb[1] - ca[1], geo.periodic), geo.cell[1], B.y - Araw.y);
+            dz = fmaf((float)wrap_cell(cb[2] - ca[2], geo.periodic), geo.cell[2], B.z - Araw.z);
+        }
+        return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    };
     float ax, ay, az;
     grel(Araw, ax, ay, az);
     const float hA = va ? h32[a] : 0.f;
     const float tA = (s32 * hA) * (s32 * hA);
-    const float tAhi = tA * kBandHi;
+    const float tAhi = tA * kBandHi, tAlo = tA * kBandLo;
     const Node q = gbox[g];
     const double hroot = nodes[0].hmax;
     const float ext = (float)fmax(fmax(q.hi[0] - q.lo[0], q.hi[1] - q.lo[1]), q.hi[2] - q.lo[2]);
@@ -255,6 +282,7 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2_count(
     uint32_t *gm = masks + (size_t)chunk_off[g] * 32 + lane;
     uint32_t cnt = 0;
     int64_t chunk = 0;
+    // ---- (1) tests
     for (int ci = 0; ci < ncand; ci++) {
         const uint2 rg = cl[ci];
         for (int64_t base = rg.x; base < rg.y; base += 32, ++chunk) {
@@ -271,59 +299,40 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2_count(
                 }
             }
             s_pos[warp][lane] = P;
-            s_h[warp][lane] = hb;
+            s_t[warp][lane] = make_float2((s32 * hb) * (s32 * hb) * kBandLo, hb);
             __syncwarp();
-            // candidates within the upper band edge: r^2 <= (s max(h_a, h_b))^2 (1 + 2^-10)
-            uint32_t hit = 0;
+            uint32_t hi = 0, lo = 0;
             if (compact) {
 #pragma unroll
                 for (int jj = 0; jj < 32; jj++) {
                     const float4 B = s_pos[warp][jj];
-                    const float dx = B.x - ax, dy = B.y - ay, dz = B.z - az;
-                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    if (r2 <= fmaxf(tAhi, B.w)) hit |= 1u << jj;
+                    const float r2 = sep2(B, true, ax, ay, az, ca);
+                    if (r2 <= fmaxf(tAhi, B.w)) hi |= 1u << jj;
+                    if (r2 < fmaxf(tAlo, s_t[warp][jj].x)) lo |= 1u << jj;
                 }
             } else {
                 const int m = (rg.y - base) < 32 ? (int)(rg.y - base) : 32;
                 for (int jj = 0; jj < m; jj++) {
-                    const float4 B = s_pos[warp][jj];
-                    int cb[3];
-                    unpack_cell(B, cb[0], cb[1], cb[2]);
-                    const float dx = fmaf((float)wrap_cell(cb[0] - ca[0], geo.periodic), geo.cell[0], B.x - Araw.x);
-                    const float dy = fmaf((float)wrap_cell(cb[1] - ca[1], geo.periodic), geo.cell[1], B.y - Araw.y);
-                    const float dz = fmaf((float)wrap_cell(cb[2] - ca[2], geo.periodic), geo.cell[2], B.z - Araw.z);
-                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    const float hm = fmaxf(hA, s_h[warp][jj]);
-                    if (r2 <= (s32 * hm) * (s32 * hm) * kBandHi) hit |= 1u << jj;
+                    const float r2 = sep2(s_pos[warp][jj], false, ax, ay, az, ca);
+                    const float hm = fmaxf(hA, s_t[warp][jj].y);
+                    const float t = (s32 * hm) * (s32 * hm);
+                    if (r2 <= t * kBandHi) hi |= 1u << jj;
+                    if (r2 < t * kBandLo) lo |= 1u << jj;
                 }
             }
-            if (!va) hit = 0;   // lanes past n keep nothing
-            if (a >= base && a < base + 32) hit &= ~(1u << (uint32_t)(a - base));   // not its own neighbour
-            // the hits: inside the lower band edge they are neighbours; in the band, FP64 decides
-            uint32_t todo = hit;
-            while (todo) {
-                const int jj = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const float hm = fmaxf(hA, s_h[warp][jj]);
-                const float t = (s32 * hm) * (s32 * hm);
-                float r2;
-                if (compact) {
-                    const float4 B = s_pos[warp][jj];
-                    const float dx = B.x - ax, dy = B.y - ay, dz = B.z - az;
-                    r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                } else {
-                    const float4 B = s_pos[warp][jj];
-                    int cb[3];
-                    unpack_cell(B, cb[0], cb[1], cb[2]);
-                    const float dx = fmaf((float)wrap_cell(cb[0] - ca[0], geo.periodic), geo.cell[0], B.x - Araw.x);
-                    const float dy = fmaf((float)wrap_cell(cb[1] - ca[1], geo.periodic), geo.cell[1], B.y - Araw.y);
-                    const float dz = fmaf((float)wrap_cell(cb[2] - ca[2], geo.periodic), geo.cell[2], B.z - Araw.z);
-                    r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                }
-                if (!(r2 < t * kBandLo) && !exact_pair(a, base + jj, x, y, z, h, s, geo)) hit &= ~(1u << jj);
+            if (!va) hi = lo = 0;   // lanes past n keep nothing
+            if (a >= base && a < base + 32) {   // not its own neighbour
+                hi &= ~(1u << (uint32_t)(a - base));
+                lo &= ~(1u << (uint32_t)(a - base));
             }
-            gm[(size_t)chunk * 32] = hit;
-            cnt += __popc(hit);
+            uint32_t band = hi & ~lo;   // inside the band: FP64 decides
+            while (band) {
+                const int jj = __ffs(band) - 1;
+                band &= band - 1;
+                if (!exact_pair(a, base + jj, x, y, z, h, s, geo)) hi &= ~(1u << jj);
+            }
+            gm[(size_t)chunk * 32] = hi;
+            cnt += __popc(hi);
             __syncwarp();
         }
     }
@@ -333,29 +342,60 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2_count(
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         sum += __shfl_xor_sync(0xffffffffu, sum, o);
     }
+    const unsigned long long slots = (unsigned long long)mx * 32ULL;
+    // ---- (2) decoupled look-back over the preceding groups (lane k reads group g-1-k)
     if (lane == 0) {
-        grp_slots[g] = (int64_t)mx * 32;
+        cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> mine(lookback[g]);
+        mine.store((g == 0 ? kGrpInc : kGrpAgg) | slots, cuda::memory_order_relaxed);
+    }
+    unsigned long long excl = 0;
+    if (g > 0) {
+        int64_t jb = g - 1;
+        uint32_t spins = 0;
+        for (;;) {
+            const int64_t j = jb - lane;
+            unsigned long long w = kGrpInc;   // before the first group: inclusive zero
+            if (j >= 0) {
+                cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> other(lookback[j]);
+                w = other.load(cuda::memory_order_relaxed);
+            }
+            const unsigned long long fl = w & ~kGrpVal;
+            const unsigned inc = __ballot_sync(0xffffffffu, fl == kGrpInc);
+            const unsigned notready = __ballot_sync(0xffffffffu, fl == 0ULL);
+            const unsigned need = inc ? (((inc & (0u - inc)) << 1) - 1u) : 0xffffffffu;
+            if (notready & need) {
+                if (++spins > kGrpSpinLimit) {
+                    if (lane == 0) atomicOr(&sc->flags, kErrTimeout);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            unsigned long long v = ((1u << lane) & need) ? (w & kGrpVal) : 0ULL;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            excl += v;
+            if (inc) break;
+            jb -= 32;
+        }
+        if (lane == 0) {
+            cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> mine(lookback[g]);
+            mine.store(kGrpInc | (excl + slots), cuda::memory_order_relaxed);
+        }
+    }
+    const int64_t off_g = (int64_t)excl;
+    if (lane == 0) {
+        grp_off[g] = off_g;
+        if (g == G - 1) grp_off[G] = off_g + (int64_t)slots;
         atomicAdd((unsigned long long *)&sc->n_pairs, (unsigned long long)sum);
     }
-}
-
-// Fill pass: expand the masks of the count pass into the cache, in candidate order.
-__global__ void __launch_bounds__(128) k_stage2_fill(int64_t G, const uint2 *__restrict__ cand,
-                                                     const uint32_t *__restrict__ cand_cnt, int cap,
-                                                     const int64_t *__restrict__ chunk_off,
-                                                     const uint32_t *__restrict__ masks,
-                                                     const int64_t *__restrict__ grp_off,
-                                                     uint32_t *__restrict__ nb_ids) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (g >= G) return;
-    const uint2 *cl = cand + (size_t)g * cap;
-    const int ncand = (int)min(cand_cnt[g], (uint32_t)cap);
-    const uint32_t *gm = masks + (size_t)chunk_off[g] * 32 + lane;
-    const int64_t off = grp_off[g] + lane;
-    const uint32_t slots = (uint32_t)((grp_off[g + 1] - grp_off[g]) / 32);
-    uint32_t cnt = 0;
-    int64_t chunk = 0;
+    if (off_g + (int64_t)slots > nb_cap) {   // cache too small: the host grows it and runs again
+        if (lane == 0) atomicOr(&sc->flags, kErrCandOverflow);
+        return;
+    }
+    // ---- (3) expand the masks into the cache
+    const int64_t off = off_g + lane;
+    uint32_t k = 0;
+    chunk = 0;
     for (int ci = 0; ci < ncand; ci++) {
         const uint2 rg = cl[ci];
         for (int64_t base = rg.x; base < rg.y; base += 32, ++chunk) {
@@ -363,8 +403,8 @@ __global__ void __launch_bounds__(128) k_stage2_fill(int64_t G, const uint2 *__r
             while (m) {
                 const int jj = __ffs(m) - 1;
                 m &= m - 1;
-                if (cnt < slots) nb_ids[off + (int64_t)cnt * 32] = (uint32_t)(base + jj);
-                ++cnt;
+                nb_ids[off + (int64_t)k * 32] = (uint32_t)(base + jj);
+                ++k;
             }
         }
     }
@@ -440,28 +480,34 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
     int r = ensure(c, &c->masks, c->masks_cap, chunks * 32, "candidate masks");
     if (r) return r;
 
-    // stage 2: count (and masks), scan, fill
-    SPH_CUDA(c, cudaMemsetAsync(&c->dscal->n_pairs, 0, sizeof(int64_t), c->stream));
+    // stage 2 in one pass; if the cache turns out too small it grows and the pass runs again
     const unsigned blocks = grid_for(G, kS2Warps);
     const float qbox = (float)(0.25 * fmin(fmin(geo.L[0], geo.L[1]), geo.L[2]));
-    k_stage2_count<<<blocks, kS2Warps * 32, 0, c->stream>>>(n, G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off,
-                                                            c->gbox, c->nodes, c->rel, c->h32, s->x, s->y, s->z,
-                                                            s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->grp_slots,
-                                                            c->dscal);
-    SPH_LAUNCH_CHECK(c, "k_stage2_count");
-    r = exclusive_scan_i64(c, c->grp_slots, c->grp_off, G);
-    if (r) return r;
-    SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->total_slots, &c->grp_off[G], sizeof(int64_t), cudaMemcpyDeviceToHost,
-                                c->stream));
-    SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->n_pairs, &c->dscal->n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost,
-                                c->stream));
-    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
-    const int64_t total = c->hscal->total_slots;
-    r = ensure(c, &c->nb_ids, c->nb_cap, total, "neighbour cache");
-    if (r) return r;
-    k_stage2_fill<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off,
-                                                                c->masks, c->grp_off, c->nb_ids);
-    SPH_LAUNCH_CHECK(c, "k_stage2_fill");
+    int64_t total = 0;
+    for (int attempt = 0;; attempt++) {
+        SPH_CUDA(c, cudaMemsetAsync(&c->dscal->n_pairs, 0, sizeof(int64_t), c->stream));
+        SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
+        SPH_CUDA(c, cudaMemsetAsync(&c->dscal->s2_ticket, 0, sizeof(uint32_t), c->stream));
+        SPH_CUDA(c, cudaMemsetAsync(c->grp_slots, 0, (size_t)G * sizeof(int64_t), c->stream));
+        k_stage2<<<blocks, kS2Warps * 32, 0, c->stream>>>(
+            n, G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->gbox, c->nodes, c->rel, c->h32, s->x, s->y,
+            s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket,
+            c->grp_off, c->nb_ids, c->nb_cap, c->dscal);
+        SPH_LAUNCH_CHECK(c, "k_stage2");
+        SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->total_slots, &c->grp_off[G], sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->n_pairs, &c->dscal->n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->flags, &c->dscal->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (c->hscal->flags & kErrTimeout) return fail(c, SPH_ERR_TIMEOUT, "stage-2 look-back wait ran out");
+        total = c->hscal->total_slots;
+        if (!(c->hscal->flags & kErrCandOverflow) && total <= c->nb_cap) break;
+        if (attempt >= 2) return fail(c, SPH_ERR_CAPACITY, "neighbour cache does not fit");
+        r = ensure(c, &c->nb_ids, c->nb_cap, total, "neighbour cache");
+        if (r) return r;
+    }
     c->total_slots = total;
     c->n_pairs = c->hscal->n_pairs;
     c->stats.n_pairs = c->n_pairs;

@@ -64,6 +64,8 @@ struct DevScalars {
     int64_t n_pairs;                  // real pairs
     uint32_t max_iters;
     uint32_t flags;
+    uint32_t s2_ticket;               // stage-2 group ticket
+    uint32_t pad_;
     unsigned long long pair_evals;    // density: neighbour evaluations summed over Newton passes
     unsigned long long dens_inrange;  // density: evaluations with q < 2
     unsigned long long inrange_pairs; // forces: pairs inside 2 max(h_a, h_b)
@@ -162,7 +164,7 @@ struct sph_ctx {
     uint32_t *cand_cnt = nullptr;      // [groups]
     int cand_cap = 0;
     uint32_t *nb_cnt = nullptr;        // [n_cap] per-particle neighbour count
-    int64_t *grp_slots = nullptr;      // [groups + 1] -> exclusive scan = group offsets
+    int64_t *grp_slots = nullptr;      // [groups + 1] stage-2 look-back words
     int64_t *grp_off = nullptr;        // [groups + 1]
     uint32_t *nb_ids = nullptr;        // cache entries, group-interleaved: off_g + k*32 + lane
     int64_t nb_cap = 0;

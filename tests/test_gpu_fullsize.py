@@ -1,0 +1,156 @@
+"""Parity at the sizes of the benchmark workloads, in the launch configuration bench.py times.
+
+* uniform 32^3 (32,768 particles, FP64 and mixed): every particle against the oracle, for the
+  converged initial state and for one full KDK step.
+* Sedov 128^3 (2,097,152 particles, FP64, the benchmark workload): every particle against the
+  oracle (uniform-grid candidates, OpenMP) for the tree, the converged state and one step;
+  neighbour sets of sampled particles against brute force.
+* uniform 256^3 (16,777,216 particles): mixed precision against FP64 for every particle
+  (density <= 1e-5 relative, accelerations <= 1e-4 of max|a|), sampled particles of the FP64 run
+  against the oracle's definitions evaluated one by one.
+
+Tolerances as in test_gpu_physics (h: 1e-9 relative, from Newton's quadratic convergence after
+|dh|/h <= 1e-6; accelerations on the same h: summation order only).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import require_gpu, to_orig
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du", "rho", "omega", "vsig")
+
+
+def _orig(out):
+    ids = out["id"].astype(np.int64)
+    return {k: to_orig(out[k], ids) for k in FIELDS}
+
+
+def _oracle_converged(w, P):
+    h, rho, om, _, _ = O.density_algF(w["x"], w["y"], w["z"], w["h"], w["mass"], P)
+    ax, ay, az, du, vs = O.forces(w["x"], w["y"], w["z"], w["vx"], w["vy"], w["vz"], w["u"], h, om, w["mass"], P)
+    st = {k: w[k].copy() for k in ("x", "y", "z", "vx", "vy", "vz", "u")}
+    st.update(h=h, rho=rho, omega=om, ax=ax, ay=ay, az=az, du=du, vsig=vs)
+    return st
+
+
+def _compare_state(g, ref, precision, what):
+    amax = np.max(np.abs(np.stack([ref["ax"], ref["ay"], ref["az"]])))
+    if precision == 0:
+        tol_h, tol_a, tol_rho = 1e-9, 1e-8 * amax, 3e-9
+    else:
+        tol_h, tol_a, tol_rho = 1e-5, 1e-4 * amax, 1e-5
+    assert np.max(np.abs(g["h"] / ref["h"] - 1)) < tol_h, what + " h"
+    assert np.max(np.abs(g["rho"] / ref["rho"] - 1)) < tol_rho, what + " rho"
+    for k in ("ax", "ay", "az"):
+        assert np.max(np.abs(g[k] - ref[k])) < tol_a, what + " " + k
+    dumax = np.max(np.abs(ref["du"]))
+    assert np.max(np.abs(g["du"] - ref["du"])) < (1e-8 if precision == 0 else 1e-4) * dumax + 1e-300, what + " du"
+    for k in ("x", "y", "z"):
+        d = np.abs(g[k] - ref[k])
+        assert np.max(np.minimum(d, 1.0 - d)) < 1e-13, what + " " + k
+
+
+def _gpu_converged_and_step(w, ref0, precision, dt):
+    from paper_2503_09713_gb300 import sph
+    s = sph.DeviceState.from_numpy(w)
+    solver = sph.Solver(sph.default_params(precision=precision), w["n"])
+    solver.converge(s)
+    g0 = _orig(s.to_numpy())
+    # one step from the oracle's converged state, with the oracle's dt
+    s1 = sph.DeviceState.from_numpy(dict(w, **{k: ref0[k] for k in ("h", "rho", "omega", "ax", "ay", "az", "du",
+                                                                       "vsig")}))
+    solver1 = sph.Solver(sph.default_params(precision=precision), w["n"])
+    used, _ = solver1.step(s1, dt)
+    g1 = _orig(s1.to_numpy())
+    solver.close()
+    solver1.close()
+    return g0, g1
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uniform32_every_particle(precision):
+    require_gpu()
+    from paper_2503_09713_gb300 import workloads
+    w = workloads.lattice(32, sigma_v=0.01, seed=12345)
+    P = O.Params()
+    ref0 = _oracle_converged(w, P)
+    dt = O.cfl(ref0["h"], ref0["vsig"], ref0["ax"], ref0["ay"], ref0["az"], P)
+    ref1 = {k: v.copy() for k, v in ref0.items()}
+    O.step(ref1, w["mass"], P, dt)
+    g0, g1 = _gpu_converged_and_step(w, ref0, precision, dt)
+    _compare_state(g0, ref0, precision, "converged")
+    _compare_state(g1, ref1, precision, "after one step")
+
+
+def test_sedov128_every_particle():
+    require_gpu()
+    from paper_2503_09713_gb300 import sph, workloads
+    w = workloads.sedov(128, seed=12346)
+    n = w["n"]
+    P = O.Params()
+    # tree at full size, bit-exact (default reduction level of the library)
+    p = sph.default_params()
+    s = sph.DeviceState.from_numpy(w)
+    solver = sph.Solver(p, n)
+    solver.build_tree(s)
+    t = solver.export_tree()
+    mu, perm = O.sort_by_key(O.morton(w["x"], w["y"], w["z"]))
+    assert np.array_equal(t["mu"], mu) and np.array_equal(t["perm"], perm)
+    xi = O.keep_mask(mu, 63, p.reduction_level)
+    idv, ml = O.compact(mu, xi)
+    assert np.array_equal(t["leaf_first"], idv)
+    tr = O.radix_tree(ml, 63)
+    for k in ("lchild", "rchild", "lflag", "rflag", "endrange"):
+        assert np.array_equal(t[k], getattr(tr, k)), k
+    bmin, bmax, hmax = O.cell_boxes(idv, tr.endrange, w["x"][perm], w["y"][perm], w["z"][perm], w["h"][perm])
+    assert np.array_equal(t["bmin"], bmin) and np.array_equal(t["bmax"], bmax) and np.array_equal(t["hmax"], hmax)
+    # neighbour sets of sampled particles (cache radius 2 chi max(h_a, h_b) at the initial h)
+    solver.find_neighbours(s)
+    off, ids = solver.export_neighbours(n)
+    gid = s.to_numpy()["id"].astype(np.int64)
+    rng = np.random.default_rng(3)
+    rows = np.concatenate([rng.integers(0, n, 48), np.arange(16)])
+    o_off, o_ids = O.subset_neighbours(w["x"], w["y"], w["z"], w["h"], 2.0 * 1.1, gid[rows])
+    for k, a in enumerate(rows):
+        assert np.array_equal(np.sort(gid[ids[off[a]:off[a + 1]]]), o_ids[o_off[k]:o_off[k + 1]])
+    solver.close()
+    # converged state and one step, every particle
+    ref0 = _oracle_converged(w, P)
+    dt = O.cfl(ref0["h"], ref0["vsig"], ref0["ax"], ref0["ay"], ref0["az"], P)
+    ref1 = {k: v.copy() for k, v in ref0.items()}
+    O.step(ref1, w["mass"], P, dt)
+    g0, g1 = _gpu_converged_and_step(w, ref0, 0, dt)
+    _compare_state(g0, ref0, 0, "converged")
+    _compare_state(g1, ref1, 0, "after one step")
+
+
+def test_uniform256_mixed_against_fp64_and_sampled_oracle():
+    torch = require_gpu()
+    from paper_2503_09713_gb300 import sph, workloads
+    w = workloads.lattice(256, sigma_v=0.1, seed=12347)
+    n = w["n"]
+    out = {}
+    for precision in (0, 1):
+        s = sph.DeviceState.from_numpy(w)
+        solver = sph.Solver(sph.default_params(precision=precision), n)
+        solver.converge(s)
+        out[precision] = _orig(s.to_numpy())
+        solver.close()
+        del s
+        torch.cuda.empty_cache()
+    g64, g32 = out[0], out[1]
+    assert np.max(np.abs(g32["rho"] / g64["rho"] - 1)) < 1e-5
+    amax = np.max(np.abs(np.stack([g64["ax"], g64["ay"], g64["az"]])))
+    for k in ("ax", "ay", "az"):
+        assert np.max(np.abs(g32[k] - g64[k])) < 1e-4 * amax
+    # sampled particles of the FP64 run against the definitions, evaluated one by one
+    rng = np.random.default_rng(9)
+    idx = rng.integers(0, n, 6)
+    r = O.subset_forces(w["x"], w["y"], w["z"], w["vx"], w["vy"], w["vz"], w["u"], w["mass"], O.Params(), idx,
+                        3.0 * w["dx"])
+    assert np.max(np.abs(g64["h"][idx] / r["h"] - 1)) < 1e-9
+    for k in ("ax", "ay", "az"):
+        assert np.max(np.abs(g64[k][idx] - r[k])) < 1e-8 * amax
