@@ -274,12 +274,9 @@ def main():
         r["solver"].close()
         return
     r64 = run_precision(torch, sph, w, 0, args.steps, max(args.warmup, 3), dist, True, clocks)
-    ms = r64["ms_per_step"]
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * world / (ms * 1e-3)
+    from paper_2503_09713_gb300 import replicas
+    ms = replicas.max_over_ranks(r64["ms_per_step"], dist, "cuda")
+    value = replicas.sum_over_ranks(n, dist, "cuda") / (ms * 1e-3)
 
     # roofline of the dominant kernel of the FP64 step (per-stage CUDA events on the library stream)
     st = r64["timing_stats"]
