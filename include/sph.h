@@ -129,6 +129,24 @@ void sph_default_params(sph_params *p);
  * scratch memory. Errors: INVALID_ARG, OOM, CUDA. */
 int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stream, sph_ctx **out);
 
+/* Batched ensemble of independent periodic boxes in one context (the ensemble workload of the
+ * benchmark; the paper runs one box per patch set, this packs many small ones so that every stage is
+ * one launch for all boxes).  Box b owns particles box_offsets[b] .. box_offsets[b+1]-1 of every
+ * state array (host int64[n_boxes+1], box_offsets[0] = 0); all boxes share the geometry and solver
+ * parameters of *p except the particle mass (host double[n_boxes], equal masses within a box) and
+ * the adiabatic index (host double[n_boxes], NULL: p->gamma).  Every entry point then works on all
+ * boxes at once: state->n must equal box_offsets[n_boxes] and state->mass is ignored; sph_build_tree
+ * reorders particles only inside their box; pairs never cross boxes; sph_step with dt > 0 advances
+ * every box by dt, with dt <= 0 each box by its own CFL step (sph_batch_dt), and reports the
+ * smallest as dt_used / dt_next.  The Morton codes carry the box index in their top bits and
+ * (63 - bits(n_boxes))/3 bits per axis.  Errors: INVALID_ARG (n_boxes outside [1, 4096], offsets not
+ * starting at 0 or decreasing, non-positive mass, gamma <= 1), OOM, CUDA. */
+int sph_batch_create(const sph_params *p, int n_boxes, const int64_t *box_offsets, const double *box_mass,
+                     const double *box_gamma, int64_t neigh_cap, void *stream, sph_ctx **out);
+
+/* CFL time step of each box from the last force evaluation of a batch context (host double[n_boxes]). */
+int sph_batch_dt(sph_ctx *ctx, double *dt_per_box);
+
 /* Free every buffer of the context (synchronises its stream).  NULL is accepted. */
 int sph_destroy(sph_ctx *ctx);
 

@@ -43,6 +43,16 @@ int stage_end(sph_ctx *c, int k) {
     return SPH_OK;
 }
 
+Groups make_groups(const sph_ctx *c, int64_t n) {
+    Groups g;
+    g.start = c->batch ? c->gstart : nullptr;
+    g.box = c->batch ? c->group_box : nullptr;
+    g.n = n;
+    return g;
+}
+
+int64_t group_count(const sph_ctx *c, int64_t n) { return c->batch ? c->batch_groups : (n + 31) / 32; }
+
 int read_scalars(sph_ctx *c) {
     SPH_CUDA(c, cudaMemcpyAsync(c->hscal, c->dscal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     SPH_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -74,7 +84,8 @@ void free_all(sph_ctx *c) {
                     c->endrange, c->lflag, c->rflag, c->child, c->node_parent, c->leaf_parent, c->visit, c->nodes, c->nodesf,
                     c->gather_tmp, c->id_tmp, c->rel, c->h32, c->h_base, c->gbox, c->gboxf, c->grp_chunks, c->chunk_off, c->masks, c->cand, c->cand_cnt, c->nb_cnt,
                     c->grp_slots, c->grp_off, c->nb_ids, c->frec, c->m_v, c->m_t, c->m_r, c->a_new, c->dhdt, c->block_part,
-                    c->hs_fields, c->hs_id, c->dscal};
+                    c->hs_fields, c->hs_id, c->dscal, c->box_of, c->box_mass, c->box_gamma, c->box_root,
+                    c->box_dt, c->box_dt_next, c->gstart, c->group_box};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hscal) cudaFreeHost(c->hscal);
@@ -102,7 +113,8 @@ int check_state(sph_ctx *c, const sph_state *s, bool need_vel) {
     if (!s) return fail(c, SPH_ERR_INVALID_ARG, "state is NULL");
     if (s->n < 1 || s->n > c->n_cap)
         return fail(c, SPH_ERR_INVALID_ARG, "n = %lld outside [1, %lld]", (long long)s->n, (long long)c->n_cap);
-    if (!(s->mass > 0)) return fail(c, SPH_ERR_INVALID_ARG, "mass must be positive");
+    if (!c->batch && !(s->mass > 0)) return fail(c, SPH_ERR_INVALID_ARG, "mass must be positive");
+    if (c->batch && s->n != c->n_cap) return fail(c, SPH_ERR_INVALID_ARG, "a batch state holds every box");
     if (!s->x || !s->y || !s->z || !s->h) return fail(c, SPH_ERR_INVALID_ARG, "x, y, z and h are required");
     if (need_vel && (!s->vx || !s->vy || !s->vz || !s->u || !s->ax || !s->ay || !s->az || !s->du || !s->rho ||
                      !s->omega || !s->vsig))
@@ -120,6 +132,11 @@ int finish_forces(sph_ctx *c) {
     c->dt_next = dt;
     c->stats.dt_next = dt;
     c->stats.force_pairs = (int64_t)c->hscal->inrange_pairs;
+    if (c->batch) {
+        std::vector<unsigned long long> bits((size_t)c->n_boxes);
+        SPH_CUDA(c, cudaMemcpy(bits.data(), c->box_dt_next, bits.size() * 8, cudaMemcpyDeviceToHost));
+        for (int b = 0; b < c->n_boxes; b++) std::memcpy(&c->h_box_dt[(size_t)b], &bits[(size_t)b], 8);
+    }
     if (c->hscal->flags & kErrTimeout) return fail(c, SPH_ERR_TIMEOUT, "device wait ran out");
     return SPH_OK;
 }
@@ -175,7 +192,13 @@ void sph_default_params(sph_params *p) {
     }
 }
 
-int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stream, sph_ctx **out) {
+}  // extern "C"
+
+namespace {
+
+// Context for n_cap particles split into at most (n_cap + 31)/32 + extra_groups groups.
+int create_ctx(const sph_params *p, int64_t n_cap, int64_t extra_groups, int n_boxes, int64_t neigh_cap,
+               void *stream, sph_ctx **out) {
     if (!out) return SPH_ERR_INVALID_ARG;
     *out = nullptr;
     sph_ctx *c = new (std::nothrow) sph_ctx();
@@ -193,7 +216,7 @@ int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stre
         return SPH_ERR_CUDA;
     }
     const int64_t N = n_cap;
-    const int64_t G = (N + 31) / 32;
+    const int64_t G = (N + 31) / 32 + extra_groups;
     const int64_t tiles = (N + 4095) / 4096;
     const int64_t chunks = (N + 2047) / 2048;
     c->sort_tiles = tiles;
@@ -217,7 +240,8 @@ int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stre
         (r = alloc(c, &c->grp_off, G + 1)) || (r = alloc(c, &c->nb_ids, c->nb_cap)) ||
         (r = alloc(c, (char **)&c->frec, (size_t)128 * N)) || (r = alloc(c, &c->m_v, N)) ||
         (r = alloc(c, &c->m_t, N)) || (r = alloc(c, &c->m_r, N)) || (r = alloc(c, &c->a_new, (size_t)4 * N)) || (r = alloc(c, &c->dhdt, N)) ||
-        (r = alloc(c, &c->block_part, (size_t)(N / 256 + 2))) || (r = alloc(c, &c->dscal, 1))) {
+        (r = alloc(c, &c->block_part, (size_t)(N / 256 + 2))) || (r = alloc(c, &c->dscal, 1)) ||
+        (r = alloc(c, &c->box_root, n_boxes))) {
         free_all(c);
         delete c;
         return r;
@@ -235,13 +259,93 @@ int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stre
         delete c;
         return SPH_ERR_CUDA;
     }
-    if (cudaMemsetAsync(c->dscal, 0, sizeof(DevScalars), c->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(c->dscal, 0, sizeof(DevScalars), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->box_root, 0, (size_t)n_boxes * sizeof(int32_t), c->stream) != cudaSuccess) {
         cudaGetLastError();
         free_all(c);
         delete c;
         return SPH_ERR_CUDA;
     }
     *out = c;
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stream, sph_ctx **out) {
+    return create_ctx(p, n_cap, 0, 1, neigh_cap, stream, out);
+}
+
+int sph_batch_create(const sph_params *p, int n_boxes, const int64_t *box_offsets, const double *box_mass,
+                     const double *box_gamma, int64_t neigh_cap, void *stream, sph_ctx **out) {
+    if (!out) return SPH_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!p || n_boxes < 1 || n_boxes > 4096 || !box_offsets || !box_mass) return SPH_ERR_INVALID_ARG;
+    if (box_offsets[0] != 0) return SPH_ERR_INVALID_ARG;
+    int64_t groups = 0;
+    for (int b = 0; b < n_boxes; b++) {
+        const int64_t nb = box_offsets[b + 1] - box_offsets[b];
+        if (nb < 0 || !(box_mass[b] > 0) || (box_gamma && !(box_gamma[b] > 1))) return SPH_ERR_INVALID_ARG;
+        groups += (nb + 31) / 32;
+    }
+    const int64_t total = box_offsets[n_boxes];
+    if (total < 1) return SPH_ERR_INVALID_ARG;
+    sph_ctx *c = nullptr;
+    int r = create_ctx(p, total, n_boxes, n_boxes, neigh_cap, stream, &c);
+    if (r) return r;
+    c->batch = true;
+    c->n_boxes = n_boxes;
+    int bits = 0;
+    while ((1 << bits) < n_boxes) ++bits;
+    c->box_bits = bits;
+    c->morton_bits = std::min(21, (63 - bits) / 3);
+    c->h_box_off.assign(box_offsets, box_offsets + n_boxes + 1);
+    c->batch_groups = groups;
+    std::vector<uint16_t> box_of((size_t)total), group_box((size_t)groups);
+    std::vector<int64_t> gstart((size_t)groups + 1);
+    std::vector<double> gam((size_t)n_boxes);
+    int64_t g = 0;
+    for (int b = 0; b < n_boxes; b++) {
+        for (int64_t i = box_offsets[b]; i < box_offsets[b + 1]; i++) box_of[(size_t)i] = (uint16_t)b;
+        for (int64_t f = box_offsets[b]; f < box_offsets[b + 1]; f += 32) {
+            gstart[(size_t)g] = f;
+            group_box[(size_t)g] = (uint16_t)b;
+            ++g;
+        }
+        gam[(size_t)b] = box_gamma ? box_gamma[b] : p->gamma;
+    }
+    gstart[(size_t)groups] = total;
+    c->h_gstart = gstart;
+    c->h_box_dt.assign((size_t)n_boxes, -1.0);
+    auto up = [&](void *dst, const void *src, size_t bytes) -> int {
+        SPH_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        return SPH_OK;
+    };
+    if ((r = alloc(c, &c->box_of, total)) || (r = alloc(c, &c->box_mass, n_boxes)) ||
+        (r = alloc(c, &c->box_gamma, n_boxes)) || (r = alloc(c, &c->box_dt, n_boxes)) ||
+        (r = alloc(c, &c->box_dt_next, n_boxes)) || (r = alloc(c, &c->gstart, groups + 1)) ||
+        (r = alloc(c, &c->group_box, groups)) || (r = up(c->box_of, box_of.data(), box_of.size() * 2)) ||
+        (r = up(c->box_mass, box_mass, (size_t)n_boxes * 8)) || (r = up(c->box_gamma, gam.data(), gam.size() * 8)) ||
+        (r = up(c->gstart, gstart.data(), gstart.size() * 8)) ||
+        (r = up(c->group_box, group_box.data(), group_box.size() * 2))) {
+        sph_destroy(c);
+        return r;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        sph_destroy(c);
+        return SPH_ERR_CUDA;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+int sph_batch_dt(sph_ctx *c, double *dt_per_box) {
+    if (!c || !dt_per_box) return SPH_ERR_INVALID_ARG;
+    if (!c->batch) return fail(c, SPH_ERR_INVALID_ARG, "not a batch context");
+    for (int b = 0; b < c->n_boxes; b++) dt_per_box[b] = c->h_box_dt[(size_t)b];
     return SPH_OK;
 }
 
@@ -312,7 +416,20 @@ int sph_compute_forces(sph_ctx *c, sph_state *s) {
 int sph_step(sph_ctx *c, sph_state *s, double dt, double *dt_used, double *dt_next) {
     int r = check_state(c, s, true);
     if (r) return r;
-    if (!(dt > 0)) {
+    if (c->batch) {
+        if (s->n != c->n_cap) return fail(c, SPH_ERR_INVALID_ARG, "a batch state holds every box");
+        std::vector<double> &bd = c->h_step_dt;
+        bd.assign((size_t)c->n_boxes, dt);
+        if (!(dt > 0)) {
+            for (int b = 0; b < c->n_boxes; b++) {
+                if (!(c->h_box_dt[(size_t)b] > 0) && c->h_box_off[b + 1] > c->h_box_off[b])
+                    return fail(c, SPH_ERR_ORDER, "dt <= 0 needs a previous force evaluation");
+                bd[(size_t)b] = c->h_box_dt[(size_t)b] > 0 ? c->h_box_dt[(size_t)b] : 0.0;
+            }
+        }
+        SPH_CUDA(c, cudaMemcpyAsync(c->box_dt, bd.data(), bd.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        dt = *std::min_element(bd.begin(), bd.end());
+    } else if (!(dt > 0)) {
         if (!(c->dt_next > 0)) return fail(c, SPH_ERR_ORDER, "dt <= 0 needs a previous force evaluation");
         dt = c->dt_next;
     }
@@ -435,9 +552,13 @@ int sph_export_neighbours(sph_ctx *c, int64_t *off, uint32_t *ids) {
     off[0] = 0;
     for (int64_t a = 0; a < n; a++) off[a + 1] = off[a] + cnt[a];
     if (ids) {
-        for (int64_t a = 0; a < n; a++) {
-            const int64_t base = goff[a >> 5] + (a & 31);
-            for (uint32_t k = 0; k < cnt[a]; k++) ids[off[a] + k] = raw[base + (int64_t)k * 32];
+        for (int64_t g = 0; g < G; g++) {
+            const int64_t first = c->batch ? c->h_gstart[(size_t)g] : 32 * g;
+            const int64_t end = c->batch ? c->h_gstart[(size_t)g + 1] : std::min<int64_t>(32 * g + 32, n);
+            for (int64_t a = first; a < end; a++) {
+                const int64_t base = goff[g] + (a - first);
+                for (uint32_t k = 0; k < cnt[a]; k++) ids[off[a] + k] = raw[base + (int64_t)k * 32];
+            }
         }
     }
     return SPH_OK;

@@ -18,6 +18,7 @@ struct DensParams {
     double mass, hfact, h_tol, h_clamp, chi;
     int max_iter;
     PairGeo geo;
+    const double *box_mass;   // per-box particle mass (batch) or nullptr
 };
 
 // Sums over the neighbours of a at smoothing length h:  sf = sum f(q),  sg = sum (3 f + q f')
@@ -93,21 +94,22 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
 }
 
 template <bool kMixed>
-__global__ void __launch_bounds__(128) k_density(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+__global__ void __launch_bounds__(128) k_density(Groups gr, int64_t G, const double *__restrict__ x, const double *__restrict__ y,
                                                  const double *__restrict__ z, const float4 *__restrict__ rel,
                                                  double *__restrict__ h, const double *__restrict__ h_base,
                                                  const uint32_t *__restrict__ nb_cnt, const int64_t *__restrict__ grp_off,
                                                  const uint32_t *__restrict__ nb_ids, DensParams dp,
                                                  double *__restrict__ rho, double *__restrict__ omega, DevScalars *sc) {
-    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= n) return;
-    const int lane = (int)(a & 31);
-    const int64_t g = a >> 5;
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= G) return;
+    const int64_t a = group_first(gr, g) + lane;
+    if (a >= group_end(gr, g)) return;
     const uint32_t cnt = nb_cnt[a];
     const uint32_t *ids = nb_ids + grp_off[g] + lane;
     double ha = h[a];
     const double hn = h_base[a];
-    const double m = dp.mass;
+    const double m = dp.box_mass ? dp.box_mass[group_box_of(gr, g)] : dp.mass;
     const double hf3 = dp.hfact * dp.hfact * dp.hfact;
     int it = 0;
     uint32_t nin = 0;
@@ -164,15 +166,18 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
     dp.chi = c->p.cache_tol;
     dp.max_iter = c->p.h_max_iter;
     dp.geo = make_pair_geo(c->p);
+    dp.box_mass = c->batch ? c->box_mass : nullptr;
+    const int64_t G = group_count(c, n);
+    const Groups gr = make_groups(c, n);
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->max_iters, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->pair_evals, 0, 2 * sizeof(unsigned long long), c->stream));
     if (c->p.precision == SPH_MIXED)
-        k_density<true><<<grid_for(n, 128), 128, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+        k_density<true><<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, s->x, s->y, s->z, c->rel, s->h, c->h_base,
                                                                  c->nb_cnt, c->grp_off, c->nb_ids, dp, s->rho,
                                                                  s->omega, c->dscal);
     else
-        k_density<false><<<grid_for(n, 128), 128, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+        k_density<false><<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, s->x, s->y, s->z, c->rel, s->h, c->h_base,
                                                                   c->nb_cnt, c->grp_off, c->nb_ids, dp, s->rho,
                                                                   s->omega, c->dscal);
     SPH_LAUNCH_CHECK(c, "k_density");

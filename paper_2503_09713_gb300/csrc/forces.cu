@@ -16,6 +16,10 @@ namespace sph {
 struct ForceParams {
     double mass, gamma, alpha_av, beta_av, alpha_u, c_cour, c_force;
     PairGeo geo;
+    const double *box_mass;    // per-box particle mass (batch) or nullptr
+    const double *box_gamma;   // per-box adiabatic index (batch) or nullptr
+    const uint16_t *box_of;    // box of each particle (batch) or nullptr
+    unsigned long long *box_dt_next;   // per-box CFL minimum (bits) or nullptr
 };
 
 // Per-particle FP64 record of the force loop: 128 bytes, read as 8 double2.
@@ -37,8 +41,9 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double r = rho[i], om = omega[i], ui = u[i], hi = h[i];
-    const double P = (fp.gamma - 1.0) * r * ui;
-    const double cs = sqrt(fp.gamma * P / r);
+    const double gam = fp.box_gamma ? fp.box_gamma[fp.box_of[i]] : fp.gamma;
+    const double P = (gam - 1.0) * r * ui;
+    const double cs = sqrt(gam * P / r);
     const double pre = P / (r * r * om);
     const double qf = 1.0 / (r * om);
     const double hinv = 1.0 / hi;
@@ -86,14 +91,19 @@ __device__ __forceinline__ double dt_candidate(double h, double vs, double ax, d
 }
 
 // Warp minimum of the CFL candidates and warp sum of the in-range pair counts (all 32 lanes
-// participate), then one atomic each per warp; positive doubles order like their bit patterns.
-__device__ __forceinline__ void dt_reduce(double t, unsigned long long npair, DevScalars *sc) {
+// participate; a warp is one group, inside one box), then one atomic each per warp; positive
+// doubles order like their bit patterns.
+__device__ __forceinline__ void dt_reduce(double t, unsigned long long npair, DevScalars *sc,
+                                          unsigned long long *box_dt_next, int box) {
     for (int o = 16; o > 0; o >>= 1) {
         t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
         npair += __shfl_xor_sync(0xffffffffu, npair, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        if (t > 0.0 && t < INFINITY) atomicMin(&sc->dt_min_bits, dbits(t));
+        if (t > 0.0 && t < INFINITY) {
+            atomicMin(&sc->dt_min_bits, dbits(t));
+            if (box_dt_next) atomicMin(&box_dt_next[box], dbits(t));
+        }
         atomicAdd(&sc->inrange_pairs, npair);
     }
 }
@@ -101,19 +111,22 @@ __device__ __forceinline__ void dt_reduce(double t, unsigned long long npair, De
 // FP64 pair loop.  A candidate is first tested in FP32 on the cell-relative offsets against the
 // current h (kPreBand margin); the survivors are decided and evaluated in FP64 with the nearest
 // image from the cell indices.  The mass factor is applied once per particle.
-__global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__restrict__ rec,
+__global__ void __launch_bounds__(128) k_forces_fp64(Groups gr, int64_t G, const FRec *__restrict__ rec,
                                                      const float4 *__restrict__ rel, const float *__restrict__ h32,
                                                      const uint32_t *__restrict__ nb_cnt,
                                                      const int64_t *__restrict__ grp_off,
                                                      const uint32_t *__restrict__ nb_ids, ForceParams fp, ForceOut out,
                                                      DevScalars *sc) {
-    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= G) return;   // whole warp
+    const int64_t a = group_first(gr, g) + lane;
+    const int box = group_box_of(gr, g);
     double tdt = INFINITY;
     unsigned long long npair = 0;
-    if (a < n) {
-    const int lane = (int)(a & 31);
+    if (a < group_end(gr, g)) {
     const uint32_t cnt = nb_cnt[a];
-    const uint32_t *ids = nb_ids + grp_off[a >> 5] + lane;
+    const uint32_t *ids = nb_ids + grp_off[g] + lane;
     FRec A;
     load_rec(&rec[a], A);
     const float4 PA = rel[a];
@@ -167,7 +180,7 @@ __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__re
             }
         }
     }
-    const double m = fp.mass;
+    const double m = fp.box_mass ? fp.box_mass[box] : fp.mass;
     axs *= m;
     ays *= m;
     azs *= m;
@@ -180,25 +193,29 @@ __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__re
     out.dhdt[a] = -A.h * A.qf * (1.0 / 3.0) * m * divs;
     tdt = dt_candidate(A.h, vs, axs, ays, azs, fp);
     }
-    dt_reduce(tdt, npair, sc);
+    dt_reduce(tdt, npair, sc, fp.box_dt_next, box);
 }
 
-__global__ void __launch_bounds__(128) k_forces_mixed(int64_t n, const float4 *__restrict__ rel,
+__global__ void __launch_bounds__(128) k_forces_mixed(Groups gr, int64_t G, const float4 *__restrict__ rel,
                                                       const float4 *__restrict__ m_v, const float4 *__restrict__ m_t,
                                                       const float4 *__restrict__ m_r, const double *__restrict__ h,
                                                       const uint32_t *__restrict__ nb_cnt,
                                                       const int64_t *__restrict__ grp_off,
                                                       const uint32_t *__restrict__ nb_ids, ForceParams fp,
                                                       ForceOut out, DevScalars *sc) {
-    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= G) return;   // whole warp
+    const int64_t a = group_first(gr, g) + lane;
+    const int box = group_box_of(gr, g);
     double tdt = INFINITY;
     unsigned long long npair = 0;
-    if (a < n) {
-    const int lane = (int)(a & 31);
+    if (a < group_end(gr, g)) {
     const uint32_t cnt = nb_cnt[a];
-    const uint32_t *ids = nb_ids + grp_off[a >> 5] + lane;
+    const uint32_t *ids = nb_ids + grp_off[g] + lane;
     const float4 PA = rel[a], VA = m_v[a], TA = m_t[a], RA = m_r[a];
-    const float mass = (float)fp.mass, alpha = (float)fp.alpha_av, beta = (float)fp.beta_av,
+    const double mass_d = fp.box_mass ? fp.box_mass[box] : fp.mass;
+    const float mass = (float)mass_d, alpha = (float)fp.alpha_av, beta = (float)fp.beta_av,
                 au = (float)fp.alpha_u;
     float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f, su = 0.f, cu = 0.f, sdiv = 0.f;
     float vs = alpha * TA.z;
@@ -261,15 +278,19 @@ __global__ void __launch_bounds__(128) k_forces_mixed(int64_t n, const float4 *_
     out.az[a] = azs;
     out.du[a] = kahan_value(su, cu);
     out.vsig[a] = (double)vs;
-    out.dhdt[a] = -h[a] * (double)TA.y * (1.0 / 3.0) * fp.mass * (double)sdiv;
+    out.dhdt[a] = -h[a] * (double)TA.y * (1.0 / 3.0) * mass_d * (double)sdiv;
     tdt = dt_candidate(h[a], (double)vs, axs, ays, azs, fp);
     }
-    dt_reduce(tdt, npair, sc);
+    dt_reduce(tdt, npair, sc, fp.box_dt_next, box);
 }
 
-__global__ void k_reset_dt(DevScalars *sc) {
-    sc->dt_min_bits = 0x7ff0000000000000ULL;
-    sc->inrange_pairs = 0ULL;
+__global__ void k_reset_dt(DevScalars *sc, unsigned long long *box_dt_next, int n_boxes) {
+    if (threadIdx.x == 0) {
+        sc->dt_min_bits = 0x7ff0000000000000ULL;
+        sc->inrange_pairs = 0ULL;
+    }
+    if (box_dt_next)
+        for (int b = threadIdx.x; b < n_boxes; b += blockDim.x) box_dt_next[b] = 0x7ff0000000000000ULL;
 }
 
 int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, double *du) {
@@ -284,22 +305,28 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     fp.c_cour = c->p.c_cour;
     fp.c_force = c->p.c_force;
     fp.geo = make_pair_geo(c->p);
+    fp.box_mass = c->batch ? c->box_mass : nullptr;
+    fp.box_gamma = c->batch ? c->box_gamma : nullptr;
+    fp.box_of = c->batch ? c->box_of : nullptr;
+    fp.box_dt_next = c->batch ? c->box_dt_next : nullptr;
     const int mixed = c->p.precision == SPH_MIXED;
+    const int64_t G = group_count(c, n);
+    const Groups gr = make_groups(c, n);
     int r;
     if ((r = stage_begin(c, kStForcePrep))) return r;
     k_force_prep<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->h,
                                                            s->rho, s->omega, fp, mixed, (FRec *)c->frec, c->m_v,
                                                            c->m_t, c->m_r, c->h32);
     SPH_LAUNCH_CHECK(c, "k_force_prep");
-    k_reset_dt<<<1, 1, 0, c->stream>>>(c->dscal);
+    k_reset_dt<<<1, 32, 0, c->stream>>>(c->dscal, fp.box_dt_next, c->n_boxes);
     SPH_LAUNCH_CHECK(c, "k_reset_dt");
     if ((r = stage_end(c, kStForcePrep)) || (r = stage_begin(c, kStForces))) return r;
     ForceOut out{ax, ay, az, du, s->vsig, c->dhdt};
     if (mixed)
-        k_forces_mixed<<<grid_for(n, 128), 128, 0, c->stream>>>(n, c->rel, c->m_v, c->m_t, c->m_r, s->h,
+        k_forces_mixed<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, c->rel, c->m_v, c->m_t, c->m_r, s->h,
                                                                 c->nb_cnt, c->grp_off, c->nb_ids, fp, out, c->dscal);
     else
-        k_forces_fp64<<<grid_for(n, 128), 128, 0, c->stream>>>(n, (const FRec *)c->frec, c->rel, c->h32, c->nb_cnt,
+        k_forces_fp64<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, (const FRec *)c->frec, c->rel, c->h32, c->nb_cnt,
                                                                c->grp_off, c->nb_ids, fp, out, c->dscal);
     SPH_LAUNCH_CHECK(c, "k_forces");
     return stage_end(c, kStForces);

@@ -11,6 +11,8 @@ namespace sph {
 struct IntParams {
     double dt;
     double h_clamp;
+    const double *box_dt;      // per-box time step (batch) or nullptr
+    const uint16_t *box_of;
     double lo[3], hi[3];
     int periodic;
 };
@@ -37,10 +39,11 @@ __global__ void k_predict(int64_t n, double *__restrict__ x, double *__restrict_
                           const double *__restrict__ dhdt, IntParams ip) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double hdt = 0.5 * ip.dt;
+    const double dt = ip.box_dt ? ip.box_dt[ip.box_of[i]] : ip.dt;
+    const double hdt = 0.5 * dt;
     const double kx = hdt * ax[i], ky = hdt * ay[i], kz = hdt * az[i], ku = hdt * du[i];
     const double hvx = vx[i] + kx, hvy = vy[i] + ky, hvz = vz[i] + kz;
-    double px = x[i] + ip.dt * hvx, py = y[i] + ip.dt * hvy, pz = z[i] + ip.dt * hvz;
+    double px = x[i] + dt * hvx, py = y[i] + dt * hvy, pz = z[i] + dt * hvz;
     if (ip.periodic) {
         px = wrap(px, ip.lo[0], ip.hi[0]);
         py = wrap(py, ip.lo[1], ip.hi[1]);
@@ -55,7 +58,7 @@ __global__ void k_predict(int64_t n, double *__restrict__ x, double *__restrict_
     u[i] = (u[i] + ku) + ku;
     if (dhdt) {
         const double h0 = h[i];
-        double hp = h0 + ip.dt * dhdt[i];
+        double hp = h0 + dt * dhdt[i];
         hp = fmin(fmax(hp, h0 / ip.h_clamp), h0 * ip.h_clamp);
         h[i] = hp;
     }
@@ -64,11 +67,12 @@ __global__ void k_predict(int64_t n, double *__restrict__ x, double *__restrict_
 __global__ void k_correct(int64_t n, double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                           double *__restrict__ u, double *__restrict__ ax, double *__restrict__ ay,
                           double *__restrict__ az, double *__restrict__ du, const double *__restrict__ anew,
-                          int64_t stride, double dt, DevScalars *sc, double *__restrict__ block_part) {
+                          int64_t stride, double dt, const double *__restrict__ box_dt,
+                          const uint16_t *__restrict__ box_of, DevScalars *sc, double *__restrict__ block_part) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dv = 0.0, v2 = 0.0;
     if (i < n) {
-        const double hdt = 0.5 * dt;
+        const double hdt = 0.5 * (box_dt ? box_dt[box_of[i]] : dt);
         const double nax = anew[i], nay = anew[stride + i], naz = anew[2 * stride + i], ndu = anew[3 * stride + i];
         const double dvx = hdt * (nax - ax[i]), dvy = hdt * (nay - ay[i]), dvz = hdt * (naz - az[i]);
         const double wx = vx[i] + dvx, wy = vy[i] + dvy, wz = vz[i] + dvz;
@@ -121,6 +125,8 @@ int integrate_predict(sph_ctx *c, sph_state *s, double dt, const double *dhdt) {
     IntParams ip;
     ip.dt = dt;
     ip.h_clamp = c->p.h_clamp;
+    ip.box_dt = c->batch ? c->box_dt : nullptr;
+    ip.box_of = c->batch ? c->box_of : nullptr;
     for (int k = 0; k < 3; k++) {
         ip.lo[k] = c->p.box_lo[k];
         ip.hi[k] = c->p.box_hi[k];
@@ -138,7 +144,8 @@ int integrate_correct(sph_ctx *c, sph_state *s, double dt) {
     k_reset_dv<<<1, 1, 0, c->stream>>>(c->dscal);
     SPH_LAUNCH_CHECK(c, "k_reset_dv");
     k_correct<<<blocks, 256, 0, c->stream>>>(n, s->vx, s->vy, s->vz, s->u, s->ax, s->ay, s->az, s->du, c->a_new,
-                                             c->n_cap, dt, c->dscal, c->block_part);
+                                             c->n_cap, dt, c->batch ? c->box_dt : nullptr,
+                                             c->batch ? c->box_of : nullptr, c->dscal, c->block_part);
     SPH_LAUNCH_CHECK(c, "k_correct");
     k_sum_parts<<<1, 256, 0, c->stream>>>(c->block_part, blocks, &c->dscal->v2_sum);
     SPH_LAUNCH_CHECK(c, "k_sum_parts");

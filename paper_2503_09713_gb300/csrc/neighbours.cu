@@ -39,14 +39,14 @@ static Geo make_geo(const sph_params &p) {
 }
 
 // ------------------------------------------------------------------ group boxes (warp per group)
-__global__ void k_group_boxes(int64_t n, int64_t G, const double *__restrict__ x, const double *__restrict__ y,
+__global__ void k_group_boxes(Groups gr, int64_t G, const double *__restrict__ x, const double *__restrict__ y,
                               const double *__restrict__ z, const double *__restrict__ h, Node *__restrict__ gbox,
                               NodeF *__restrict__ gboxf) {
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (g >= G) return;
-    const int64_t a = g * 32 + lane;
-    const bool va = a < n;
+    const int64_t a = group_first(gr, g) + lane;
+    const bool va = a < group_end(gr, g);
     double lo[3], hi[3];
     const double p[3] = {va ? x[a] : 0.0, va ? y[a] : 0.0, va ? z[a] : 0.0};
     for (int k = 0; k < 3; k++) {
@@ -89,15 +89,17 @@ __device__ __forceinline__ float walk_radius(float s, float h1, float h2) {
     return __fmul_ru(__fmul_ru(s, fmaxf(h1, h2)), 1.0f + 1.0f / 65536.0f);
 }
 
-__global__ void __launch_bounds__(128) k_walk(int64_t G, int64_t L, const NodeF *__restrict__ gboxf,
+__global__ void __launch_bounds__(128) k_walk(Groups gr, int64_t G, int64_t L, const NodeF *__restrict__ gboxf,
                                              const NodeF *__restrict__ nodesf, const int32_t *__restrict__ child,
-                                             const int64_t *__restrict__ leaf_first, float s, Geo geo,
+                                             const int64_t *__restrict__ leaf_first,
+                                             const int32_t *__restrict__ box_root, float s, Geo geo,
                                              uint2 *__restrict__ cand, uint32_t *__restrict__ cand_cnt, int cap,
                                              int64_t *__restrict__ grp_chunks, uint32_t *flags) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
+    const int32_t rootc = box_root[group_box_of(gr, g)];   // the walk stays inside the group's box
     const NodeF q = load_nodef(&gboxf[g]);
-    const NodeF root = load_nodef(&nodesf[0]);
+    const NodeF root = load_nodef(&nodesf[rootc]);
     const float rmax = walk_radius(s, q.hmax, root.hmax);
     // periodic images of the group box that can reach the box (offsets added with outward rounding)
     int nsh[3];
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(128) k_walk(int64_t G, int64_t L, const NodeF 
                 const float qhi[3] = {__fadd_ru(q.hi[0], sh[0][ix]), __fadd_ru(q.hi[1], sh[1][iy]),
                                       __fadd_ru(q.hi[2], sh[2][iz])};
                 int sp = 0;
-                stack[sp++] = 0;
+                stack[sp++] = rootc;
                 while (sp > 0) {
                     const int32_t c = stack[--sp];
                     const NodeF nd = load_nodef(&nodesf[c]);
@@ -226,7 +228,7 @@ constexpr uint32_t kGrpSpinLimit = 1u << 22;
 // a box; the kernel asks for a quarter box (warp-uniform), otherwise every separation is wrapped on
 // its own.  Pairs within a relative 2^-10 of the radius are decided in FP64 (exact_pair).
 __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
-    int64_t n, int64_t G, const uint2 *__restrict__ cand, const uint32_t *__restrict__ cand_cnt, int cap,
+    Groups gr, const int32_t *__restrict__ box_root, int64_t G, const uint2 *__restrict__ cand, const uint32_t *__restrict__ cand_cnt, int cap,
     const int64_t *__restrict__ chunk_off, const Node *__restrict__ gbox, const Node *__restrict__ nodes,
     const float4 *__restrict__ rel, const float *__restrict__ h32, const double *__restrict__ x,
     const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h, double s,
@@ -240,12 +242,13 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
     if (lane == 0) g = atomicAdd(ticket, 1u);
     g = __shfl_sync(0xffffffffu, g, 0);
     if (g >= G) return;
-    const int64_t a = g * 32 + lane;
-    const bool va = a < n;
+    const int64_t first = group_first(gr, g);
+    const int64_t a = first + lane;
+    const bool va = a < group_end(gr, g);
     const float s32 = (float)s;
-    const float4 Araw = rel[va ? a : g * 32];
+    const float4 Araw = rel[va ? a : first];
     int rcx, rcy, rcz;
-    unpack_cell(rel[g * 32], rcx, rcy, rcz);
+    unpack_cell(rel[first], rcx, rcy, rcz);
     auto grel = [&](const float4 P, float &px, float &py, float &pz) {
         int cx, cy, cz;
         unpack_cell(P, cx, cy, cz);
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
     const float tA = (s32 * hA) * (s32 * hA);
     const float tAhi = tA * kBandHi, tAlo = tA * kBandLo;
     const Node q = gbox[g];
-    const double hroot = nodes[0].hmax;
+    const double hroot = nodes[box_root[group_box_of(gr, g)]].hmax;
     const float ext = (float)fmax(fmax(q.hi[0] - q.lo[0], q.hi[1] - q.lo[1]), q.hi[2] - q.lo[2]);
     const bool compact = ext + (float)(s * hroot) < quarter_box;   // warp-uniform
     int ca[3];
@@ -436,7 +439,8 @@ static int ensure(sph_ctx *c, T **p, int64_t &cap, int64_t need, const char *wha
 int neighbours_build(sph_ctx *c, const sph_state *s) {
     if (!c->tree_valid) return fail(c, SPH_ERR_ORDER, "sph_find_neighbours before sph_build_tree");
     const int64_t n = s->n;
-    const int64_t G = (n + 31) / 32;
+    const int64_t G = group_count(c, n);
+    const Groups gr = make_groups(c, n);
     const int64_t L = c->n_leaves;
     const Geo geo = make_geo(c->p);
     const double sc = 2.0 * c->p.cache_tol;   // R_kern * chi
@@ -445,15 +449,15 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
 
     k_h32<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->h, c->h32, c->h_base);
     SPH_LAUNCH_CHECK(c, "k_h32");
-    k_group_boxes<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(n, G, s->x, s->y, s->z, s->h, c->gbox, c->gboxf);
+    k_group_boxes<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, s->x, s->y, s->z, s->h, c->gbox, c->gboxf);
     SPH_LAUNCH_CHECK(c, "k_group_boxes");
 
     // stage 1, growing the candidate capacity while a list overflows
     for (int attempt = 0;; attempt++) {
         SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
-        k_walk<<<grid_for(G, 128), 128, 0, c->stream>>>(G, L, c->gboxf, c->nodesf, c->child, c->leaf_first,
-                                                        (float)sc, geo, c->cand, c->cand_cnt, c->cand_cap,
-                                                        c->grp_chunks, &c->dscal->flags);
+        k_walk<<<grid_for(G, 128), 128, 0, c->stream>>>(gr, G, L, c->gboxf, c->nodesf, c->child, c->leaf_first,
+                                                        c->box_root, (float)sc, geo, c->cand, c->cand_cnt,
+                                                        c->cand_cap, c->grp_chunks, &c->dscal->flags);
         SPH_LAUNCH_CHECK(c, "k_walk");
         int r = exclusive_scan_i64(c, c->grp_chunks, c->chunk_off, G);
         if (r) return r;
@@ -490,7 +494,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         SPH_CUDA(c, cudaMemsetAsync(&c->dscal->s2_ticket, 0, sizeof(uint32_t), c->stream));
         SPH_CUDA(c, cudaMemsetAsync(c->grp_slots, 0, (size_t)G * sizeof(int64_t), c->stream));
         k_stage2<<<blocks, kS2Warps * 32, 0, c->stream>>>(
-            n, G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->gbox, c->nodes, c->rel, c->h32, s->x, s->y,
+            gr, c->box_root, G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->gbox, c->nodes, c->rel, c->h32, s->x, s->y,
             s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket,
             c->grp_off, c->nb_ids, c->nb_cap, c->dscal);
         SPH_LAUNCH_CHECK(c, "k_stage2");

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/sph.h"
@@ -53,6 +54,23 @@ __device__ __forceinline__ NodeF to_float_outward(const Node &b) {
     f.pad = 0.f;
     return f;
 }
+
+// Groups of at most 32 consecutive particles, never spanning two boxes.  Without a table (one box)
+// group g is particles 32g .. min(32g+32, n).
+struct Groups {
+    const int64_t *start;     // [G + 1] or nullptr
+    const uint16_t *box;      // [G] or nullptr
+    int64_t n;
+};
+__device__ __forceinline__ int64_t group_first(const Groups &gr, int64_t g) {
+    return gr.start ? gr.start[g] : 32 * g;
+}
+__device__ __forceinline__ int64_t group_end(const Groups &gr, int64_t g) {
+    if (gr.start) return gr.start[g + 1];
+    const int64_t e = 32 * g + 32;
+    return e < gr.n ? e : gr.n;
+}
+__device__ __forceinline__ int group_box_of(const Groups &gr, int64_t g) { return gr.box ? gr.box[g] : 0; }
 
 // Device scalars written by kernels and read back by the host in one copy.
 struct DevScalars {
@@ -187,6 +205,25 @@ struct sph_ctx {
     double *hs_fields = nullptr;       // [16][n_cap]
     uint32_t *hs_id = nullptr;
 
+    // ---- boxes (one for sph_create, several for sph_batch_create) and groups ----
+    bool batch = false;
+    int n_boxes = 1;
+    int box_bits = 0;                  // bits of the box index at the top of the key
+    int morton_bits = 21;              // bits per axis of the Morton code
+    std::vector<int64_t> h_box_off;    // [n_boxes + 1] host copy (batch)
+    uint16_t *box_of = nullptr;        // [n_cap] box of each particle position (batch)
+    double *box_mass = nullptr;        // [n_boxes] (batch)
+    double *box_gamma = nullptr;       // [n_boxes] (batch)
+    int32_t *box_root = nullptr;       // [n_boxes] node at the root of each box's subtree
+    double *box_dt = nullptr;          // [n_boxes] time step of the current step (batch)
+    unsigned long long *box_dt_next = nullptr;  // [n_boxes] CFL minimum (bits) of the last force pass
+    std::vector<double> h_box_dt;      // host copy of the last CFL step per box
+    std::vector<double> h_step_dt;     // time step of each box in the current step
+    int64_t *gstart = nullptr;         // [groups + 1] first particle of each group (batch)
+    uint16_t *group_box = nullptr;     // [groups] box of each group (batch)
+    std::vector<int64_t> h_gstart;     // host copy (batch)
+    int64_t batch_groups = 0;
+
     // ---- scalars / flags ----
     sph::DevScalars *dscal = nullptr;
     sph::DevScalars *hscal = nullptr;  // pinned host mirror
@@ -226,6 +263,8 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
 int integrate_predict(sph_ctx *c, sph_state *s, double dt, const double *dhdt);
 int integrate_correct(sph_ctx *c, sph_state *s, double dt);
 int read_scalars(sph_ctx *c);
+Groups make_groups(const sph_ctx *c, int64_t n);
+int64_t group_count(const sph_ctx *c, int64_t n);
 // Per-stage timing: stage_begin/stage_end bracket the launches of one stage on the context stream;
 // with timing on, stage_end waits for the stage and adds its duration to stats.stage_ms[k].
 enum Stage { kStPredict = 0, kStTree, kStNeigh, kStDensity, kStForcePrep, kStForces, kStCorrect, kStCount };
@@ -234,6 +273,7 @@ int stage_end(sph_ctx *c, int k);
 int exclusive_scan_i64(sph_ctx *c, const int64_t *in, int64_t *out, int64_t n);  // out[n] = total
 
 // ---------------------------------------------------------------- device helpers
+
 __device__ __forceinline__ double min_image(double d, double L, double halfL, int periodic) {
     if (periodic) {
         if (d > halfL) d -= L;

@@ -24,10 +24,11 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v) {
 // App. B "Morton codes": remap to [0,1) by (x-lo)/(hi-lo), integer grid of 2^21 per axis,
 // interleave X0 Y0 Z0 X1 ... with x most significant.  inv_span is 1/span when span is a power of
 // two (then the product equals the quotient bit for bit) and 0 otherwise (divide).
-__device__ __forceinline__ uint64_t quantise(double x, double lo, double span, double inv_span) {
+__device__ __forceinline__ uint64_t quantise(double x, double lo, double span, double inv_span, int bits = 21) {
     double s = inv_span != 0.0 ? (x - lo) * inv_span : (x - lo) / span;
-    double g = s * 2097152.0;  // 2^21, exact scale
-    const double top = 2097151.0;
+    const double scale = (double)(1ULL << bits);   // exact power of two
+    double g = s * scale;
+    const double top = scale - 1.0;
     if (!(g >= 0.0)) g = 0.0;
     if (g > top) g = top;
     return (uint64_t)floor(g);
@@ -38,18 +39,23 @@ struct Box3 {
     double inv_span[3];   // exact reciprocal when span is a power of two, else 0
 };
 
+// In a batch the key is (box index << 3*bits) | Morton code with `bits` bits per axis, so that the
+// sort keeps each box's particles together and every box is a subtree of the radix tree.
 __global__ void k_morton(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                          const double *__restrict__ z, const double *__restrict__ h, Box3 b,
-                         uint64_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t *flags) {
+                         uint64_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t *flags,
+                         const uint16_t *__restrict__ box_of, int bits) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double px = x[i], py = y[i], pz = z[i], ph = h[i];
     if (!isfinite(px) || !isfinite(py) || !isfinite(pz) || !isfinite(ph) || !(ph > 0.0))
         atomicOr(flags, kErrNonFinite);
-    const uint64_t X = quantise(px, b.lo[0], b.span[0], b.inv_span[0]);
-    const uint64_t Y = quantise(py, b.lo[1], b.span[1], b.inv_span[1]);
-    const uint64_t Z = quantise(pz, b.lo[2], b.span[2], b.inv_span[2]);
-    keys[i] = (spread3(X) << 2) | (spread3(Y) << 1) | spread3(Z);
+    const uint64_t X = quantise(px, b.lo[0], b.span[0], b.inv_span[0], bits);
+    const uint64_t Y = quantise(py, b.lo[1], b.span[1], b.inv_span[1], bits);
+    const uint64_t Z = quantise(pz, b.lo[2], b.span[2], b.inv_span[2], bits);
+    uint64_t key = (spread3(X) << 2) | (spread3(Y) << 1) | spread3(Z);
+    if (box_of) key |= (uint64_t)box_of[i] << (3 * bits);
+    keys[i] = key;
     vals[i] = (uint32_t)i;
 }
 
@@ -457,6 +463,38 @@ __global__ void k_boxes(int64_t L, const int64_t *__restrict__ leaf_first, const
     }
 }
 
+// Root of each box's subtree (batch): the node whose leaves all carry the box index and whose parent
+// mixes boxes; a box with one leaf has that leaf as its root.
+__global__ void k_box_roots(int64_t L, const uint64_t *__restrict__ mu_leaf, const int32_t *__restrict__ endrange,
+                            const int32_t *__restrict__ node_parent, const int32_t *__restrict__ leaf_parent,
+                            int shift, int32_t *__restrict__ box_root) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nin = L - 1;
+    if (t >= nin + L) return;
+    auto range_box = [&](int64_t node, uint64_t &b_lo, uint64_t &b_hi) {
+        int64_t lo, hi;
+        if (node < nin) {
+            const int64_t e = endrange[node];
+            lo = node < e ? node : e;
+            hi = node < e ? e : node;
+        } else {
+            lo = hi = node - nin;
+        }
+        b_lo = mu_leaf[lo] >> shift;
+        b_hi = mu_leaf[hi] >> shift;
+    };
+    uint64_t a0, a1;
+    range_box(t, a0, a1);
+    if (a0 != a1) return;
+    const int64_t parent = (t < nin) ? node_parent[t] : (L > 1 ? leaf_parent[t - nin] : -1);
+    if (parent >= 0) {
+        uint64_t p0, p1;
+        range_box(parent, p0, p1);
+        if (p0 == p1) return;
+    }
+    box_root[a0] = (int32_t)t;
+}
+
 static double pow2_reciprocal(double v) {
     int e = 0;
     const double m = std::frexp(v, &e);
@@ -494,7 +532,8 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
 
     // A1 Morton codes
     k_morton<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, s->h, bx, c->keys[0], c->vals[0],
-                                                      &c->dscal->flags);
+                                                      &c->dscal->flags, c->batch ? c->box_of : nullptr,
+                                                      c->morton_bits);
     SPH_LAUNCH_CHECK(c, "k_morton");
     // A2 sort
     int r = radix_sort(c, n);
@@ -576,6 +615,12 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
                                                                c->rflag, c->endrange, c->child, c->node_parent,
                                                                c->leaf_parent);
         SPH_LAUNCH_CHECK(c, "k_karras");
+    }
+    // subtree root of every box
+    if (c->batch) {
+        k_box_roots<<<grid_for(2 * L - 1, 256), 256, 0, c->stream>>>(L, c->mu_leaf, c->endrange, c->node_parent,
+                                                                     c->leaf_parent, 3 * c->morton_bits, c->box_root);
+        SPH_LAUNCH_CHECK(c, "k_box_roots");
     }
     // A6 boxes + h_max
     r = boxes(c, s);

@@ -86,6 +86,8 @@ def load():
         "sph_default_params": (None, [P(sph_params)]),
         "sph_create": (_i, [P(sph_params), _i64, _i64, _p, P(_p)]),
         "sph_destroy": (_i, [_p]),
+        "sph_batch_create": (_i, [P(sph_params), _i, _p, _p, _p, _i64, _p, P(_p)]),
+        "sph_batch_dt": (_i, [_p, _p]),
         "sph_set_params": (_i, [_p, P(sph_params)]),
         "sph_build_tree": (_i, [_p, P(sph_state)]),
         "sph_find_neighbours": (_i, [_p, P(sph_state), P(_i64)]),
@@ -141,6 +143,25 @@ def sph_create(params: sph_params, n_cap: int, neigh_cap: int = 0, stream: int |
     code = load().sph_create(ctypes.byref(params), int(n_cap), int(neigh_cap), _p(stream or 0), ctypes.byref(ctx))
     _check(None, code)
     return ctx
+
+
+def sph_batch_create(params: sph_params, box_offsets, box_mass, box_gamma=None, neigh_cap: int = 0,
+                     stream: int | None = None):
+    off = np.ascontiguousarray(box_offsets, dtype=np.int64)
+    mass = np.ascontiguousarray(box_mass, dtype=np.float64)
+    gam = None if box_gamma is None else np.ascontiguousarray(box_gamma, dtype=np.float64)
+    ctx = _p()
+    code = load().sph_batch_create(ctypes.byref(params), len(off) - 1, off.ctypes.data, mass.ctypes.data,
+                                   gam.ctypes.data if gam is not None else None, int(neigh_cap), _p(stream or 0),
+                                   ctypes.byref(ctx))
+    _check(None, code)
+    return ctx
+
+
+def sph_batch_dt(ctx, n_boxes: int) -> np.ndarray:
+    out = np.zeros(n_boxes)
+    _check(ctx, load().sph_batch_dt(ctx, out.ctypes.data))
+    return out
 
 
 def sph_destroy(ctx):
@@ -268,11 +289,29 @@ def host_state(d: dict) -> tuple:
 class Solver:
     """Owns one context; methods mirror the ABI on a DeviceState."""
 
-    def __init__(self, params: sph_params, n_cap: int, neigh_cap: int = 0, stream: int | None = None):
+    def __init__(self, params: sph_params, n_cap: int, neigh_cap: int = 0, stream: int | None = None, _ctx=None):
+        if _ctx is not None:
+            self.ctx = _ctx
+            return
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.ctx = sph_create(params, n_cap, neigh_cap, stream)
+        self.n_boxes = 1
+
+    @classmethod
+    def batch(cls, params: sph_params, box_offsets, box_mass, box_gamma=None, neigh_cap: int = 0,
+              stream: int | None = None):
+        """Context over an ensemble of independent boxes (sph_batch_create)."""
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        s = cls(params, 0, _ctx=sph_batch_create(params, box_offsets, box_mass, box_gamma, neigh_cap, stream))
+        s.n_boxes = len(box_offsets) - 1
+        return s
+
+    def batch_dt(self) -> np.ndarray:
+        return sph_batch_dt(self.ctx, self.n_boxes)
 
     def close(self):
         if self.ctx:
