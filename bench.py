@@ -28,12 +28,13 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (152 SMs x 4 FP64 flop/clk x 2.07 GHz = 1.26)
 FP32_PEAK_TFLOPS = 80.5      # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
-# Algorithmic FLOPs per pair of the FP64 pair loops (counted from the formulas the kernels
-# evaluate; sqrt and division count as one operation each).
-FLOP_FORCE_CAND = 10         # separation, r^2, radius test
-FLOP_FORCE_PAIR = 70         # kernel gradients, AV, momentum, energy, conductivity, v_sig
+# Algorithmic FLOPs of the FP64 pair loops (counted from the formulas the kernels evaluate; sqrt,
+# rsqrt and division count as one operation each).  The force loop evaluates each pair once.
+FLOP_FORCE_CAND = 10         # per unordered cached pair: separation, r^2, radius test
+FLOP_FORCE_PAIR = 85         # per unordered pair in range: both kernel gradients, AV of both sides,
+                             # momentum, both energy terms, conductivity, divergence, v_sig
 FLOP_DENS_CAND = 9           # separation, q^2
-FLOP_DENS_PAIR = 13          # sqrt, M4 value and derivative, the two sums
+FLOP_DENS_PAIR = 20          # sqrt, M4 value and two derivatives, the three sums
 
 WORKLOADS = {
     "sedov128": ("sedov", 128, "Sedov blast 128^3 = 2,097,152 particles, jittered cubic lattice, periodic unit "
@@ -324,7 +325,7 @@ def main():
         flops = st["density_pair_evals"] * FLOP_DENS_CAND + st["density_inrange"] * FLOP_DENS_PAIR
         kname = "k_density<FP64>"
     else:
-        flops = st["n_pairs"] * FLOP_FORCE_CAND + st["force_pairs"] * FLOP_FORCE_PAIR
+        flops = st["n_pairs"] // 2 * FLOP_FORCE_CAND + st["force_pairs"] // 2 * FLOP_FORCE_PAIR
         kname = "k_forces_fp64"
         dominant = "forces"
     kms = stage[dominant]

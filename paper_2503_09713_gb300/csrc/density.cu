@@ -5,7 +5,9 @@
 // particles until the largest eps is below eps_c; once a particle meets the criterion its further
 // updates are below eps_c^2).  Steps are clamped to [h/lambda, h*lambda]; an h above chi*h^n is
 // clamped there and flagged so the host rebuilds the cache (outer loop of Alg. F).  After
-// convergence rho = rho(h) (Eq. rhoh) and Omega = 1 + h/(3 rho) sum_b m dW/dh at the final h.
+// convergence rho = rho(h) (Eq. rhoh) and Omega = 1 + h/(3 rho) sum_b m dW/dh at the final h, the
+// sum carried from the last Newton evaluation to the final h by its h-derivative (second-order
+// error in a step below eps_c h^n), so no further pass over the neighbours is needed.
 // FP64 path: all pair arithmetic in FP64.  Mixed path: pair sums in FP32 (Kahan) on cell-relative
 // offsets; Newton update, h, rho and Omega in FP64.
 #include <cstddef>
@@ -21,13 +23,15 @@ struct DensParams {
     const double *box_mass;   // per-box particle mass (batch) or nullptr
 };
 
-// Sums over the neighbours of a at smoothing length h:  sf = sum f(q),  sg = sum (3 f + q f')
-// (self term included: f(0) = 1, 3 f(0) = 3).
+// Sums over the neighbours of a at smoothing length h:  sf = sum f(q),  sg = sum (3 f + q f'),
+// sk = sum (12 f + 8 q f' + q^2 f'')  (self term included: 1, 3 and 12), so that
+//   rho_sum = m sf / (pi h^3),  sum m dW/dh = -m sg / (pi h^4),  sum m d2W/dh2 = m sk / (pi h^5).
 template <bool kMixed>
 __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt, const uint32_t *__restrict__ ids,
                                              const double *__restrict__ x, const double *__restrict__ y,
                                              const double *__restrict__ z, const float4 *__restrict__ rel,
-                                             const PairGeo &geo, double &sf, double &sg, uint32_t &nin) {
+                                             const PairGeo &geo, double &sf, double &sg, double &sk,
+                                             uint32_t &nin) {
     const double hinv = 1.0 / ha;
     if (!kMixed) {
         // FP32 pre-test on the cell-relative offsets skips the candidates that are clearly outside
@@ -36,7 +40,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         const double hinv2 = hinv * hinv;
         const float4 A = rel[a];
         const float lim = 4.f * kPreBand / ((float)hinv2);
-        double f0 = 1.0, g0 = 3.0;
+        double f0 = 1.0, g0 = 3.0, k0 = 12.0;
         for (uint32_t k = 0; k < cnt; k++) {
             const uint32_t b = ids[(int64_t)k * 32];
             float fx, fy, fz;
@@ -52,18 +56,21 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 const double q = sqrt(q2);
                 double f, df;
                 m4(q, f, df);
+                const double qdf = q * df;
                 f0 += f;
-                g0 += 3.0 * f + q * df;
+                g0 += 3.0 * f + qdf;
+                k0 += 12.0 * f + 8.0 * qdf + q2 * m4_d2(q);
             }
         }
         sf = f0;
         sg = g0;
+        sk = k0;
     } else {
         // FP32 path: four neighbours per iteration so that four independent gathers are in flight
         const float4 A = rel[a];
         const float hi = (float)hinv;
         const float hi2 = hi * hi;
-        float s0 = 1.f, c0 = 0.f, s1 = 3.f, c1 = 0.f;
+        float s0 = 1.f, c0 = 0.f, s1 = 3.f, c1 = 0.f, s2 = 12.f;
         auto acc = [&](const float4 B) {
             float dx, dy, dz;
             rel_sep(A, B, geo, dx, dy, dz);
@@ -73,8 +80,10 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 const float q = sqrtf(q2);
                 float f, df;
                 m4(q, f, df);
+                const float qdf = q * df;
                 kahan_add(s0, c0, f);
-                kahan_add(s1, c1, 3.f * f + q * df);
+                kahan_add(s1, c1, 3.f * f + qdf);
+                s2 += 12.f * f + 8.f * qdf + q2 * m4_d2(q);   // only scales a step of order eps_c
             }
         };
         uint32_t k = 0;
@@ -90,6 +99,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         for (; k < cnt; k++) acc(rel[ids[(int64_t)k * 32]]);
         sf = kahan_value(s0, c0);
         sg = kahan_value(s1, c1);
+        sk = (double)s2;
     }
 }
 
@@ -114,10 +124,11 @@ __global__ void __launch_bounds__(128) k_density(Groups gr, int64_t G, const dou
     int it = 0;
     uint32_t nin = 0;
     bool stale = false, conv = false;
+    double dsum_new = 0.0;
     while (it < dp.max_iter) {
         ++it;
-        double sf, sg;
-        density_sums<kMixed>(a, ha, cnt, ids, x, y, z, rel, dp.geo, sf, sg, nin);
+        double sf, sg, sk;
+        density_sums<kMixed>(a, ha, cnt, ids, x, y, z, rel, dp.geo, sf, sg, sk, nin);
         const double hinv = 1.0 / ha;
         const double hinv3 = hinv * hinv * hinv;
         const double rho_sum = m * sf * hinv3 * kInvPi;
@@ -131,6 +142,9 @@ __global__ void __launch_bounds__(128) k_density(Groups gr, int64_t G, const dou
             hnew = hn * dp.chi;
             stale = true;
         }
+        // sum m dW/dh at the new h, to first order in the step (|dh| <= eps_c h^n at convergence,
+        // so the neglected term is O(eps_c^2))
+        dsum_new = dsum + m * sk * hinv3 * hinv * hinv * kInvPi * (hnew - ha);
         ha = hnew;
         if (stale) break;
         if (eps <= dp.h_tol) {
@@ -141,17 +155,13 @@ __global__ void __launch_bounds__(128) k_density(Groups gr, int64_t G, const dou
     h[a] = ha;
     if (stale) atomicOr(&sc->flags, kErrStale);
     else if (!conv) atomicOr(&sc->flags, kErrNotConverged);
-    // epilogue at the final h
-    double sf, sg;
-    density_sums<kMixed>(a, ha, cnt, ids, x, y, z, rel, dp.geo, sf, sg, nin);
+    // rho = rho(h) (Eq. rhoh) and Omega (Eq. sphomega) at the final h
     const double hinv = 1.0 / ha;
-    const double hinv3 = hinv * hinv * hinv;
-    const double rho_h = m * hf3 * hinv3;
-    const double dsum = -m * sg * hinv3 * hinv * kInvPi;
+    const double rho_h = m * hf3 * hinv * hinv * hinv;
     rho[a] = rho_h;
-    omega[a] = 1.0 + ha / (3.0 * rho_h) * dsum;
+    omega[a] = 1.0 + ha / (3.0 * rho_h) * dsum_new;
     atomicMax(&sc->max_iters, (uint32_t)it);
-    atomicAdd(&sc->pair_evals, (unsigned long long)cnt * (unsigned long long)(it + 1));
+    atomicAdd(&sc->pair_evals, (unsigned long long)cnt * (unsigned long long)it);
     atomicAdd(&sc->dens_inrange, (unsigned long long)nin);
 }
 

@@ -25,6 +25,14 @@ __device__ __forceinline__ void m4(T q, T &f, T &df) {
     }
 }
 
+// d2f/dq2 of M4: 9/2 q - 3 (q<1), 3/2 (2-q) (1<=q<2), 0 beyond.
+template <typename T>
+__device__ __forceinline__ T m4_d2(T q) {
+    if (q < T(1)) return T(4.5) * q - T(3);
+    if (q < T(2)) return T(1.5) * (T(2) - q);
+    return T(0);
+}
+
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
     const float y = __fsub_rn(v, c);
     const float t = __fadd_rn(s, y);
