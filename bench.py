@@ -29,10 +29,10 @@ FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (152 SMs x 4 FP64 flop/clk x 2
 FP32_PEAK_TFLOPS = 80.5      # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
 # Algorithmic FLOPs of the FP64 pair loops (counted from the formulas the kernels evaluate; sqrt,
-# rsqrt and division count as one operation each).  The force loop evaluates each pair once.
-FLOP_FORCE_CAND = 10         # per unordered cached pair: separation, r^2, radius test
-FLOP_FORCE_PAIR = 85         # per unordered pair in range: both kernel gradients, AV of both sides,
-                             # momentum, both energy terms, conductivity, divergence, v_sig
+# rsqrt and division count as one operation each), per ordered pair (a, b).
+FLOP_FORCE_CAND = 10         # per cached pair: separation, r^2, radius test
+FLOP_FORCE_PAIR = 72         # per pair in range: kernel gradients, AV, momentum, energy, conductivity,
+                             # divergence, v_sig
 FLOP_DENS_CAND = 9           # separation, q^2
 FLOP_DENS_PAIR = 20          # sqrt, M4 value and two derivatives, the three sums
 
@@ -187,12 +187,18 @@ def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349) -> dict
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     st = solver.stats()
+    solver.set_timing(True)
+    solver.reset_timing()
+    solver.step(s)
+    stage = solver.stats()["stage_ms"]
     solver.close()
     n = int(off[-1])
     return {"value": n / (ms * 1e-3), "unit": "particles/s", "ms_per_step": ms, "boxes": len(boxes), "particles": n,
             "smallest_box": int(min(b["n"] for b in boxes)), "largest_box": int(max(b["n"] for b in boxes)),
             "dtype": "f32 pair sums (Kahan) / f64 state", "launches_per_step": (st["kernel_launches"] - l0) / steps,
-            "timing": "per-box CFL steps, one context, one launch per stage for all boxes"}
+            "timing": "per-box CFL steps, one context, one launch per stage for all boxes", "stage_ms": stage,
+            "density_iters_max": st["density_iters_max"], "outer_passes": st["outer_passes"],
+            "cache_pairs": st["n_pairs"], "stage2_chunks": st["cand_chunks"]}
 
 
 def e2e_run(torch, sph, solver, s, steps: int):
@@ -257,7 +263,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
-    ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
+    ap.add_argument("--only", choices=["fp64", "mixed", "ensemble"], default=None,
                     help="run one precision only (profiling); the headline needs both")
     args = ap.parse_args()
 
@@ -306,6 +312,9 @@ def main():
     w = make_workload(args.workload, rank)
     n = w["n"]
     clocks = ClockSampler(local)
+    if args.only == "ensemble":
+        print(json.dumps({"workload": "ensemble", **run_ensemble(torch, sph, args.steps, max(args.warmup, 3))}))
+        return
     if args.only == "mixed":
         r = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, clocks)
         print(json.dumps({"workload": args.workload, "precision": "mixed", "ms_per_step": r["ms_per_step"],
@@ -325,7 +334,7 @@ def main():
         flops = st["density_pair_evals"] * FLOP_DENS_CAND + st["density_inrange"] * FLOP_DENS_PAIR
         kname = "k_density<FP64>"
     else:
-        flops = st["n_pairs"] // 2 * FLOP_FORCE_CAND + st["force_pairs"] // 2 * FLOP_FORCE_PAIR
+        flops = st["n_pairs"] * FLOP_FORCE_CAND + st["force_pairs"] * FLOP_FORCE_PAIR
         kname = "k_forces_fp64"
         dominant = "forces"
     kms = stage[dominant]

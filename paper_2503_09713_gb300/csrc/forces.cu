@@ -108,16 +108,9 @@ __device__ __forceinline__ void dt_reduce(double t, unsigned long long npair, De
     }
 }
 
-// FP64 pair loop, each pair evaluated once.  The cache is symmetric (b is a neighbour of a exactly
-// when a is one of b), so particle a takes the pairs with b > a: it keeps its own sums in registers
-// and adds b's share (opposite momentum term, b's energy term, the opposite conduction term, b's
-// divergence term, b's signal speed) with atomic operations; its own sums are added atomically at
-// the end, because other particles add to them too.  A candidate is first tested in FP32 on the
-// cell-relative offsets against the current h (kPreBand margin); the survivors are decided and
-// evaluated in FP64 with the nearest image from the cell indices.  Accumulators hold the sums
-// without the mass factor, k_forces_finish applies it.
-__device__ __forceinline__ unsigned long long *as_bits(double *p) { return reinterpret_cast<unsigned long long *>(p); }
-
+// FP64 pair loop.  A candidate is first tested in FP32 on the cell-relative offsets against the
+// current h (kPreBand margin); the survivors are decided and evaluated in FP64 with the nearest
+// image from the cell indices.  The mass factor is applied once per particle.
 __global__ void __launch_bounds__(128) k_forces_fp64(Groups gr, int64_t G, const FRec *__restrict__ rec,
                                                      const float4 *__restrict__ rel, const float *__restrict__ h32,
                                                      const uint32_t *__restrict__ nb_cnt,
@@ -126,9 +119,12 @@ __global__ void __launch_bounds__(128) k_forces_fp64(Groups gr, int64_t G, const
                                                      DevScalars *sc) {
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (g >= G) return;
+    if (g >= G) return;   // whole warp
     const int64_t a = group_first(gr, g) + lane;
-    if (a >= group_end(gr, g)) return;
+    const int box = group_box_of(gr, g);
+    double tdt = INFINITY;
+    unsigned long long npair = 0;
+    if (a < group_end(gr, g)) {
     const uint32_t cnt = nb_cnt[a];
     const uint32_t *ids = nb_ids + grp_off[g] + lane;
     FRec A;
@@ -138,10 +134,8 @@ __global__ void __launch_bounds__(128) k_forces_fp64(Groups gr, int64_t G, const
     const PairGeo &geo = fp.geo;
     double axs = 0.0, ays = 0.0, azs = 0.0, dus = 0.0, divs = 0.0;
     double vs = A.acs;
-    unsigned long long npair = 0;
     for (uint32_t k = 0; k < cnt; k++) {
         const uint32_t b = ids[(int64_t)k * 32];
-        if ((int64_t)b <= a) continue;
         float fx, fy, fz;
         int sx, sy, sz;
         rel_sep_shift(PA, rel[b], geo, fx, fy, fz, sx, sy, sz);
@@ -156,7 +150,7 @@ __global__ void __launch_bounds__(128) k_forces_fp64(Groups gr, int64_t G, const
         const double hm = A.h > B.h ? A.h : B.h;
         const double rad = __dmul_rn(2.0, hm);
         if (!(r2 < __dmul_rn(rad, rad))) continue;
-        npair += 2;
+        ++npair;
         const double rinv = rsqrt(r2);
         const double r = r2 * rinv;
         double f, dfa, dfb;
@@ -171,64 +165,35 @@ __global__ void __launch_bounds__(128) k_forces_fp64(Groups gr, int64_t G, const
             Aa -= 0.5 * (A.acs - w) * vdotr * A.qf;
             Ab -= 0.5 * (B.acs - w) * vdotr * B.qf;
             vs = fmax(vs, A.acs - w);
-            atomicMax(as_bits(&out.vsig[b]), dbits(B.acs - w));
         }
         const double sc_ = (Aa * Fa + Ab * Fb) * rinv;
-        const double px = sc_ * dx, py = sc_ * dy, pz = sc_ * dz;
-        axs -= px;
-        ays -= py;
-        azs -= pz;
-        double dua = Aa * vdotr * Fa;
-        double dub = Ab * vdotr * Fb;
+        axs -= sc_ * dx;
+        ays -= sc_ * dy;
+        azs -= sc_ * dz;
+        dus += Aa * vdotr * Fa;
         divs += vdotr * Fa;
         if (fp.alpha_u != 0.0) {
             const double t = 2.0 * fabs(A.P - B.P);   // v_sig^u = sqrt(t / (rho_a + rho_b))
             if (t > 0.0) {
                 const double vsu = t * rsqrt(t * (A.rho + B.rho));
-                const double cond = fp.alpha_u * vsu * (A.u - B.u) * 0.5 * (Fa * A.qf + Fb * B.qf);
-                dua += cond;
-                dub -= cond;
+                dus += fp.alpha_u * vsu * (A.u - B.u) * 0.5 * (Fa * A.qf + Fb * B.qf);
             }
         }
-        dus += dua;
-        atomicAdd(&out.ax[b], px);
-        atomicAdd(&out.ay[b], py);
-        atomicAdd(&out.az[b], pz);
-        atomicAdd(&out.du[b], dub);
-        atomicAdd(&out.dhdt[b], vdotr * Fb);
     }
-    atomicAdd(&out.ax[a], axs);
-    atomicAdd(&out.ay[a], ays);
-    atomicAdd(&out.az[a], azs);
-    atomicAdd(&out.du[a], dus);
-    atomicAdd(&out.dhdt[a], divs);
-    atomicMax(as_bits(&out.vsig[a]), dbits(vs));
-    if (npair) atomicAdd(&sc->inrange_pairs, npair);
-}
-
-// Mass factor, dh/dt, v_sig (at least alpha c_s) and the CFL candidates (per warp = group = box).
-__global__ void __launch_bounds__(128) k_forces_finish(Groups gr, int64_t G, const FRec *__restrict__ rec,
-                                                       ForceParams fp, ForceOut out, DevScalars *sc) {
-    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (g >= G) return;
-    const int64_t a = group_first(gr, g) + lane;
-    const int box = group_box_of(gr, g);
     const double m = fp.box_mass ? fp.box_mass[box] : fp.mass;
-    double tdt = INFINITY;
-    if (a < group_end(gr, g)) {
-        const FRec A = rec[a];
-        const double axs = m * out.ax[a], ays = m * out.ay[a], azs = m * out.az[a];
-        out.ax[a] = axs;
-        out.ay[a] = ays;
-        out.az[a] = azs;
-        out.du[a] = m * out.du[a];
-        out.dhdt[a] = -A.h * A.qf * (1.0 / 3.0) * m * out.dhdt[a];
-        const double vs = fmax(out.vsig[a], A.acs);
-        out.vsig[a] = vs;
-        tdt = dt_candidate(A.h, vs, axs, ays, azs, fp);
+    axs *= m;
+    ays *= m;
+    azs *= m;
+    dus *= m;
+    out.ax[a] = axs;
+    out.ay[a] = ays;
+    out.az[a] = azs;
+    out.du[a] = dus;
+    out.vsig[a] = vs;
+    out.dhdt[a] = -A.h * A.qf * (1.0 / 3.0) * m * divs;
+    tdt = dt_candidate(A.h, vs, axs, ays, azs, fp);
     }
-    dt_reduce(tdt, 0ULL, sc, fp.box_dt_next, box);
+    dt_reduce(tdt, npair, sc, fp.box_dt_next, box);
 }
 
 __global__ void __launch_bounds__(128) k_forces_mixed(Groups gr, int64_t G, const float4 *__restrict__ rel,
@@ -361,15 +326,9 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
         k_forces_mixed<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, c->rel, c->m_v, c->m_t, c->m_r, s->h,
                                                                 c->nb_cnt, c->grp_off, c->nb_ids, fp, out, c->dscal);
     else
-    {
-        for (double *p : {ax, ay, az, du, s->vsig, c->dhdt})
-            SPH_CUDA(c, cudaMemsetAsync(p, 0, (size_t)n * sizeof(double), c->stream));
         k_forces_fp64<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, (const FRec *)c->frec, c->rel, c->h32,
                                                                     c->nb_cnt, c->grp_off, c->nb_ids, fp, out,
                                                                     c->dscal);
-        SPH_LAUNCH_CHECK(c, "k_forces_fp64");
-        k_forces_finish<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, (const FRec *)c->frec, fp, out, c->dscal);
-    }
     SPH_LAUNCH_CHECK(c, "k_forces");
     return stage_end(c, kStForces);
 }
