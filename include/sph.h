@@ -100,6 +100,9 @@ typedef struct {
     int32_t *endrange;              /* [L-1] */
     double *bmin, *bmax;            /* [3*(2L-1)] tight per-node box, node-major (x,y,z) */
     double *hmax;                   /* [2L-1] largest h in the node */
+    int64_t *group_start;  /* [G+1] first particle of each neighbour-search group, [G] = n, with
+                            * G = sph_stats.n_groups: the largest nodes holding at most 32 particles
+                            * of one box (a leaf of more than 32 is cut into runs of 32) */
 } sph_tree_view;
 
 /* Per-call statistics (host copy, filled by the library after each stage). */

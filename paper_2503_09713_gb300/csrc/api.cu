@@ -43,15 +43,39 @@ int stage_end(sph_ctx *c, int k) {
     return SPH_OK;
 }
 
-Groups make_groups(const sph_ctx *c, int64_t n) {
+Groups make_groups(const sph_ctx *c) {
     Groups g;
-    g.start = c->batch ? c->gstart : nullptr;
+    g.start = c->gstart;
     g.box = c->batch ? c->group_box : nullptr;
-    g.n = n;
     return g;
 }
 
-int64_t group_count(const sph_ctx *c, int64_t n) { return c->batch ? c->batch_groups : (n + 31) / 32; }
+// Per-group arrays for G groups (their number is known only after a tree build); grown with a
+// margin, contents not kept.
+int ensure_groups(sph_ctx *c, int64_t G) {
+    if (G <= c->g_cap) return SPH_OK;
+    const int64_t cap = G + G / 4 + 64;
+    void **ptrs[] = {(void **)&c->gbox, (void **)&c->gboxf, (void **)&c->grp_chunks, (void **)&c->chunk_off,
+                     (void **)&c->cand, (void **)&c->cand_cnt, (void **)&c->grp_slots, (void **)&c->grp_off,
+                     (void **)&c->gstart, (void **)&c->group_box};
+    const size_t bytes[] = {(size_t)cap * sizeof(Node), (size_t)cap * sizeof(NodeF), (size_t)(cap + 1) * 8,
+                            (size_t)(cap + 1) * 8, (size_t)cap * c->cand_cap * sizeof(uint2), (size_t)cap * 4,
+                            (size_t)(cap + 1) * 8, (size_t)(cap + 1) * 8, (size_t)(cap + 1) * 8,
+                            (size_t)cap * 2};
+    c->g_cap = 0;
+    for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); k++) {
+        if (*ptrs[k]) SPH_CUDA(c, cudaFree(*ptrs[k]));
+        *ptrs[k] = nullptr;
+    }
+    for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); k++) {
+        if (cudaMalloc(ptrs[k], bytes[k]) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, SPH_ERR_OOM, "per-group arrays for %lld groups", (long long)cap);
+        }
+    }
+    c->g_cap = cap;
+    return SPH_OK;
+}
 
 int read_scalars(sph_ctx *c) {
     SPH_CUDA(c, cudaMemcpyAsync(c->hscal, c->dscal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
@@ -82,7 +106,7 @@ void free_all(sph_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->digit_hist, c->lookback, c->tile_ctr,
                     c->mask[0], c->mask[1], c->scan_tmp, c->leaf_first, c->mu_leaf, c->lchild, c->rchild,
                     c->endrange, c->lflag, c->rflag, c->child, c->node_parent, c->leaf_parent, c->visit, c->nodes, c->nodesf,
-                    c->gather_tmp, c->id_tmp, c->rel, c->h32, c->h_base, c->gbox, c->gboxf, c->grp_chunks, c->chunk_off, c->masks, c->cand, c->cand_cnt, c->nb_cnt,
+                    c->gather_tmp, c->id_tmp, c->rel, c->h32, c->h_base, c->gbox, c->gboxf, c->grp_chunks, c->chunk_off, c->masks, c->cand, c->cand_cnt, c->nb_cnt, c->nb_ptr,
                     c->grp_slots, c->grp_off, c->nb_ids, c->frec, c->m_v, c->m_t, c->m_r, c->a_new, c->dhdt, c->block_part,
                     c->hs_fields, c->hs_id, c->dscal, c->box_of, c->box_mass, c->box_gamma, c->box_root,
                     c->box_dt, c->box_dt_next, c->gstart, c->group_box};
@@ -196,8 +220,8 @@ void sph_default_params(sph_params *p) {
 
 namespace {
 
-// Context for n_cap particles split into at most (n_cap + 31)/32 + extra_groups groups.
-int create_ctx(const sph_params *p, int64_t n_cap, int64_t extra_groups, int n_boxes, int64_t neigh_cap,
+// Context for n_cap particles in n_boxes boxes.
+int create_ctx(const sph_params *p, int64_t n_cap, int n_boxes, int64_t neigh_cap,
                void *stream, sph_ctx **out) {
     if (!out) return SPH_ERR_INVALID_ARG;
     *out = nullptr;
@@ -216,7 +240,7 @@ int create_ctx(const sph_params *p, int64_t n_cap, int64_t extra_groups, int n_b
         return SPH_ERR_CUDA;
     }
     const int64_t N = n_cap;
-    const int64_t G = (N + 31) / 32 + extra_groups;
+    const int64_t G = (N + 31) / 32 + n_boxes;   // per-group arrays: first guess, grown by ensure_groups
     const int64_t tiles = (N + 4095) / 4096;
     const int64_t chunks = (N + 2047) / 2048;
     c->sort_tiles = tiles;
@@ -234,10 +258,8 @@ int create_ctx(const sph_params *p, int64_t n_cap, int64_t extra_groups, int n_b
         (r = alloc(c, &c->leaf_parent, N)) || (r = alloc(c, &c->visit, N)) || (r = alloc(c, &c->nodes, 2 * N)) || (r = alloc(c, &c->nodesf, 2 * N)) ||
         (r = alloc(c, &c->gather_tmp, (size_t)16 * N)) || (r = alloc(c, &c->id_tmp, N)) ||
         (r = alloc(c, &c->rel, N)) || (r = alloc(c, &c->h32, N)) || (r = alloc(c, &c->h_base, N)) ||
-        (r = alloc(c, &c->gbox, G)) || (r = alloc(c, &c->gboxf, G)) || (r = alloc(c, &c->grp_chunks, G + 1)) ||
-        (r = alloc(c, &c->chunk_off, G + 1)) || (r = alloc(c, &c->cand, (size_t)G * c->cand_cap)) || (r = alloc(c, &c->masks, (size_t)G * 40 * 32)) ||
-        (r = alloc(c, &c->cand_cnt, G)) || (r = alloc(c, &c->nb_cnt, N)) || (r = alloc(c, &c->grp_slots, G + 1)) ||
-        (r = alloc(c, &c->grp_off, G + 1)) || (r = alloc(c, &c->nb_ids, c->nb_cap)) ||
+        (r = ensure_groups(c, G)) || (r = alloc(c, &c->masks, (size_t)G * 40 * 32)) ||
+        (r = alloc(c, &c->nb_cnt, N)) || (r = alloc(c, &c->nb_ptr, N)) || (r = alloc(c, &c->nb_ids, c->nb_cap)) ||
         (r = alloc(c, (char **)&c->frec, (size_t)128 * N)) || (r = alloc(c, &c->m_v, N)) ||
         (r = alloc(c, &c->m_t, N)) || (r = alloc(c, &c->m_r, N)) || (r = alloc(c, &c->a_new, (size_t)4 * N)) || (r = alloc(c, &c->dhdt, N)) ||
         (r = alloc(c, &c->block_part, (size_t)(N / 256 + 2))) || (r = alloc(c, &c->dscal, 1)) ||
@@ -275,7 +297,7 @@ int create_ctx(const sph_params *p, int64_t n_cap, int64_t extra_groups, int n_b
 extern "C" {
 
 int sph_create(const sph_params *p, int64_t n_cap, int64_t neigh_cap, void *stream, sph_ctx **out) {
-    return create_ctx(p, n_cap, 0, 1, neigh_cap, stream, out);
+    return create_ctx(p, n_cap, 1, neigh_cap, stream, out);
 }
 
 int sph_batch_create(const sph_params *p, int n_boxes, const int64_t *box_offsets, const double *box_mass,
@@ -284,16 +306,14 @@ int sph_batch_create(const sph_params *p, int n_boxes, const int64_t *box_offset
     *out = nullptr;
     if (!p || n_boxes < 1 || n_boxes > 4096 || !box_offsets || !box_mass) return SPH_ERR_INVALID_ARG;
     if (box_offsets[0] != 0) return SPH_ERR_INVALID_ARG;
-    int64_t groups = 0;
     for (int b = 0; b < n_boxes; b++) {
         const int64_t nb = box_offsets[b + 1] - box_offsets[b];
         if (nb < 0 || !(box_mass[b] > 0) || (box_gamma && !(box_gamma[b] > 1))) return SPH_ERR_INVALID_ARG;
-        groups += (nb + 31) / 32;
     }
     const int64_t total = box_offsets[n_boxes];
     if (total < 1) return SPH_ERR_INVALID_ARG;
     sph_ctx *c = nullptr;
-    int r = create_ctx(p, total, n_boxes, n_boxes, neigh_cap, stream, &c);
+    int r = create_ctx(p, total, n_boxes, neigh_cap, stream, &c);
     if (r) return r;
     c->batch = true;
     c->n_boxes = n_boxes;
@@ -302,22 +322,12 @@ int sph_batch_create(const sph_params *p, int n_boxes, const int64_t *box_offset
     c->box_bits = bits;
     c->morton_bits = std::min(21, (63 - bits) / 3);
     c->h_box_off.assign(box_offsets, box_offsets + n_boxes + 1);
-    c->batch_groups = groups;
-    std::vector<uint16_t> box_of((size_t)total), group_box((size_t)groups);
-    std::vector<int64_t> gstart((size_t)groups + 1);
+    std::vector<uint16_t> box_of((size_t)total);
     std::vector<double> gam((size_t)n_boxes);
-    int64_t g = 0;
     for (int b = 0; b < n_boxes; b++) {
         for (int64_t i = box_offsets[b]; i < box_offsets[b + 1]; i++) box_of[(size_t)i] = (uint16_t)b;
-        for (int64_t f = box_offsets[b]; f < box_offsets[b + 1]; f += 32) {
-            gstart[(size_t)g] = f;
-            group_box[(size_t)g] = (uint16_t)b;
-            ++g;
-        }
         gam[(size_t)b] = box_gamma ? box_gamma[b] : p->gamma;
     }
-    gstart[(size_t)groups] = total;
-    c->h_gstart = gstart;
     c->h_box_dt.assign((size_t)n_boxes, -1.0);
     auto up = [&](void *dst, const void *src, size_t bytes) -> int {
         SPH_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
@@ -325,11 +335,8 @@ int sph_batch_create(const sph_params *p, int n_boxes, const int64_t *box_offset
     };
     if ((r = alloc(c, &c->box_of, total)) || (r = alloc(c, &c->box_mass, n_boxes)) ||
         (r = alloc(c, &c->box_gamma, n_boxes)) || (r = alloc(c, &c->box_dt, n_boxes)) ||
-        (r = alloc(c, &c->box_dt_next, n_boxes)) || (r = alloc(c, &c->gstart, groups + 1)) ||
-        (r = alloc(c, &c->group_box, groups)) || (r = up(c->box_of, box_of.data(), box_of.size() * 2)) ||
-        (r = up(c->box_mass, box_mass, (size_t)n_boxes * 8)) || (r = up(c->box_gamma, gam.data(), gam.size() * 8)) ||
-        (r = up(c->gstart, gstart.data(), gstart.size() * 8)) ||
-        (r = up(c->group_box, group_box.data(), group_box.size() * 2))) {
+        (r = alloc(c, &c->box_dt_next, n_boxes)) || (r = up(c->box_of, box_of.data(), box_of.size() * 2)) ||
+        (r = up(c->box_mass, box_mass, (size_t)n_boxes * 8)) || (r = up(c->box_gamma, gam.data(), gam.size() * 8))) {
         sph_destroy(c);
         return r;
     }
@@ -519,7 +526,8 @@ int sph_export_tree(sph_ctx *c, sph_tree_view *v) {
         (r = cp(v->leaf_first, c->leaf_first, (L + 1) * 8)) || (r = cp(v->mu_leaf, c->mu_leaf, L * 8)) ||
         (r = cp(v->lchild, c->lchild, nin * 4)) || (r = cp(v->rchild, c->rchild, nin * 4)) ||
         (r = cp(v->lflag, c->lflag, nin)) || (r = cp(v->rflag, c->rflag, nin)) ||
-        (r = cp(v->endrange, c->endrange, nin * 4)))
+        (r = cp(v->endrange, c->endrange, nin * 4)) ||
+        (r = cp(v->group_start, c->gstart, (c->n_groups + 1) * 8)))
         return r;
     if (v->bmin || v->bmax || v->hmax) {
         std::vector<Node> nd((size_t)nodes);
@@ -542,10 +550,11 @@ int sph_export_neighbours(sph_ctx *c, int64_t *off, uint32_t *ids) {
     if (!c->cache_valid) return fail(c, SPH_ERR_ORDER, "no neighbour cache");
     const int64_t n = c->n, G = c->n_groups;
     std::vector<uint32_t> cnt((size_t)n);
-    std::vector<int64_t> goff((size_t)G + 1);
+    std::vector<int64_t> goff((size_t)G + 1), gst((size_t)G + 1);
     std::vector<uint32_t> raw((size_t)std::max<int64_t>(c->total_slots, 1));
     SPH_CUDA(c, cudaMemcpyAsync(cnt.data(), c->nb_cnt, n * 4, cudaMemcpyDeviceToHost, c->stream));
     SPH_CUDA(c, cudaMemcpyAsync(goff.data(), c->grp_off, (G + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    SPH_CUDA(c, cudaMemcpyAsync(gst.data(), c->gstart, (G + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
     if (c->total_slots > 0)
         SPH_CUDA(c, cudaMemcpyAsync(raw.data(), c->nb_ids, c->total_slots * 4, cudaMemcpyDeviceToHost, c->stream));
     SPH_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -553,11 +562,10 @@ int sph_export_neighbours(sph_ctx *c, int64_t *off, uint32_t *ids) {
     for (int64_t a = 0; a < n; a++) off[a + 1] = off[a] + cnt[a];
     if (ids) {
         for (int64_t g = 0; g < G; g++) {
-            const int64_t first = c->batch ? c->h_gstart[(size_t)g] : 32 * g;
-            const int64_t end = c->batch ? c->h_gstart[(size_t)g + 1] : std::min<int64_t>(32 * g + 32, n);
+            const int64_t first = gst[(size_t)g], end = gst[(size_t)g + 1], size = end - first;
             for (int64_t a = first; a < end; a++) {
                 const int64_t base = goff[g] + (a - first);
-                for (uint32_t k = 0; k < cnt[a]; k++) ids[off[a] + k] = raw[base + (int64_t)k * 32];
+                for (uint32_t k = 0; k < cnt[a]; k++) ids[off[a] + k] = raw[base + (int64_t)k * size];
             }
         }
     }

@@ -21,6 +21,7 @@ struct DensParams {
     int max_iter;
     PairGeo geo;
     const double *box_mass;   // per-box particle mass (batch) or nullptr
+    const uint16_t *box_of;   // box of each particle (batch) or nullptr
 };
 
 // Sums over the neighbours of a at smoothing length h:  sf = sum f(q),  sg = sum (3 f + q f'),
@@ -28,6 +29,7 @@ struct DensParams {
 //   rho_sum = m sf / (pi h^3),  sum m dW/dh = -m sg / (pi h^4),  sum m d2W/dh2 = m sk / (pi h^5).
 template <bool kMixed>
 __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt, const uint32_t *__restrict__ ids,
+                                             int64_t st,
                                              const double *__restrict__ x, const double *__restrict__ y,
                                              const double *__restrict__ z, const float4 *__restrict__ rel,
                                              const PairGeo &geo, double &sf, double &sg, double &sk,
@@ -42,7 +44,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         const float lim = 4.f * kPreBand / ((float)hinv2);
         double f0 = 1.0, g0 = 3.0, k0 = 12.0;
         for (uint32_t k = 0; k < cnt; k++) {
-            const uint32_t b = ids[(int64_t)k * 32];
+            const uint32_t b = ids[(int64_t)k * st];
             float fx, fy, fz;
             int sx, sy, sz;
             rel_sep_shift(A, rel[b], geo, fx, fy, fz, sx, sy, sz);
@@ -86,17 +88,31 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 s2 += 12.f * f + 8.f * qdf + q2 * m4_d2(q);   // only scales a step of order eps_c
             }
         };
+        // software pipeline: the indices of the next four neighbours are loaded while the current
+        // four are gathered and summed
         uint32_t k = 0;
+        uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+        if (cnt >= 4) {
+            n0 = ids[0];
+            n1 = ids[st];
+            n2 = ids[2 * st];
+            n3 = ids[3 * st];
+        }
         for (; k + 4 <= cnt; k += 4) {
-            const uint32_t b0 = ids[(int64_t)k * 32], b1 = ids[(int64_t)(k + 1) * 32];
-            const uint32_t b2 = ids[(int64_t)(k + 2) * 32], b3 = ids[(int64_t)(k + 3) * 32];
+            const uint32_t b0 = n0, b1 = n1, b2 = n2, b3 = n3;
+            if (k + 8 <= cnt) {
+                n0 = ids[(int64_t)(k + 4) * st];
+                n1 = ids[(int64_t)(k + 5) * st];
+                n2 = ids[(int64_t)(k + 6) * st];
+                n3 = ids[(int64_t)(k + 7) * st];
+            }
             const float4 B0 = rel[b0], B1 = rel[b1], B2 = rel[b2], B3 = rel[b3];
             acc(B0);
             acc(B1);
             acc(B2);
             acc(B3);
         }
-        for (; k < cnt; k++) acc(rel[ids[(int64_t)k * 32]]);
+        for (; k < cnt; k++) acc(rel[ids[(int64_t)k * st]]);
         sf = kahan_value(s0, c0);
         sg = kahan_value(s1, c1);
         sk = (double)s2;
@@ -104,22 +120,21 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
 }
 
 template <bool kMixed>
-__global__ void __launch_bounds__(128) k_density(Groups gr, int64_t G, const double *__restrict__ x, const double *__restrict__ y,
+__global__ void __launch_bounds__(128) k_density(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                                                  const double *__restrict__ z, const float4 *__restrict__ rel,
                                                  double *__restrict__ h, const double *__restrict__ h_base,
-                                                 const uint32_t *__restrict__ nb_cnt, const int64_t *__restrict__ grp_off,
+                                                 const uint32_t *__restrict__ nb_cnt,
+                                                 const unsigned long long *__restrict__ nb_ptr,
                                                  const uint32_t *__restrict__ nb_ids, DensParams dp,
                                                  double *__restrict__ rho, double *__restrict__ omega, DevScalars *sc) {
-    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (g >= G) return;
-    const int64_t a = group_first(gr, g) + lane;
-    if (a >= group_end(gr, g)) return;
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one thread per particle
+    if (a >= n) return;
     const uint32_t cnt = nb_cnt[a];
-    const uint32_t *ids = nb_ids + grp_off[g] + lane;
+    int64_t st;
+    const uint32_t *ids = nb_list(nb_ids, nb_ptr[a], st);
     double ha = h[a];
     const double hn = h_base[a];
-    const double m = dp.box_mass ? dp.box_mass[group_box_of(gr, g)] : dp.mass;
+    const double m = dp.box_mass ? dp.box_mass[dp.box_of[a]] : dp.mass;
     const double hf3 = dp.hfact * dp.hfact * dp.hfact;
     int it = 0;
     uint32_t nin = 0;
@@ -128,7 +143,7 @@ __global__ void __launch_bounds__(128) k_density(Groups gr, int64_t G, const dou
     while (it < dp.max_iter) {
         ++it;
         double sf, sg, sk;
-        density_sums<kMixed>(a, ha, cnt, ids, x, y, z, rel, dp.geo, sf, sg, sk, nin);
+        density_sums<kMixed>(a, ha, cnt, ids, st, x, y, z, rel, dp.geo, sf, sg, sk, nin);
         const double hinv = 1.0 / ha;
         const double hinv3 = hinv * hinv * hinv;
         const double rho_sum = m * sf * hinv3 * kInvPi;
@@ -177,18 +192,17 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
     dp.max_iter = c->p.h_max_iter;
     dp.geo = make_pair_geo(c->p);
     dp.box_mass = c->batch ? c->box_mass : nullptr;
-    const int64_t G = group_count(c, n);
-    const Groups gr = make_groups(c, n);
+    dp.box_of = c->batch ? c->box_of : nullptr;
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->max_iters, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->pair_evals, 0, 2 * sizeof(unsigned long long), c->stream));
     if (c->p.precision == SPH_MIXED)
-        k_density<true><<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, s->x, s->y, s->z, c->rel, s->h, c->h_base,
-                                                                 c->nb_cnt, c->grp_off, c->nb_ids, dp, s->rho,
+        k_density<true><<<grid_for(n, 128), 128, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+                                                                 c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
                                                                  s->omega, c->dscal);
     else
-        k_density<false><<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, s->x, s->y, s->z, c->rel, s->h, c->h_base,
-                                                                  c->nb_cnt, c->grp_off, c->nb_ids, dp, s->rho,
+        k_density<false><<<grid_for(n, 128), 128, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+                                                                  c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
                                                                   s->omega, c->dscal);
     SPH_LAUNCH_CHECK(c, "k_density");
     static_assert(offsetof(DevScalars, flags) == offsetof(DevScalars, max_iters) + sizeof(uint32_t), "layout");

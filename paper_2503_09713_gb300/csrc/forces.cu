@@ -91,42 +91,49 @@ __device__ __forceinline__ double dt_candidate(double h, double vs, double ax, d
 }
 
 // Warp minimum of the CFL candidates and warp sum of the in-range pair counts (all 32 lanes
-// participate; a warp is one group, inside one box), then one atomic each per warp; positive
-// doubles order like their bit patterns.
+// participate), then one atomic each per warp; positive doubles order like their bit patterns.  A
+// warp whose particles lie in one box updates that box's minimum once; a warp across a box boundary
+// updates it lane by lane.
 __device__ __forceinline__ void dt_reduce(double t, unsigned long long npair, DevScalars *sc,
                                           unsigned long long *box_dt_next, int box) {
+    double tw = t;
     for (int o = 16; o > 0; o >>= 1) {
-        t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
+        tw = fmin(tw, __shfl_xor_sync(0xffffffffu, tw, o));
         npair += __shfl_xor_sync(0xffffffffu, npair, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        if (t > 0.0 && t < INFINITY) {
-            atomicMin(&sc->dt_min_bits, dbits(t));
-            if (box_dt_next) atomicMin(&box_dt_next[box], dbits(t));
-        }
+    const bool lane0 = (threadIdx.x & 31) == 0;
+    if (lane0) {
+        if (tw > 0.0 && tw < INFINITY) atomicMin(&sc->dt_min_bits, dbits(tw));
         atomicAdd(&sc->inrange_pairs, npair);
+    }
+    if (box_dt_next) {
+        const int box0 = __shfl_sync(0xffffffffu, box, 0);
+        if (__all_sync(0xffffffffu, box == box0)) {
+            if (lane0 && tw > 0.0 && tw < INFINITY) atomicMin(&box_dt_next[box0], dbits(tw));
+        } else if (t > 0.0 && t < INFINITY) {
+            atomicMin(&box_dt_next[box], dbits(t));
+        }
     }
 }
 
 // FP64 pair loop.  A candidate is first tested in FP32 on the cell-relative offsets against the
 // current h (kPreBand margin); the survivors are decided and evaluated in FP64 with the nearest
 // image from the cell indices.  The mass factor is applied once per particle.
-__global__ void __launch_bounds__(128) k_forces_fp64(Groups gr, int64_t G, const FRec *__restrict__ rec,
+__global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__restrict__ rec,
                                                      const float4 *__restrict__ rel, const float *__restrict__ h32,
                                                      const uint32_t *__restrict__ nb_cnt,
-                                                     const int64_t *__restrict__ grp_off,
+                                                     const unsigned long long *__restrict__ nb_ptr,
                                                      const uint32_t *__restrict__ nb_ids, ForceParams fp, ForceOut out,
                                                      DevScalars *sc) {
-    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (g >= G) return;   // whole warp
-    const int64_t a = group_first(gr, g) + lane;
-    const int box = group_box_of(gr, g);
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one thread per particle
+    if (a - (threadIdx.x & 31) >= n) return;   // whole warp past the end
+    const int box = (a < n && fp.box_of) ? fp.box_of[a] : 0;
     double tdt = INFINITY;
     unsigned long long npair = 0;
-    if (a < group_end(gr, g)) {
+    if (a < n) {
     const uint32_t cnt = nb_cnt[a];
-    const uint32_t *ids = nb_ids + grp_off[g] + lane;
+    int64_t st;
+    const uint32_t *ids = nb_list(nb_ids, nb_ptr[a], st);
     FRec A;
     load_rec(&rec[a], A);
     const float4 PA = rel[a];
@@ -135,7 +142,7 @@ __global__ void __launch_bounds__(128) k_forces_fp64(Groups gr, int64_t G, const
     double axs = 0.0, ays = 0.0, azs = 0.0, dus = 0.0, divs = 0.0;
     double vs = A.acs;
     for (uint32_t k = 0; k < cnt; k++) {
-        const uint32_t b = ids[(int64_t)k * 32];
+        const uint32_t b = ids[(int64_t)k * st];
         float fx, fy, fz;
         int sx, sy, sz;
         rel_sep_shift(PA, rel[b], geo, fx, fy, fz, sx, sy, sz);
@@ -196,23 +203,22 @@ __global__ void __launch_bounds__(128) k_forces_fp64(Groups gr, int64_t G, const
     dt_reduce(tdt, npair, sc, fp.box_dt_next, box);
 }
 
-__global__ void __launch_bounds__(128) k_forces_mixed(Groups gr, int64_t G, const float4 *__restrict__ rel,
+__global__ void __launch_bounds__(128) k_forces_mixed(int64_t n, const float4 *__restrict__ rel,
                                                       const float4 *__restrict__ m_v, const float4 *__restrict__ m_t,
                                                       const float4 *__restrict__ m_r, const double *__restrict__ h,
                                                       const uint32_t *__restrict__ nb_cnt,
-                                                      const int64_t *__restrict__ grp_off,
+                                                      const unsigned long long *__restrict__ nb_ptr,
                                                       const uint32_t *__restrict__ nb_ids, ForceParams fp,
                                                       ForceOut out, DevScalars *sc) {
-    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (g >= G) return;   // whole warp
-    const int64_t a = group_first(gr, g) + lane;
-    const int box = group_box_of(gr, g);
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one thread per particle
+    if (a - (threadIdx.x & 31) >= n) return;   // whole warp past the end
+    const int box = (a < n && fp.box_of) ? fp.box_of[a] : 0;
     double tdt = INFINITY;
     unsigned long long npair = 0;
-    if (a < group_end(gr, g)) {
+    if (a < n) {
     const uint32_t cnt = nb_cnt[a];
-    const uint32_t *ids = nb_ids + grp_off[g] + lane;
+    int64_t st;
+    const uint32_t *ids = nb_list(nb_ids, nb_ptr[a], st);
     const float4 PA = rel[a], VA = m_v[a], TA = m_t[a], RA = m_r[a];
     const double mass_d = fp.box_mass ? fp.box_mass[box] : fp.mass;
     const float mass = (float)mass_d, alpha = (float)fp.alpha_av, beta = (float)fp.beta_av,
@@ -262,14 +268,14 @@ __global__ void __launch_bounds__(128) k_forces_mixed(Groups gr, int64_t G, cons
     // two neighbours per iteration: their gathers are issued together
     uint32_t k = 0;
     for (; k + 2 <= cnt; k += 2) {
-        const uint32_t b0 = ids[(int64_t)k * 32], b1 = ids[(int64_t)(k + 1) * 32];
+        const uint32_t b0 = ids[(int64_t)k * st], b1 = ids[(int64_t)(k + 1) * st];
         const float4 P0 = rel[b0], P1 = rel[b1];
         const float4 V0 = m_v[b0], V1 = m_v[b1];
         pair(b0, P0, V0);
         pair(b1, P1, V1);
     }
     if (k < cnt) {
-        const uint32_t b = ids[(int64_t)k * 32];
+        const uint32_t b = ids[(int64_t)k * st];
         pair(b, rel[b], m_v[b]);
     }
     const double axs = kahan_value(sx, cx), ays = kahan_value(sy, cy), azs = kahan_value(sz, cz);
@@ -278,8 +284,13 @@ __global__ void __launch_bounds__(128) k_forces_mixed(Groups gr, int64_t G, cons
     out.az[a] = azs;
     out.du[a] = kahan_value(su, cu);
     out.vsig[a] = (double)vs;
-    out.dhdt[a] = -h[a] * (double)TA.y * (1.0 / 3.0) * mass_d * (double)sdiv;
-    tdt = dt_candidate(h[a], (double)vs, axs, ays, azs, fp);
+    const float ha = (float)h[a];
+    out.dhdt[a] = (double)(-ha * TA.y * (1.0f / 3.0f) * mass * sdiv);
+    // CFL candidate in FP32 (a time-step estimate; the FP64 path evaluates it in FP64)
+    const float am = sqrtf((float)(axs * axs + ays * ays + azs * azs));
+    const float t1 = (float)fp.c_cour * ha / vs;
+    const float t2 = am > 0.f ? (float)fp.c_force * sqrtf(ha / am) : INFINITY;
+    tdt = (double)fminf(t1, t2);
     }
     dt_reduce(tdt, npair, sc, fp.box_dt_next, box);
 }
@@ -310,8 +321,6 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     fp.box_of = c->batch ? c->box_of : nullptr;
     fp.box_dt_next = c->batch ? c->box_dt_next : nullptr;
     const int mixed = c->p.precision == SPH_MIXED;
-    const int64_t G = group_count(c, n);
-    const Groups gr = make_groups(c, n);
     int r;
     if ((r = stage_begin(c, kStForcePrep))) return r;
     k_force_prep<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->h,
@@ -323,11 +332,11 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     if ((r = stage_end(c, kStForcePrep)) || (r = stage_begin(c, kStForces))) return r;
     ForceOut out{ax, ay, az, du, s->vsig, c->dhdt};
     if (mixed)
-        k_forces_mixed<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, c->rel, c->m_v, c->m_t, c->m_r, s->h,
-                                                                c->nb_cnt, c->grp_off, c->nb_ids, fp, out, c->dscal);
+        k_forces_mixed<<<grid_for(n, 128), 128, 0, c->stream>>>(n, c->rel, c->m_v, c->m_t, c->m_r, s->h,
+                                                                c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out, c->dscal);
     else
-        k_forces_fp64<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, (const FRec *)c->frec, c->rel, c->h32,
-                                                                    c->nb_cnt, c->grp_off, c->nb_ids, fp, out,
+        k_forces_fp64<<<grid_for(n, 128), 128, 0, c->stream>>>(n, (const FRec *)c->frec, c->rel, c->h32,
+                                                                    c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out,
                                                                     c->dscal);
     SPH_LAUNCH_CHECK(c, "k_forces");
     return stage_end(c, kStForces);

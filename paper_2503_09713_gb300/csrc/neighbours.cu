@@ -1,6 +1,6 @@
 // Neighbour cache (App. C "Two-stages neighbour cache", App. D interaction criteria).
 //
-// Stage 1: every group of 32 consecutive (Morton-ordered) particles walks the radix tree once with
+// Stage 1: every group (a tree node of at most 32 particles, see Groups) walks the radix tree once with
 // the group-group criterion  AABB_g  intersects  AABB_c (+) s*max(h_max,g, h_max,c),  s = R_kern*chi,
 // shifting the group box by the periodic images it can reach.  The walk runs on FP32 copies of the
 // boxes rounded outwards, so it keeps every cell the FP64 test keeps.  Leaves found one after the
@@ -11,7 +11,8 @@
 // relative 2^-10 of the radius are decided in FP64 exactly as the definition states, so the kept set
 // is the FP64 set.  The count pass stores, per 32-candidate chunk and lane, the bit mask of kept
 // candidates; after a scan over groups the fill pass only expands those masks.  Layout of the cache:
-// particle a = 32g + lane owns entries off_g + 32k + lane, k < count_a.
+// particle a = start_g + lane of a group of size_g particles owns entries off_g + size_g k + lane,
+// k < count_a.
 #include <cuda/atomic>
 
 #include "sph_internal.cuh"
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
     const float4 *__restrict__ rel, const float *__restrict__ h32, const double *__restrict__ x,
     const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h, double s,
     float quarter_box, Geo geo, uint32_t *__restrict__ masks, uint32_t *__restrict__ nb_cnt,
-    unsigned long long *lookback, uint32_t *ticket, int64_t *__restrict__ grp_off, uint32_t *__restrict__ nb_ids,
+    unsigned long long *__restrict__ nb_ptr, unsigned long long *lookback, uint32_t *ticket, int64_t *__restrict__ grp_off, uint32_t *__restrict__ nb_ids,
     int64_t nb_cap, DevScalars *sc) {
     __shared__ float4 s_pos[kS2Warps][32];
     __shared__ float2 s_t[kS2Warps][32];   // (s h_b)^2 (1 - 2^-10), h_b
@@ -244,7 +245,8 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
     if (g >= G) return;
     const int64_t first = group_first(gr, g);
     const int64_t a = first + lane;
-    const bool va = a < group_end(gr, g);
+    const int64_t gsize = group_end(gr, g) - first;
+    const bool va = lane < gsize;
     const float s32 = (float)s;
     const float4 Araw = rel[va ? a : first];
     int rcx, rcy, rcz;
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
                     if (r2 < t * kBandLo) lo |= 1u << jj;
                 }
             }
-            if (!va) hi = lo = 0;   // lanes past n keep nothing
+            if (!va) hi = lo = 0;   // lanes past the group keep nothing
             if (a >= base && a < base + 32) {   // not its own neighbour
                 hi &= ~(1u << (uint32_t)(a - base));
                 lo &= ~(1u << (uint32_t)(a - base));
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         sum += __shfl_xor_sync(0xffffffffu, sum, o);
     }
-    const unsigned long long slots = (unsigned long long)mx * 32ULL;
+    const unsigned long long slots = (unsigned long long)mx * (unsigned long long)gsize;
     // ---- (2) decoupled look-back over the preceding groups (lane k reads group g-1-k)
     if (lane == 0) {
         cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> mine(lookback[g]);
@@ -386,6 +388,7 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
         }
     }
     const int64_t off_g = (int64_t)excl;
+    if (va) nb_ptr[a] = pack_nb_ptr(off_g + lane, gsize);
     if (lane == 0) {
         grp_off[g] = off_g;
         if (g == G - 1) grp_off[G] = off_g + (int64_t)slots;
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
             while (m) {
                 const int jj = __ffs(m) - 1;
                 m &= m - 1;
-                nb_ids[off + (int64_t)k * 32] = (uint32_t)(base + jj);
+                nb_ids[off + (int64_t)k * gsize] = (uint32_t)(base + jj);
                 ++k;
             }
         }
@@ -439,13 +442,12 @@ static int ensure(sph_ctx *c, T **p, int64_t &cap, int64_t need, const char *wha
 int neighbours_build(sph_ctx *c, const sph_state *s) {
     if (!c->tree_valid) return fail(c, SPH_ERR_ORDER, "sph_find_neighbours before sph_build_tree");
     const int64_t n = s->n;
-    const int64_t G = group_count(c, n);
-    const Groups gr = make_groups(c, n);
+    const int64_t G = c->n_groups;
+    const Groups gr = make_groups(c);
     const int64_t L = c->n_leaves;
     const Geo geo = make_geo(c->p);
     const double sc = 2.0 * c->p.cache_tol;   // R_kern * chi
     c->cache_valid = false;
-    c->n_groups = G;
 
     k_h32<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->h, c->h32, c->h_base);
     SPH_LAUNCH_CHECK(c, "k_h32");
@@ -472,9 +474,9 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         if (attempt >= 6) return fail(c, SPH_ERR_CAPACITY, "candidate range list overflow (cap %d)", c->cand_cap);
         const int newcap = c->cand_cap * 2;
         uint2 *nc = nullptr;
-        if (cudaMalloc(&nc, (size_t)G * newcap * sizeof(uint2)) != cudaSuccess) {
+        if (cudaMalloc(&nc, (size_t)c->g_cap * newcap * sizeof(uint2)) != cudaSuccess) {
             cudaGetLastError();
-            return fail(c, SPH_ERR_OOM, "candidate list of %lld x %d", (long long)G, newcap);
+            return fail(c, SPH_ERR_OOM, "candidate list of %lld x %d", (long long)c->g_cap, newcap);
         }
         SPH_CUDA(c, cudaFree(c->cand));
         c->cand = nc;
@@ -495,7 +497,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         SPH_CUDA(c, cudaMemsetAsync(c->grp_slots, 0, (size_t)G * sizeof(int64_t), c->stream));
         k_stage2<<<blocks, kS2Warps * 32, 0, c->stream>>>(
             gr, c->box_root, G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->gbox, c->nodes, c->rel, c->h32, s->x, s->y,
-            s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket,
+            s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->nb_ptr, (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket,
             c->grp_off, c->nb_ids, c->nb_cap, c->dscal);
         SPH_LAUNCH_CHECK(c, "k_stage2");
         SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->total_slots, &c->grp_off[G], sizeof(int64_t), cudaMemcpyDeviceToHost,

@@ -13,7 +13,7 @@ namespace sph {
 
 constexpr int kMortonBits = 21;          // bits per axis; 63-bit codes (App. B)
 constexpr int kCodeBits = 3 * kMortonBits;
-constexpr int kGroup = 32;               // particles per neighbour-search group (one warp)
+constexpr int kGroup = 32;               // largest neighbour-search group (one warp)
 constexpr int kCellBits = 10;            // cell grid of the FP32 relative coordinates: 2^10 per axis
 constexpr int kStackDepth = 66;          // tree-walk stack (tree depth <= 63 for distinct 63-bit codes)
 constexpr double kPi = 3.14159265358979323846;
@@ -55,22 +55,27 @@ __device__ __forceinline__ NodeF to_float_outward(const Node &b) {
     return f;
 }
 
-// Groups of at most 32 consecutive particles, never spanning two boxes.  Without a table (one box)
-// group g is particles 32g .. min(32g+32, n).
+// Groups of the neighbour search: the largest tree nodes holding at most 32 particles and lying in
+// one box, so a group is a Morton cell (spatially compact, a run of consecutive particles); a leaf
+// with more than 32 particles is cut into runs of 32.  Group g is particles start[g] .. start[g+1].
 struct Groups {
-    const int64_t *start;     // [G + 1] or nullptr
-    const uint16_t *box;      // [G] or nullptr
-    int64_t n;
+    const int64_t *start;     // [G + 1]
+    const uint16_t *box;      // [G] or nullptr (one box)
 };
-__device__ __forceinline__ int64_t group_first(const Groups &gr, int64_t g) {
-    return gr.start ? gr.start[g] : 32 * g;
-}
-__device__ __forceinline__ int64_t group_end(const Groups &gr, int64_t g) {
-    if (gr.start) return gr.start[g + 1];
-    const int64_t e = 32 * g + 32;
-    return e < gr.n ? e : gr.n;
-}
+__device__ __forceinline__ int64_t group_first(const Groups &gr, int64_t g) { return gr.start[g]; }
+__device__ __forceinline__ int64_t group_end(const Groups &gr, int64_t g) { return gr.start[g + 1]; }
 __device__ __forceinline__ int group_box_of(const Groups &gr, int64_t g) { return gr.box ? gr.box[g] : 0; }
+
+// Where a particle's neighbour list starts in the cache and its stride (the size of its group):
+// offset in the low 58 bits, stride above.  Entry k of the list is ids[offset + k * stride].
+constexpr int kNbStrideShift = 58;
+__device__ __forceinline__ unsigned long long pack_nb_ptr(int64_t off, int64_t stride) {
+    return ((unsigned long long)stride << kNbStrideShift) | (unsigned long long)off;
+}
+__device__ __forceinline__ const uint32_t *nb_list(const uint32_t *nb_ids, unsigned long long w, int64_t &stride) {
+    stride = (int64_t)(w >> kNbStrideShift);
+    return nb_ids + (int64_t)(w & ((1ULL << kNbStrideShift) - 1));
+}
 
 // Device scalars written by kernels and read back by the host in one copy.
 struct DevScalars {
@@ -88,6 +93,7 @@ struct DevScalars {
     unsigned long long dens_inrange;  // density: evaluations with q < 2
     unsigned long long inrange_pairs; // forces: pairs inside 2 max(h_a, h_b)
     double v2_sum;                    // sum |v|^2 after the corrector
+    int64_t n_groups;                 // groups of the last tree build
 };
 
 struct Buffer {
@@ -171,7 +177,8 @@ struct sph_ctx {
     double *h_base = nullptr;          // [n_cap] h^n of the cache
 
     // ---- neighbour cache ----
-    int64_t n_groups = 0;
+    int64_t n_groups = 0;              // groups of the current tree (tree_build)
+    int64_t g_cap = 0;                 // capacity of the per-group arrays
     sph::Node *gbox = nullptr;         // [groups] group boxes
     sph::NodeF *gboxf = nullptr;       // [groups] FP32 outward copy
     int64_t *grp_chunks = nullptr;     // [groups + 1] candidate chunks per group -> scan
@@ -182,9 +189,10 @@ struct sph_ctx {
     uint32_t *cand_cnt = nullptr;      // [groups]
     int cand_cap = 0;
     uint32_t *nb_cnt = nullptr;        // [n_cap] per-particle neighbour count
+    unsigned long long *nb_ptr = nullptr;  // [n_cap] list start and stride (pack_nb_ptr)
     int64_t *grp_slots = nullptr;      // [groups + 1] stage-2 look-back words
     int64_t *grp_off = nullptr;        // [groups + 1]
-    uint32_t *nb_ids = nullptr;        // cache entries, group-interleaved: off_g + k*32 + lane
+    uint32_t *nb_ids = nullptr;        // cache entries, group-interleaved: off_g + k*size_g + lane
     int64_t nb_cap = 0;
     int64_t n_pairs = 0, total_slots = 0;
     bool cache_valid = false;
@@ -219,10 +227,8 @@ struct sph_ctx {
     unsigned long long *box_dt_next = nullptr;  // [n_boxes] CFL minimum (bits) of the last force pass
     std::vector<double> h_box_dt;      // host copy of the last CFL step per box
     std::vector<double> h_step_dt;     // time step of each box in the current step
-    int64_t *gstart = nullptr;         // [groups + 1] first particle of each group (batch)
+    int64_t *gstart = nullptr;         // [groups + 1] first particle of each group
     uint16_t *group_box = nullptr;     // [groups] box of each group (batch)
-    std::vector<int64_t> h_gstart;     // host copy (batch)
-    int64_t batch_groups = 0;
 
     // ---- scalars / flags ----
     sph::DevScalars *dscal = nullptr;
@@ -263,8 +269,8 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
 int integrate_predict(sph_ctx *c, sph_state *s, double dt, const double *dhdt);
 int integrate_correct(sph_ctx *c, sph_state *s, double dt);
 int read_scalars(sph_ctx *c);
-Groups make_groups(const sph_ctx *c, int64_t n);
-int64_t group_count(const sph_ctx *c, int64_t n);
+Groups make_groups(const sph_ctx *c);
+int ensure_groups(sph_ctx *c, int64_t G);   // grow the per-group arrays to G groups
 // Per-stage timing: stage_begin/stage_end bracket the launches of one stage on the context stream;
 // with timing on, stage_end waits for the stage and adds its duration to stats.stage_ms[k].
 enum Stage { kStPredict = 0, kStTree, kStNeigh, kStDensity, kStForcePrep, kStForces, kStCorrect, kStCount };

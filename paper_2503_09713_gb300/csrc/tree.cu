@@ -2,6 +2,7 @@
 // reorder of the particle arrays, duplicate mask + reduction passes (Alg. mortonmask), compaction
 // into leaves, Karras radix tree (Table arrays_fig_karras) and bottom-up tight boxes + h_max.
 #include <cuda/atomic>
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -495,6 +496,83 @@ __global__ void k_box_roots(int64_t L, const uint64_t *__restrict__ mu_leaf, con
     box_root[a0] = (int32_t)t;
 }
 
+// ====================================================================================== groups
+// Groups of the neighbour search: the largest nodes with at most kGroup particles inside one box.
+// Node t marks the first particle of its range when it qualifies and its parent does not; a leaf
+// with more than kGroup particles marks every kGroup-th particle; in a batch every box start is
+// marked too.  An exclusive scan of the marks numbers the groups in particle order.
+__global__ void k_group_marks(int64_t L, int64_t n, const int64_t *__restrict__ leaf_first,
+                              const uint64_t *__restrict__ mu_leaf, const int32_t *__restrict__ endrange,
+                              const int32_t *__restrict__ node_parent, const int32_t *__restrict__ leaf_parent,
+                              int shift, const uint16_t *__restrict__ box_of, int64_t *__restrict__ marks) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nin = L - 1;
+    if (t < n && (t == 0 || (box_of && box_of[t] != box_of[t - 1]))) marks[t] = 1;
+    if (t >= nin + L) return;
+    auto leaves = [&](int64_t node, int64_t &lo, int64_t &hi) {
+        if (node < nin) {
+            const int64_t e = endrange[node];
+            lo = node < e ? node : e;
+            hi = node < e ? e : node;
+        } else {
+            lo = hi = node - nin;
+        }
+    };
+    auto qualifies = [&](int64_t node) {
+        int64_t lo, hi;
+        leaves(node, lo, hi);
+        return leaf_first[hi + 1] - leaf_first[lo] <= kGroup && (mu_leaf[lo] >> shift) == (mu_leaf[hi] >> shift);
+    };
+    int64_t lo, hi;
+    leaves(t, lo, hi);
+    const int64_t pf = leaf_first[lo], pl = leaf_first[hi + 1];
+    if (qualifies(t)) {
+        const int64_t parent = (t < nin) ? node_parent[t] : (L > 1 ? leaf_parent[t - nin] : -1);
+        if (parent < 0 || !qualifies(parent)) marks[pf] = 1;
+    } else if (t >= nin) {
+        for (int64_t q = pf; q < pl; q += kGroup) marks[q] = 1;
+    }
+}
+
+__global__ void k_group_table(int64_t n, const int64_t *__restrict__ marks, const int64_t *__restrict__ pos,
+                              const uint16_t *__restrict__ box_of, int64_t *__restrict__ gstart,
+                              uint16_t *__restrict__ group_box) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    if (marks[t]) {
+        const int64_t g = pos[t];
+        gstart[g] = t;
+        if (box_of) group_box[g] = box_of[t];
+    }
+    if (t == n - 1) gstart[pos[n]] = n;
+}
+
+static int make_group_table(sph_ctx *c, int64_t n) {
+    const int64_t L = c->n_leaves;
+    int64_t *marks = reinterpret_cast<int64_t *>(c->gather_tmp);   // free after the reorder
+    int64_t *pos = marks + c->n_cap;                                // [n + 1]
+    SPH_CUDA(c, cudaMemsetAsync(marks, 0, (size_t)n * sizeof(int64_t), c->stream));
+    const int64_t threads = std::max<int64_t>(n, 2 * L - 1);
+    k_group_marks<<<grid_for(threads, 256), 256, 0, c->stream>>>(
+        L, n, c->leaf_first, c->mu_leaf, c->endrange, c->node_parent, c->leaf_parent, 3 * c->morton_bits,
+        c->batch ? c->box_of : nullptr, marks);
+    SPH_LAUNCH_CHECK(c, "k_group_marks");
+    int r = exclusive_scan_i64(c, marks, pos, n);
+    if (r) return r;
+    SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->n_groups, &pos[n], sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int64_t G = c->hscal->n_groups;
+    if (G < 1 || G > n) return fail(c, SPH_ERR_CUDA, "bad group count %lld", (long long)G);
+    r = ensure_groups(c, G);
+    if (r) return r;
+    k_group_table<<<grid_for(n, 256), 256, 0, c->stream>>>(n, marks, pos, c->batch ? c->box_of : nullptr,
+                                                           c->gstart, c->group_box);
+    SPH_LAUNCH_CHECK(c, "k_group_table");
+    c->n_groups = G;
+    c->stats.n_groups = G;
+    return SPH_OK;
+}
+
 static double pow2_reciprocal(double v) {
     int e = 0;
     const double m = std::frexp(v, &e);
@@ -622,6 +700,9 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
                                                                      c->leaf_parent, 3 * c->morton_bits, c->box_root);
         SPH_LAUNCH_CHECK(c, "k_box_roots");
     }
+    // groups of the neighbour search (tree nodes of at most kGroup particles)
+    r = make_group_table(c, n);
+    if (r) return r;
     // A6 boxes + h_max
     r = boxes(c, s);
     if (r) return r;

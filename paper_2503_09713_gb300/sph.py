@@ -51,7 +51,7 @@ class sph_state(ctypes.Structure):
 
 class sph_tree_view(ctypes.Structure):
     _fields_ = [(f, _p) for f in ("mu", "perm", "leaf_first", "mu_leaf", "lchild", "rchild", "lflag", "rflag",
-                                  "endrange", "bmin", "bmax", "hmax")]
+                                  "endrange", "bmin", "bmax", "hmax", "group_start")]
 
 
 class sph_stats(ctypes.Structure):
@@ -236,6 +236,9 @@ def sph_export_tree(ctx) -> dict:
            "mu_leaf": np.zeros(L, np.uint64), "lchild": np.zeros(nin, np.int32), "rchild": np.zeros(nin, np.int32),
            "lflag": np.zeros(nin, np.uint8), "rflag": np.zeros(nin, np.uint8), "endrange": np.zeros(nin, np.int32),
            "bmin": np.zeros((nodes, 3)), "bmax": np.zeros((nodes, 3)), "hmax": np.zeros(nodes)}
+    st = sph_stats()
+    _check(ctx, lib.sph_get_stats(ctx, ctypes.byref(st)))
+    out["group_start"] = np.zeros(st.n_groups + 1, np.int64)
     v = sph_tree_view(**{k: (a.ctypes.data if a.size else None) for k, a in out.items()})
     _check(ctx, lib.sph_export_tree(ctx, ctypes.byref(v)))
     return out

@@ -57,6 +57,10 @@ def test_batch_matches_oracle_box_by_box(precision):
     assert all(np.all((ids[off[b]:off[b + 1]] >= off[b]) & (ids[off[b]:off[b + 1]] < off[b + 1]))
                for b in range(len(boxes)))                     # particles stay in their box
     g0 = {k: to_orig(out[k], ids) for k in FIELDS}
+    gs = solver.export_tree()["group_start"]                   # groups: runs of <= 32 inside one box
+    assert gs[0] == 0 and gs[-1] == off[-1] and np.all(np.diff(gs) >= 1) and np.all(np.diff(gs) <= 32)
+    box = np.searchsorted(off, np.arange(off[-1]), side="right") - 1
+    assert np.array_equal(box[gs[:-1]], box[gs[1:] - 1])
     dts = solver.batch_dt()
     for b, (ref, P) in enumerate(refs):
         _check(g0, ref, off[b], off[b + 1], precision, f"box {b} converged")

@@ -23,6 +23,34 @@ def _build(x, y, z, h, n_red, lo=(0, 0, 0), hi=(1, 1, 1)):
     return t, out
 
 
+def expected_groups(leaf_first, tr, n):
+    """Neighbour-search groups from the oracle's tree: the largest nodes holding at most 32
+    particles, a leaf of more than 32 cut into runs of 32; returns the group starts and n."""
+    L = len(leaf_first) - 1
+    nin = L - 1
+
+    def particles(t):
+        if t < nin:
+            e = int(tr.endrange[t])
+            lo, hi = min(t, e), max(t, e)
+        else:
+            lo = hi = t - nin
+        return int(leaf_first[lo]), int(leaf_first[hi + 1])
+
+    starts, stack = [], [0]   # node 0: the root (internal, or the only leaf when L == 1)
+    while stack:
+        t = stack.pop()
+        pf, pl = particles(t)
+        if pl - pf <= 32:
+            starts.append(pf)
+        elif t >= nin:
+            starts.extend(range(pf, pl, 32))
+        else:
+            stack.append(nin + int(tr.lchild[t]) if tr.lflag[t] else int(tr.lchild[t]))
+            stack.append(nin + int(tr.rchild[t]) if tr.rflag[t] else int(tr.rchild[t]))
+    return np.array(sorted(starts) + [n], dtype=np.int64)
+
+
 def _check_against_oracle(x, y, z, h, n_red, lo=(0, 0, 0), hi=(1, 1, 1)):
     t, out = _build(x, y, z, h, n_red, lo, hi)
     m = O.morton(x, y, z, lo, hi)
@@ -41,6 +69,7 @@ def _check_against_oracle(x, y, z, h, n_red, lo=(0, 0, 0), hi=(1, 1, 1)):
         assert np.array_equal(t[k], getattr(tr, k)), k
     bmin, bmax, hmax = O.cell_boxes(idv, tr.endrange, xs, ys, zs, hs)
     assert np.array_equal(t["bmin"], bmin) and np.array_equal(t["bmax"], bmax) and np.array_equal(t["hmax"], hmax)
+    assert np.array_equal(t["group_start"], expected_groups(idv, tr, len(x)))
     return len(ml)
 
 
@@ -78,6 +107,7 @@ def test_tree_edge_sizes():
     x = np.full(n, 0.3); y = np.full(n, 0.6); z = np.full(n, 0.9)
     t, _ = _build(x, y, z, np.full(n, 0.05), 2)
     assert list(t["leaf_first"]) == [0, n]
+    assert list(t["group_start"]) == [0, 32, 64, 96, n]   # one leaf of 100 cut into runs of 32
 
 
 def test_karras_table_through_gpu(golden):
