@@ -35,6 +35,11 @@ FLOP_FORCE_PAIR = 72         # per pair in range: kernel gradients, AV, momentum
                              # divergence, v_sig
 FLOP_DENS_CAND = 9           # separation, q^2
 FLOP_DENS_PAIR = 20          # sqrt, M4 value and two derivatives, the three sums
+# FP32 pair loop of the mixed path (an FMA counts 2; Kahan additions 4 each; the artificial
+# viscosity, evaluated only for approaching pairs, is not counted)
+FLOP_FORCE32_CAND = 16       # cell-relative separation, r^2, radius test
+FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan), energy and
+                             # conductivity (Kahan), divergence
 
 WORKLOADS = {
     "sedov128": ("sedov", 128, "Sedov blast 128^3 = 2,097,152 particles, jittered cubic lattice, periodic unit "
@@ -360,9 +365,17 @@ def main():
     if not args.no_mixed and args.only != "fp64":
         r32 = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, None)
         ms32 = r32["ms_per_step"]
+        st32 = r32["timing_stats"]
+        f32 = st32["n_pairs"] * FLOP_FORCE32_CAND + st32["force_pairs"] * FLOP_FORCE32_PAIR
+        kms32 = r32["stage_ms"]["forces"]
+        ach32 = f32 / (kms32 * 1e-3) / 1e12
         line["mixed"] = {"value": n * world / (ms32 * 1e-3), "unit": "particles/s", "ms_per_step": ms32,
                          "dtype": "f32 pair sums (Kahan) / f64 state", "speedup_vs_fp64": ms / ms32,
-                         "stage_ms": r32["stage_ms"]}
+                         "stage_ms": r32["stage_ms"],
+                         "roofline": {"bound": "alu", "kernel": "k_forces_mixed", "achieved": ach32,
+                                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach32 / FP32_PEAK_TFLOPS,
+                                      "traffic": None, "peak_source": "nominal FP32 rate (unit counts x 2.07 GHz)",
+                                      "kernel_ms": kms32, "flops_per_launch": f32}}
         r32["solver"].close()
 
     if not args.no_ensemble and args.only is None:

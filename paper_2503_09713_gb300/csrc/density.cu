@@ -29,7 +29,7 @@ struct DensParams {
 //   rho_sum = m sf / (pi h^3),  sum m dW/dh = -m sg / (pi h^4),  sum m d2W/dh2 = m sk / (pi h^5).
 template <bool kMixed>
 __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt, const uint32_t *__restrict__ ids,
-                                             int64_t st,
+                                             uint32_t st,
                                              const double *__restrict__ x, const double *__restrict__ y,
                                              const double *__restrict__ z, const float4 *__restrict__ rel,
                                              const PairGeo &geo, double &sf, double &sg, double &sk,
@@ -44,7 +44,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         const float lim = 4.f * kPreBand / ((float)hinv2);
         double f0 = 1.0, g0 = 3.0, k0 = 12.0;
         for (uint32_t k = 0; k < cnt; k++) {
-            const uint32_t b = ids[(int64_t)k * st];
+            const uint32_t b = ids[k * st];
             float fx, fy, fz;
             int sx, sy, sz;
             rel_sep_shift(A, rel[b], geo, fx, fy, fz, sx, sy, sz);
@@ -101,10 +101,10 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         for (; k + 4 <= cnt; k += 4) {
             const uint32_t b0 = n0, b1 = n1, b2 = n2, b3 = n3;
             if (k + 8 <= cnt) {
-                n0 = ids[(int64_t)(k + 4) * st];
-                n1 = ids[(int64_t)(k + 5) * st];
-                n2 = ids[(int64_t)(k + 6) * st];
-                n3 = ids[(int64_t)(k + 7) * st];
+                n0 = ids[(k + 4) * st];
+                n1 = ids[(k + 5) * st];
+                n2 = ids[(k + 6) * st];
+                n3 = ids[(k + 7) * st];
             }
             const float4 B0 = rel[b0], B1 = rel[b1], B2 = rel[b2], B3 = rel[b3];
             acc(B0);
@@ -112,7 +112,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
             acc(B2);
             acc(B3);
         }
-        for (; k < cnt; k++) acc(rel[ids[(int64_t)k * st]]);
+        for (; k < cnt; k++) acc(rel[ids[k * st]]);
         sf = kahan_value(s0, c0);
         sg = kahan_value(s1, c1);
         sk = (double)s2;
@@ -128,16 +128,17 @@ __global__ void __launch_bounds__(128) k_density(int64_t n, const double *__rest
                                                  const uint32_t *__restrict__ nb_ids, DensParams dp,
                                                  double *__restrict__ rho, double *__restrict__ omega, DevScalars *sc) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one thread per particle
-    if (a >= n) return;
+    if (a - (threadIdx.x & 31) >= n) return;   // whole warp past the end
+    int it = 0;
+    uint32_t nin = 0, evals = 0, flag = 0;
+    if (a < n) {
     const uint32_t cnt = nb_cnt[a];
-    int64_t st;
+    uint32_t st;
     const uint32_t *ids = nb_list(nb_ids, nb_ptr[a], st);
     double ha = h[a];
     const double hn = h_base[a];
     const double m = dp.box_mass ? dp.box_mass[dp.box_of[a]] : dp.mass;
     const double hf3 = dp.hfact * dp.hfact * dp.hfact;
-    int it = 0;
-    uint32_t nin = 0;
     bool stale = false, conv = false;
     double dsum_new = 0.0;
     while (it < dp.max_iter) {
@@ -168,16 +169,25 @@ __global__ void __launch_bounds__(128) k_density(int64_t n, const double *__rest
         }
     }
     h[a] = ha;
-    if (stale) atomicOr(&sc->flags, kErrStale);
-    else if (!conv) atomicOr(&sc->flags, kErrNotConverged);
+    flag = stale ? kErrStale : (conv ? 0u : kErrNotConverged);
     // rho = rho(h) (Eq. rhoh) and Omega (Eq. sphomega) at the final h
     const double hinv = 1.0 / ha;
     const double rho_h = m * hf3 * hinv * hinv * hinv;
     rho[a] = rho_h;
     omega[a] = 1.0 + ha / (3.0 * rho_h) * dsum_new;
-    atomicMax(&sc->max_iters, (uint32_t)it);
-    atomicAdd(&sc->pair_evals, (unsigned long long)cnt * (unsigned long long)it);
-    atomicAdd(&sc->dens_inrange, (unsigned long long)nin);
+    evals = cnt * (uint32_t)it;
+    }
+    // counters: one atomic per warp (same-address atomics from every thread serialise in L2)
+    const uint32_t wit = __reduce_max_sync(0xffffffffu, (uint32_t)it);
+    const uint32_t wev = __reduce_add_sync(0xffffffffu, evals);
+    const uint32_t wnin = __reduce_add_sync(0xffffffffu, nin);
+    const uint32_t wfl = __reduce_or_sync(0xffffffffu, flag);
+    if ((threadIdx.x & 31) == 0) {
+        if (wfl) atomicOr(&sc->flags, wfl);
+        atomicMax(&sc->max_iters, wit);
+        atomicAdd(&sc->pair_evals, (unsigned long long)wev);
+        atomicAdd(&sc->dens_inrange, (unsigned long long)wnin);
+    }
 }
 
 int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
@@ -198,12 +208,12 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->pair_evals, 0, 2 * sizeof(unsigned long long), c->stream));
     if (c->p.precision == SPH_MIXED)
         k_density<true><<<grid_for(n, 128), 128, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
-                                                                 c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
-                                                                 s->omega, c->dscal);
+                                                                 c->nb_cnt, c->nb_ptr, c->nb_ids, dp,
+                                                                 s->rho, s->omega, c->dscal);
     else
         k_density<false><<<grid_for(n, 128), 128, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
-                                                                  c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
-                                                                  s->omega, c->dscal);
+                                                                  c->nb_cnt, c->nb_ptr, c->nb_ids, dp,
+                                                                  s->rho, s->omega, c->dscal);
     SPH_LAUNCH_CHECK(c, "k_density");
     static_assert(offsetof(DevScalars, flags) == offsetof(DevScalars, max_iters) + sizeof(uint32_t), "layout");
     SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->max_iters, &c->dscal->max_iters, 2 * sizeof(uint32_t),

@@ -48,9 +48,10 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
     const double qf = 1.0 / (r * om);
     const double hinv = 1.0 / hi;
     if (mixed) {
-        m_v[i] = make_float4((float)vx[i], (float)vy[i], (float)vz[i], (float)hinv);
-        m_t[i] = make_float4((float)pre, (float)qf, (float)cs, (float)P);
-        m_r[i] = make_float4((float)r, (float)ui, 0.f, 0.f);
+        const float hinvf = (float)hinv;
+        m_v[i] = make_float4((float)vx[i], (float)vy[i], (float)vz[i], hinvf);
+        m_t[i] = make_float4((float)pre, (float)qf, (float)(fp.alpha_av * cs), (float)P);
+        m_r[i] = make_float4((float)r, (float)ui, hinvf * hinvf * hinvf * hinvf * kInvPiF, 0.f);
     } else {
         FRec f;
         f.x = x[i]; f.y = y[i]; f.z = z[i]; f.h = hi;
@@ -130,10 +131,13 @@ __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__re
     const int box = (a < n && fp.box_of) ? fp.box_of[a] : 0;
     double tdt = INFINITY;
     unsigned long long npair = 0;
+    const uint32_t cnt = a < n ? nb_cnt[a] : 0u;
+    const unsigned long long pw = a < n ? nb_ptr[a] : 0ULL;
+    uint32_t st;
+    const uint32_t *ids = nb_list(nb_ids, pw, st);
+    const int64_t lbeg = ids - nb_ids;
+    prefetch_lists_l2(nb_ids, lbeg, cnt ? lbeg + (int64_t)(cnt - 1) * st + 1 : lbeg);
     if (a < n) {
-    const uint32_t cnt = nb_cnt[a];
-    int64_t st;
-    const uint32_t *ids = nb_list(nb_ids, nb_ptr[a], st);
     FRec A;
     load_rec(&rec[a], A);
     const float4 PA = rel[a];
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__re
     double axs = 0.0, ays = 0.0, azs = 0.0, dus = 0.0, divs = 0.0;
     double vs = A.acs;
     for (uint32_t k = 0; k < cnt; k++) {
-        const uint32_t b = ids[(int64_t)k * st];
+        const uint32_t b = ids[k * st];
         float fx, fy, fz;
         int sx, sy, sz;
         rel_sep_shift(PA, rel[b], geo, fx, fy, fz, sx, sy, sz);
@@ -215,23 +219,26 @@ __global__ void __launch_bounds__(128) k_forces_mixed(int64_t n, const float4 *_
     const int box = (a < n && fp.box_of) ? fp.box_of[a] : 0;
     double tdt = INFINITY;
     unsigned long long npair = 0;
+    const uint32_t cnt = a < n ? nb_cnt[a] : 0u;
+    const unsigned long long pw = a < n ? nb_ptr[a] : 0ULL;
+    uint32_t st;
+    const uint32_t *ids = nb_list(nb_ids, pw, st);
+    const int64_t lbeg = ids - nb_ids;
+    prefetch_lists_l2(nb_ids, lbeg, cnt ? lbeg + (int64_t)(cnt - 1) * st + 1 : lbeg);
     if (a < n) {
-    const uint32_t cnt = nb_cnt[a];
-    int64_t st;
-    const uint32_t *ids = nb_list(nb_ids, nb_ptr[a], st);
     const float4 PA = rel[a], VA = m_v[a], TA = m_t[a], RA = m_r[a];
     const double mass_d = fp.box_mass ? fp.box_mass[box] : fp.mass;
-    const float mass = (float)mass_d, alpha = (float)fp.alpha_av, beta = (float)fp.beta_av,
-                au = (float)fp.alpha_u;
+    const float mass = (float)mass_d, beta = (float)fp.beta_av, au = (float)fp.alpha_u;
+    // the mass factor is applied once per particle; the sums are the pair terms divided by m
     float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f, su = 0.f, cu = 0.f, sdiv = 0.f;
-    float vs = alpha * TA.z;
+    float vs = TA.z;   // alpha_AV c_s,a
     const float hia = VA.w;
-    const float Fa_n = hia * hia * hia * hia * kInvPiF;
+    const float Fa_n = RA.z;   // 1/(pi h_a^4)
     // one pair; B's position and velocity are already loaded
     auto pair = [&](uint32_t b, const float4 PB, const float4 VB) {
         float dx, dy, dz;
         rel_sep(PA, PB, fp.geo, dx, dy, dz);
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float him = fminf(hia, VB.w);
         if (!(r2 * him * him < 4.f)) return;
         ++npair;
@@ -239,50 +246,50 @@ __global__ void __launch_bounds__(128) k_forces_mixed(int64_t n, const float4 *_
         const float4 RB = m_r[b];
         const float rinv = rsqrtf(r2);
         const float r = r2 * rinv;
-        float f, dfa, dfb;
-        m4(r * hia, f, dfa);
-        m4(r * VB.w, f, dfb);
-        const float Fa = dfa * Fa_n;
-        const float hib = VB.w;
-        const float Fb = dfb * (hib * hib * hib * hib * kInvPiF);
-        const float vdotr = ((VA.x - VB.x) * dx + (VA.y - VB.y) * dy + (VA.z - VB.z) * dz) * rinv;
+        const float Fa = m4_df_sel(r * hia) * Fa_n;
+        const float Fb = m4_df_sel(r * VB.w) * RB.z;
+        const float vdotr = fmaf(VA.z - VB.z, dz, fmaf(VA.y - VB.y, dy, (VA.x - VB.x) * dx)) * rinv;
         float Aa = TA.x, Ab = TB.x;
         if (vdotr < 0.f) {
-            const float w = beta * vdotr;
-            Aa += -0.5f * (alpha * TA.z - w) * vdotr * TA.y;
-            Ab += -0.5f * (alpha * TB.z - w) * vdotr * TB.y;
-            vs = fmaxf(vs, alpha * TA.z - w);
+            const float w = beta * vdotr;   // -beta |v.rhat|
+            Aa = fmaf(-0.5f * (TA.z - w) * vdotr, TA.y, Aa);
+            Ab = fmaf(-0.5f * (TB.z - w) * vdotr, TB.y, Ab);
+            vs = fmaxf(vs, TA.z - w);
         }
-        const float sc_ = mass * (Aa * Fa + Ab * Fb) * rinv;
+        const float sc_ = fmaf(Aa, Fa, Ab * Fb) * rinv;
         kahan_add(sx, cx, -sc_ * dx);
         kahan_add(sy, cy, -sc_ * dy);
         kahan_add(sz, cz, -sc_ * dz);
-        float dut = mass * Aa * vdotr * Fa;
-        sdiv += vdotr * Fa;
+        const float vfa = vdotr * Fa;
+        float dut = Aa * vfa;
+        sdiv += vfa;
         if (au != 0.f) {
-            const float vsu = sqrtf(fabsf(TA.w - TB.w) / (0.5f * (RA.x + RB.x)));
-            dut += mass * au * vsu * (RA.y - RB.y) * 0.5f * (Fa * TA.y + Fb * TB.y);
+            // v_sig^u = sqrt(|P_a - P_b| / (rho_a + rho_b)/2) = t / sqrt(t (rho_a + rho_b)/2)
+            const float t = fabsf(TA.w - TB.w);
+            const float vsu = t > 0.f ? t * rsqrtf(0.5f * t * (RA.x + RB.x)) : 0.f;
+            dut = fmaf(au * vsu * (RA.y - RB.y) * 0.5f, fmaf(Fa, TA.y, Fb * TB.y), dut);
         }
         kahan_add(su, cu, dut);
     };
     // two neighbours per iteration: their gathers are issued together
     uint32_t k = 0;
     for (; k + 2 <= cnt; k += 2) {
-        const uint32_t b0 = ids[(int64_t)k * st], b1 = ids[(int64_t)(k + 1) * st];
+        const uint32_t b0 = ids[k * st], b1 = ids[(k + 1) * st];
         const float4 P0 = rel[b0], P1 = rel[b1];
         const float4 V0 = m_v[b0], V1 = m_v[b1];
         pair(b0, P0, V0);
         pair(b1, P1, V1);
     }
     if (k < cnt) {
-        const uint32_t b = ids[(int64_t)k * st];
+        const uint32_t b = ids[k * st];
         pair(b, rel[b], m_v[b]);
     }
-    const double axs = kahan_value(sx, cx), ays = kahan_value(sy, cy), azs = kahan_value(sz, cz);
+    const double axs = mass_d * kahan_value(sx, cx), ays = mass_d * kahan_value(sy, cy),
+                 azs = mass_d * kahan_value(sz, cz);
     out.ax[a] = axs;
     out.ay[a] = ays;
     out.az[a] = azs;
-    out.du[a] = kahan_value(su, cu);
+    out.du[a] = mass_d * kahan_value(su, cu);
     out.vsig[a] = (double)vs;
     const float ha = (float)h[a];
     out.dhdt[a] = (double)(-ha * TA.y * (1.0f / 3.0f) * mass * sdiv);

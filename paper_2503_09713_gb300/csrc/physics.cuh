@@ -1,6 +1,8 @@
 // Device helpers of the SPH pair loops: M4 kernel (Sect. 2.1), geometry of the neighbour cache,
 // Kahan summation for the FP32 pair sums of the mixed-precision path.
 #pragma once
+#include <climits>
+
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -31,6 +33,33 @@ __device__ __forceinline__ T m4_d2(T q) {
     if (q < T(1)) return T(4.5) * q - T(3);
     if (q < T(2)) return T(1.5) * (T(2) - q);
     return T(0);
+}
+
+// dW/dq shape of M4 without branches (both pieces evaluated, one selected): lanes of a warp hold
+// different q, so a branch would run both pieces anyway.
+__device__ __forceinline__ float m4_df_sel(float q) {
+    const float t = fmaxf(2.f - q, 0.f);
+    const float outer = -0.75f * t * t;
+    const float inner = q * fmaf(2.25f, q, -3.f);
+    return q < 1.f ? inner : outer;
+}
+
+// L2 prefetch of the neighbour-list entries of a warp's particles.  Within a group the lists are
+// interleaved and consecutive groups follow each other in the cache, so the entries of 32
+// consecutive particles form one contiguous range; the warp prefetches it line by line so that the
+// list loads of the pair loop hit L2 instead of DRAM.  All 32 lanes call it; [beg, end) is the
+// lane's own range (empty for a lane without a particle).
+__device__ __forceinline__ void prefetch_lists_l2(const uint32_t *nb_ids, int64_t beg, int64_t end) {
+    long long lo = end > beg ? beg : LLONG_MAX, hi = end > beg ? end : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lo >= hi) return;
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(nb_ids + lo) & ~(uintptr_t)127;
+    const uintptr_t a1 = reinterpret_cast<uintptr_t>(nb_ids + hi);
+    for (uintptr_t ad = a0 + (uintptr_t)(threadIdx.x & 31) * 128; ad < a1; ad += 32 * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ad));
 }
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {

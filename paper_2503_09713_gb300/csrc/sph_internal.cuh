@@ -72,8 +72,8 @@ constexpr int kNbStrideShift = 58;
 __device__ __forceinline__ unsigned long long pack_nb_ptr(int64_t off, int64_t stride) {
     return ((unsigned long long)stride << kNbStrideShift) | (unsigned long long)off;
 }
-__device__ __forceinline__ const uint32_t *nb_list(const uint32_t *nb_ids, unsigned long long w, int64_t &stride) {
-    stride = (int64_t)(w >> kNbStrideShift);
+__device__ __forceinline__ const uint32_t *nb_list(const uint32_t *nb_ids, unsigned long long w, uint32_t &stride) {
+    stride = (uint32_t)(w >> kNbStrideShift);
     return nb_ids + (int64_t)(w & ((1ULL << kNbStrideShift) - 1));
 }
 
