@@ -55,10 +55,10 @@ Groups make_groups(const sph_ctx *c) {
 int ensure_groups(sph_ctx *c, int64_t G) {
     if (G <= c->g_cap) return SPH_OK;
     const int64_t cap = G + G / 4 + 64;
-    void **ptrs[] = {(void **)&c->gbox, (void **)&c->gboxf, (void **)&c->grp_chunks, (void **)&c->chunk_off,
+    void **ptrs[] = {(void **)&c->gboxf, (void **)&c->grp_chunks, (void **)&c->chunk_off,
                      (void **)&c->cand, (void **)&c->cand_cnt, (void **)&c->grp_slots, (void **)&c->grp_off,
                      (void **)&c->gstart, (void **)&c->group_box};
-    const size_t bytes[] = {(size_t)cap * sizeof(Node), (size_t)cap * sizeof(NodeF), (size_t)(cap + 1) * 8,
+    const size_t bytes[] = {(size_t)cap * sizeof(NodeF), (size_t)(cap + 1) * 8,
                             (size_t)(cap + 1) * 8, (size_t)cap * c->cand_cap * sizeof(uint2), (size_t)cap * 4,
                             (size_t)(cap + 1) * 8, (size_t)(cap + 1) * 8, (size_t)(cap + 1) * 8,
                             (size_t)cap * 2};
@@ -106,7 +106,7 @@ void free_all(sph_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->digit_hist, c->lookback, c->tile_ctr,
                     c->mask[0], c->mask[1], c->scan_tmp, c->leaf_first, c->mu_leaf, c->lchild, c->rchild,
                     c->endrange, c->lflag, c->rflag, c->child, c->node_parent, c->leaf_parent, c->visit, c->nodes, c->nodesf,
-                    c->gather_tmp, c->id_tmp, c->rel, c->h32, c->h_base, c->gbox, c->gboxf, c->grp_chunks, c->chunk_off, c->masks, c->cand, c->cand_cnt, c->nb_cnt, c->nb_ptr,
+                    c->gather_tmp, c->id_tmp, c->rel, c->h32, c->h_base, c->gboxf, c->grp_chunks, c->chunk_off, c->masks, c->cand, c->cand_cnt, c->nb_cnt, c->nb_ptr,
                     c->grp_slots, c->grp_off, c->nb_ids, c->frec, c->m_v, c->m_t, c->m_r, c->a_new, c->dhdt, c->block_part,
                     c->hs_fields, c->hs_id, c->dscal, c->box_of, c->box_mass, c->box_gamma, c->box_root,
                     c->box_dt, c->box_dt_next, c->gstart, c->group_box};

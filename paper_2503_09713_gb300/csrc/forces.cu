@@ -40,23 +40,27 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
                              float4 *__restrict__ m_r, float *__restrict__ h32) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double r = rho[i], om = omega[i], ui = u[i], hi = h[i];
     const double gam = fp.box_gamma ? fp.box_gamma[fp.box_of[i]] : fp.gamma;
-    const double P = (gam - 1.0) * r * ui;
-    const double cs = sqrt(gam * P / r);
-    const double pre = P / (r * r * om);
-    const double qf = 1.0 / (r * om);
-    const double hinv = 1.0 / hi;
     if (mixed) {
-        const float hinvf = (float)hinv;
+        // FP32 records for the FP32 pair sums: P = (gamma-1) rho u, c_s = sqrt(gamma (gamma-1) u),
+        // P/(rho^2 Omega) = (gamma-1) u / (rho Omega), 1/(rho Omega), 1/(pi h^4)
+        const float r = (float)rho[i], om = (float)omega[i], ui = (float)u[i], g = (float)gam;
+        const float qf = 1.f / (r * om);
+        const float hinvf = 1.f / (float)h[i];
         m_v[i] = make_float4((float)vx[i], (float)vy[i], (float)vz[i], hinvf);
-        m_t[i] = make_float4((float)pre, (float)qf, (float)(fp.alpha_av * cs), (float)P);
-        m_r[i] = make_float4((float)r, (float)ui, hinvf * hinvf * hinvf * hinvf * kInvPiF, 0.f);
+        m_t[i] = make_float4((g - 1.f) * ui * qf, qf, (float)fp.alpha_av * sqrtf(g * (g - 1.f) * ui),
+                             (g - 1.f) * r * ui);
+        m_r[i] = make_float4(r, ui, hinvf * hinvf * hinvf * hinvf * kInvPiF, 0.f);
     } else {
+        // the same quantities in FP64, with two divisions and one square root per particle
+        const double r = rho[i], om = omega[i], ui = u[i], hi = h[i];
+        const double qf = 1.0 / (r * om);
+        const double hinv = 1.0 / hi;
         FRec f;
         f.x = x[i]; f.y = y[i]; f.z = z[i]; f.h = hi;
         f.vx = vx[i]; f.vy = vy[i]; f.vz = vz[i]; f.u = ui;
-        f.pre = pre; f.qf = qf; f.acs = fp.alpha_av * cs; f.P = P;
+        f.pre = (gam - 1.0) * ui * qf; f.qf = qf; f.acs = fp.alpha_av * sqrt(gam * (gam - 1.0) * ui);
+        f.P = (gam - 1.0) * r * ui;
         f.rho = r; f.hinv = hinv; f.fn = hinv * hinv * hinv * hinv * kInvPi; f.pad = 0.0;
         rec[i] = f;
         h32[i] = (float)hi;

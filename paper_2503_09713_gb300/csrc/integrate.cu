@@ -10,7 +10,7 @@ namespace sph {
 
 struct IntParams {
     double dt;
-    double h_clamp;
+    double h_clamp, inv_h_clamp;
     const double *box_dt;      // per-box time step (batch) or nullptr
     const uint16_t *box_of;
     double lo[3], hi[3];
@@ -59,7 +59,7 @@ __global__ void k_predict(int64_t n, double *__restrict__ x, double *__restrict_
     if (dhdt) {
         const double h0 = h[i];
         double hp = h0 + dt * dhdt[i];
-        hp = fmin(fmax(hp, h0 / ip.h_clamp), h0 * ip.h_clamp);
+        hp = fmin(fmax(hp, h0 * ip.inv_h_clamp), h0 * ip.h_clamp);
         h[i] = hp;
     }
 }
@@ -70,7 +70,7 @@ __global__ void k_correct(int64_t n, double *__restrict__ vx, double *__restrict
                           int64_t stride, double dt, const double *__restrict__ box_dt,
                           const uint16_t *__restrict__ box_of, DevScalars *sc, double *__restrict__ block_part) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double dv = 0.0, v2 = 0.0;
+    float dv = 0.f, v2 = 0.f;
     if (i < n) {
         const double hdt = 0.5 * (box_dt ? box_dt[box_of[i]] : dt);
         const double nax = anew[i], nay = anew[stride + i], naz = anew[2 * stride + i], ndu = anew[3 * stride + i];
@@ -84,18 +84,21 @@ __global__ void k_correct(int64_t n, double *__restrict__ vx, double *__restrict
         ay[i] = nay;
         az[i] = naz;
         du[i] = ndu;
-        dv = sqrt(dvx * dvx + dvy * dvy + dvz * dvz);
-        v2 = wx * wx + wy * wy + wz * wz;
+        // |dv| and |v|^2 only feed the step-quality ratio of Eq. cvleapfrog: FP32 is enough
+        const float fx = (float)dvx, fy = (float)dvy, fz = (float)dvz;
+        const float gx = (float)wx, gy = (float)wy, gz = (float)wz;
+        dv = sqrtf(fx * fx + fy * fy + fz * fz);
+        v2 = gx * gx + gy * gy + gz * gz;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        dv = fmax(dv, __shfl_xor_sync(0xffffffffu, dv, o));
+        dv = fmaxf(dv, __shfl_xor_sync(0xffffffffu, dv, o));
         v2 += __shfl_xor_sync(0xffffffffu, v2, o);
     }
     __shared__ double part[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-        part[warp] = v2;
-        if (dv > 0.0) atomicMax(&sc->dv_max_bits, dbits(dv));
+        part[warp] = (double)v2;
+        if (dv > 0.f) atomicMax(&sc->dv_max_bits, dbits((double)dv));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -125,6 +128,7 @@ int integrate_predict(sph_ctx *c, sph_state *s, double dt, const double *dhdt) {
     IntParams ip;
     ip.dt = dt;
     ip.h_clamp = c->p.h_clamp;
+    ip.inv_h_clamp = 1.0 / c->p.h_clamp;
     ip.box_dt = c->batch ? c->box_dt : nullptr;
     ip.box_of = c->batch ? c->box_of : nullptr;
     for (int k = 0; k < 3; k++) {

@@ -40,29 +40,24 @@ static Geo make_geo(const sph_params &p) {
 }
 
 // ------------------------------------------------------------------ group boxes (warp per group)
+// FP32 box of each group, rounded outwards from the FP64 positions (min/max in FP32 on the ALU
+// pipe: the walk and the stage-2 extent only need a box that contains the group).
 __global__ void k_group_boxes(Groups gr, int64_t G, const double *__restrict__ x, const double *__restrict__ y,
-                              const double *__restrict__ z, const double *__restrict__ h, Node *__restrict__ gbox,
-                              NodeF *__restrict__ gboxf) {
+                              const double *__restrict__ z, const double *__restrict__ h, NodeF *__restrict__ gboxf) {
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (g >= G) return;
     const int64_t a = group_first(gr, g) + lane;
     const bool va = a < group_end(gr, g);
-    double lo[3], hi[3];
     const double p[3] = {va ? x[a] : 0.0, va ? y[a] : 0.0, va ? z[a] : 0.0};
+    NodeF b;
     for (int k = 0; k < 3; k++) {
-        lo[k] = warp_min_d(va ? p[k] : INFINITY);
-        hi[k] = warp_max_d(va ? p[k] : -INFINITY);
+        b.lo[k] = warp_min_f(va ? __double2float_rd(p[k]) : INFINITY);
+        b.hi[k] = warp_max_f(va ? __double2float_ru(p[k]) : -INFINITY);
     }
-    const double hm = warp_max_d(va ? h[a] : 0.0);
-    if (lane == 0) {
-        Node b;
-        for (int k = 0; k < 3; k++) { b.lo[k] = lo[k]; b.hi[k] = hi[k]; }
-        b.hmax = hm;
-        b.pad = 0.0;
-        gbox[g] = b;
-        gboxf[g] = to_float_outward(b);
-    }
+    b.hmax = warp_max_f(va ? __double2float_ru(h[a]) : 0.f);
+    b.pad = 0.f;
+    if (lane == 0) gboxf[g] = b;
 }
 
 // ------------------------------------------------------------------ stage 1: tree walk per group
@@ -230,7 +225,7 @@ constexpr uint32_t kGrpSpinLimit = 1u << 22;
 // its own.  Pairs within a relative 2^-10 of the radius are decided in FP64 (exact_pair).
 __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
     Groups gr, const int32_t *__restrict__ box_root, int64_t G, const uint2 *__restrict__ cand, const uint32_t *__restrict__ cand_cnt, int cap,
-    const int64_t *__restrict__ chunk_off, const Node *__restrict__ gbox, const Node *__restrict__ nodes,
+    const int64_t *__restrict__ chunk_off, const NodeF *__restrict__ gboxf, const Node *__restrict__ nodes,
     const float4 *__restrict__ rel, const float *__restrict__ h32, const double *__restrict__ x,
     const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h, double s,
     float quarter_box, Geo geo, uint32_t *__restrict__ masks, uint32_t *__restrict__ nb_cnt,
@@ -276,9 +271,9 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
     const float hA = va ? h32[a] : 0.f;
     const float tA = (s32 * hA) * (s32 * hA);
     const float tAhi = tA * kBandHi, tAlo = tA * kBandLo;
-    const Node q = gbox[g];
+    const NodeF q = gboxf[g];
     const double hroot = nodes[box_root[group_box_of(gr, g)]].hmax;
-    const float ext = (float)fmax(fmax(q.hi[0] - q.lo[0], q.hi[1] - q.lo[1]), q.hi[2] - q.lo[2]);
+    const float ext = fmaxf(fmaxf(__fsub_ru(q.hi[0], q.lo[0]), __fsub_ru(q.hi[1], q.lo[1])), __fsub_ru(q.hi[2], q.lo[2]));
     const bool compact = ext + (float)(s * hroot) < quarter_box;   // warp-uniform
     int ca[3];
     unpack_cell(Araw, ca[0], ca[1], ca[2]);
@@ -451,7 +446,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
 
     k_h32<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->h, c->h32, c->h_base);
     SPH_LAUNCH_CHECK(c, "k_h32");
-    k_group_boxes<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, s->x, s->y, s->z, s->h, c->gbox, c->gboxf);
+    k_group_boxes<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, s->x, s->y, s->z, s->h, c->gboxf);
     SPH_LAUNCH_CHECK(c, "k_group_boxes");
 
     // stage 1, growing the candidate capacity while a list overflows
@@ -496,7 +491,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         SPH_CUDA(c, cudaMemsetAsync(&c->dscal->s2_ticket, 0, sizeof(uint32_t), c->stream));
         SPH_CUDA(c, cudaMemsetAsync(c->grp_slots, 0, (size_t)G * sizeof(int64_t), c->stream));
         k_stage2<<<blocks, kS2Warps * 32, 0, c->stream>>>(
-            gr, c->box_root, G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->gbox, c->nodes, c->rel, c->h32, s->x, s->y,
+            gr, c->box_root, G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->gboxf, c->nodes, c->rel, c->h32, s->x, s->y,
             s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->nb_ptr, (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket,
             c->grp_off, c->nb_ids, c->nb_cap, c->dscal);
         SPH_LAUNCH_CHECK(c, "k_stage2");

@@ -179,8 +179,7 @@ struct sph_ctx {
     // ---- neighbour cache ----
     int64_t n_groups = 0;              // groups of the current tree (tree_build)
     int64_t g_cap = 0;                 // capacity of the per-group arrays
-    sph::Node *gbox = nullptr;         // [groups] group boxes
-    sph::NodeF *gboxf = nullptr;       // [groups] FP32 outward copy
+    sph::NodeF *gboxf = nullptr;       // [groups] FP32 group boxes, rounded outwards
     int64_t *grp_chunks = nullptr;     // [groups + 1] candidate chunks per group -> scan
     int64_t *chunk_off = nullptr;      // [groups + 1]
     uint32_t *masks = nullptr;         // [chunks * 32] stage-2 hit masks
@@ -292,12 +291,13 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
     return (unsigned long long)__double_as_longlong(v);
 }
 
-__device__ __forceinline__ double warp_min_d(double v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+// Warp-wide FP32 min / max (all 32 lanes).
+__device__ __forceinline__ float warp_min_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
-__device__ __forceinline__ double warp_max_d(double v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+__device__ __forceinline__ float warp_max_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 

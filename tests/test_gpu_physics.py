@@ -164,6 +164,7 @@ def test_step_vs_oracle(precision):
     s = sph.DeviceState.from_numpy(d)
     solver = sph.Solver(sph.default_params(precision=precision), w["n"])
     used, dtn = solver.step(s, dt)
+    dvr_gpu = solver.stats()["dv_ratio"]
     out = s.to_numpy()
     solver.close()
     ids = out["id"].astype(np.int64)
@@ -180,3 +181,5 @@ def test_step_vs_oracle(precision):
         dxk = np.minimum(dxk, 1.0 - dxk)
         assert np.max(dxk) < 1e-14
     assert abs(dtn / dtn_ref - 1) < (1e-8 if precision == 0 else 1e-4)
+    if precision == 0:   # step-quality ratio max|dv| / rms|v| (its |dv| and |v|^2 are FP32 statistics)
+        assert dvr > 0 and abs(dvr_gpu / dvr - 1) < 1e-5
