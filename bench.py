@@ -41,6 +41,27 @@ FLOP_FORCE32_CAND = 16       # cell-relative separation, r^2, radius test
 FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan), energy and
                              # conductivity (Kahan), divergence
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the roofline kernels,
+# from one ncu capture of the Sedov 128^3 step (profiles/forces_sedov128_traffic.md), valid only for
+# the kernel sources it was taken on: the SHA-256 of those files is stored beside each figure and a
+# mismatch reports null.
+TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
+                   "paper_2503_09713_gb300/csrc/sph_internal.cuh")
+TRAFFIC = {}
+
+
+def kernel_traffic(name):
+    import hashlib
+    t = TRAFFIC.get(name)
+    if not t:
+        return None
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return t["bytes"] if h.hexdigest() == t["src_sha256"] else None
+
+
 WORKLOADS = {
     "sedov128": ("sedov", 128, "Sedov blast 128^3 = 2,097,152 particles, jittered cubic lattice, periodic unit "
                                "box, background rho 1 u 1e-8, E 1 within 2 h0 of the centre, M4 hfact 1.2, "
@@ -345,7 +366,7 @@ def main():
     kms = stage[dominant]
     achieved = flops / (kms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": kernel_traffic(kname),
                 "peak_source": "nominal FP64 rate (unit counts x 2.07 GHz)", "kernel_ms": kms,
                 "flops_per_launch": flops, "stage_ms": stage}
 
@@ -374,7 +395,8 @@ def main():
                          "stage_ms": r32["stage_ms"],
                          "roofline": {"bound": "alu", "kernel": "k_forces_mixed", "achieved": ach32,
                                       "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach32 / FP32_PEAK_TFLOPS,
-                                      "traffic": None, "peak_source": "nominal FP32 rate (unit counts x 2.07 GHz)",
+                                      "traffic": kernel_traffic("k_forces_mixed"),
+                                      "peak_source": "nominal FP32 rate (unit counts x 2.07 GHz)",
                                       "kernel_ms": kms32, "flops_per_launch": f32}}
         r32["solver"].close()
 

@@ -53,15 +53,15 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
             const double dy = image_diff(ya, y[b], sy, geo.L[1]);
             const double dz = image_diff(za, z[b], sz, geo.L[2]);
             const double q2 = (dx * dx + dy * dy + dz * dz) * hinv2;
-            if (q2 < 4.0) {
+            if (nonneg_lt(q2, 4.0)) {
                 ++nin;
                 const double q = sqrt(q2);
                 double f, df;
-                m4(q, f, df);
+                m4d(q, f, df);
                 const double qdf = q * df;
                 f0 += f;
                 g0 += 3.0 * f + qdf;
-                k0 += 12.0 * f + 8.0 * qdf + q2 * m4_d2(q);
+                k0 += 12.0 * f + 8.0 * qdf + q2 * m4d_d2(q);
             }
         }
         sf = f0;

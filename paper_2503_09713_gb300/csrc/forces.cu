@@ -162,24 +162,24 @@ __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__re
         const double dy = image_diff(A.y, B.y, sy, geo.L[1]);
         const double dz = image_diff(A.z, B.z, sz, geo.L[2]);
         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        const double hm = A.h > B.h ? A.h : B.h;
+        const double hm = nonneg_max(A.h, B.h);
         const double rad = __dmul_rn(2.0, hm);
-        if (!(r2 < __dmul_rn(rad, rad))) continue;
+        if (!nonneg_lt(r2, __dmul_rn(rad, rad))) continue;
         ++npair;
         const double rinv = rsqrt(r2);
         const double r = r2 * rinv;
         double f, dfa, dfb;
-        m4(r * A.hinv, f, dfa);
-        m4(r * B.hinv, f, dfb);
+        m4d(r * A.hinv, f, dfa);
+        m4d(r * B.hinv, f, dfb);
         const double Fa = dfa * A.fn;
         const double Fb = dfb * B.fn;
         const double vdotr = ((A.vx - B.vx) * dx + (A.vy - B.vy) * dy + (A.vz - B.vz) * dz) * rinv;
         double Aa = A.pre, Ab = B.pre;
-        if (vdotr < 0.0) {
+        if (__double_as_longlong(vdotr) < 0) {   // sign bit: approaching (-0 changes nothing below)
             const double w = fp.beta_av * vdotr;   // = -beta |v.rhat|
             Aa -= 0.5 * (A.acs - w) * vdotr * A.qf;
             Ab -= 0.5 * (B.acs - w) * vdotr * B.qf;
-            vs = fmax(vs, A.acs - w);
+            vs = nonneg_max(vs, A.acs - w);
         }
         const double sc_ = (Aa * Fa + Ab * Fb) * rinv;
         axs -= sc_ * dx;
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__re
         divs += vdotr * Fa;
         if (fp.alpha_u != 0.0) {
             const double t = 2.0 * fabs(A.P - B.P);   // v_sig^u = sqrt(t / (rho_a + rho_b))
-            if (t > 0.0) {
+            if (__double_as_longlong(t) > 0) {
                 const double vsu = t * rsqrt(t * (A.rho + B.rho));
                 dus += fp.alpha_u * vsu * (A.u - B.u) * 0.5 * (Fa * A.qf + Fb * B.qf);
             }

@@ -27,6 +27,34 @@ __device__ __forceinline__ void m4(T q, T &f, T &df) {
     }
 }
 
+// Order of non-negative doubles through their bit patterns: an integer compare on the ALU pipe
+// gives the same answer as the FP64 compare, which would occupy the FP64 pipe (the limiter of the
+// FP64 pair loops on this GPU, where FP64 issues at 1/64 of FP32).
+__device__ __forceinline__ bool nonneg_lt(double a, double b) {
+    return __double_as_longlong(a) < __double_as_longlong(b);
+}
+__device__ __forceinline__ double nonneg_max(double a, double b) { return nonneg_lt(a, b) ? b : a; }
+
+// M4 for q >= 0 in FP64 with the piece chosen by nonneg_lt.
+__device__ __forceinline__ void m4d(double q, double &f, double &df) {
+    if (nonneg_lt(q, 1.0)) {
+        f = 1.0 + q * q * (-1.5 + 0.75 * q);
+        df = q * (-3.0 + 2.25 * q);
+    } else if (nonneg_lt(q, 2.0)) {
+        const double t = 2.0 - q;
+        f = 0.25 * t * t * t;
+        df = -0.75 * t * t;
+    } else {
+        f = 0.0;
+        df = 0.0;
+    }
+}
+__device__ __forceinline__ double m4d_d2(double q) {
+    if (nonneg_lt(q, 1.0)) return 4.5 * q - 3.0;
+    if (nonneg_lt(q, 2.0)) return 1.5 * (2.0 - q);
+    return 0.0;
+}
+
 // d2f/dq2 of M4: 9/2 q - 3 (q<1), 3/2 (2-q) (1<=q<2), 0 beyond.
 template <typename T>
 __device__ __forceinline__ T m4_d2(T q) {
