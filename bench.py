@@ -47,7 +47,10 @@ FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan)
 # mismatch reports null.
 TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
                    "paper_2503_09713_gb300/csrc/sph_internal.cuh")
-TRAFFIC = {}
+TRAFFIC = {
+    "k_forces_fp64": {"bytes": 1073115392 + 95789056, "src_sha256": "e3c025842a31808b68612c42723860a2bb3d83aa645ac0f5688478dc9472d132"},
+    "k_forces_mixed": {"bytes": 892540928 + 92871424, "src_sha256": "e3c025842a31808b68612c42723860a2bb3d83aa645ac0f5688478dc9472d132"},
+}
 
 
 def kernel_traffic(name):
