@@ -378,7 +378,8 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "particles": n,
                        "parallelism": f"replicas x{world}" if world > 1 else "single box",
-                       "l2": "inputs larger than L2 (state 0.3 GB, neighbour cache 0.8 GB per replica)",
+                       "l2": f"inputs larger than L2 (state {16 * 8 * n / 1e9:.1f} GB, neighbour cache "
+                             f"{4 * st['cache_slots'] / 1e9:.1f} GB per replica; L2 0.13 GB)",
                        "leaves": st["n_leaves"], "cache_pairs": st["n_pairs"],
                        "density_iters_max": st["density_iters_max"],
                        "density_passes_avg": st["density_pair_evals"] / max(st["n_pairs"], 1),

@@ -10,6 +10,57 @@ namespace sph {
 
 int64_t scan_scratch_elems(int64_t n);
 
+// Grow a set of device arrays to new byte sizes (contents not kept); on failure all are freed.
+static int regrow(sph_ctx *c, void **const *ptrs, const size_t *bytes, size_t count, const char *what) {
+    for (size_t k = 0; k < count; k++) {
+        if (*ptrs[k]) SPH_CUDA(c, cudaFree(*ptrs[k]));
+        *ptrs[k] = nullptr;
+    }
+    for (size_t k = 0; k < count; k++) {
+        if (cudaMalloc(ptrs[k], bytes[k]) != cudaSuccess) {
+            cudaGetLastError();
+            for (size_t j = 0; j < count; j++) {
+                if (*ptrs[j]) cudaFree(*ptrs[j]);
+                *ptrs[j] = nullptr;
+            }
+            return fail(c, SPH_ERR_OOM, "%s", what);
+        }
+    }
+    return SPH_OK;
+}
+
+// Arrays indexed by leaf or node (their number L is known only after the compaction of A4).
+int ensure_tree(sph_ctx *c, int64_t L) {
+    if (L <= c->l_cap) return SPH_OK;
+    const int64_t cap = L + L / 4 + 64;
+    void **ptrs[] = {(void **)&c->lchild, (void **)&c->rchild, (void **)&c->endrange, (void **)&c->lflag,
+                     (void **)&c->rflag, (void **)&c->child, (void **)&c->node_parent, (void **)&c->leaf_parent,
+                     (void **)&c->visit, (void **)&c->nodes, (void **)&c->nodesf};
+    const size_t bytes[] = {(size_t)cap * 4, (size_t)cap * 4, (size_t)cap * 4, (size_t)cap, (size_t)cap,
+                            (size_t)cap * 8, (size_t)cap * 4, (size_t)cap * 4, (size_t)cap * 4,
+                            (size_t)cap * 2 * sizeof(Node), (size_t)cap * 2 * sizeof(NodeF)};
+    c->l_cap = 0;
+    int r = regrow(c, ptrs, bytes, sizeof(ptrs) / sizeof(ptrs[0]), "tree arrays");
+    if (r) return r;
+    c->l_cap = cap;
+    return SPH_OK;
+}
+
+// Per-particle records of the force loop of the current precision, allocated on first use.
+int ensure_force_records(sph_ctx *c) {
+    const size_t N = (size_t)c->n_cap;
+    if (c->p.precision == SPH_MIXED) {
+        if (c->m_v) return SPH_OK;
+        void **ptrs[] = {(void **)&c->m_v, (void **)&c->m_t, (void **)&c->m_r};
+        const size_t bytes[] = {N * 16, N * 16, N * 16};
+        return regrow(c, ptrs, bytes, 3, "mixed force records");
+    }
+    if (c->frec) return SPH_OK;
+    void **ptrs[] = {(void **)&c->frec};
+    const size_t bytes[] = {N * 128};
+    return regrow(c, ptrs, bytes, 1, "FP64 force records");
+}
+
 int fail(sph_ctx *c, int code, const char *fmt, ...) {
     if (c) {
         char buf[512];
@@ -63,16 +114,8 @@ int ensure_groups(sph_ctx *c, int64_t G) {
                             (size_t)(cap + 1) * 8, (size_t)(cap + 1) * 8, (size_t)(cap + 1) * 8,
                             (size_t)cap * 2};
     c->g_cap = 0;
-    for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); k++) {
-        if (*ptrs[k]) SPH_CUDA(c, cudaFree(*ptrs[k]));
-        *ptrs[k] = nullptr;
-    }
-    for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); k++) {
-        if (cudaMalloc(ptrs[k], bytes[k]) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(c, SPH_ERR_OOM, "per-group arrays for %lld groups", (long long)cap);
-        }
-    }
+    int r = regrow(c, ptrs, bytes, sizeof(ptrs) / sizeof(ptrs[0]), "per-group arrays");
+    if (r) return r;
     c->g_cap = cap;
     return SPH_OK;
 }
@@ -244,24 +287,21 @@ int create_ctx(const sph_params *p, int64_t n_cap, int n_boxes, int64_t neigh_ca
     const int64_t tiles = (N + 4095) / 4096;
     const int64_t chunks = (N + 2047) / 2048;
     c->sort_tiles = tiles;
-    c->cand_cap = 256;
+    c->cand_cap = 128;
     c->nb_cap = neigh_cap > 0 ? neigh_cap : 96 * N;
-    c->masks_cap = G * 40 * 32;
+    c->masks_cap = G * 16 * 32;   // grown by the cache build when the candidate chunks need more
     const int64_t scan_elems = 2 * (chunks + 1) + scan_scratch_elems(chunks) + scan_scratch_elems(G + 1) + 64;
     if ((r = alloc(c, &c->keys[0], N)) || (r = alloc(c, &c->keys[1], N)) || (r = alloc(c, &c->vals[0], N)) ||
         (r = alloc(c, &c->vals[1], N)) || (r = alloc(c, &c->digit_hist, 8 * 256)) ||
         (r = alloc(c, &c->lookback, (size_t)8 * tiles * 256)) || (r = alloc(c, &c->tile_ctr, 8)) ||
         (r = alloc(c, &c->mask[0], N)) || (r = alloc(c, &c->mask[1], N)) || (r = alloc(c, &c->scan_tmp, scan_elems)) ||
-        (r = alloc(c, &c->leaf_first, N + 1)) || (r = alloc(c, &c->mu_leaf, N)) || (r = alloc(c, &c->lchild, N)) ||
-        (r = alloc(c, &c->rchild, N)) || (r = alloc(c, &c->endrange, N)) || (r = alloc(c, &c->lflag, N)) ||
-        (r = alloc(c, &c->rflag, N)) || (r = alloc(c, &c->child, 2 * N)) || (r = alloc(c, &c->node_parent, N)) ||
-        (r = alloc(c, &c->leaf_parent, N)) || (r = alloc(c, &c->visit, N)) || (r = alloc(c, &c->nodes, 2 * N)) || (r = alloc(c, &c->nodesf, 2 * N)) ||
-        (r = alloc(c, &c->gather_tmp, (size_t)16 * N)) || (r = alloc(c, &c->id_tmp, N)) ||
+        (r = alloc(c, &c->leaf_first, N + 1)) || (r = alloc(c, &c->mu_leaf, N)) ||
+        (r = ensure_tree(c, std::max<int64_t>(N / 6, 1))) ||
+        (r = alloc(c, &c->gather_tmp, (size_t)kGatherBatch * N)) || (r = alloc(c, &c->id_tmp, N)) ||
         (r = alloc(c, &c->rel, N)) || (r = alloc(c, &c->h32, N)) || (r = alloc(c, &c->h_base, N)) ||
-        (r = ensure_groups(c, G)) || (r = alloc(c, &c->masks, (size_t)G * 40 * 32)) ||
+        (r = ensure_groups(c, G)) || (r = alloc(c, &c->masks, (size_t)c->masks_cap)) ||
         (r = alloc(c, &c->nb_cnt, N)) || (r = alloc(c, &c->nb_ptr, N)) || (r = alloc(c, &c->nb_ids, c->nb_cap)) ||
-        (r = alloc(c, (char **)&c->frec, (size_t)128 * N)) || (r = alloc(c, &c->m_v, N)) ||
-        (r = alloc(c, &c->m_t, N)) || (r = alloc(c, &c->m_r, N)) || (r = alloc(c, &c->a_new, (size_t)4 * N)) || (r = alloc(c, &c->dhdt, N)) ||
+        (r = alloc(c, &c->a_new, (size_t)4 * N)) || (r = alloc(c, &c->dhdt, N)) ||
         (r = alloc(c, &c->block_part, (size_t)(N / 256 + 2))) || (r = alloc(c, &c->dscal, 1)) ||
         (r = alloc(c, &c->box_root, n_boxes))) {
         free_all(c);

@@ -332,7 +332,8 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     fp.box_of = c->batch ? c->box_of : nullptr;
     fp.box_dt_next = c->batch ? c->box_dt_next : nullptr;
     const int mixed = c->p.precision == SPH_MIXED;
-    int r;
+    int r = ensure_force_records(c);
+    if (r) return r;
     if ((r = stage_begin(c, kStForcePrep))) return r;
     k_force_prep<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->h,
                                                            s->rho, s->omega, fp, mixed, (FRec *)c->frec, c->m_v,

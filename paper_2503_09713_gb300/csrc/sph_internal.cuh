@@ -17,6 +17,7 @@ constexpr int kGroup = 32;               // largest neighbour-search group (one 
 constexpr int kCellBits = 10;            // cell grid of the FP32 relative coordinates: 2^10 per axis
 constexpr int kStackDepth = 66;          // tree-walk stack (tree depth <= 63 for distinct 63-bit codes)
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kGatherBatch = 4;          // state fields reordered per gather pass (scratch: 4 x n_cap doubles)
 
 // Device error word bits (ctx->d_flags[0]).
 enum : uint32_t {
@@ -167,10 +168,11 @@ struct sph_ctx {
     sph::Node *nodes = nullptr;        // [2 n_cap]
     sph::NodeF *nodesf = nullptr;      // [2 n_cap] FP32 outward copy for the walk
     int64_t n_leaves = 0;
+    int64_t l_cap = 0;                 // capacity of the leaf- and node-indexed arrays (ensure_tree)
     bool tree_valid = false;
 
     // ---- reorder scratch and per-particle derived arrays ----
-    double *gather_tmp = nullptr;      // [16][n_cap]
+    double *gather_tmp = nullptr;      // [kGatherBatch][n_cap]
     uint32_t *id_tmp = nullptr;
     float4 *rel = nullptr;             // [n_cap] FP32 cell offsets + packed cell index
     float *h32 = nullptr;              // [n_cap]
@@ -270,6 +272,8 @@ int integrate_correct(sph_ctx *c, sph_state *s, double dt);
 int read_scalars(sph_ctx *c);
 Groups make_groups(const sph_ctx *c);
 int ensure_groups(sph_ctx *c, int64_t G);   // grow the per-group arrays to G groups
+int ensure_tree(sph_ctx *c, int64_t L);     // grow the leaf- and node-indexed arrays to L leaves
+int ensure_force_records(sph_ctx *c);       // force records of the current precision
 // Per-stage timing: stage_begin/stage_end bracket the launches of one stage on the context stream;
 // with timing on, stage_end waits for the stage and adds its duration to stats.stage_ms[k].
 enum Stage { kStPredict = 0, kStTree, kStNeigh, kStDensity, kStForcePrep, kStForces, kStCorrect, kStCount };

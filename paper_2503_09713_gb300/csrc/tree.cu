@@ -619,31 +619,32 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
     c->mu = c->keys[0];
     c->perm = c->vals[0];
 
-    // reorder the particle arrays
-    GatherArgs g{};
-    double *fields[15] = {s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->h, s->ax, s->ay, s->az, s->du,
-                          s->rho, s->omega, s->vsig};
+    // reorder the particle arrays, kGatherBatch fields per pass through the scratch block
+    const double *fields[16];
+    double *fields_dst[16];
+    const double *all[15] = {s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->h, s->ax, s->ay, s->az, s->du,
+                             s->rho, s->omega, s->vsig};
     const int nf_all = gather_outputs ? 15 : 12;
     int nf = 0;
-    for (int f = 0; f < nf_all; f++) {
-        if (!fields[f]) continue;
-        g.src[nf] = fields[f];
-        g.dst[nf] = c->gather_tmp + (size_t)nf * c->n_cap;
-        nf++;
+    for (int f = 0; f < nf_all; f++)
+        if (all[f]) fields[nf++] = all[f];
+    if (c->dhdt_valid) fields[nf++] = c->dhdt;   // dh/dt of the last force pass travels with its particles
+    for (int f = 0; f < nf; f++) fields_dst[f] = const_cast<double *>(fields[f]);
+    for (int f0 = 0; f0 < nf || (f0 == 0 && s->id); f0 += kGatherBatch) {
+        GatherArgs g{};
+        g.nf = std::min(kGatherBatch, nf - f0);
+        for (int k = 0; k < g.nf; k++) {
+            g.src[k] = fields[f0 + k];
+            g.dst[k] = c->gather_tmp + (size_t)k * c->n_cap;
+        }
+        g.id_src = s->id;
+        g.id_dst = (f0 == 0 && s->id) ? c->id_tmp : nullptr;
+        k_gather<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->perm, g);
+        SPH_LAUNCH_CHECK(c, "k_gather");
+        for (int k = 0; k < g.nf; k++)
+            SPH_CUDA(c, cudaMemcpyAsync(fields_dst[f0 + k], g.dst[k], (size_t)n * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->stream));
     }
-    if (c->dhdt_valid) {   // dh/dt of the last force pass travels with its particles
-        g.src[nf] = c->dhdt;
-        g.dst[nf] = c->gather_tmp + (size_t)nf * c->n_cap;
-        nf++;
-    }
-    g.nf = nf;
-    g.id_src = s->id;
-    g.id_dst = s->id ? c->id_tmp : nullptr;
-    k_gather<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->perm, g);
-    SPH_LAUNCH_CHECK(c, "k_gather");
-    for (int f = 0; f < nf; f++)
-        SPH_CUDA(c, cudaMemcpyAsync(const_cast<double *>(g.src[f]), g.dst[f], (size_t)n * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, c->stream));
     if (s->id)
         SPH_CUDA(c, cudaMemcpyAsync(s->id, c->id_tmp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
                                     c->stream));
@@ -686,6 +687,8 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
     const int64_t L = c->hscal->n_leaves;
     if (L < 1 || L > n) return fail(c, SPH_ERR_CUDA, "bad leaf count %lld", (long long)L);
     c->n_leaves = L;
+    r = ensure_tree(c, L);
+    if (r) return r;
 
     // A5 Karras
     if (L > 1) {

@@ -8,6 +8,8 @@
 * uniform 256^3 (16,777,216 particles): mixed precision against FP64 for every particle
   (density <= 1e-5 relative, accelerations <= 1e-4 of max|a|), sampled particles of the FP64 run
   against the oracle's definitions evaluated one by one.
+* Sedov 512^3 (134,217,728 particles): the same checks on the converged state, and sampled
+  particles after one FP64 step.
 
 Tolerances as in test_gpu_physics (h: 1e-9 relative, from Newton's quadratic convergence after
 |dh|/h <= 1e-6; accelerations on the same h: summation order only).
@@ -154,3 +156,80 @@ def test_uniform256_mixed_against_fp64_and_sampled_oracle():
     assert np.max(np.abs(g64["h"][idx] / r["h"] - 1)) < 1e-9
     for k in ("ax", "ay", "az"):
         assert np.max(np.abs(g64[k][idx] - r[k])) < 1e-8 * amax
+
+
+def _fetch(s, fields):
+    """Selected fields of a device state, in the original particle order (host copies)."""
+    ids = s.t["id"].cpu().numpy().view(np.uint32).astype(np.int64)
+    return {f: to_orig(s.t[f].cpu().numpy(), ids) for f in fields}
+
+
+def _local(st, idx, radius):
+    """The particles within `radius` (periodic unit box) of any particle in idx, as sub-arrays, and
+    the positions of idx in them.  The oracle's answer for a particle depends only on particles
+    within 2 * (2 h_hi) of it, so evaluating it on this neighbourhood (radius above 4 h_hi) is
+    exact and avoids its O(n) candidate scans over 134 M particles."""
+    keep = np.zeros(len(st["x"]), dtype=bool)
+    for a in idx:
+        d2 = np.zeros(len(st["x"]))
+        for k in ("x", "y", "z"):
+            d = np.abs(st[k] - st[k][a])
+            d = np.minimum(d, 1.0 - d)
+            d2 += d * d
+        keep |= d2 < radius * radius
+    sel = np.flatnonzero(keep)
+    sub = {k: np.ascontiguousarray(st[k][sel]) for k in ("x", "y", "z", "vx", "vy", "vz", "u")}
+    return sub, np.searchsorted(sel, idx)
+
+
+def test_sedov512_sampled_and_mixed_against_fp64():
+    """Sedov 512^3 (134,217,728 particles), the largest configuration, in the launch configuration
+    bench.py uses: FP64 converged state and the state after one CFL step on sampled particles
+    (blast and background) against the oracle's definitions evaluated one by one; the mixed
+    path against FP64 for every particle."""
+    torch = require_gpu()
+    if torch.cuda.mem_get_info()[1] < 200e9:
+        pytest.skip("needs a GPU with more than 200 GB")
+    from paper_2503_09713_gb300 import sph, workloads
+    w = workloads.sedov(512, seed=12346)
+    n = w["n"]
+    P = O.Params()
+    h_hi = 1.5 * w["dx"]   # the density stays within a few per cent of the lattice's in one step
+    rng = np.random.default_rng(11)
+    idx = np.concatenate([rng.choice(np.flatnonzero(w["u"] > 1e-6), 3, replace=False), rng.integers(0, n, 3)])
+    state_fields = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du")
+    got = {}
+    for precision in (0, 1):
+        s = sph.DeviceState.from_numpy(w)
+        solver = sph.Solver(sph.default_params(precision=precision), n)
+        solver.converge(s)
+        got[precision] = _fetch(s, ("h", "rho", "ax", "ay", "az", "du"))
+        if precision == 0:
+            used, _ = solver.step(s, 0.0)
+            assert used > 0
+            after = _fetch(s, state_fields)
+        solver.close()
+        del s, solver
+        torch.cuda.empty_cache()
+    g64, g32 = got[0], got[1]
+    amax = np.max(np.abs(np.stack([g64["ax"], g64["ay"], g64["az"]])))
+    sub, j = _local(w, idx, 4.5 * h_hi)
+    r = O.subset_forces(*[sub[k] for k in ("x", "y", "z", "vx", "vy", "vz", "u")], w["mass"], P, j, h_hi)
+    assert np.max(np.abs(g64["h"][idx] / r["h"] - 1)) < 1e-9
+    for k in ("ax", "ay", "az"):
+        assert np.max(np.abs(g64[k][idx] - r[k])) < 1e-8 * amax, k
+    assert np.max(np.abs(g32["rho"] / g64["rho"] - 1)) < 1e-5
+    for k in ("ax", "ay", "az"):
+        assert np.max(np.abs(g32[k] - g64[k])) < 1e-4 * amax, k
+    # after the step the state holds v^{n+1}, u^{n+1}; its accelerations were evaluated at the
+    # predicted v* = v^{n+1} - dt/2 (a^{n+1} - a^n) and u* likewise (App. G), so the oracle gets those
+    hdt = 0.5 * used
+    mid = dict(after)
+    for v, a in (("vx", "ax"), ("vy", "ay"), ("vz", "az"), ("u", "du")):
+        mid[v] = after[v] - hdt * (after[a] - g64[a])
+    sub1, j1 = _local(mid, idx, 4.5 * h_hi)
+    r1 = O.subset_forces(*[sub1[k] for k in ("x", "y", "z", "vx", "vy", "vz", "u")], w["mass"], P, j1, h_hi)
+    amax1 = np.max(np.abs(np.stack([after["ax"], after["ay"], after["az"]])))
+    assert np.max(np.abs(after["h"][idx] / r1["h"] - 1)) < 1e-9
+    for k in ("ax", "ay", "az"):
+        assert np.max(np.abs(after[k][idx] - r1[k])) < 1e-8 * amax1, k
