@@ -146,6 +146,7 @@ def run_precision(torch, sph, w, precision: int, steps: int, warmup: int, dist, 
     s = sph.DeviceState.from_numpy(w)
     solver = sph.Solver(p, w["n"])
     solver.converge(s)
+    shape, _ = solver.autotune(s)     # launch shapes and reduction level, before the warm-up
     for _ in range(warmup):
         solver.step(s)
     stream = torch.cuda.current_stream()
@@ -171,7 +172,7 @@ def run_precision(torch, sph, w, precision: int, steps: int, warmup: int, dist, 
     st = solver.stats()
     launches = (st["kernel_launches"] - launches0) / steps
     out = {"ms_per_step": ms, "wall_ms_per_step": 1e3 * t_wall / steps, "launches_per_step": launches,
-           "clocks": clk, "stats": st}
+           "clocks": clk, "stats": st, "launch": shape}
     if timing_pass:
         solver.set_timing(True)
         solver.reset_timing()
@@ -202,6 +203,7 @@ def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349) -> dict
     s = sph.DeviceState.from_numpy(cat)
     solver = sph.Solver.batch(sph.default_params(precision=sph.SPH_MIXED), off, mass, gam)
     solver.converge(s)
+    shape, _ = solver.autotune(s)
     for _ in range(warmup):
         solver.step(s)
     stream = torch.cuda.current_stream()
@@ -227,7 +229,7 @@ def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349) -> dict
             "dtype": "f32 pair sums (Kahan) / f64 state", "launches_per_step": (st["kernel_launches"] - l0) / steps,
             "timing": "per-box CFL steps, one context, one launch per stage for all boxes", "stage_ms": stage,
             "density_iters_max": st["density_iters_max"], "outer_passes": st["outer_passes"],
-            "cache_pairs": st["n_pairs"], "stage2_chunks": st["cand_chunks"]}
+            "cache_pairs": st["n_pairs"], "stage2_chunks": st["cand_chunks"], "launch": shape}
 
 
 def e2e_run(torch, sph, solver, s, steps: int):
@@ -385,7 +387,7 @@ def main():
                        "density_passes_avg": st["density_pair_evals"] / max(st["n_pairs"], 1),
                        "cache_slots": st["cache_slots"], "stage2_chunks": st["cand_chunks"]},
             "clocks": r64["clocks"], "gpu_launches": int(round(r64["launches_per_step"] * args.steps)),
-            "roofline": roofline}
+            "roofline": roofline, "launch": r64["launch"]}
 
     if not args.no_mixed and args.only != "fp64":
         r32 = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, None)
@@ -396,7 +398,7 @@ def main():
         ach32 = f32 / (kms32 * 1e-3) / 1e12
         line["mixed"] = {"value": n * world / (ms32 * 1e-3), "unit": "particles/s", "ms_per_step": ms32,
                          "dtype": "f32 pair sums (Kahan) / f64 state", "speedup_vs_fp64": ms / ms32,
-                         "stage_ms": r32["stage_ms"],
+                         "stage_ms": r32["stage_ms"], "launch": r32["launch"],
                          "roofline": {"bound": "alu", "kernel": "k_forces_mixed", "achieved": ach32,
                                       "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach32 / FP32_PEAK_TFLOPS,
                                       "traffic": kernel_traffic("k_forces_mixed"),

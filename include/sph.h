@@ -123,6 +123,18 @@ typedef struct {
                                 preparation, force loop, corrector, unused */
 } sph_stats;
 
+/* Launch shapes of the pair kernels and the tree reduction level, chosen by sph_autotune or set by
+ * the caller (defaults: 128, 128, 128, 4, p->reduction_level).  None of them changes a result: the
+ * neighbour lists and every per-particle sum are the same for any choice (the cache build keeps the
+ * FP64 set and orders each list by particle index). */
+typedef struct {
+    int density_block;    /* threads per block of the density kernel: 64, 128 or 256 */
+    int forces_block;     /* threads per block of the force kernels: 64, 128 or 256 */
+    int walk_block;       /* threads per block of the stage-1 tree walk: 64, 128 or 256 */
+    int stage2_warps;     /* warps (groups in flight) per block of the stage-2 kernel: 1 .. 8 */
+    int reduction_level;  /* n_red of App. C (copied into the context's parameters) */
+} sph_launch;
+
 /* Fill *p with the paper's defaults and a periodic unit box.  Never fails. */
 void sph_default_params(sph_params *p);
 
@@ -213,6 +225,23 @@ int sph_export_neighbours(sph_ctx *ctx, int64_t *off, uint32_t *ids);
 
 /* Statistics of the last calls. */
 int sph_get_stats(sph_ctx *ctx, sph_stats *st);
+
+/* Launch shapes in use (*out) / to use from the next call on (*in).  Errors: INVALID_ARG for a
+ * shape outside the ranges of sph_launch. */
+int sph_get_launch(sph_ctx *ctx, sph_launch *out);
+int sph_set_launch(sph_ctx *ctx, const sph_launch *in);
+
+/* Autotuner of the launch shapes (no counterpart in the paper; the paper reports the optimum
+ * reduction level of its own hardware, App. C, "around 10 particles per leaf").  Times A1-A9 on *s
+ * (device pointers, as sph_step) for each candidate: the reduction levels 1-7, then, one knob at a
+ * time, the stage-2 warps per block {2, 4, 8} and the density, force and walk block sizes
+ * {64, 128, 256}, two runs each with CUDA events (the faster counts), and keeps the fastest
+ * combination in the context.  A1-A9 leave the physical state unchanged: the particles are
+ * reordered, h is re-converged (it moves by less than h_tol * h) and a, du, rho, Omega, v_sig are
+ * recomputed; velocities, u and positions are untouched.  *s should be converged (a previous
+ * density + force call or sph_step).  *best (may be NULL) receives the chosen shapes, *ms_best
+ * (may be NULL) the A1-A9 time with them.  Errors: as sph_step. */
+int sph_autotune(sph_ctx *ctx, sph_state *s, sph_launch *best, double *ms_best);
 
 /* Enable (1) or disable (0) per-stage CUDA-event timing.  With timing on, every stage waits for its
  * own completion, so stage boundaries serialise with the host; kernel durations are unaffected. */

@@ -3,6 +3,7 @@
 #include <cstring>
 #include <vector>
 #include <algorithm>
+#include <initializer_list>
 
 #include "sph_internal.cuh"
 
@@ -274,6 +275,7 @@ int create_ctx(const sph_params *p, int64_t n_cap, int n_boxes, int64_t neigh_ca
     if (r) { delete c; return r; }
     if (n_cap < 1 || n_cap > (int64_t)1 << 30) { delete c; return SPH_ERR_INVALID_ARG; }
     c->p = *p;
+    c->launch.reduction_level = p->reduction_level;
     c->stream = (cudaStream_t)stream;
     c->n_cap = n_cap;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
@@ -409,6 +411,7 @@ int sph_set_params(sph_ctx *c, const sph_params *p) {
     int r = check_params(c, p);
     if (r) return r;
     c->p = *p;
+    c->launch.reduction_level = p->reduction_level;
     c->tree_valid = c->cache_valid = c->density_valid = c->forces_valid = false;
     c->dhdt_valid = false;
     c->dt_next = -1.0;
@@ -617,6 +620,93 @@ int sph_get_stats(sph_ctx *c, sph_stats *st) {
     c->stats.kernel_launches = c->launches;
     *st = c->stats;
     return SPH_OK;
+}
+
+int sph_get_launch(sph_ctx *c, sph_launch *out) {
+    if (!c || !out) return SPH_ERR_INVALID_ARG;
+    *out = c->launch;
+    return SPH_OK;
+}
+
+int sph_set_launch(sph_ctx *c, const sph_launch *in) {
+    if (!c || !in) return SPH_ERR_INVALID_ARG;
+    auto blk_ok = [](int b) { return b == 64 || b == 128 || b == 256; };
+    if (!blk_ok(in->density_block) || !blk_ok(in->forces_block) || !blk_ok(in->walk_block) ||
+        in->stage2_warps < 1 || in->stage2_warps > 8 || in->reduction_level < 0 || in->reduction_level > 16)
+        return fail(c, SPH_ERR_INVALID_ARG, "launch shape out of range");
+    if (in->reduction_level != c->p.reduction_level) {
+        c->p.reduction_level = in->reduction_level;
+        c->tree_valid = c->cache_valid = false;
+    }
+    c->launch = *in;
+    return SPH_OK;
+}
+
+static int autotune(sph_ctx *c, sph_state *s, sph_launch *best, double *ms_best) {
+    int r;
+    // A1-A9 with launch shapes L, timed with events on the context stream; the faster of two runs
+    auto run = [&](const sph_launch &L, double &ms) -> int {
+        int rr = sph_set_launch(c, &L);
+        if (rr) return rr;
+        ms = 1e300;
+        for (int rep = 0; rep < 2; rep++) {
+            SPH_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+            int iters = 0;
+            if ((rr = tree_build(c, s, true)) || (rr = neighbours_build(c, s)) ||
+                (rr = density_with_restarts(c, s, &iters, c->p.max_outer)) ||
+                (rr = forces_run(c, s, s->ax, s->ay, s->az, s->du)) || (rr = finish_forces(c)))
+                return rr;
+            SPH_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+            SPH_CUDA(c, cudaEventSynchronize(c->ev[1]));
+            float t = 0.f;
+            SPH_CUDA(c, cudaEventElapsedTime(&t, c->ev[0], c->ev[1]));
+            ms = std::min(ms, (double)t);
+        }
+        return SPH_OK;
+    };
+    sph_launch cur = c->launch;
+    double cur_ms = 0.0;
+    if ((r = run(cur, cur_ms))) return r;
+    auto try_values = [&](int sph_launch::*field, std::initializer_list<int> values) -> int {
+        for (int v : values) {
+            if (cur.*field == v) continue;
+            sph_launch cand = cur;
+            cand.*field = v;
+            double ms = 0.0;
+            int rr = run(cand, ms);
+            if (rr) return rr;
+            if (ms < cur_ms) {
+                cur = cand;
+                cur_ms = ms;
+            }
+        }
+        return SPH_OK;
+    };
+    if ((r = try_values(&sph_launch::reduction_level, {1, 2, 3, 4, 5, 6, 7})) ||
+        (r = try_values(&sph_launch::stage2_warps, {2, 4, 8})) ||
+        (r = try_values(&sph_launch::density_block, {64, 128, 256})) ||
+        (r = try_values(&sph_launch::forces_block, {64, 128, 256})) ||
+        (r = try_values(&sph_launch::walk_block, {64, 128, 256})))
+        return r;
+    // leave the context (tree, cache, outputs) in the chosen configuration
+    double ms = 0.0;
+    if ((r = run(cur, ms))) return r;
+    c->forces_valid = true;
+    c->dhdt_valid = true;
+    if (best) *best = cur;
+    if (ms_best) *ms_best = std::min(cur_ms, ms);
+    return SPH_OK;
+}
+
+int sph_autotune(sph_ctx *c, sph_state *s, sph_launch *best, double *ms_best) {
+    int r = check_state(c, s, true);
+    if (r) return r;
+    c->n = s->n;
+    const bool timing = c->timing;   // per-stage timing would add a synchronisation per stage
+    c->timing = false;
+    r = autotune(c, s, best, ms_best);
+    c->timing = timing;
+    return r;
 }
 
 int sph_set_timing(sph_ctx *c, int enable) {

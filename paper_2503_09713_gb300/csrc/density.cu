@@ -120,7 +120,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
 }
 
 template <bool kMixed>
-__global__ void __launch_bounds__(128) k_density(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+__global__ void __launch_bounds__(256, kMixed ? 3 : 1) k_density(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                                                  const double *__restrict__ z, const float4 *__restrict__ rel,
                                                  double *__restrict__ h, const double *__restrict__ h_base,
                                                  const uint32_t *__restrict__ nb_cnt,
@@ -203,15 +203,16 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
     dp.geo = make_pair_geo(c->p);
     dp.box_mass = c->batch ? c->box_mass : nullptr;
     dp.box_of = c->batch ? c->box_of : nullptr;
+    const int blk = c->launch.density_block;
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->max_iters, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->pair_evals, 0, 2 * sizeof(unsigned long long), c->stream));
     if (c->p.precision == SPH_MIXED)
-        k_density<true><<<grid_for(n, 128), 128, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+        k_density<true><<<grid_for(n, blk), blk, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
                                                                  c->nb_cnt, c->nb_ptr, c->nb_ids, dp,
                                                                  s->rho, s->omega, c->dscal);
     else
-        k_density<false><<<grid_for(n, 128), 128, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+        k_density<false><<<grid_for(n, blk), blk, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
                                                                   c->nb_cnt, c->nb_ptr, c->nb_ids, dp,
                                                                   s->rho, s->omega, c->dscal);
     SPH_LAUNCH_CHECK(c, "k_density");

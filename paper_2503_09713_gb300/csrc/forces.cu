@@ -124,7 +124,7 @@ __device__ __forceinline__ void dt_reduce(double t, unsigned long long npair, De
 // FP64 pair loop.  A candidate is first tested in FP32 on the cell-relative offsets against the
 // current h (kPreBand margin); the survivors are decided and evaluated in FP64 with the nearest
 // image from the cell indices.  The mass factor is applied once per particle.
-__global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__restrict__ rec,
+__global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__restrict__ rec,
                                                      const float4 *__restrict__ rel, const float *__restrict__ h32,
                                                      const uint32_t *__restrict__ nb_cnt,
                                                      const unsigned long long *__restrict__ nb_ptr,
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(128) k_forces_fp64(int64_t n, const FRec *__re
     dt_reduce(tdt, npair, sc, fp.box_dt_next, box);
 }
 
-__global__ void __launch_bounds__(128) k_forces_mixed(int64_t n, const float4 *__restrict__ rel,
+__global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *__restrict__ rel,
                                                       const float4 *__restrict__ m_v, const float4 *__restrict__ m_t,
                                                       const float4 *__restrict__ m_r, const double *__restrict__ h,
                                                       const uint32_t *__restrict__ nb_cnt,
@@ -343,11 +343,12 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     SPH_LAUNCH_CHECK(c, "k_reset_dt");
     if ((r = stage_end(c, kStForcePrep)) || (r = stage_begin(c, kStForces))) return r;
     ForceOut out{ax, ay, az, du, s->vsig, c->dhdt};
+    const int blk = c->launch.forces_block;
     if (mixed)
-        k_forces_mixed<<<grid_for(n, 128), 128, 0, c->stream>>>(n, c->rel, c->m_v, c->m_t, c->m_r, s->h,
+        k_forces_mixed<<<grid_for(n, blk), blk, 0, c->stream>>>(n, c->rel, c->m_v, c->m_t, c->m_r, s->h,
                                                                 c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out, c->dscal);
     else
-        k_forces_fp64<<<grid_for(n, 128), 128, 0, c->stream>>>(n, (const FRec *)c->frec, c->rel, c->h32,
+        k_forces_fp64<<<grid_for(n, blk), blk, 0, c->stream>>>(n, (const FRec *)c->frec, c->rel, c->h32,
                                                                     c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out,
                                                                     c->dscal);
     SPH_LAUNCH_CHECK(c, "k_forces");

@@ -85,7 +85,7 @@ __device__ __forceinline__ float walk_radius(float s, float h1, float h2) {
     return __fmul_ru(__fmul_ru(s, fmaxf(h1, h2)), 1.0f + 1.0f / 65536.0f);
 }
 
-__global__ void __launch_bounds__(128) k_walk(Groups gr, int64_t G, int64_t L, const NodeF *__restrict__ gboxf,
+__global__ void __launch_bounds__(256) k_walk(Groups gr, int64_t G, int64_t L, const NodeF *__restrict__ gboxf,
                                              const NodeF *__restrict__ nodesf, const int32_t *__restrict__ child,
                                              const int64_t *__restrict__ leaf_first,
                                              const int32_t *__restrict__ box_root, float s, Geo geo,
@@ -204,7 +204,7 @@ __device__ __forceinline__ bool exact_pair(int64_t a, int64_t b, const double *_
     return r2 < __dmul_rn(rad, rad);
 }
 
-constexpr int kS2Warps = 4;
+constexpr int kS2MaxWarps = 8;   // stage-2 warps per block: 1 .. 8 (sph_launch.stage2_warps)
 constexpr float kBandLo = 1.0f - 1.0f / 1024.0f;
 constexpr float kBandHi = 1.0f + 1.0f / 1024.0f;
 
@@ -223,7 +223,7 @@ constexpr uint32_t kGrpSpinLimit = 1u << 22;
 // in the tree), so its wrapped coordinate is its nearest image whenever ext + s*h_max is below half
 // a box; the kernel asks for a quarter box (warp-uniform), otherwise every separation is wrapped on
 // its own.  Pairs within a relative 2^-10 of the radius are decided in FP64 (exact_pair).
-__global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
+__global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     Groups gr, const int32_t *__restrict__ box_root, int64_t G, const uint2 *__restrict__ cand, const uint32_t *__restrict__ cand_cnt, int cap,
     const int64_t *__restrict__ chunk_off, const NodeF *__restrict__ gboxf, const Node *__restrict__ nodes,
     const float4 *__restrict__ rel, const float *__restrict__ h32, const double *__restrict__ x,
@@ -231,9 +231,11 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
     float quarter_box, Geo geo, uint32_t *__restrict__ masks, uint32_t *__restrict__ nb_cnt,
     unsigned long long *__restrict__ nb_ptr, unsigned long long *lookback, uint32_t *ticket, int64_t *__restrict__ grp_off, uint32_t *__restrict__ nb_ids,
     int64_t nb_cap, DevScalars *sc) {
-    __shared__ float4 s_pos[kS2Warps][32];
-    __shared__ float2 s_t[kS2Warps][32];   // (s h_b)^2 (1 - 2^-10), h_b
+    // per warp: 32 candidates (FP32 position + threshold) and (s h_b)^2 (1 - 2^-10), h_b
+    extern __shared__ float4 s2_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *s_posw = s2_smem + warp * 32;
+    float2 *s_tw = reinterpret_cast<float2 *>(s2_smem + (blockDim.x >> 5) * 32) + warp * 32;
     int64_t g = 0;
     if (lane == 0) g = atomicAdd(ticket, 1u);
     g = __shfl_sync(0xffffffffu, g, 0);
@@ -298,23 +300,23 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_stage2(
                     P = make_float4(px, py, pz, (s32 * hb) * (s32 * hb) * kBandHi);
                 }
             }
-            s_pos[warp][lane] = P;
-            s_t[warp][lane] = make_float2((s32 * hb) * (s32 * hb) * kBandLo, hb);
+            s_posw[lane] = P;
+            s_tw[lane] = make_float2((s32 * hb) * (s32 * hb) * kBandLo, hb);
             __syncwarp();
             uint32_t hi = 0, lo = 0;
             if (compact) {
 #pragma unroll
                 for (int jj = 0; jj < 32; jj++) {
-                    const float4 B = s_pos[warp][jj];
+                    const float4 B = s_posw[jj];
                     const float r2 = sep2(B, true, ax, ay, az, ca);
                     if (r2 <= fmaxf(tAhi, B.w)) hi |= 1u << jj;
-                    if (r2 < fmaxf(tAlo, s_t[warp][jj].x)) lo |= 1u << jj;
+                    if (r2 < fmaxf(tAlo, s_tw[jj].x)) lo |= 1u << jj;
                 }
             } else {
                 const int m = (rg.y - base) < 32 ? (int)(rg.y - base) : 32;
                 for (int jj = 0; jj < m; jj++) {
-                    const float r2 = sep2(s_pos[warp][jj], false, ax, ay, az, ca);
-                    const float hm = fmaxf(hA, s_t[warp][jj].y);
+                    const float r2 = sep2(s_posw[jj], false, ax, ay, az, ca);
+                    const float hm = fmaxf(hA, s_tw[jj].y);
                     const float t = (s32 * hm) * (s32 * hm);
                     if (r2 <= t * kBandHi) hi |= 1u << jj;
                     if (r2 < t * kBandLo) lo |= 1u << jj;
@@ -452,7 +454,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
     // stage 1, growing the candidate capacity while a list overflows
     for (int attempt = 0;; attempt++) {
         SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
-        k_walk<<<grid_for(G, 128), 128, 0, c->stream>>>(gr, G, L, c->gboxf, c->nodesf, c->child, c->leaf_first,
+        k_walk<<<grid_for(G, c->launch.walk_block), c->launch.walk_block, 0, c->stream>>>(gr, G, L, c->gboxf, c->nodesf, c->child, c->leaf_first,
                                                         c->box_root, (float)sc, geo, c->cand, c->cand_cnt,
                                                         c->cand_cap, c->grp_chunks, &c->dscal->flags);
         SPH_LAUNCH_CHECK(c, "k_walk");
@@ -482,7 +484,9 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
     if (r) return r;
 
     // stage 2 in one pass; if the cache turns out too small it grows and the pass runs again
-    const unsigned blocks = grid_for(G, kS2Warps);
+    const int s2w = c->launch.stage2_warps;
+    const unsigned blocks = grid_for(G, s2w);
+    const size_t s2_smem = (size_t)s2w * 32 * (sizeof(float4) + sizeof(float2));
     const float qbox = (float)(0.25 * fmin(fmin(geo.L[0], geo.L[1]), geo.L[2]));
     int64_t total = 0;
     for (int attempt = 0;; attempt++) {
@@ -490,7 +494,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
         SPH_CUDA(c, cudaMemsetAsync(&c->dscal->s2_ticket, 0, sizeof(uint32_t), c->stream));
         SPH_CUDA(c, cudaMemsetAsync(c->grp_slots, 0, (size_t)G * sizeof(int64_t), c->stream));
-        k_stage2<<<blocks, kS2Warps * 32, 0, c->stream>>>(
+        k_stage2<<<blocks, s2w * 32, s2_smem, c->stream>>>(
             gr, c->box_root, G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->gboxf, c->nodes, c->rel, c->h32, s->x, s->y,
             s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->nb_ptr, (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket,
             c->grp_off, c->nb_ids, c->nb_cap, c->dscal);

@@ -236,6 +236,7 @@ struct sph_ctx {
     sph::DevScalars *hscal = nullptr;  // pinned host mirror
     double dt_next = -1.0;
     sph_stats stats{};
+    sph_launch launch{128, 128, 128, 4, 3};  // launch shapes (sph_set_launch / sph_autotune)
     int64_t launches = 0;              // kernels launched by this context
     bool timing = false;               // per-stage CUDA-event timing (sph_set_timing)
     cudaEvent_t ev[2] = {nullptr, nullptr};

@@ -60,6 +60,11 @@ class sph_stats(ctypes.Structure):
                 ("density_iters_max", _i), ("outer_passes", _i), ("n_red", _i), ("dt_next", _d), ("dv_ratio", _d),
                 ("kernel_launches", _i64), ("density_pair_evals", _i64), ("density_inrange", _i64), ("force_pairs", _i64), ("stage_ms", _d * 8)]
 
+class sph_launch(ctypes.Structure):
+    _fields_ = [("density_block", _i), ("forces_block", _i), ("walk_block", _i), ("stage2_warps", _i),
+                ("reduction_level", _i)]
+
+
 STAGES = ("predict", "tree", "neighbours", "density", "force_prep", "forces", "correct")
 
 
@@ -101,6 +106,9 @@ def load():
         "sph_get_stats": (_i, [_p, P(sph_stats)]),
         "sph_set_timing": (_i, [_p, _i]),
         "sph_reset_timing": (_i, [_p]),
+        "sph_get_launch": (_i, [_p, P(sph_launch)]),
+        "sph_set_launch": (_i, [_p, P(sph_launch)]),
+        "sph_autotune": (_i, [_p, P(sph_state), P(sph_launch), P(_d)]),
         "sph_sort_morton_noalloc": (_i, [_i64, _p, _p, _p, P(_d * 3), P(_d * 3), _p, _p, _p]),
         "sph_last_error": (ctypes.c_char_p, [_p]),
         "sph_error_string": (ctypes.c_char_p, [_i]),
@@ -244,6 +252,23 @@ def sph_export_tree(ctx) -> dict:
     return out
 
 
+def sph_get_launch(ctx) -> dict:
+    l = sph_launch()
+    _check(ctx, load().sph_get_launch(ctx, ctypes.byref(l)))
+    return {f: getattr(l, f) for f, _ in sph_launch._fields_}
+
+
+def sph_set_launch(ctx, **shape):
+    l = sph_launch(**{**sph_get_launch(ctx), **shape})
+    _check(ctx, load().sph_set_launch(ctx, ctypes.byref(l)))
+
+
+def sph_autotune(ctx, st: sph_state) -> tuple:
+    l, ms = sph_launch(), _d()
+    _check(ctx, load().sph_autotune(ctx, ctypes.byref(st), ctypes.byref(l), ctypes.byref(ms)))
+    return {f: getattr(l, f) for f, _ in sph_launch._fields_}, ms.value
+
+
 def sph_export_neighbours(ctx, n: int, n_pairs: int):
     off = np.zeros(n + 1, np.int64)
     ids = np.zeros(max(n_pairs, 1), np.uint32)
@@ -363,6 +388,16 @@ class Solver:
 
     def stats(self) -> dict:
         return sph_get_stats(self.ctx)
+
+    def launch(self) -> dict:
+        return sph_get_launch(self.ctx)
+
+    def set_launch(self, **shape):
+        sph_set_launch(self.ctx, **shape)
+
+    def autotune(self, s: DeviceState) -> tuple:
+        """Pick the fastest launch shapes / reduction level on state s (see sph_autotune)."""
+        return sph_autotune(self.ctx, s.c())
 
     def set_timing(self, on: bool):
         sph_set_timing(self.ctx, on)
