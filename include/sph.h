@@ -45,12 +45,16 @@ typedef enum {
     SPH_ERR_NONFINITE = -9        /* a NaN/Inf appeared in positions or smoothing lengths */
 } sph_status;
 
-enum { SPH_KERNEL_M4 = 0 };
+/* Smoothing kernels of Sect. 2.1: Schoenberg B-splines M4 (R_kern = 2), M5 (2.5), M6 (3) and the
+ * Wendland functions C2, C4, C6 (R_kern = 2), W(r, h) = C_norm f(r/h) / h^3 normalised in 3-D. */
+enum { SPH_KERNEL_M4 = 0, SPH_KERNEL_M5 = 1, SPH_KERNEL_M6 = 2, SPH_KERNEL_C2 = 3, SPH_KERNEL_C4 = 4,
+       SPH_KERNEL_C6 = 5 };
 enum { SPH_FP64 = 0, SPH_MIXED = 1 };
 
 /* Solver parameters (Sect. 2.1, App. F, App. G).  sph_default_params fills the paper's values. */
 typedef struct {
-    int kernel;           /* SPH_KERNEL_M4 (cubic spline, R_kern = 2) */
+    int kernel;           /* SPH_KERNEL_*; M4 by default (the paper's tests use M4 with hfact 1.2
+                             and M6 with hfact 1.0) */
     int precision;        /* SPH_FP64: all pair arithmetic in FP64.  SPH_MIXED: FP64 positions, h
                              iteration and integration; FP32 pair sums on cell-relative offsets with
                              Kahan-compensated accumulation */

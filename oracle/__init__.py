@@ -73,6 +73,7 @@ class Params:
     hi: tuple = (1.0, 1.0, 1.0)
     periodic: int = 1
     h_max_iter: int = 200
+    kernel: int = 0          # 0 M4, 1 M5, 2 M6, 3 Wendland C2, 4 C4, 5 C6 (Sect. 2.1)
 
     def c(self) -> OrcParams:
         return OrcParams(self.hfact, self.gamma, self.alpha_av, self.beta_av, self.alpha_u, self.c_cour,
@@ -93,6 +94,11 @@ def _setup(lib):
         "orc_compact": (_i64, [_i64, _p, _p, _p, _p]),
         "orc_radix_tree": (None, [_i64, _p, _i32, _p, _p, _p, _p, _p]),
         "orc_cell_boxes": (None, [_i64, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
+        "orc_set_kernel": (None, [_i32]),
+        "orc_kernel_R": (_d, [_i32]),
+        "orc_kernel_C": (_d, [_i32]),
+        "orc_kernel_f": (_d, [_i32, _d]),
+        "orc_kernel_df": (_d, [_i32, _d]),
         "orc_m4_f": (_d, [_d]),
         "orc_m4_df": (_d, [_d]),
         "orc_W": (_d, [_d, _d]),
@@ -232,15 +238,42 @@ def m4_df(q):
     return _load().orc_m4_df(float(q))
 
 
-def W(r, h):
+KERNELS = {"M4": 0, "M5": 1, "M6": 2, "C2": 3, "C4": 4, "C6": 5}
+
+
+def _kernel(kind):
+    """Select the smoothing kernel every oracle function uses (a module setting of the C oracle)."""
+    _load().orc_set_kernel(int(kind))
+
+
+def kernel_f(kind, q):
+    return _load().orc_kernel_f(int(kind), float(q))
+
+
+def kernel_df(kind, q):
+    return _load().orc_kernel_df(int(kind), float(q))
+
+
+def kernel_R(kind):
+    return _load().orc_kernel_R(int(kind))
+
+
+def kernel_C(kind):
+    return _load().orc_kernel_C(int(kind))
+
+
+def W(r, h, kernel=0):
+    _kernel(kernel)
     return _load().orc_W(float(r), float(h))
 
 
-def dWdh(r, h):
+def dWdh(r, h, kernel=0):
+    _kernel(kernel)
     return _load().orc_dWdh(float(r), float(h))
 
 
-def F(r, h):
+def F(r, h, kernel=0):
+    _kernel(kernel)
     return _load().orc_F(float(r), float(h))
 
 
@@ -263,8 +296,9 @@ def neighbours(x, y, z, hc, s, lo=(0, 0, 0), hi=(1, 1, 1), periodic=1, method=No
 
 
 # ---- Density / smoothing length (App. F) ----
-def density_root(x, y, z, hfact, h_hi, lo=(0, 0, 0), hi=(1, 1, 1), periodic=1, method=None):
+def density_root(x, y, z, hfact, h_hi, lo=(0, 0, 0), hi=(1, 1, 1), periodic=1, method=None, kernel=0):
     """Unique root h_a of sum_b m W(r_ab,h_a) = m (hfact/h_a)^3 by bisection (equal masses)."""
+    _kernel(kernel)
     x, y, z = _f64(x), _f64(y), _f64(z)
     lo, hi = _box(lo, hi)
     n = len(x)
@@ -280,6 +314,7 @@ def density_root(x, y, z, hfact, h_hi, lo=(0, 0, 0), hi=(1, 1, 1), periodic=1, m
 
 def density_algF(x, y, z, h, mass, params: Params, method=None):
     """App. F iteration.  Returns (h, rho, omega, inner_iterations, outer_passes)."""
+    _kernel(params.kernel)
     x, y, z = _f64(x), _f64(y), _f64(z)
     h = _f64(h).copy()
     n = len(x)
@@ -296,8 +331,9 @@ def density_algF(x, y, z, h, mass, params: Params, method=None):
     return h, rho, om, it, outer.value
 
 
-def density_at(x, y, z, h, mass, hfact, lo=(0, 0, 0), hi=(1, 1, 1), periodic=1, method=None):
+def density_at(x, y, z, h, mass, hfact, lo=(0, 0, 0), hi=(1, 1, 1), periodic=1, method=None, kernel=0):
     """(rho_sum, Omega) at fixed h."""
+    _kernel(kernel)
     x, y, z, h = _f64(x), _f64(y), _f64(z), _f64(h)
     lo, hi = _box(lo, hi)
     n = len(x)
@@ -313,6 +349,7 @@ def density_at(x, y, z, h, mass, hfact, lo=(0, 0, 0), hi=(1, 1, 1), periodic=1, 
 # ---- Forces, CFL, step (Sect. 2.1, App. G) ----
 def forces(x, y, z, vx, vy, vz, u, h, omega, mass, params: Params, method=None):
     """Returns (ax, ay, az, du, vsig)."""
+    _kernel(params.kernel)
     arrs = [_f64(a) for a in (x, y, z, vx, vy, vz, u, h, omega)]
     n = len(arrs[0])
     if method is None:
@@ -325,6 +362,7 @@ def forces(x, y, z, vx, vy, vz, u, h, omega, mass, params: Params, method=None):
 
 
 def cfl(h, vsig, ax, ay, az, params: Params):
+    _kernel(params.kernel)
     arrs = [_f64(a) for a in (h, vsig, ax, ay, az)]
     p = params.c()
     return _load().orc_cfl(len(arrs[0]), ctypes.byref(p), *[_ptr(a) for a in arrs])
@@ -336,6 +374,7 @@ _STATE_KEYS = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du"
 def step(state: dict, mass, params: Params, dt, method=None):
     """One KDK step on a dict of float64 arrays (keys x..vsig), in place.  Returns
     (dt_next, inner_iterations, dv_ratio)."""
+    _kernel(params.kernel)
     for k in _STATE_KEYS:
         state[k] = _f64(state[k])
     n = len(state["x"])
@@ -355,6 +394,7 @@ def step(state: dict, mass, params: Params, dt, method=None):
 def subset_forces(x, y, z, vx, vy, vz, u, mass, params: Params, idx, h_hi):
     """Root h, Omega and (ax, ay, az, du, vsig) of the particles idx, by brute force over all n.
     Returns a dict of arrays aligned with idx."""
+    _kernel(params.kernel)
     arrs = [_f64(a) for a in (x, y, z, vx, vy, vz, u)]
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     m = len(idx)

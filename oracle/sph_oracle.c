@@ -240,17 +240,121 @@ double orc_m4_df(double q) /* df/dq */
     return 0.0;
 }
 
-double orc_W(double r, double h) { return orc_m4_f(r / h) / (ORC_PI * h * h * h); }
+/* ====================================================================================== */
+/* The other kernels of Sect. 2.1 ("B-splines like M4, M5, M6, or Wendland functions like C2, */
+/* C4, C6"), each as its textbook piecewise definition on q = r/h with its support R_kern and  */
+/* its 3-D normalisation C_norm (4 pi C_norm int_0^R f q^2 dq = 1):                            */
+/*   M5 (R 5/2, C 1/(20 pi)):  (5/2-q)^4 - 5 (3/2-q)^4 + 10 (1/2-q)^4 on [0,1/2), dropping the  */
+/*      last and then the middle term on [1/2,3/2) and [3/2,5/2)                               */
+/*   M6 (R 3, C 1/(120 pi)):  (3-q)^5 - 6 (2-q)^5 + 15 (1-q)^5 on [0,1), likewise              */
+/*   Wendland (R 2):  C2 = (1-q/2)^4 (1+2q), C 21/(16 pi);  C4 = (1-q/2)^6 (1+3q+35/12 q^2),    */
+/*      C 495/(256 pi);  C6 = (1-q/2)^8 (1+4q+25/4 q^2+4q^3), C 1365/(512 pi)                   */
+/* The kernel in use is a module setting (orc_set_kernel; 0 = M4, 1 = M5, 2 = M6, 3 = C2,       */
+/* 4 = C4, 5 = C6), read by every function below.                                              */
+/* ====================================================================================== */
+static int orc_kind = 0;
+
+void orc_set_kernel(int kind) { orc_kind = kind; }
+
+double orc_kernel_R(int kind)
+{
+    if (kind == 1) return 2.5;
+    if (kind == 2) return 3.0;
+    return 2.0;
+}
+
+double orc_kernel_C(int kind)
+{
+    switch (kind) {
+    case 1: return 1.0 / (20.0 * ORC_PI);
+    case 2: return 1.0 / (120.0 * ORC_PI);
+    case 3: return 21.0 / (16.0 * ORC_PI);
+    case 4: return 495.0 / (256.0 * ORC_PI);
+    case 5: return 1365.0 / (512.0 * ORC_PI);
+    default: return 1.0 / ORC_PI;
+    }
+}
+
+static double p4(double v) { return v * v * v * v; }
+static double p5(double v) { return v * v * v * v * v; }
+
+double orc_kernel_f(int kind, double q)
+{
+    double w = 1.0 - 0.5 * q;
+    switch (kind) {
+    case 1:
+        if (q < 0.5) return p4(2.5 - q) - 5.0 * p4(1.5 - q) + 10.0 * p4(0.5 - q);
+        if (q < 1.5) return p4(2.5 - q) - 5.0 * p4(1.5 - q);
+        if (q < 2.5) return p4(2.5 - q);
+        return 0.0;
+    case 2:
+        if (q < 1.0) return p5(3.0 - q) - 6.0 * p5(2.0 - q) + 15.0 * p5(1.0 - q);
+        if (q < 2.0) return p5(3.0 - q) - 6.0 * p5(2.0 - q);
+        if (q < 3.0) return p5(3.0 - q);
+        return 0.0;
+    case 3:
+        if (q < 2.0) return pow(w, 4.0) * (1.0 + 2.0 * q);
+        return 0.0;
+    case 4:
+        if (q < 2.0) return pow(w, 6.0) * (1.0 + 3.0 * q + 35.0 / 12.0 * q * q);
+        return 0.0;
+    case 5:
+        if (q < 2.0) return pow(w, 8.0) * (1.0 + 4.0 * q + 25.0 / 4.0 * q * q + 4.0 * q * q * q);
+        return 0.0;
+    default:
+        return orc_m4_f(q);
+    }
+}
+
+/* df/dq, differentiated term by term (chain and product rules as written, not simplified). */
+double orc_kernel_df(int kind, double q)
+{
+    double w = 1.0 - 0.5 * q;
+    switch (kind) {
+    case 1: {
+        double d = 0.0;
+        if (q < 2.5) d += -4.0 * pow(2.5 - q, 3.0);
+        if (q < 1.5) d += 20.0 * pow(1.5 - q, 3.0);
+        if (q < 0.5) d += -40.0 * pow(0.5 - q, 3.0);
+        return d;
+    }
+    case 2: {
+        double d = 0.0;
+        if (q < 3.0) d += -5.0 * p4(3.0 - q);
+        if (q < 2.0) d += 30.0 * p4(2.0 - q);
+        if (q < 1.0) d += -75.0 * p4(1.0 - q);
+        return d;
+    }
+    case 3:
+        if (q < 2.0) return 4.0 * pow(w, 3.0) * (-0.5) * (1.0 + 2.0 * q) + pow(w, 4.0) * 2.0;
+        return 0.0;
+    case 4:
+        if (q < 2.0)
+            return 6.0 * pow(w, 5.0) * (-0.5) * (1.0 + 3.0 * q + 35.0 / 12.0 * q * q) +
+                   pow(w, 6.0) * (3.0 + 35.0 / 6.0 * q);
+        return 0.0;
+    case 5:
+        if (q < 2.0)
+            return 8.0 * pow(w, 7.0) * (-0.5) * (1.0 + 4.0 * q + 25.0 / 4.0 * q * q + 4.0 * q * q * q) +
+                   pow(w, 8.0) * (4.0 + 25.0 / 2.0 * q + 12.0 * q * q);
+        return 0.0;
+    default:
+        return orc_m4_df(q);
+    }
+}
+
+double orc_W(double r, double h) { return orc_kernel_C(orc_kind) * orc_kernel_f(orc_kind, r / h) / (h * h * h); }
 
 /* dW/dh at fixed r. */
 double orc_dWdh(double r, double h)
 {
     double q = r / h;
-    return -(3.0 * orc_m4_f(q) + q * orc_m4_df(q)) / (ORC_PI * h * h * h * h);
+    return -orc_kernel_C(orc_kind) * (3.0 * orc_kernel_f(orc_kind, q) + q * orc_kernel_df(orc_kind, q)) /
+           (h * h * h * h);
 }
 
 /* F_ab(h) = rhat . grad_a W_ab(h) = dW/dr (Sect. 2.1 definition of F_ab). */
-double orc_F(double r, double h) { return orc_m4_df(r / h) / (ORC_PI * h * h * h * h); }
+double orc_F(double r, double h) { return orc_kernel_C(orc_kind) * orc_kernel_df(orc_kind, r / h) / (h * h * h * h); }
 
 /* ====================================================================================== */
 /* Neighbour sets (App. D criteria, App. C neighbour caches).                                */
@@ -466,7 +570,7 @@ static void orc_rho_sums(int64_t a, double h, double mass, const orc_nlist *nl,
         int64_t b = nl->ids[k];
         double d[3];
         double r = orc_dist(x, y, z, a, b, boxL, periodic, d);
-        if (r < 2.0 * h) {
+        if (r < orc_kernel_R(orc_kind) * h) {
             s0 += mass * orc_W(r, h);
             s1 += mass * orc_dWdh(r, h);
         }
@@ -485,11 +589,12 @@ static void orc_rho_sums(int64_t a, double h, double mass, const orc_nlist *nl,
 static double orc_phi(int64_t a, double h, const orc_nlist *nl, const double *x, const double *y,
                       const double *z, const double *boxL, int periodic, double hfact)
 {
-    double s = orc_m4_f(0.0) / ORC_PI;
+    double C = orc_kernel_C(orc_kind);
+    double s = C * orc_kernel_f(orc_kind, 0.0);
     for (int64_t k = nl->off[a]; k < nl->off[a + 1]; k++) {
         double d[3];
         double r = orc_dist(x, y, z, a, nl->ids[k], boxL, periodic, d);
-        s += orc_m4_f(r / h) / ORC_PI;
+        s += C * orc_kernel_f(orc_kind, r / h);
     }
     return s - hfact * hfact * hfact;
 }
@@ -504,8 +609,9 @@ int64_t orc_density_root(int64_t n, const double *x, const double *y, const doub
     double *hc = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
     for (int64_t i = 0; i < n; i++) hc[i] = h_hi;
     orc_nlist nl;
-    if (method == 0) orc_nlist_brute(n, x, y, z, hc, 2.0, boxL, periodic, &nl);
-    else orc_nlist_grid(n, x, y, z, hc, 2.0, lo, boxL, periodic, &nl);
+    double R = orc_kernel_R(orc_kind);
+    if (method == 0) orc_nlist_brute(n, x, y, z, hc, R, boxL, periodic, &nl);
+    else orc_nlist_grid(n, x, y, z, hc, R, lo, boxL, periodic, &nl);
     int64_t bad = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad)
     for (int64_t a = 0; a < n; a++) {
@@ -555,8 +661,9 @@ int orc_density_algF(int64_t n, double mass, const orc_params *p, const double *
         outer++;
         for (int64_t a = 0; a < n; a++) hn[a] = h[a];
         orc_nlist nl;
-        if (method == 0) orc_nlist_brute(n, x, y, z, hn, 2.0 * p->cache_tol, boxL, p->periodic, &nl);
-        else orc_nlist_grid(n, x, y, z, hn, 2.0 * p->cache_tol, p->lo, boxL, p->periodic, &nl);
+        double s = orc_kernel_R(orc_kind) * p->cache_tol;
+        if (method == 0) orc_nlist_brute(n, x, y, z, hn, s, boxL, p->periodic, &nl);
+        else orc_nlist_grid(n, x, y, z, hn, s, p->lo, boxL, p->periodic, &nl);
         double maxeps = INFINITY;
         while (maxeps > p->h_tol) {
             if (total >= p->h_max_iter) { failed = 1; break; }
@@ -615,8 +722,9 @@ void orc_density_at(int64_t n, double mass, double hfact, const double *x, const
 {
     double boxL[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
     orc_nlist nl;
-    if (method == 0) orc_nlist_brute(n, x, y, z, h, 2.0, boxL, periodic, &nl);
-    else orc_nlist_grid(n, x, y, z, h, 2.0, lo, boxL, periodic, &nl);
+    double R = orc_kernel_R(orc_kind);
+    if (method == 0) orc_nlist_brute(n, x, y, z, h, R, boxL, periodic, &nl);
+    else orc_nlist_grid(n, x, y, z, h, R, lo, boxL, periodic, &nl);
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t a = 0; a < n; a++) {
         double rs, ds;
@@ -658,8 +766,9 @@ void orc_forces(int64_t n, double mass, const orc_params *p, const double *x, co
         cs[a] = sqrt(p->gamma * P[a] / rho[a]);
     }
     orc_nlist nl;
-    if (method == 0) orc_nlist_brute(n, x, y, z, h, 2.0, boxL, p->periodic, &nl);
-    else orc_nlist_grid(n, x, y, z, h, 2.0, p->lo, boxL, p->periodic, &nl);
+    double R = orc_kernel_R(orc_kind);
+    if (method == 0) orc_nlist_brute(n, x, y, z, h, R, boxL, p->periodic, &nl);
+    else orc_nlist_grid(n, x, y, z, h, R, p->lo, boxL, p->periodic, &nl);
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t a = 0; a < n; a++) {
         double acc[3] = {0.0, 0.0, 0.0}, dua = 0.0;
@@ -856,7 +965,8 @@ int64_t orc_subset_forces(int64_t n, double mass, const orc_params *p, const dou
     for (int64_t s = 0; s < m; s++) {
         int64_t a = idx[s];
         int64_t *cand;
-        int64_t nc = orc_candidates(n, x, y, z, a, 2.0 * h_hi, boxL, p->periodic, &cand);
+        double R = orc_kernel_R(orc_kind);
+        int64_t nc = orc_candidates(n, x, y, z, a, R * h_hi, boxL, p->periodic, &cand);
         double ha, oma;
         orc_one_root(a, cand, nc, x, y, z, mass, p->hfact, h_hi, boxL, p->periodic, &ha, &oma);
         double rho_a = mass * pow(p->hfact / ha, 3.0);
@@ -867,7 +977,7 @@ int64_t orc_subset_forces(int64_t n, double mass, const orc_params *p, const dou
         for (int64_t k = 0; k < nc; k++) {
             int64_t b = cand[k];
             int64_t *cb;
-            int64_t nb = orc_candidates(n, x, y, z, b, 2.0 * h_hi, boxL, p->periodic, &cb);
+            int64_t nb = orc_candidates(n, x, y, z, b, R * h_hi, boxL, p->periodic, &cb);
             double hb, omb;
             orc_one_root(b, cb, nb, x, y, z, mass, p->hfact, h_hi, boxL, p->periodic, &hb, &omb);
             free(cb);
@@ -875,7 +985,7 @@ int64_t orc_subset_forces(int64_t n, double mass, const orc_params *p, const dou
             double d[3];
             double r = orc_dist(x, y, z, a, b, boxL, p->periodic, d);
             double hm = ha > hb ? ha : hb;
-            if (!(r < 2.0 * hm)) continue;
+            if (!(r < R * hm)) continue;
             double rho_b = mass * pow(p->hfact / hb, 3.0);
             double P_b = (p->gamma - 1.0) * rho_b * u[b];
             double c_b = sqrt(p->gamma * P_b / rho_b);

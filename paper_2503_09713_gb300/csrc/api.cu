@@ -163,7 +163,7 @@ void free_all(sph_ctx *c) {
 
 int check_params(sph_ctx *c, const sph_params *p) {
     if (!p) return fail(c, SPH_ERR_INVALID_ARG, "params is NULL");
-    if (p->kernel != SPH_KERNEL_M4) return fail(c, SPH_ERR_INVALID_ARG, "only the M4 kernel is built");
+    if (p->kernel < SPH_KERNEL_M4 || p->kernel > SPH_KERNEL_C6) return fail(c, SPH_ERR_INVALID_ARG, "unknown kernel");
     if (p->precision != SPH_FP64 && p->precision != SPH_MIXED)
         return fail(c, SPH_ERR_INVALID_ARG, "precision must be SPH_FP64 or SPH_MIXED");
     if (!(p->hfact > 0) || !(p->gamma > 1) || !(p->h_tol > 0) || !(p->h_clamp > 1) || !(p->cache_tol >= 1) ||

@@ -24,10 +24,11 @@ struct DensParams {
     const uint16_t *box_of;   // box of each particle (batch) or nullptr
 };
 
-// Sums over the neighbours of a at smoothing length h:  sf = sum f(q),  sg = sum (3 f + q f'),
-// sk = sum (12 f + 8 q f' + q^2 f'')  (self term included: 1, 3 and 12), so that
-//   rho_sum = m sf / (pi h^3),  sum m dW/dh = -m sg / (pi h^4),  sum m d2W/dh2 = m sk / (pi h^5).
-template <bool kMixed>
+// Sums over the neighbours of a at smoothing length h (kernel K):  sf = sum f(q),
+// sg = sum (3 f + q f'),  sk = sum (12 f + 8 q f' + q^2 f'')  (self term included: f(0) times 1, 3
+// and 12), so that rho_sum = m C sf / h^3,  sum m dW/dh = -m C sg / h^4,
+// sum m d2W/dh2 = m C sk / h^5.
+template <typename K, bool kMixed>
 __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt, const uint32_t *__restrict__ ids,
                                              uint32_t st,
                                              const double *__restrict__ x, const double *__restrict__ y,
@@ -37,12 +38,12 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
     const double hinv = 1.0 / ha;
     if (!kMixed) {
         // FP32 pre-test on the cell-relative offsets skips the candidates that are clearly outside
-        // 2h; the others are evaluated in FP64 with the image shift taken from the cell indices.
+        // R h; the others are evaluated in FP64 with the image shift taken from the cell indices.
         const double xa = x[a], ya = y[a], za = z[a];
         const double hinv2 = hinv * hinv;
         const float4 A = rel[a];
-        const float lim = 4.f * kPreBand / ((float)hinv2);
-        double f0 = 1.0, g0 = 3.0, k0 = 12.0;
+        const float lim = (float)(K::R * K::R) * kPreBand / ((float)hinv2);
+        double f0 = K::F0, g0 = 3.0 * K::F0, k0 = 12.0 * K::F0;
         for (uint32_t k = 0; k < cnt; k++) {
             const uint32_t b = ids[k * st];
             float fx, fy, fz;
@@ -53,15 +54,15 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
             const double dy = image_diff(ya, y[b], sy, geo.L[1]);
             const double dz = image_diff(za, z[b], sz, geo.L[2]);
             const double q2 = (dx * dx + dy * dy + dz * dz) * hinv2;
-            if (nonneg_lt(q2, 4.0)) {
+            if (nonneg_lt(q2, K::R * K::R)) {
                 ++nin;
                 const double q = sqrt(q2);
                 double f, df;
-                m4d(q, f, df);
+                K::eval(q, f, df);
                 const double qdf = q * df;
                 f0 += f;
                 g0 += 3.0 * f + qdf;
-                k0 += 12.0 * f + 8.0 * qdf + q2 * m4d_d2(q);
+                k0 += 12.0 * f + 8.0 * qdf + q2 * K::d2(q);
             }
         }
         sf = f0;
@@ -72,20 +73,21 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         const float4 A = rel[a];
         const float hi = (float)hinv;
         const float hi2 = hi * hi;
-        float s0 = 1.f, c0 = 0.f, s1 = 3.f, c1 = 0.f, s2 = 12.f;
+        constexpr float R2 = (float)(K::R * K::R);
+        float s0 = (float)K::F0, c0 = 0.f, s1 = (float)(3.0 * K::F0), c1 = 0.f, s2 = (float)(12.0 * K::F0);
         auto acc = [&](const float4 B) {
             float dx, dy, dz;
             rel_sep(A, B, geo, dx, dy, dz);
             const float q2 = (dx * dx + dy * dy + dz * dz) * hi2;
-            if (q2 < 4.f) {
+            if (q2 < R2) {
                 ++nin;
                 const float q = sqrtf(q2);
                 float f, df;
-                m4(q, f, df);
+                K::eval(q, f, df);
                 const float qdf = q * df;
                 kahan_add(s0, c0, f);
                 kahan_add(s1, c1, 3.f * f + qdf);
-                s2 += 12.f * f + 8.f * qdf + q2 * m4_d2(q);   // only scales a step of order eps_c
+                s2 += 12.f * f + 8.f * qdf + q2 * K::d2(q);   // only scales a step of order eps_c
             }
         };
         // software pipeline: the indices of the next four neighbours are loaded while the current
@@ -119,7 +121,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
     }
 }
 
-template <bool kMixed>
+template <typename K, bool kMixed>
 __global__ void __launch_bounds__(256, kMixed ? 3 : 1) k_density(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                                                  const double *__restrict__ z, const float4 *__restrict__ rel,
                                                  double *__restrict__ h, const double *__restrict__ h_base,
@@ -144,11 +146,11 @@ __global__ void __launch_bounds__(256, kMixed ? 3 : 1) k_density(int64_t n, cons
     while (it < dp.max_iter) {
         ++it;
         double sf, sg, sk;
-        density_sums<kMixed>(a, ha, cnt, ids, st, x, y, z, rel, dp.geo, sf, sg, sk, nin);
+        density_sums<K, kMixed>(a, ha, cnt, ids, st, x, y, z, rel, dp.geo, sf, sg, sk, nin);
         const double hinv = 1.0 / ha;
         const double hinv3 = hinv * hinv * hinv;
-        const double rho_sum = m * sf * hinv3 * kInvPi;
-        const double dsum = -m * sg * hinv3 * hinv * kInvPi;   // sum_b m dW/dh
+        const double rho_sum = m * sf * hinv3 * K::C;
+        const double dsum = -m * sg * hinv3 * hinv * K::C;   // sum_b m dW/dh
         const double rho_h = m * hf3 * hinv3;
         double hnew = ha - (rho_sum - rho_h) / (dsum + 3.0 * rho_h * hinv);
         if (hnew > ha * dp.h_clamp) hnew = ha * dp.h_clamp;
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(256, kMixed ? 3 : 1) k_density(int64_t n, cons
         }
         // sum m dW/dh at the new h, to first order in the step (|dh| <= eps_c h^n at convergence,
         // so the neglected term is O(eps_c^2))
-        dsum_new = dsum + m * sk * hinv3 * hinv * hinv * kInvPi * (hnew - ha);
+        dsum_new = dsum + m * sk * hinv3 * hinv * hinv * K::C * (hnew - ha);
         ha = hnew;
         if (stale) break;
         if (eps <= dp.h_tol) {
@@ -207,14 +209,18 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->max_iters, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->pair_evals, 0, 2 * sizeof(unsigned long long), c->stream));
-    if (c->p.precision == SPH_MIXED)
-        k_density<true><<<grid_for(n, blk), blk, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
-                                                                 c->nb_cnt, c->nb_ptr, c->nb_ids, dp,
-                                                                 s->rho, s->omega, c->dscal);
-    else
-        k_density<false><<<grid_for(n, blk), blk, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
-                                                                  c->nb_cnt, c->nb_ptr, c->nb_ids, dp,
-                                                                  s->rho, s->omega, c->dscal);
+    with_kernel(c->p.kernel, [&](auto kern) {
+        using K = decltype(kern);
+        if (c->p.precision == SPH_MIXED)
+            k_density<K, true><<<grid_for(n, blk), blk, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+                                                                        c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
+                                                                        s->omega, c->dscal);
+        else
+            k_density<K, false><<<grid_for(n, blk), blk, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+                                                                         c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
+                                                                         s->omega, c->dscal);
+        return 0;
+    });
     SPH_LAUNCH_CHECK(c, "k_density");
     static_assert(offsetof(DevScalars, flags) == offsetof(DevScalars, max_iters) + sizeof(uint32_t), "layout");
     SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->max_iters, &c->dscal->max_iters, 2 * sizeof(uint32_t),

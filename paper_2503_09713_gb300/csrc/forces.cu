@@ -6,7 +6,7 @@
 //            + sum_b m alpha_u v_sig^u (u_a - u_b) 1/2 [F_ab(h_a)/(Omega_a rho_a) + F_ab(h_b)/(Omega_b rho_b)]
 //   q^a_ab = -1/2 rho_a (alpha c_s,a + beta |v_ab.rhat|) (v_ab.rhat)  when v_ab.rhat < 0, else 0
 //   v_sig^dt_a = max_b (alpha c_s,a + beta max(0, -v_ab.rhat)),  alpha c_s,a without neighbours
-// over pairs with r_ab < 2 max(h_a, h_b).  Per-particle factors (P/(rho^2 Omega), 1/(rho Omega), c_s,
+// over pairs with r_ab < R_kern max(h_a, h_b).  Per-particle factors (P/(rho^2 Omega), 1/(rho Omega), c_s,
 // P, rho, 1/h) are computed once per particle by a preparation kernel.  The mixed path evaluates
 // each pair in FP32 from cell-relative offsets and accumulates with Kahan compensation.
 #include "physics.cuh"
@@ -15,6 +15,7 @@ namespace sph {
 
 struct ForceParams {
     double mass, gamma, alpha_av, beta_av, alpha_u, c_cour, c_force;
+    double kern_c;             // C_norm of the smoothing kernel
     PairGeo geo;
     const double *box_mass;    // per-box particle mass (batch) or nullptr
     const double *box_gamma;   // per-box adiabatic index (batch) or nullptr
@@ -23,7 +24,7 @@ struct ForceParams {
 };
 
 // Per-particle FP64 record of the force loop: 128 bytes, read as 8 double2.
-// pre = P/(rho^2 Omega), qf = 1/(rho Omega), fn = 1/(pi h^4), acs = alpha_AV c_s.
+// pre = P/(rho^2 Omega), qf = 1/(rho Omega), fn = C_norm/h^4, acs = alpha_AV c_s.
 struct __align__(16) FRec {
     double x, y, z, h;
     double vx, vy, vz, u;
@@ -50,7 +51,7 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
         m_v[i] = make_float4((float)vx[i], (float)vy[i], (float)vz[i], hinvf);
         m_t[i] = make_float4((g - 1.f) * ui * qf, qf, (float)fp.alpha_av * sqrtf(g * (g - 1.f) * ui),
                              (g - 1.f) * r * ui);
-        m_r[i] = make_float4(r, ui, hinvf * hinvf * hinvf * hinvf * kInvPiF, 0.f);
+        m_r[i] = make_float4(r, ui, hinvf * hinvf * hinvf * hinvf * (float)fp.kern_c, 0.f);
     } else {
         // the same quantities in FP64, with two divisions and one square root per particle
         const double r = rho[i], om = omega[i], ui = u[i], hi = h[i];
@@ -61,7 +62,7 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
         f.vx = vx[i]; f.vy = vy[i]; f.vz = vz[i]; f.u = ui;
         f.pre = (gam - 1.0) * ui * qf; f.qf = qf; f.acs = fp.alpha_av * sqrt(gam * (gam - 1.0) * ui);
         f.P = (gam - 1.0) * r * ui;
-        f.rho = r; f.hinv = hinv; f.fn = hinv * hinv * hinv * hinv * kInvPi; f.pad = 0.0;
+        f.rho = r; f.hinv = hinv; f.fn = hinv * hinv * hinv * hinv * fp.kern_c; f.pad = 0.0;
         rec[i] = f;
         h32[i] = (float)hi;
     }
@@ -124,6 +125,7 @@ __device__ __forceinline__ void dt_reduce(double t, unsigned long long npair, De
 // FP64 pair loop.  A candidate is first tested in FP32 on the cell-relative offsets against the
 // current h (kPreBand margin); the survivors are decided and evaluated in FP64 with the nearest
 // image from the cell indices.  The mass factor is applied once per particle.
+template <typename K>
 __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__restrict__ rec,
                                                      const float4 *__restrict__ rel, const float *__restrict__ h32,
                                                      const uint32_t *__restrict__ nb_cnt,
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
         int sx, sy, sz;
         rel_sep_shift(PA, rel[b], geo, fx, fy, fz, sx, sy, sz);
         const float hmf = fmaxf(hA, h32[b]);
-        if (fx * fx + fy * fy + fz * fz > 4.f * kPreBand * hmf * hmf) continue;
+        if (fx * fx + fy * fy + fz * fz > (float)(K::R * K::R) * kPreBand * hmf * hmf) continue;
         FRec B;
         load_rec(&rec[b], B);
         const double dx = image_diff(A.x, B.x, sx, geo.L[0]);
@@ -163,14 +165,14 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
         const double dz = image_diff(A.z, B.z, sz, geo.L[2]);
         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
         const double hm = nonneg_max(A.h, B.h);
-        const double rad = __dmul_rn(2.0, hm);
+        const double rad = __dmul_rn(K::R, hm);
         if (!nonneg_lt(r2, __dmul_rn(rad, rad))) continue;
         ++npair;
         const double rinv = rsqrt(r2);
         const double r = r2 * rinv;
         double f, dfa, dfb;
-        m4d(r * A.hinv, f, dfa);
-        m4d(r * B.hinv, f, dfb);
+        K::eval(r * A.hinv, f, dfa);
+        K::eval(r * B.hinv, f, dfb);
         const double Fa = dfa * A.fn;
         const double Fb = dfb * B.fn;
         const double vdotr = ((A.vx - B.vx) * dx + (A.vy - B.vy) * dy + (A.vz - B.vz) * dz) * rinv;
@@ -211,6 +213,7 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
     dt_reduce(tdt, npair, sc, fp.box_dt_next, box);
 }
 
+template <typename K>
 __global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *__restrict__ rel,
                                                       const float4 *__restrict__ m_v, const float4 *__restrict__ m_t,
                                                       const float4 *__restrict__ m_r, const double *__restrict__ h,
@@ -237,21 +240,24 @@ __global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *_
     float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f, su = 0.f, cu = 0.f, sdiv = 0.f;
     float vs = TA.z;   // alpha_AV c_s,a
     const float hia = VA.w;
-    const float Fa_n = RA.z;   // 1/(pi h_a^4)
+    const float Fa_n = RA.z;   // C_norm/h_a^4
     // one pair; B's position and velocity are already loaded
     auto pair = [&](uint32_t b, const float4 PB, const float4 VB) {
         float dx, dy, dz;
         rel_sep(PA, PB, fp.geo, dx, dy, dz);
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float him = fminf(hia, VB.w);
-        if (!(r2 * him * him < 4.f)) return;
+        if (!(r2 * him * him < (float)(K::R * K::R))) return;
         ++npair;
         const float4 TB = m_t[b];
         const float4 RB = m_r[b];
         const float rinv = rsqrtf(r2);
         const float r = r2 * rinv;
-        const float Fa = m4_df_sel(r * hia) * Fa_n;
-        const float Fb = m4_df_sel(r * VB.w) * RB.z;
+        float f_, dfa, dfb;
+        K::eval(r * hia, f_, dfa);
+        K::eval(r * VB.w, f_, dfb);
+        const float Fa = dfa * Fa_n;
+        const float Fb = dfb * RB.z;
         const float vdotr = fmaf(VA.z - VB.z, dz, fmaf(VA.y - VB.y, dy, (VA.x - VB.x) * dx)) * rinv;
         float Aa = TA.x, Ab = TB.x;
         if (vdotr < 0.f) {
@@ -326,6 +332,7 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     fp.alpha_u = c->p.alpha_u;
     fp.c_cour = c->p.c_cour;
     fp.c_force = c->p.c_force;
+    fp.kern_c = with_kernel(c->p.kernel, [](auto kern) { return decltype(kern)::C; });
     fp.geo = make_pair_geo(c->p);
     fp.box_mass = c->batch ? c->box_mass : nullptr;
     fp.box_gamma = c->batch ? c->box_gamma : nullptr;
@@ -344,13 +351,18 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     if ((r = stage_end(c, kStForcePrep)) || (r = stage_begin(c, kStForces))) return r;
     ForceOut out{ax, ay, az, du, s->vsig, c->dhdt};
     const int blk = c->launch.forces_block;
-    if (mixed)
-        k_forces_mixed<<<grid_for(n, blk), blk, 0, c->stream>>>(n, c->rel, c->m_v, c->m_t, c->m_r, s->h,
-                                                                c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out, c->dscal);
-    else
-        k_forces_fp64<<<grid_for(n, blk), blk, 0, c->stream>>>(n, (const FRec *)c->frec, c->rel, c->h32,
-                                                                    c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out,
-                                                                    c->dscal);
+    with_kernel(c->p.kernel, [&](auto kern) {
+        using K = decltype(kern);
+        if (mixed)
+            k_forces_mixed<K><<<grid_for(n, blk), blk, 0, c->stream>>>(n, c->rel, c->m_v, c->m_t, c->m_r, s->h,
+                                                                       c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out,
+                                                                       c->dscal);
+        else
+            k_forces_fp64<K><<<grid_for(n, blk), blk, 0, c->stream>>>(n, (const FRec *)c->frec, c->rel, c->h32,
+                                                                      c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out,
+                                                                      c->dscal);
+        return 0;
+    });
     SPH_LAUNCH_CHECK(c, "k_forces");
     return stage_end(c, kStForces);
 }

@@ -15,7 +15,7 @@
 // k < count_a.
 #include <cuda/atomic>
 
-#include "sph_internal.cuh"
+#include "physics.cuh"
 
 namespace sph {
 
@@ -443,7 +443,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
     const Groups gr = make_groups(c);
     const int64_t L = c->n_leaves;
     const Geo geo = make_geo(c->p);
-    const double sc = 2.0 * c->p.cache_tol;   // R_kern * chi
+    const double sc = kernel_radius(c->p.kernel) * c->p.cache_tol;   // R_kern * chi
     c->cache_valid = false;
 
     k_h32<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->h, c->h32, c->h_base);

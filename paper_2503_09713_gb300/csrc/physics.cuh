@@ -1,4 +1,4 @@
-// Device helpers of the SPH pair loops: M4 kernel (Sect. 2.1), geometry of the neighbour cache,
+// Device helpers of the SPH pair loops: smoothing kernels (Sect. 2.1), geometry of the neighbour cache,
 // Kahan summation for the FP32 pair sums of the mixed-precision path.
 #pragma once
 #include <climits>
@@ -6,26 +6,6 @@
 #include "sph_internal.cuh"
 
 namespace sph {
-
-constexpr double kInvPi = 0.31830988618379067154;
-constexpr float kInvPiF = 0.31830988618379067154f;
-
-// M4 cubic spline, R_kern = 2: f(q) = 1 - 3/2 q^2 + 3/4 q^3 (q<1), (2-q)^3/4 (1<=q<2), 0 beyond;
-// df = df/dq.  W = f(q)/(pi h^3).
-template <typename T>
-__device__ __forceinline__ void m4(T q, T &f, T &df) {
-    if (q < T(1)) {
-        f = T(1) + q * q * (T(-1.5) + T(0.75) * q);
-        df = q * (T(-3) + T(2.25) * q);
-    } else if (q < T(2)) {
-        const T t = T(2) - q;
-        f = T(0.25) * t * t * t;
-        df = T(-0.75) * t * t;
-    } else {
-        f = T(0);
-        df = T(0);
-    }
-}
 
 // Order of non-negative doubles through their bit patterns: an integer compare on the ALU pipe
 // gives the same answer as the FP64 compare, which would occupy the FP64 pipe (the limiter of the
@@ -35,41 +15,138 @@ __device__ __forceinline__ bool nonneg_lt(double a, double b) {
 }
 __device__ __forceinline__ double nonneg_max(double a, double b) { return nonneg_lt(a, b) ? b : a; }
 
-// M4 for q >= 0 in FP64 with the piece chosen by nonneg_lt.
-__device__ __forceinline__ void m4d(double q, double &f, double &df) {
-    if (nonneg_lt(q, 1.0)) {
-        f = 1.0 + q * q * (-1.5 + 0.75 * q);
-        df = q * (-3.0 + 2.25 * q);
-    } else if (nonneg_lt(q, 2.0)) {
-        const double t = 2.0 - q;
-        f = 0.25 * t * t * t;
-        df = -0.75 * t * t;
-    } else {
-        f = 0.0;
-        df = 0.0;
+// Positive part (a - q)_+ for q >= 0 (FP64: integer compare; FP32: max).
+__device__ __forceinline__ double posp(double a, double q) { return nonneg_lt(q, a) ? a - q : 0.0; }
+__device__ __forceinline__ float posp(float a, float q) { return fmaxf(a - q, 0.f); }
+
+// ------------------------------------------------------------------ smoothing kernels (Sect. 2.1)
+// W(r, h) = C f(q) / h^3, q = r/h, f = 0 for q >= R; normalised in 3-D (4 pi C int f q^2 dq = 1).
+// B-splines as sums of truncated powers (Schoenberg):  M4 = (2-q)_+^3/4 - (1-q)_+^3,
+// M5 = (5/2-q)_+^4 - 5 (3/2-q)_+^4 + 10 (1/2-q)_+^4, M6 = (3-q)_+^5 - 6 (2-q)_+^5 + 15 (1-q)_+^5;
+// Wendland functions with t = (1 - q/2)_+:  C2 = t^4 (1 + 2q), C4 = t^6 (1 + 3q + 35/12 q^2),
+// C6 = t^8 (1 + 4q + 25/4 q^2 + 4q^3).  Every branch is evaluated and selected (no divergence).
+// eval: f and f' = df/dq; d2: f''.
+template <int K>
+struct Kernel;
+
+template <>
+struct Kernel<SPH_KERNEL_M4> {
+    static constexpr double R = 2.0, C = 0.31830988618379067154, F0 = 1.0;
+    template <typename T>
+    __device__ static void eval(T q, T &f, T &df) {
+        const T t2 = posp(T(2), q), t1 = posp(T(1), q);
+        f = T(0.25) * t2 * t2 * t2 - t1 * t1 * t1;
+        df = T(-0.75) * t2 * t2 + T(3) * t1 * t1;
+    }
+    template <typename T>
+    __device__ static T d2(T q) { return T(1.5) * posp(T(2), q) - T(6) * posp(T(1), q); }
+};
+
+template <>
+struct Kernel<SPH_KERNEL_M5> {
+    static constexpr double R = 2.5, C = 0.31830988618379067154 / 20.0, F0 = 14.375;
+    template <typename T>
+    __device__ static void eval(T q, T &f, T &df) {
+        const T a = posp(T(2.5), q), b = posp(T(1.5), q), c = posp(T(0.5), q);
+        const T a3 = a * a * a, b3 = b * b * b, c3 = c * c * c;
+        f = a3 * a - T(5) * b3 * b + T(10) * c3 * c;
+        df = T(-4) * (a3 - T(5) * b3 + T(10) * c3);
+    }
+    template <typename T>
+    __device__ static T d2(T q) {
+        const T a = posp(T(2.5), q), b = posp(T(1.5), q), c = posp(T(0.5), q);
+        return T(12) * (a * a - T(5) * b * b + T(10) * c * c);
+    }
+};
+
+template <>
+struct Kernel<SPH_KERNEL_M6> {
+    static constexpr double R = 3.0, C = 0.31830988618379067154 / 120.0, F0 = 66.0;
+    template <typename T>
+    __device__ static void eval(T q, T &f, T &df) {
+        const T a = posp(T(3), q), b = posp(T(2), q), c = posp(T(1), q);
+        const T a4 = (a * a) * (a * a), b4 = (b * b) * (b * b), c4 = (c * c) * (c * c);
+        f = a4 * a - T(6) * b4 * b + T(15) * c4 * c;
+        df = T(-5) * (a4 - T(6) * b4 + T(15) * c4);
+    }
+    template <typename T>
+    __device__ static T d2(T q) {
+        const T a = posp(T(3), q), b = posp(T(2), q), c = posp(T(1), q);
+        return T(20) * (a * a * a - T(6) * b * b * b + T(15) * c * c * c);
+    }
+};
+
+template <>
+struct Kernel<SPH_KERNEL_C2> {
+    static constexpr double R = 2.0, C = 21.0 / 16.0 * 0.31830988618379067154, F0 = 1.0;
+    template <typename T>
+    __device__ static void eval(T q, T &f, T &df) {
+        const T t = T(0.5) * posp(T(2), q), t3 = t * t * t;
+        f = t3 * t * (T(1) + T(2) * q);
+        df = T(-5) * q * t3;
+    }
+    template <typename T>
+    __device__ static T d2(T q) {
+        const T t = T(0.5) * posp(T(2), q);
+        return t * t * (T(10) * q - T(5));
+    }
+};
+
+template <>
+struct Kernel<SPH_KERNEL_C4> {
+    static constexpr double R = 2.0, C = 495.0 / 256.0 * 0.31830988618379067154, F0 = 1.0;
+    template <typename T>
+    __device__ static void eval(T q, T &f, T &df) {
+        const T t = T(0.5) * posp(T(2), q), t2 = t * t, t5 = t2 * t2 * t;
+        f = t5 * t * (T(1) + q * (T(3) + T(35.0 / 12.0) * q));
+        df = T(-14.0 / 3.0) * q * (T(1) + T(2.5) * q) * t5;
+    }
+    template <typename T>
+    __device__ static T d2(T q) {
+        const T t = T(0.5) * posp(T(2), q), t2 = t * t;
+        return T(-14.0 / 3.0) * t2 * t2 * (T(1) + q * (T(2) - T(8.75) * q));
+    }
+};
+
+template <>
+struct Kernel<SPH_KERNEL_C6> {
+    static constexpr double R = 2.0, C = 1365.0 / 512.0 * 0.31830988618379067154, F0 = 1.0;
+    template <typename T>
+    __device__ static void eval(T q, T &f, T &df) {
+        const T t = T(0.5) * posp(T(2), q), t2 = t * t, t4 = t2 * t2, t7 = t4 * t2 * t;
+        f = t7 * t * (T(1) + q * (T(4) + q * (T(6.25) + T(4) * q)));
+        df = T(-5.5) * q * (T(1) + q * (T(3.5) + T(4) * q)) * t7;
+    }
+    template <typename T>
+    __device__ static T d2(T q) {
+        const T t = T(0.5) * posp(T(2), q), t2 = t * t;
+        return T(-5.5) * t2 * t2 * t2 * (T(1) + q * (T(3) + q * (T(-3.75) - T(20) * q)));
+    }
+};
+
+// Support radius of a kernel id (host side).
+inline double kernel_radius(int k) {
+    switch (k) {
+        case SPH_KERNEL_M5: return Kernel<SPH_KERNEL_M5>::R;
+        case SPH_KERNEL_M6: return Kernel<SPH_KERNEL_M6>::R;
+        case SPH_KERNEL_C2: return Kernel<SPH_KERNEL_C2>::R;
+        case SPH_KERNEL_C4: return Kernel<SPH_KERNEL_C4>::R;
+        case SPH_KERNEL_C6: return Kernel<SPH_KERNEL_C6>::R;
+        default: return Kernel<SPH_KERNEL_M4>::R;
     }
 }
-__device__ __forceinline__ double m4d_d2(double q) {
-    if (nonneg_lt(q, 1.0)) return 4.5 * q - 3.0;
-    if (nonneg_lt(q, 2.0)) return 1.5 * (2.0 - q);
-    return 0.0;
-}
 
-// d2f/dq2 of M4: 9/2 q - 3 (q<1), 3/2 (2-q) (1<=q<2), 0 beyond.
-template <typename T>
-__device__ __forceinline__ T m4_d2(T q) {
-    if (q < T(1)) return T(4.5) * q - T(3);
-    if (q < T(2)) return T(1.5) * (T(2) - q);
-    return T(0);
-}
-
-// dW/dq shape of M4 without branches (both pieces evaluated, one selected): lanes of a warp hold
-// different q, so a branch would run both pieces anyway.
-__device__ __forceinline__ float m4_df_sel(float q) {
-    const float t = fmaxf(2.f - q, 0.f);
-    const float outer = -0.75f * t * t;
-    const float inner = q * fmaf(2.25f, q, -3.f);
-    return q < 1.f ? inner : outer;
+// Calls body(Kernel<K>{}) with the kernel of id k (host side, for launch dispatch).
+template <typename F>
+inline auto with_kernel(int k, F &&body) {
+    switch (k) {
+        case SPH_KERNEL_M5: return body(Kernel<SPH_KERNEL_M5>{});
+        case SPH_KERNEL_M6: return body(Kernel<SPH_KERNEL_M6>{});
+        case SPH_KERNEL_C2: return body(Kernel<SPH_KERNEL_C2>{});
+        case SPH_KERNEL_C4: return body(Kernel<SPH_KERNEL_C4>{});
+        case SPH_KERNEL_C6: return body(Kernel<SPH_KERNEL_C6>{});
+        default: return body(Kernel<SPH_KERNEL_M4>{});
+    }
 }
 
 // L2 prefetch of the neighbour-list entries of a warp's particles.  Within a group the lists are

@@ -183,3 +183,33 @@ def test_step_vs_oracle(precision):
     assert abs(dtn / dtn_ref - 1) < (1e-8 if precision == 0 else 1e-4)
     if precision == 0:   # step-quality ratio max|dv| / rms|v| (its |dv| and |v|^2 are FP32 statistics)
         assert dvr > 0 and abs(dvr_gpu / dvr - 1) < 1e-5
+
+
+KERNEL_HFACT = [("M4", 0, 1.2), ("M5", 1, 1.2), ("M6", 2, 1.0), ("C2", 3, 1.2), ("C4", 4, 1.2), ("C6", 5, 1.2)]
+
+
+@pytest.mark.parametrize("name,kernel,hfact", KERNEL_HFACT)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_kernel_family_vs_oracle(name, kernel, hfact, precision):
+    """Every kernel of Sect. 2.1 through the GPU path (cache radius R chi h, density root, forces)
+    against the oracle with the same kernel: converged h, rho and accelerations."""
+    require_gpu()
+    from paper_2503_09713_gb300 import sph, workloads
+    w = workloads.lattice(14, sigma_v=0.1, jitter=0.1, seed=60 + kernel, hfact=hfact)
+    w["u"] = 1.0 + 0.5 * np.random.default_rng(kernel).uniform(size=w["n"])
+    P = O.Params(kernel=kernel, hfact=hfact)
+    h, rho, om, _, _ = O.density_algF(w["x"], w["y"], w["z"], w["h"], w["mass"], P)
+    ax, ay, az, du, vs = O.forces(w["x"], w["y"], w["z"], w["vx"], w["vy"], w["vz"], w["u"], h, om, w["mass"], P)
+    s = sph.DeviceState.from_numpy(w)
+    solver = sph.Solver(sph.default_params(precision=precision, kernel=kernel, hfact=hfact), w["n"])
+    solver.converge(s)
+    out = s.to_numpy()
+    solver.close()
+    ids = out["id"].astype(np.int64)
+    g = {k: to_orig(out[k], ids) for k in ("h", "rho", "ax", "ay", "az", "du")}
+    amax = np.max(np.abs(np.stack([ax, ay, az])))
+    tol_h, tol_a = (1e-9, 1e-8) if precision == 0 else (1e-5, 1e-4)
+    assert np.max(np.abs(g["h"] / h - 1)) < tol_h
+    assert np.max(np.abs(g["rho"] / rho - 1)) < 3 * tol_h
+    for k, ref in (("ax", ax), ("ay", ay), ("az", az)):
+        assert np.max(np.abs(g[k] - ref)) < tol_a * amax, k
