@@ -141,8 +141,8 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------------- GPU arm
 def run_precision(torch, sph, w, precision: int, steps: int, warmup: int, dist, timing_pass: bool,
-                  clocks: ClockSampler | None):
-    p = sph.default_params(precision=precision)
+                  clocks: ClockSampler | None, morton_bits: int = 21):
+    p = sph.default_params(precision=precision, morton_bits=morton_bits)
     s = sph.DeviceState.from_numpy(w)
     solver = sph.Solver(p, w["n"])
     solver.converge(s)
@@ -294,6 +294,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--morton-bits", type=int, default=21,
+                    help="bits per axis of the Morton codes (21: 63-bit codes; 10: the 30-bit u32 variant)")
     ap.add_argument("--only", choices=["fp64", "mixed", "ensemble"], default=None,
                     help="run one precision only (profiling); the headline needs both")
     args = ap.parse_args()
@@ -347,12 +349,12 @@ def main():
         print(json.dumps({"workload": "ensemble", **run_ensemble(torch, sph, args.steps, max(args.warmup, 3))}))
         return
     if args.only == "mixed":
-        r = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, clocks)
+        r = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, clocks, args.morton_bits)
         print(json.dumps({"workload": args.workload, "precision": "mixed", "ms_per_step": r["ms_per_step"],
                           "particles_per_s": n / (r["ms_per_step"] * 1e-3), "stage_ms": r["stage_ms"]}))
         r["solver"].close()
         return
-    r64 = run_precision(torch, sph, w, 0, args.steps, max(args.warmup, 3), dist, True, clocks)
+    r64 = run_precision(torch, sph, w, 0, args.steps, max(args.warmup, 3), dist, True, clocks, args.morton_bits)
     from paper_2503_09713_gb300 import replicas
     ms = replicas.max_over_ranks(r64["ms_per_step"], dist, "cuda")
     value = replicas.sum_over_ranks(n, dist, "cuda") / (ms * 1e-3)
@@ -390,7 +392,7 @@ def main():
             "roofline": roofline, "launch": r64["launch"]}
 
     if not args.no_mixed and args.only != "fp64":
-        r32 = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, None)
+        r32 = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, None, args.morton_bits)
         ms32 = r32["ms_per_step"]
         st32 = r32["timing_stats"]
         f32 = st32["n_pairs"] * FLOP_FORCE32_CAND + st32["force_pairs"] * FLOP_FORCE32_PAIR

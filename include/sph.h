@@ -74,6 +74,10 @@ typedef struct {
     int max_outer;        /* cache rebuilds inside sph_step before SPH_ERR_CACHE_STALE; 8 */
     double box_lo[3];
     double box_hi[3];
+    int morton_bits;      /* bits per axis of the Morton codes (App. B): 21 (63-bit codes, default) down
+                             to 1; 10 gives the 30-bit codes of the paper's u32 variant, sorted in 4
+                             radix passes instead of 8.  A batch keeps the box index above
+                             3 * min(morton_bits, (63 - box bits) / 3) */
 } sph_params;
 
 /* Particle state.  Arrays: float64[n] (id: uint32[n]).  Inputs/outputs per function below. */

@@ -169,6 +169,7 @@ int check_params(sph_ctx *c, const sph_params *p) {
     if (!(p->hfact > 0) || !(p->gamma > 1) || !(p->h_tol > 0) || !(p->h_clamp > 1) || !(p->cache_tol >= 1) ||
         !(p->c_cour > 0) || !(p->c_force > 0) || p->alpha_av < 0 || p->beta_av < 0 || p->alpha_u < 0)
         return fail(c, SPH_ERR_INVALID_ARG, "parameter out of range");
+    if (p->morton_bits < 1 || p->morton_bits > 21) return fail(c, SPH_ERR_INVALID_ARG, "morton_bits outside 1..21");
     if (p->h_max_iter < 1 || p->reduction_level < 0 || p->reduction_level > 16 || p->max_outer < 1)
         return fail(c, SPH_ERR_INVALID_ARG, "iteration limits out of range");
     for (int k = 0; k < 3; k++)
@@ -254,6 +255,7 @@ void sph_default_params(sph_params *p) {
     p->reduction_level = 3;
     p->periodic = 1;
     p->max_outer = 8;
+    p->morton_bits = 21;
     for (int k = 0; k < 3; k++) {
         p->box_lo[k] = 0.0;
         p->box_hi[k] = 1.0;
@@ -276,6 +278,7 @@ int create_ctx(const sph_params *p, int64_t n_cap, int n_boxes, int64_t neigh_ca
     if (n_cap < 1 || n_cap > (int64_t)1 << 30) { delete c; return SPH_ERR_INVALID_ARG; }
     c->p = *p;
     c->launch.reduction_level = p->reduction_level;
+    c->morton_bits = p->morton_bits;
     c->stream = (cudaStream_t)stream;
     c->n_cap = n_cap;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
@@ -362,7 +365,7 @@ int sph_batch_create(const sph_params *p, int n_boxes, const int64_t *box_offset
     int bits = 0;
     while ((1 << bits) < n_boxes) ++bits;
     c->box_bits = bits;
-    c->morton_bits = std::min(21, (63 - bits) / 3);
+    c->morton_bits = std::min(p->morton_bits, (63 - bits) / 3);
     c->h_box_off.assign(box_offsets, box_offsets + n_boxes + 1);
     std::vector<uint16_t> box_of((size_t)total);
     std::vector<double> gam((size_t)n_boxes);
@@ -412,6 +415,7 @@ int sph_set_params(sph_ctx *c, const sph_params *p) {
     if (r) return r;
     c->p = *p;
     c->launch.reduction_level = p->reduction_level;
+    c->morton_bits = c->batch ? std::min(p->morton_bits, (63 - c->box_bits) / 3) : p->morton_bits;
     c->tree_valid = c->cache_valid = c->density_valid = c->forces_valid = false;
     c->dhdt_valid = false;
     c->dt_next = -1.0;

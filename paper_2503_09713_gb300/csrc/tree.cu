@@ -219,8 +219,10 @@ static size_t onesweep_smem() {
     return (size_t)kRsTile * 8 + (size_t)kRsTile * 4 + (size_t)kRsWarps * 256 * 4 + 256 * 4 * 2 + 16;
 }
 
-static int radix_sort(sph_ctx *c, int64_t n) {
-    // keys[0], vals[0] hold the input; after 8 passes the result is back in keys[0], vals[0]
+// keys[0], vals[0] hold the input; one pass per 8-bit digit of the key_bits significant bits; the
+// result is in keys[passes & 1], vals[passes & 1] (returned).
+static int radix_sort(sph_ctx *c, int64_t n, int key_bits, int *out_buf) {
+    const int passes = std::max(1, (key_bits + 7) / 8);
     const int64_t tiles = (n + kRsTile - 1) / kRsTile;
     SPH_CUDA(c, cudaMemsetAsync(c->digit_hist, 0, 8 * 256 * sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(c->lookback, 0, (size_t)8 * tiles * 256 * sizeof(uint32_t), c->stream));
@@ -237,13 +239,14 @@ static int radix_sort(sph_ctx *c, int64_t n) {
         SPH_CUDA(c, cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr_set = true;
     }
-    for (int p = 0; p < 8; p++) {
+    for (int p = 0; p < passes; p++) {
         const int src = p & 1, dst = src ^ 1;
         k_onesweep<<<(unsigned)tiles, kRsThreads, sm, c->stream>>>(
             c->keys[src], c->vals[src], c->keys[dst], c->vals[dst], n, 8 * p, c->digit_hist + 256 * p,
             c->lookback + (size_t)p * tiles * 256, c->tile_ctr + p, &c->dscal->flags);
         SPH_LAUNCH_CHECK(c, "k_onesweep");
     }
+    *out_buf = passes & 1;
     return SPH_OK;
 }
 
@@ -614,10 +617,11 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
                                                       c->morton_bits);
     SPH_LAUNCH_CHECK(c, "k_morton");
     // A2 sort
-    int r = radix_sort(c, n);
+    int buf = 0;
+    int r = radix_sort(c, n, 3 * c->morton_bits + c->box_bits, &buf);
     if (r) return r;
-    c->mu = c->keys[0];
-    c->perm = c->vals[0];
+    c->mu = c->keys[buf];
+    c->perm = c->vals[buf];
 
     // reorder the particle arrays, kGatherBatch fields per pass through the scratch block
     const double *fields[16];

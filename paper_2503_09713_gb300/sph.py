@@ -42,7 +42,8 @@ class sph_params(ctypes.Structure):
     _fields_ = [("kernel", _i), ("precision", _i), ("hfact", _d), ("gamma", _d), ("alpha_av", _d),
                 ("beta_av", _d), ("alpha_u", _d), ("c_cour", _d), ("c_force", _d), ("h_tol", _d),
                 ("h_clamp", _d), ("cache_tol", _d), ("h_max_iter", _i), ("reduction_level", _i),
-                ("periodic", _i), ("max_outer", _i), ("box_lo", _d * 3), ("box_hi", _d * 3)]
+                ("periodic", _i), ("max_outer", _i), ("box_lo", _d * 3), ("box_hi", _d * 3),
+                ("morton_bits", _i)]
 
 
 class sph_state(ctypes.Structure):

@@ -40,7 +40,30 @@ def test_host_only_entry_points(lib):
     assert lib.sph_destroy(None) == sph.SPH_OK
 
 
-def test_struct_layouts_match_header():
-    # sph_params: 2 ints, 10 doubles, 4 ints, 6 doubles
-    assert ctypes.sizeof(sph.sph_params) == 8 + 80 + 16 + 48
-    assert ctypes.sizeof(sph.sph_state) == 8 + 8 + 16 * 8
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a struct of include/sph.h, from the C compiler (gcc, host)."""
+    import os
+    import subprocess
+    import tempfile
+    inc = os.path.join(os.path.dirname(sph.HEADER))
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sph.h"', "int main(void) {",
+             f'  printf("%zu\\n", sizeof({struct}));']
+    lines += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        with open(src, "w") as fh:
+            fh.write("\n".join(lines))
+        subprocess.run(["gcc", "-I", inc, src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(v) for v in out[1:]]
+
+
+@pytest.mark.parametrize("name", ["sph_params", "sph_state", "sph_tree_view", "sph_stats", "sph_launch"])
+def test_struct_layouts_match_header(name):
+    """Every ctypes mirror of an ABI struct has the C compiler's size and field offsets."""
+    cls = getattr(sph, name)
+    fields = [f for f, _ in cls._fields_]
+    size, offs = _c_layout(name, fields)
+    assert ctypes.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offs

@@ -9,13 +9,13 @@ from gpu_common import random_positions, require_gpu
 pytestmark = pytest.mark.gpu
 
 
-def _build(x, y, z, h, n_red, lo=(0, 0, 0), hi=(1, 1, 1)):
+def _build(x, y, z, h, n_red, lo=(0, 0, 0), hi=(1, 1, 1), bits=21):
     require_gpu()
     from paper_2503_09713_gb300 import sph
     n = len(x)
     d = {"x": x, "y": y, "z": z, "h": h, "mass": 1.0 / n}
     s = sph.DeviceState.from_numpy(d)
-    solver = sph.Solver(sph.default_params(reduction_level=n_red, box_lo=lo, box_hi=hi), n)
+    solver = sph.Solver(sph.default_params(reduction_level=n_red, box_lo=lo, box_hi=hi, morton_bits=bits), n)
     solver.build_tree(s)
     t = solver.export_tree()
     out = s.to_numpy()
@@ -51,20 +51,20 @@ def expected_groups(leaf_first, tr, n):
     return np.array(sorted(starts) + [n], dtype=np.int64)
 
 
-def _check_against_oracle(x, y, z, h, n_red, lo=(0, 0, 0), hi=(1, 1, 1)):
-    t, out = _build(x, y, z, h, n_red, lo, hi)
-    m = O.morton(x, y, z, lo, hi)
+def _check_against_oracle(x, y, z, h, n_red, lo=(0, 0, 0), hi=(1, 1, 1), bits=21):
+    t, out = _build(x, y, z, h, n_red, lo, hi, bits)
+    m = O.morton(x, y, z, lo, hi, bits=bits)
     mu, perm = O.sort_by_key(m)
     assert np.array_equal(t["mu"], mu)
     assert np.array_equal(t["perm"], perm)
     assert np.array_equal(out["id"], perm)
     xs, ys, zs, hs = x[perm], y[perm], z[perm], h[perm]
     assert np.array_equal(out["x"], xs) and np.array_equal(out["h"], hs)
-    xi = O.keep_mask(mu, 63, n_red)
+    xi = O.keep_mask(mu, 3 * bits, n_red)
     idv, ml = O.compact(mu, xi)
     assert np.array_equal(t["leaf_first"], idv)
     assert np.array_equal(t["mu_leaf"], ml)
-    tr = O.radix_tree(ml, 63)
+    tr = O.radix_tree(ml, 3 * bits)
     for k in ("lchild", "rchild", "lflag", "rflag", "endrange"):
         assert np.array_equal(t[k], getattr(tr, k)), k
     bmin, bmax, hmax = O.cell_boxes(idv, tr.endrange, xs, ys, zs, hs)
@@ -89,6 +89,15 @@ def test_tree_other_boxes(lo, hi):
     lo, hi = np.array(lo), np.array(hi)
     x, y, z = [lo[k] + (hi[k] - lo[k]) * p for k, p in enumerate((x, y, z))]
     _check_against_oracle(x, y, z, np.full(6000, 0.05), 2, tuple(lo), tuple(hi))
+
+
+@pytest.mark.parametrize("kind,n,n_red", [("uniform", 20000, 3), ("cluster", 9001, 2), ("dups", 4099, 1)])
+def test_tree_u32_codes(kind, n, n_red):
+    """The 30-bit codes of the u32 variant (10 bits per axis, App. B; 4 radix passes): codes,
+    permutation, leaves, Karras tables, boxes and groups against the oracle at 10 bits."""
+    x, y, z = random_positions(n, 31 + n_red, kind)
+    h = np.random.default_rng(6).uniform(0.01, 0.02, size=n)
+    _check_against_oracle(x, y, z, h, n_red, bits=10)
 
 
 def test_tree_lattice_reduction_levels():
