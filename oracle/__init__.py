@@ -53,7 +53,9 @@ _p = ctypes.c_void_p
 class OrcParams(ctypes.Structure):
     _fields_ = [("hfact", _d), ("gamma", _d), ("alpha_av", _d), ("beta_av", _d), ("alpha_u", _d),
                 ("c_cour", _d), ("c_force", _d), ("h_tol", _d), ("h_clamp", _d), ("cache_tol", _d),
-                ("lo", _d * 3), ("hi", _d * 3), ("periodic", _i32), ("h_max_iter", _i32)]
+                ("lo", _d * 3), ("hi", _d * 3), ("periodic", _i32), ("h_max_iter", _i32),
+                ("av_switch", _i32), ("max_corr", _i32), ("alpha_min", _d), ("sigma_decay", _d), ("eps_v", _d),
+                ("lambda_stiff", _d)]
 
 
 @dataclass
@@ -74,11 +76,19 @@ class Params:
     periodic: int = 1
     h_max_iter: int = 200
     kernel: int = 0          # 0 M4, 1 M5, 2 M6, 3 Wendland C2, 4 C4, 5 C6 (Sect. 2.1)
+    av_switch: int = 0       # 1: alpha evolves per particle (App. G "Shock detection"), alpha_av = max
+    max_corr: int = 4        # most corrector passes per step
+    alpha_min: float = 0.0
+    sigma_decay: float = 0.1
+    eps_v: float = 0.0       # epsilon_v of Eq. cvleapfrog (the paper: 1e-2); 0: no corrector re-run
+    lambda_stiff: float = 1.0
 
     def c(self) -> OrcParams:
         return OrcParams(self.hfact, self.gamma, self.alpha_av, self.beta_av, self.alpha_u, self.c_cour,
                          self.c_force, self.h_tol, self.h_clamp, self.cache_tol, (_d * 3)(*self.lo),
-                         (_d * 3)(*self.hi), int(self.periodic), int(self.h_max_iter))
+                         (_d * 3)(*self.hi), int(self.periodic), int(self.h_max_iter), int(self.av_switch),
+                         int(self.max_corr), float(self.alpha_min), float(self.sigma_decay), float(self.eps_v),
+                         float(self.lambda_stiff))
 
 
 def _setup(lib):
@@ -112,6 +122,10 @@ def _setup(lib):
         "orc_forces": (None, [_i64, _d, P, _p, _p, _p, _p, _p, _p, _p, _p, _p, _i32, _p, _p, _p, _p, _p]),
         "orc_cfl": (_d, [_i64, P, _p, _p, _p, _p, _p]),
         "orc_step": (_d, [_i64, _d, P, _d] + [_p] * 15 + [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_d)]),
+        "orc_step_ext": (_d, [_i64, _d, P, _d] + [_p] * 17 + [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_d),
+                                                             ctypes.POINTER(_i32)]),
+        "orc_forces_alpha": (None, [_i64, _d, P] + [_p] * 10 + [_i32] + [_p] * 5),
+        "orc_alpha_update": (None, [_i64, _d, P] + [_p] * 12 + [_d, _i32, _p]),
         "orc_num_threads": (_i32, []),
         "orc_subset_forces": (_i64, [_i64, _d, P] + [_p] * 7 + [_d, _i64, _p] + [_p] * 7),
         "orc_subset_neighbours": (_i64, [_i64, _p, _p, _p, _p, _d, _p, _p, _i32, _i64, _p, _p, _p]),
@@ -373,7 +387,9 @@ _STATE_KEYS = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du"
 
 def step(state: dict, mass, params: Params, dt, method=None):
     """One KDK step on a dict of float64 arrays (keys x..vsig), in place.  Returns
-    (dt_next, inner_iterations, dv_ratio)."""
+    (dt_next, inner_iterations, dv_ratio).  With params.av_switch the dict needs "alpha" (per
+    particle, updated in place); with params.eps_v > 0 it may hold "lambda_cfl" (the CFL multiplier,
+    1 when absent, updated) and receives "corrector_passes"."""
     _kernel(params.kernel)
     for k in _STATE_KEYS:
         state[k] = _f64(state[k])
@@ -382,12 +398,49 @@ def step(state: dict, mass, params: Params, dt, method=None):
         method = 0 if n <= 4096 else 1
     it = _i32(0)
     dvr = _d(0.0)
+    passes = _i32(0)
     p = params.c()
-    dtn = _load().orc_step(n, float(mass), ctypes.byref(p), float(dt), *[_ptr(state[k]) for k in _STATE_KEYS],
-                           int(method), ctypes.byref(it), ctypes.byref(dvr))
+    alpha = None
+    if params.av_switch:
+        state["alpha"] = _f64(state["alpha"])
+        alpha = _ptr(state["alpha"])
+    lam = _d(float(state.get("lambda_cfl", 1.0)))
+    dtn = _load().orc_step_ext(n, float(mass), ctypes.byref(p), float(dt), *[_ptr(state[k]) for k in _STATE_KEYS],
+                               alpha, ctypes.byref(lam), int(method), ctypes.byref(it), ctypes.byref(dvr),
+                               ctypes.byref(passes))
     if dtn < 0:
         raise RuntimeError("oracle h iteration exceeded h_max_iter")
+    state["lambda_cfl"] = lam.value
+    state["corrector_passes"] = passes.value
     return dtn, it.value, dvr.value
+
+
+def alpha_update(x, y, z, vx, vy, vz, ax, ay, az, u, h, omega, mass, params: Params, dt, alpha, method=None):
+    """The shock-switch step of alpha (orc_alpha_update) on copies; returns the new alpha."""
+    _kernel(params.kernel)
+    arrs = [_f64(a) for a in (x, y, z, vx, vy, vz, ax, ay, az, u, h, omega)]
+    n = len(arrs[0])
+    if method is None:
+        method = 0 if n <= 4096 else 1
+    out = _f64(alpha).copy()
+    p = params.c()
+    _load().orc_alpha_update(n, float(mass), ctypes.byref(p), *[_ptr(a) for a in arrs], float(dt), int(method),
+                             _ptr(out))
+    return out
+
+
+def forces_alpha(x, y, z, vx, vy, vz, u, h, omega, alpha, mass, params: Params, method=None):
+    """forces() with a per-particle alpha (v_sig,a = alpha_a c_s,a + beta |v_ab . rhat|)."""
+    _kernel(params.kernel)
+    arrs = [_f64(a) for a in (x, y, z, vx, vy, vz, u, h, omega, alpha)]
+    n = len(arrs[0])
+    if method is None:
+        method = 0 if n <= 4096 else 1
+    outs = [np.zeros(n) for _ in range(5)]
+    p = params.c()
+    _load().orc_forces_alpha(n, float(mass), ctypes.byref(p), *[_ptr(a) for a in arrs], int(method),
+                             *[_ptr(o) for o in outs])
+    return tuple(outs)
 
 
 # ---- sampled evaluation for full-size inputs ----

@@ -548,6 +548,14 @@ typedef struct {
     double lo[3], hi[3];
     int periodic;
     int h_max_iter;
+    /* shock switch, CFL multiplier and corrector re-runs (App. G "CFL multiplier", "Shock
+     * detection"); av_switch = 0 and eps_v = 0 give the fixed-alpha step above */
+    int av_switch;       /* 1: alpha_a evolves (Eq. evolalphaanalytic), alpha_av is alpha_max */
+    int max_corr;        /* most corrector passes per step */
+    double alpha_min;    /* floor of alpha_loc */
+    double sigma_decay;  /* tau_a = h_a / (sigma_decay c_s,a) */
+    double eps_v;        /* epsilon_v of Eq. cvleapfrog; 0: no re-run */
+    double lambda_stiff; /* lambda_stiff of the CFL multiplier recovery */
 } orc_params;
 
 static double orc_dist(const double *x, const double *y, const double *z, int64_t a, int64_t b,
@@ -751,10 +759,10 @@ void orc_density_at(int64_t n, double mass, double hfact, const double *x, const
 /*   - rho_a = rho(h_a) (Eq. rhoh), P_a = (gamma-1) rho_a u_a, c_s,a = sqrt(gamma P_a/rho_a).   */
 /* Inputs are per-particle h, Omega (rho follows from h); outputs ax,ay,az,du,vsig.           */
 /* ====================================================================================== */
-void orc_forces(int64_t n, double mass, const orc_params *p, const double *x, const double *y,
-                const double *z, const double *vx, const double *vy, const double *vz, const double *u,
-                const double *h, const double *omega, int method,
-                double *ax, double *ay, double *az, double *du, double *vsig)
+void orc_forces_alpha(int64_t n, double mass, const orc_params *p, const double *x, const double *y,
+                      const double *z, const double *vx, const double *vy, const double *vz, const double *u,
+                      const double *h, const double *omega, const double *alpha, int method,
+                      double *ax, double *ay, double *az, double *du, double *vsig)
 {
     double boxL[3] = {p->hi[0] - p->lo[0], p->hi[1] - p->lo[1], p->hi[2] - p->lo[2]};
     double *rho = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
@@ -772,7 +780,8 @@ void orc_forces(int64_t n, double mass, const orc_params *p, const double *x, co
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t a = 0; a < n; a++) {
         double acc[3] = {0.0, 0.0, 0.0}, dua = 0.0;
-        double vs = p->alpha_av * cs[a];
+        double al_a = alpha ? alpha[a] : p->alpha_av;
+        double vs = al_a * cs[a];
         for (int64_t k = nl.off[a]; k < nl.off[a + 1]; k++) {
             int64_t b = nl.ids[k];
             double d[3];
@@ -783,9 +792,10 @@ void orc_forces(int64_t n, double mass, const orc_params *p, const double *x, co
             double Fa = orc_F(r, h[a]);
             double Fb = orc_F(r, h[b]);
             double qa = 0.0, qb = 0.0;
+            double al_b = alpha ? alpha[b] : p->alpha_av;
             if (vdotr < 0.0) {
-                double vsa = p->alpha_av * cs[a] + p->beta_av * fabs(vdotr);
-                double vsb = p->alpha_av * cs[b] + p->beta_av * fabs(vdotr);
+                double vsa = al_a * cs[a] + p->beta_av * fabs(vdotr);
+                double vsb = al_b * cs[b] + p->beta_av * fabs(vdotr);
                 qa = -0.5 * rho[a] * vsa * vdotr;
                 qb = -0.5 * rho[b] * vsb * vdotr;
             }
@@ -799,7 +809,7 @@ void orc_forces(int64_t n, double mass, const orc_params *p, const double *x, co
                 dua += mass * p->alpha_u * vsu * (u[a] - u[b]) * 0.5 *
                        (Fa / (omega[a] * rho[a]) + Fb / (omega[b] * rho[b]));
             }
-            double vsdt = p->alpha_av * cs[a] + p->beta_av * (vdotr < 0.0 ? -vdotr : 0.0);
+            double vsdt = al_a * cs[a] + p->beta_av * (vdotr < 0.0 ? -vdotr : 0.0);
             if (vsdt > vs) vs = vsdt;
         }
         ax[a] = acc[0]; ay[a] = acc[1]; az[a] = acc[2];
@@ -808,6 +818,83 @@ void orc_forces(int64_t n, double mass, const orc_params *p, const double *x, co
     }
     orc_nlist_free(&nl);
     free(rho); free(P); free(cs);
+}
+
+/* Fixed alpha = alpha_av for every particle. */
+void orc_forces(int64_t n, double mass, const orc_params *p, const double *x, const double *y,
+                const double *z, const double *vx, const double *vy, const double *vz, const double *u,
+                const double *h, const double *omega, int method,
+                double *ax, double *ay, double *az, double *du, double *vsig)
+{
+    orc_forces_alpha(n, mass, p, x, y, z, vx, vy, vz, u, h, omega, NULL, method, ax, ay, az, du, vsig);
+}
+
+/* ====================================================================================== */
+/* Shock detection (App. G, Eq. evolalphaanalytic and its implicit step; the paper refers to     */
+/* Phantom, Price et al. 2018, Sect. 2.2.9, for the switch).  Reading:                           */
+/*   velocity and acceleration gradients by the SPH estimator at h_a,                              */
+/*     (d_j v^i)_a = -1/(Omega_a rho_a) sum_b m (v_a^i - v_b^i) F_ab(h_a) rhat_ab^j,  likewise a;   */
+/*   d(div v)/dt = div a - (d_i v^j)(d_j v^i);                                                    */
+/*   xi_a = |div v|^2 / (|div v|^2 + |curl v|^2)   (0 when both vanish);                           */
+/*   A_a = xi_a max(-d(div v)/dt, 0);  alpha_loc = max(alpha_min, min(10 h_a^2 A_a / c_s,a^2,       */
+/*   alpha_max));  tau_a = h_a / (sigma_decay c_s,a);                                              */
+/*   alpha^{n+1} = max((alpha^n + alpha_loc dt/tau)/(1 + dt/tau), alpha_loc)  (the paper's step).  */
+/* Evaluated after the predictor and the h iteration, with v* and a^n (alpha_loc(v*, grad v*,      */
+/* grad a^n)) and c_s from u*; alpha_max = alpha_av.                                                */
+/* ====================================================================================== */
+void orc_alpha_update(int64_t n, double mass, const orc_params *p, const double *x, const double *y,
+                      const double *z, const double *vx, const double *vy, const double *vz, const double *ax,
+                      const double *ay, const double *az, const double *u, const double *h,
+                      const double *omega, double dt, int method, double *alpha)
+{
+    double boxL[3] = {p->hi[0] - p->lo[0], p->hi[1] - p->lo[1], p->hi[2] - p->lo[2]};
+    orc_nlist nl;
+    double R = orc_kernel_R(orc_kind);
+    if (method == 0) orc_nlist_brute(n, x, y, z, h, R, boxL, p->periodic, &nl);
+    else orc_nlist_grid(n, x, y, z, h, R, p->lo, boxL, p->periodic, &nl);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t a = 0; a < n; a++) {
+        double G[3][3] = {{0.0}}, diva = 0.0;
+        const double va[3] = {vx[a], vy[a], vz[a]}, aa[3] = {ax[a], ay[a], az[a]};
+        for (int64_t k = nl.off[a]; k < nl.off[a + 1]; k++) {
+            int64_t b = nl.ids[k];
+            double d[3];
+            double r = orc_dist(x, y, z, a, b, boxL, p->periodic, d);
+            if (!(r < R * h[a])) continue;   /* the estimator uses W(h_a) only */
+            double rhat[3] = {d[0] / r, d[1] / r, d[2] / r};
+            double Fa = orc_F(r, h[a]);
+            const double vb[3] = {vx[b], vy[b], vz[b]}, ab[3] = {ax[b], ay[b], az[b]};
+            for (int i = 0; i < 3; i++) {
+                for (int j = 0; j < 3; j++) G[i][j] += mass * (va[i] - vb[i]) * Fa * rhat[j];
+                diva += mass * (aa[i] - ab[i]) * Fa * rhat[i];
+            }
+        }
+        double rho = mass * pow(p->hfact / h[a], 3.0);
+        double fac = -1.0 / (omega[a] * rho);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) G[i][j] *= fac;   /* G[i][j] = d_j v^i */
+        diva *= fac;
+        double divv = G[0][0] + G[1][1] + G[2][2];
+        double cx = G[2][1] - G[1][2], cy = G[0][2] - G[2][0], cz = G[1][0] - G[0][1];
+        double tr = 0.0;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) tr += G[i][j] * G[j][i];
+        double ddiv = diva - tr;
+        double den = divv * divv + (cx * cx + cy * cy + cz * cz);
+        double xi = den > 0.0 ? divv * divv / den : 0.0;
+        double A = xi * (ddiv < 0.0 ? -ddiv : 0.0);
+        double cs = sqrt(p->gamma * (p->gamma - 1.0) * u[a]);
+        double aloc = A > 0.0 ? p->alpha_av : 0.0;   /* c_s = 0: the limit of the ratio */
+        if (cs > 0.0) {
+            aloc = 10.0 * h[a] * h[a] * A / (cs * cs);
+            if (aloc > p->alpha_av) aloc = p->alpha_av;
+        }
+        if (aloc < p->alpha_min) aloc = p->alpha_min;
+        double q = cs > 0.0 ? dt * p->sigma_decay * cs / h[a] : 0.0;   /* dt / tau */
+        double an = (alpha[a] + aloc * q) / (1.0 + q);
+        alpha[a] = an > aloc ? an : aloc;
+    }
+    orc_nlist_free(&nl);
 }
 
 /* CFL time step (App. G, "Choice of the timestep"): min_a min(C_cour h_a / v_sig,a, C_force sqrt(h_a/|a_a|)). */
@@ -847,16 +934,30 @@ static double orc_wrap(double x, double lo, double hi)
 /* max_i |dv_i| / sqrt(<|v|^2>) for the correction dv_i = dt/2 (a^{n+1}_i - a^n_i) (Eq. deltavi;   */
 /* reading of Eq. cvleapfrog, whose printed ratio is always >= 1).                              */
 /* ====================================================================================== */
-double orc_step(int64_t n, double mass, const orc_params *p, double dt,
-                double *x, double *y, double *z, double *vx, double *vy, double *vz, double *u, double *h,
-                double *ax, double *ay, double *az, double *du, double *rho, double *omega, double *vsig,
-                int method, int *iters, double *dv_ratio)
+/* One step with the extensions of App. G: when alpha is non-NULL and p->av_switch, alpha_a is   */
+/* updated (orc_alpha_update) after the h iteration and used by the forces; when p->eps_v > 0,    */
+/* the corrector is re-run while Eq. cvleapfrog fails (reading below), at most p->max_corr passes, */
+/* and *lambda (the CFL multiplier, NULL: none) is halved in a step whose first pass failed, else   */
+/* relaxed by lambda <- (1 + lambda_stiff lambda)/(1 + lambda_stiff) ("CFL multiplier"); the      */
+/* returned time step is lambda times the CFL step.  Reading of Eq. cvleapfrog (as printed its ratio is always >= 1): pass k compares */
+/* max_i |v_i^(k) - w_i^(k)| = dt/2 |a_i^(k) - a_i^(k-1)| (a^(0) = a^n), w^(k) the velocity the     */
+/* forces of pass k used (v* for k = 1, where the difference is Eq. deltavi; v^(k-1) afterwards,   */
+/* the paper's "v* <- v^{n+1}"), with                                                              */
+/* sqrt(<|v^(k)|^2>) and fails at >= eps_v (never when nothing moves).  Each pass restarts the     */
+/* correction from v* and u*: v^(k) = v* + dt/2 (a^(k) - a^n).  *passes: corrector passes used.     */
+double orc_step_ext(int64_t n, double mass, const orc_params *p, double dt,
+                    double *x, double *y, double *z, double *vx, double *vy, double *vz, double *u, double *h,
+                    double *ax, double *ay, double *az, double *du, double *rho, double *omega, double *vsig,
+                    double *alpha, double *lambda, int method, int *iters, double *dv_ratio, int *passes)
 {
     size_t sz = (size_t)(n > 0 ? n : 1) * sizeof(double);
     double *a0x = (double *)malloc(sz), *a0y = (double *)malloc(sz), *a0z = (double *)malloc(sz),
-           *du0 = (double *)malloc(sz);
+           *du0 = (double *)malloc(sz), *vsx = (double *)malloc(sz), *vsy = (double *)malloc(sz),
+           *vsz = (double *)malloc(sz), *us = (double *)malloc(sz), *apx = (double *)malloc(sz),
+           *apy = (double *)malloc(sz), *apz = (double *)malloc(sz);
     for (int64_t a = 0; a < n; a++) {
         a0x[a] = ax[a]; a0y[a] = ay[a]; a0z[a] = az[a]; du0[a] = du[a];
+        apx[a] = ax[a]; apy[a] = ay[a]; apz[a] = az[a];
         double hvx = vx[a] + 0.5 * dt * ax[a], hvy = vy[a] + 0.5 * dt * ay[a], hvz = vz[a] + 0.5 * dt * az[a];
         double hu = u[a] + 0.5 * dt * du[a];
         x[a] = orc_wrap(x[a] + dt * hvx, p->lo[0], p->hi[0]);
@@ -866,24 +967,65 @@ double orc_step(int64_t n, double mass, const orc_params *p, double dt,
         vy[a] = hvy + 0.5 * dt * ay[a];
         vz[a] = hvz + 0.5 * dt * az[a];
         u[a] = hu + 0.5 * dt * du[a];
+        vsx[a] = vx[a]; vsy[a] = vy[a]; vsz[a] = vz[a]; us[a] = u[a];   /* v*, u* */
     }
     int outer = 0;
     int it = orc_density_algF(n, mass, p, x, y, z, h, rho, omega, method, &outer);
     if (iters) *iters = it;
-    if (it < 0) { free(a0x); free(a0y); free(a0z); free(du0); return -1.0; }
-    orc_forces(n, mass, p, x, y, z, vx, vy, vz, u, h, omega, method, ax, ay, az, du, vsig);
-    double dvmax = 0.0, v2 = 0.0;
-    for (int64_t a = 0; a < n; a++) {
-        double dvx = 0.5 * dt * (ax[a] - a0x[a]), dvy = 0.5 * dt * (ay[a] - a0y[a]), dvz = 0.5 * dt * (az[a] - a0z[a]);
-        vx[a] += dvx; vy[a] += dvy; vz[a] += dvz;
-        u[a] += 0.5 * dt * (du[a] - du0[a]);
-        double dv = sqrt((dvx * dvx + dvy * dvy) + dvz * dvz);
-        if (dv > dvmax) dvmax = dv;
-        v2 += (vx[a] * vx[a] + vy[a] * vy[a]) + vz[a] * vz[a];
+    if (it < 0) {
+        free(a0x); free(a0y); free(a0z); free(du0); free(vsx); free(vsy); free(vsz); free(us);
+        free(apx); free(apy); free(apz);
+        return -1.0;
     }
-    if (dv_ratio) *dv_ratio = (v2 > 0.0) ? dvmax / sqrt(v2 / (double)n) : 0.0;
-    free(a0x); free(a0y); free(a0z); free(du0);
-    return orc_cfl(n, p, h, vsig, ax, ay, az);
+    const double *al = (p->av_switch && alpha) ? alpha : NULL;
+    if (al) orc_alpha_update(n, mass, p, x, y, z, vx, vy, vz, a0x, a0y, a0z, u, h, omega, dt, method, alpha);
+    double ratio = 0.0;
+    int k = 0, failed = 0;
+    for (;;) {
+        k++;
+        orc_forces_alpha(n, mass, p, x, y, z, vx, vy, vz, u, h, omega, al, method, ax, ay, az, du, vsig);
+        double errmax = 0.0, v2 = 0.0;
+        for (int64_t a = 0; a < n; a++) {
+            /* v^(k) - w^(k) = dt/2 (a^(k) - a^(k-1)), a^(0) = a^n: both start from v* */
+            double ex = 0.5 * dt * (ax[a] - apx[a]), ey = 0.5 * dt * (ay[a] - apy[a]),
+                   ez = 0.5 * dt * (az[a] - apz[a]);
+            double e = sqrt((ex * ex + ey * ey) + ez * ez);
+            if (e > errmax) errmax = e;
+            apx[a] = ax[a]; apy[a] = ay[a]; apz[a] = az[a];
+            vx[a] = vsx[a] + 0.5 * dt * (ax[a] - a0x[a]);
+            vy[a] = vsy[a] + 0.5 * dt * (ay[a] - a0y[a]);
+            vz[a] = vsz[a] + 0.5 * dt * (az[a] - a0z[a]);
+            u[a] = us[a] + 0.5 * dt * (du[a] - du0[a]);
+            v2 += (vx[a] * vx[a] + vy[a] * vy[a]) + vz[a] * vz[a];
+        }
+        ratio = (v2 > 0.0) ? errmax / sqrt(v2 / (double)n) : 0.0;
+        int fails = p->eps_v > 0.0 && !(ratio < p->eps_v);
+        if (k == 1) {
+            if (dv_ratio) *dv_ratio = ratio;
+            failed = fails;
+        }
+        if (!fails || k >= p->max_corr) break;
+    }
+    if (passes) *passes = k;
+    if (lambda) {
+        if (failed) *lambda *= 0.5;
+        else *lambda = (1.0 + p->lambda_stiff * *lambda) / (1.0 + p->lambda_stiff);
+    }
+    free(a0x); free(a0y); free(a0z); free(du0); free(vsx); free(vsy); free(vsz); free(us);
+    free(apx); free(apy); free(apz);
+    return (lambda ? *lambda : 1.0) * orc_cfl(n, p, h, vsig, ax, ay, az);
+}
+
+double orc_step(int64_t n, double mass, const orc_params *p, double dt,
+                double *x, double *y, double *z, double *vx, double *vy, double *vz, double *u, double *h,
+                double *ax, double *ay, double *az, double *du, double *rho, double *omega, double *vsig,
+                int method, int *iters, double *dv_ratio)
+{
+    orc_params q = *p;
+    q.av_switch = 0;
+    q.eps_v = 0.0;
+    return orc_step_ext(n, mass, &q, dt, x, y, z, vx, vy, vz, u, h, ax, ay, az, du, rho, omega, vsig, NULL, NULL,
+                        method, iters, dv_ratio, NULL);
 }
 
 int orc_num_threads(void)
