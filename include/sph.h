@@ -78,6 +78,15 @@ typedef struct {
                              to 1; 10 gives the 30-bit codes of the paper's u32 variant, sorted in 4
                              radix passes instead of 8.  A batch keeps the box index above
                              3 * min(morton_bits, (63 - box bits) / 3) */
+    /* Extensions of App. G (off by default: av_switch = 0, eps_v = 0 give the fixed-alpha step):  */
+    int av_switch;        /* 1: per-particle alpha_a (sph_state.alpha) evolved by the shock switch,
+                             Eq. evolalphaanalytic with its implicit step; alpha_av is alpha_max */
+    int max_corr;         /* most corrector passes per step (>= 1); 4 */
+    double alpha_min;     /* floor of alpha_loc; 0 */
+    double sigma_decay;   /* tau_a = h_a / (sigma_decay c_s,a); 0.1 */
+    double eps_v;         /* epsilon_v of Eq. cvleapfrog (the paper uses 1e-2); 0 disables the check,
+                             the corrector re-runs and the CFL multiplier */
+    double lambda_stiff;  /* lambda_stiff of the CFL multiplier relaxation; 1 */
 } sph_params;
 
 /* Particle state.  Arrays: float64[n] (id: uint32[n]).  Inputs/outputs per function below. */
@@ -93,6 +102,8 @@ typedef struct {
     double *rho, *omega;      /* density rho(h) and grad-h term Omega (outputs of density) */
     double *vsig;             /* signal speed v_sig^dt (output of forces) */
     uint32_t *id;             /* original particle index (permuted with the particles) */
+    double *alpha;            /* per-particle alpha_AV (in/out, permuted with the particles) when
+                                 params.av_switch = 1; NULL otherwise */
 } sph_state;
 
 /* Host view of the tree for sph_export_tree.  The caller allocates every non-NULL array with the
@@ -128,7 +139,9 @@ typedef struct {
     int64_t force_pairs;     /* pairs inside 2 max(h_a, h_b) in the last force call */
     double stage_ms[8];      /* with sph_set_timing(ctx, 1): accumulated device time per stage since the
                                 last sph_reset_timing: predictor, tree, neighbours, density, force
-                                preparation, force loop, corrector, unused */
+                                preparation, force loop, corrector, shock switch */
+    double cfl_multiplier;   /* lambda_CFL after the last sph_step (1 while eps_v = 0) */
+    int corrector_passes;    /* corrector passes of the last sph_step */
 } sph_stats;
 
 /* Launch shapes of the pair kernels and the tree reduction level, chosen by sph_autotune or set by

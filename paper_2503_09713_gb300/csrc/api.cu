@@ -151,7 +151,7 @@ void free_all(sph_ctx *c) {
                     c->mask[0], c->mask[1], c->scan_tmp, c->leaf_first, c->mu_leaf, c->lchild, c->rchild,
                     c->endrange, c->lflag, c->rflag, c->child, c->node_parent, c->leaf_parent, c->visit, c->nodes, c->nodesf,
                     c->gather_tmp, c->id_tmp, c->rel, c->h32, c->h_base, c->gboxf, c->grp_chunks, c->chunk_off, c->masks, c->cand, c->cand_cnt, c->nb_cnt, c->nb_ptr,
-                    c->grp_slots, c->grp_off, c->nb_ids, c->frec, c->m_v, c->m_t, c->m_r, c->a_new, c->dhdt, c->block_part,
+                    c->grp_slots, c->grp_off, c->nb_ids, c->frec, c->m_v, c->m_t, c->m_r, c->a_new, c->dhdt, c->block_part, c->rerun,
                     c->hs_fields, c->hs_id, c->dscal, c->box_of, c->box_mass, c->box_gamma, c->box_root,
                     c->box_dt, c->box_dt_next, c->gstart, c->group_box};
     for (void *p : ptrs)
@@ -170,6 +170,9 @@ int check_params(sph_ctx *c, const sph_params *p) {
         !(p->c_cour > 0) || !(p->c_force > 0) || p->alpha_av < 0 || p->beta_av < 0 || p->alpha_u < 0)
         return fail(c, SPH_ERR_INVALID_ARG, "parameter out of range");
     if (p->morton_bits < 1 || p->morton_bits > 21) return fail(c, SPH_ERR_INVALID_ARG, "morton_bits outside 1..21");
+    if ((p->av_switch != 0 && p->av_switch != 1) || p->max_corr < 1 || !(p->alpha_min >= 0) ||
+        !(p->alpha_min <= p->alpha_av) || !(p->sigma_decay >= 0) || !(p->eps_v >= 0) || !(p->lambda_stiff >= 0))
+        return fail(c, SPH_ERR_INVALID_ARG, "shock-switch / corrector parameters out of range");
     if (p->h_max_iter < 1 || p->reduction_level < 0 || p->reduction_level > 16 || p->max_outer < 1)
         return fail(c, SPH_ERR_INVALID_ARG, "iteration limits out of range");
     for (int k = 0; k < 3; k++)
@@ -189,6 +192,8 @@ int check_state(sph_ctx *c, const sph_state *s, bool need_vel) {
                      !s->omega || !s->vsig))
         return fail(c, SPH_ERR_INVALID_ARG, "v, u, a, du, rho, omega and vsig are required");
     if (c->tree_valid && s->n != c->n && need_vel) return fail(c, SPH_ERR_ORDER, "n changed since the tree build");
+    if (need_vel && c->p.av_switch && !s->alpha)
+        return fail(c, SPH_ERR_INVALID_ARG, "av_switch = 1 needs sph_state.alpha");
     return SPH_OK;
 }
 
@@ -256,6 +261,12 @@ void sph_default_params(sph_params *p) {
     p->periodic = 1;
     p->max_outer = 8;
     p->morton_bits = 21;
+    p->av_switch = 0;
+    p->max_corr = 4;
+    p->alpha_min = 0.0;
+    p->sigma_decay = 0.1;
+    p->eps_v = 0.0;
+    p->lambda_stiff = 1.0;
     for (int k = 0; k < 3; k++) {
         p->box_lo[k] = 0.0;
         p->box_hi[k] = 1.0;
@@ -320,6 +331,7 @@ int create_ctx(const sph_params *p, int64_t n_cap, int n_boxes, int64_t neigh_ca
         return SPH_ERR_OOM;
     }
     std::memset(c->hscal, 0, sizeof(DevScalars));
+    c->stats.cfl_multiplier = 1.0;
     if (cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess) {
         cudaGetLastError();
         free_all(c);
@@ -462,6 +474,10 @@ int sph_compute_forces(sph_ctx *c, sph_state *s) {
     if (r) return r;
     r = finish_forces(c);
     if (r) return r;
+    c->dt_next *= c->cfl_lambda;   // the CFL multiplier of the running step sequence
+    c->stats.dt_next = c->dt_next;
+    if (c->batch)
+        for (double &v : c->h_box_dt) v *= c->cfl_lambda;
     c->forces_valid = true;
     c->dhdt_valid = true;
     return SPH_OK;
@@ -499,18 +515,57 @@ int sph_step(sph_ctx *c, sph_state *s, double dt, double *dt_used, double *dt_ne
     // A8 density / h with the outer restart
     int iters = 0;
     if ((r = density_with_restarts(c, s, &iters, c->p.max_outer))) return r;
-    // A9 forces into a_new
-    const int64_t st = c->n_cap;
-    if ((r = forces_run(c, s, c->a_new, c->a_new + st, c->a_new + 2 * st, c->a_new + 3 * st))) return r;
-    // A10 corrector
-    if ((r = stage_begin(c, kStCorrect)) || (r = integrate_correct(c, s, dt)) || (r = stage_end(c, kStCorrect)))
+    // shock switch: alpha^{n+1} from v*, grad v*, grad a^n at the new positions and h (App. G)
+    if (c->p.av_switch &&
+        ((r = stage_begin(c, kStSwitch)) || (r = switch_run(c, s, dt)) || (r = stage_end(c, kStSwitch))))
         return r;
-    if ((r = finish_forces(c))) return r;
-    double dvm;
-    unsigned long long b = c->hscal->dv_max_bits;
-    std::memcpy(&dvm, &b, sizeof dvm);
-    const double v2 = c->hscal->v2_sum;
-    c->stats.dv_ratio = v2 > 0 ? dvm / std::sqrt(v2 / (double)s->n) : 0.0;
+    const int64_t st = c->n_cap;
+    const bool check = c->p.eps_v > 0.0;
+    if (check) {   // v*, u*, a^n, du^n for the corrector re-runs
+        if (!c->rerun && (r = alloc(c, &c->rerun, (size_t)8 * st))) return r;
+        double *src[8] = {s->vx, s->vy, s->vz, s->u, s->ax, s->ay, s->az, s->du};
+        for (int f = 0; f < 8; f++)
+            SPH_CUDA(c, cudaMemcpyAsync(c->rerun + (size_t)f * st, src[f], (size_t)s->n * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->stream));
+    }
+    // A9 forces into a_new, A10 corrector; re-runs with v* <- v^{n+1} while Eq. cvleapfrog fails
+    double ratio = 0.0;
+    bool failed = false;
+    int pass = 0;
+    for (;;) {
+        ++pass;
+        if ((r = forces_run(c, s, c->a_new, c->a_new + st, c->a_new + 2 * st, c->a_new + 3 * st))) return r;
+        if ((r = stage_begin(c, kStCorrect)) ||
+            (r = (pass == 1 ? integrate_correct(c, s, dt) : integrate_correct_again(c, s, dt))) ||
+            (r = stage_end(c, kStCorrect)))
+            return r;
+        if ((r = finish_forces(c))) return r;
+        double dvm;
+        unsigned long long b = c->hscal->dv_max_bits;
+        std::memcpy(&dvm, &b, sizeof dvm);
+        const double v2 = c->hscal->v2_sum;
+        ratio = v2 > 0 ? dvm / std::sqrt(v2 / (double)s->n) : 0.0;
+        const bool fails = check && !(ratio < c->p.eps_v);
+        if (pass == 1) {
+            c->stats.dv_ratio = ratio;
+            failed = fails;
+        }
+        if (!fails || pass >= c->p.max_corr) break;
+    }
+    c->corr_passes = pass;
+    // CFL multiplier: halved in a step whose first pass failed, else relaxed towards 1
+    if (check) {
+        if (failed) c->cfl_lambda *= 0.5;
+        else c->cfl_lambda = (1.0 + c->p.lambda_stiff * c->cfl_lambda) / (1.0 + c->p.lambda_stiff);
+    } else {
+        c->cfl_lambda = 1.0;
+    }
+    c->dt_next *= c->cfl_lambda;
+    c->stats.dt_next = c->dt_next;
+    if (c->batch)
+        for (double &v : c->h_box_dt) v *= c->cfl_lambda;
+    c->stats.cfl_multiplier = c->cfl_lambda;
+    c->stats.corrector_passes = pass;
     c->forces_valid = true;
     c->dhdt_valid = true;
     if (dt_used) *dt_used = dt;

@@ -36,8 +36,8 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
                              const double *__restrict__ z, const double *__restrict__ vx,
                              const double *__restrict__ vy, const double *__restrict__ vz,
                              const double *__restrict__ u, const double *__restrict__ h,
-                             const double *__restrict__ rho, const double *__restrict__ omega, ForceParams fp,
-                             int mixed, FRec *__restrict__ rec, float4 *__restrict__ m_v, float4 *__restrict__ m_t,
+                             const double *__restrict__ rho, const double *__restrict__ omega,
+                             const double *__restrict__ alpha, ForceParams fp, int mixed, FRec *__restrict__ rec, float4 *__restrict__ m_v, float4 *__restrict__ m_t,
                              float4 *__restrict__ m_r, float *__restrict__ h32) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -49,7 +49,8 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
         const float qf = 1.f / (r * om);
         const float hinvf = 1.f / (float)h[i];
         m_v[i] = make_float4((float)vx[i], (float)vy[i], (float)vz[i], hinvf);
-        m_t[i] = make_float4((g - 1.f) * ui * qf, qf, (float)fp.alpha_av * sqrtf(g * (g - 1.f) * ui),
+        const float al = (float)(alpha ? alpha[i] : fp.alpha_av);
+        m_t[i] = make_float4((g - 1.f) * ui * qf, qf, al * sqrtf(g * (g - 1.f) * ui),
                              (g - 1.f) * r * ui);
         m_r[i] = make_float4(r, ui, hinvf * hinvf * hinvf * hinvf * (float)fp.kern_c, 0.f);
     } else {
@@ -60,7 +61,8 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
         FRec f;
         f.x = x[i]; f.y = y[i]; f.z = z[i]; f.h = hi;
         f.vx = vx[i]; f.vy = vy[i]; f.vz = vz[i]; f.u = ui;
-        f.pre = (gam - 1.0) * ui * qf; f.qf = qf; f.acs = fp.alpha_av * sqrt(gam * (gam - 1.0) * ui);
+        f.pre = (gam - 1.0) * ui * qf; f.qf = qf;
+        f.acs = (alpha ? alpha[i] : fp.alpha_av) * sqrt(gam * (gam - 1.0) * ui);
         f.P = (gam - 1.0) * r * ui;
         f.rho = r; f.hinv = hinv; f.fn = hinv * hinv * hinv * hinv * fp.kern_c; f.pad = 0.0;
         rec[i] = f;
@@ -343,7 +345,8 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     if (r) return r;
     if ((r = stage_begin(c, kStForcePrep))) return r;
     k_force_prep<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->h,
-                                                           s->rho, s->omega, fp, mixed, (FRec *)c->frec, c->m_v,
+                                                           s->rho, s->omega, c->p.av_switch ? s->alpha : nullptr,
+                                                           fp, mixed, (FRec *)c->frec, c->m_v,
                                                            c->m_t, c->m_r, c->h32);
     SPH_LAUNCH_CHECK(c, "k_force_prep");
     k_reset_dt<<<1, 32, 0, c->stream>>>(c->dscal, fp.box_dt_next, c->n_boxes);

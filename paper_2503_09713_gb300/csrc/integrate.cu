@@ -108,6 +108,56 @@ __global__ void k_correct(int64_t n, double *__restrict__ vx, double *__restrict
     }
 }
 
+// Corrector pass k > 1 (App. G: the acceleration recomputed with v* <- v^{n+1}): from the saved
+// v*, u*, a^n, du^n of the step, v^(k) = v* + dt/2 (a^(k) - a^n), likewise u; the change from the
+// previous pass, |v^(k) - v^(k-1)| = dt/2 |a^(k) - a^(k-1)|, and |v^(k)|^2 feed the check of
+// Eq. cvleapfrog as in the first pass.  a, du take a^(k), du^(k).
+__global__ void k_correct_again(int64_t n, double *__restrict__ vx, double *__restrict__ vy,
+                                double *__restrict__ vz, double *__restrict__ u, double *__restrict__ ax,
+                                double *__restrict__ ay, double *__restrict__ az, double *__restrict__ du,
+                                const double *__restrict__ anew, int64_t stride, const double *__restrict__ save,
+                                double dt, const double *__restrict__ box_dt, const uint16_t *__restrict__ box_of,
+                                DevScalars *sc, double *__restrict__ block_part) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float dv = 0.f, v2 = 0.f;
+    if (i < n) {
+        const double hdt = 0.5 * (box_dt ? box_dt[box_of[i]] : dt);
+        const double nax = anew[i], nay = anew[stride + i], naz = anew[2 * stride + i], ndu = anew[3 * stride + i];
+        const double ex = hdt * (nax - ax[i]), ey = hdt * (nay - ay[i]), ez = hdt * (naz - az[i]);
+        const double wx = save[i] + hdt * (nax - save[4 * stride + i]);
+        const double wy = save[stride + i] + hdt * (nay - save[5 * stride + i]);
+        const double wz = save[2 * stride + i] + hdt * (naz - save[6 * stride + i]);
+        vx[i] = wx;
+        vy[i] = wy;
+        vz[i] = wz;
+        u[i] = save[3 * stride + i] + hdt * (ndu - save[7 * stride + i]);
+        ax[i] = nax;
+        ay[i] = nay;
+        az[i] = naz;
+        du[i] = ndu;
+        const float fx = (float)ex, fy = (float)ey, fz = (float)ez;
+        const float gx = (float)wx, gy = (float)wy, gz = (float)wz;
+        dv = sqrtf(fx * fx + fy * fy + fz * fz);
+        v2 = gx * gx + gy * gy + gz * gz;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dv = fmaxf(dv, __shfl_xor_sync(0xffffffffu, dv, o));
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+    }
+    __shared__ double part[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        part[warp] = (double)v2;
+        if (dv > 0.f) atomicMax(&sc->dv_max_bits, dbits((double)dv));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += part[w];
+        block_part[blockIdx.x] = s;
+    }
+}
+
 // Deterministic sum of the per-block partials (one block).
 __global__ void k_sum_parts(const double *__restrict__ part, int64_t m, double *out) {
     __shared__ double sh[256];
@@ -151,6 +201,21 @@ int integrate_correct(sph_ctx *c, sph_state *s, double dt) {
                                              c->n_cap, dt, c->batch ? c->box_dt : nullptr,
                                              c->batch ? c->box_of : nullptr, c->dscal, c->block_part);
     SPH_LAUNCH_CHECK(c, "k_correct");
+    k_sum_parts<<<1, 256, 0, c->stream>>>(c->block_part, blocks, &c->dscal->v2_sum);
+    SPH_LAUNCH_CHECK(c, "k_sum_parts");
+    return SPH_OK;
+}
+
+int integrate_correct_again(sph_ctx *c, sph_state *s, double dt) {
+    const int64_t n = s->n;
+    const unsigned blocks = grid_for(n, 256);
+    k_reset_dv<<<1, 1, 0, c->stream>>>(c->dscal);
+    SPH_LAUNCH_CHECK(c, "k_reset_dv");
+    k_correct_again<<<blocks, 256, 0, c->stream>>>(n, s->vx, s->vy, s->vz, s->u, s->ax, s->ay, s->az, s->du,
+                                                   c->a_new, c->n_cap, c->rerun, dt,
+                                                   c->batch ? c->box_dt : nullptr, c->batch ? c->box_of : nullptr,
+                                                   c->dscal, c->block_part);
+    SPH_LAUNCH_CHECK(c, "k_correct_again");
     k_sum_parts<<<1, 256, 0, c->stream>>>(c->block_part, blocks, &c->dscal->v2_sum);
     SPH_LAUNCH_CHECK(c, "k_sum_parts");
     return SPH_OK;

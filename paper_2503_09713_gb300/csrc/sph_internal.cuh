@@ -207,6 +207,9 @@ struct sph_ctx {
     double *dhdt = nullptr;            // [n_cap] dh/dt from the last force pass (Morton order of the state)
     bool dhdt_valid = false;
     double *block_part = nullptr;      // per-block partial sums
+    double *rerun = nullptr;           // [8][n_cap] v*, u*, a^n, du^n of the step (corrector re-runs)
+    double cfl_lambda = 1.0;           // CFL multiplier lambda_CFL (App. G)
+    int corr_passes = 0;               // corrector passes of the last step
     bool density_valid = false;
     bool forces_valid = false;
 
@@ -270,6 +273,8 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale);
 int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, double *du);
 int integrate_predict(sph_ctx *c, sph_state *s, double dt, const double *dhdt);
 int integrate_correct(sph_ctx *c, sph_state *s, double dt);
+int integrate_correct_again(sph_ctx *c, sph_state *s, double dt);   // corrector re-run from v*, u*
+int switch_run(sph_ctx *c, sph_state *s, double dt);               // shock-switch step of alpha
 int read_scalars(sph_ctx *c);
 Groups make_groups(const sph_ctx *c);
 int ensure_groups(sph_ctx *c, int64_t G);   // grow the per-group arrays to G groups
@@ -277,7 +282,8 @@ int ensure_tree(sph_ctx *c, int64_t L);     // grow the leaf- and node-indexed a
 int ensure_force_records(sph_ctx *c);       // force records of the current precision
 // Per-stage timing: stage_begin/stage_end bracket the launches of one stage on the context stream;
 // with timing on, stage_end waits for the stage and adds its duration to stats.stage_ms[k].
-enum Stage { kStPredict = 0, kStTree, kStNeigh, kStDensity, kStForcePrep, kStForces, kStCorrect, kStCount };
+enum Stage { kStPredict = 0, kStTree, kStNeigh, kStDensity, kStForcePrep, kStForces, kStCorrect, kStSwitch,
+             kStCount };
 int stage_begin(sph_ctx *c, int k);
 int stage_end(sph_ctx *c, int k);
 int exclusive_scan_i64(sph_ctx *c, const int64_t *in, int64_t *out, int64_t n);  // out[n] = total

@@ -624,8 +624,8 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
     c->perm = c->vals[buf];
 
     // reorder the particle arrays, kGatherBatch fields per pass through the scratch block
-    const double *fields[16];
-    double *fields_dst[16];
+    const double *fields[18];
+    double *fields_dst[18];
     const double *all[15] = {s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->h, s->ax, s->ay, s->az, s->du,
                              s->rho, s->omega, s->vsig};
     const int nf_all = gather_outputs ? 15 : 12;
@@ -633,6 +633,7 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
     for (int f = 0; f < nf_all; f++)
         if (all[f]) fields[nf++] = all[f];
     if (c->dhdt_valid) fields[nf++] = c->dhdt;   // dh/dt of the last force pass travels with its particles
+    if (s->alpha) fields[nf++] = s->alpha;       // per-particle alpha of the shock switch
     for (int f = 0; f < nf; f++) fields_dst[f] = const_cast<double *>(fields[f]);
     for (int f0 = 0; f0 < nf || (f0 == 0 && s->id); f0 += kGatherBatch) {
         GatherArgs g{};

@@ -43,11 +43,12 @@ class sph_params(ctypes.Structure):
                 ("beta_av", _d), ("alpha_u", _d), ("c_cour", _d), ("c_force", _d), ("h_tol", _d),
                 ("h_clamp", _d), ("cache_tol", _d), ("h_max_iter", _i), ("reduction_level", _i),
                 ("periodic", _i), ("max_outer", _i), ("box_lo", _d * 3), ("box_hi", _d * 3),
-                ("morton_bits", _i)]
+                ("morton_bits", _i), ("av_switch", _i), ("max_corr", _i), ("alpha_min", _d),
+                ("sigma_decay", _d), ("eps_v", _d), ("lambda_stiff", _d)]
 
 
 class sph_state(ctypes.Structure):
-    _fields_ = [("n", _i64), ("mass", _d)] + [(f, _p) for f in FIELDS] + [("id", _p)]
+    _fields_ = [("n", _i64), ("mass", _d)] + [(f, _p) for f in FIELDS] + [("id", _p), ("alpha", _p)]
 
 
 class sph_tree_view(ctypes.Structure):
@@ -59,14 +60,15 @@ class sph_stats(ctypes.Structure):
     _fields_ = [("n", _i64), ("n_leaves", _i64), ("n_groups", _i64), ("n_pairs", _i64), ("cache_slots", _i64),
                 ("cand_chunks", _i64),
                 ("density_iters_max", _i), ("outer_passes", _i), ("n_red", _i), ("dt_next", _d), ("dv_ratio", _d),
-                ("kernel_launches", _i64), ("density_pair_evals", _i64), ("density_inrange", _i64), ("force_pairs", _i64), ("stage_ms", _d * 8)]
+                ("kernel_launches", _i64), ("density_pair_evals", _i64), ("density_inrange", _i64), ("force_pairs", _i64), ("stage_ms", _d * 8),
+                ("cfl_multiplier", _d), ("corrector_passes", _i)]
 
 class sph_launch(ctypes.Structure):
     _fields_ = [("density_block", _i), ("forces_block", _i), ("walk_block", _i), ("stage2_warps", _i),
                 ("reduction_level", _i)]
 
 
-STAGES = ("predict", "tree", "neighbours", "density", "force_prep", "forces", "correct")
+STAGES = ("predict", "tree", "neighbours", "density", "force_prep", "forces", "correct", "switch")
 
 
 class SPHError(RuntimeError):
@@ -279,20 +281,23 @@ def sph_export_neighbours(ctx, n: int, n_pairs: int):
 
 # ---------------------------------------------------------------- device state (PyTorch memory)
 class DeviceState:
-    """Particle arrays as float64 CUDA tensors (id: int32 holding the uint32 original index)."""
+    """Particle arrays as float64 CUDA tensors (id: int32 holding the uint32 original index; alpha:
+    per-particle viscosity for the shock switch, present only when requested)."""
 
-    def __init__(self, n: int, mass: float, device: str = "cuda"):
+    def __init__(self, n: int, mass: float, device: str = "cuda", alpha: bool = False):
         import torch
         self.n = int(n)
         self.mass = float(mass)
         self.t = {f: torch.zeros(self.n, dtype=torch.float64, device=device) for f in FIELDS}
         self.t["id"] = torch.arange(self.n, dtype=torch.int32, device=device)
+        if alpha:
+            self.t["alpha"] = torch.ones(self.n, dtype=torch.float64, device=device)
 
     @classmethod
     def from_numpy(cls, d: dict, device: str = "cuda"):
         import torch
-        s = cls(len(d["x"]), d["mass"], device)
-        for f in FIELDS:
+        s = cls(len(d["x"]), d["mass"], device, alpha="alpha" in d)
+        for f in FIELDS + ("alpha",):
             if f in d:
                 s.t[f].copy_(torch.from_numpy(np.ascontiguousarray(d[f], dtype=np.float64)))
         return s
@@ -300,18 +305,24 @@ class DeviceState:
     def to_numpy(self) -> dict:
         out = {f: self.t[f].cpu().numpy() for f in FIELDS}
         out["id"] = self.t["id"].cpu().numpy().view(np.uint32)
+        if "alpha" in self.t:
+            out["alpha"] = self.t["alpha"].cpu().numpy()
         out["mass"] = self.mass
         return out
 
     def c(self) -> sph_state:
-        return sph_state(self.n, self.mass, *[self.t[f].data_ptr() for f in FIELDS], self.t["id"].data_ptr())
+        return sph_state(self.n, self.mass, *[self.t[f].data_ptr() for f in FIELDS], self.t["id"].data_ptr(),
+                         self.t["alpha"].data_ptr() if "alpha" in self.t else None)
 
 
 def host_state(d: dict) -> tuple:
     """sph_state over host numpy arrays (kept alive by the returned dict) for sph_step_host."""
     arrs = {f: np.ascontiguousarray(d[f], dtype=np.float64) for f in FIELDS}
     arrs["id"] = np.ascontiguousarray(d.get("id", np.arange(len(arrs["x"]))), dtype=np.uint32)
-    st = sph_state(len(arrs["x"]), float(d["mass"]), *[arrs[f].ctypes.data for f in FIELDS], arrs["id"].ctypes.data)
+    if "alpha" in d:
+        arrs["alpha"] = np.ascontiguousarray(d["alpha"], dtype=np.float64)
+    st = sph_state(len(arrs["x"]), float(d["mass"]), *[arrs[f].ctypes.data for f in FIELDS], arrs["id"].ctypes.data,
+                   arrs["alpha"].ctypes.data if "alpha" in arrs else None)
     return st, arrs
 
 
