@@ -27,6 +27,11 @@ SPH_ERR_CUDA = -7
 SPH_ERR_ORDER = -8
 SPH_ERR_NONFINITE = -9
 SPH_KERNEL_M4 = 0
+SPH_KERNEL_M5 = 1
+SPH_KERNEL_M6 = 2
+SPH_KERNEL_C2 = 3
+SPH_KERNEL_C4 = 4
+SPH_KERNEL_C6 = 5
 SPH_FP64 = 0
 SPH_MIXED = 1
 

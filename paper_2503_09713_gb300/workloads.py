@@ -14,6 +14,16 @@ Recipes (numpy PCG64; seed = 12345 + workload index unless given):
     set-up (Sect. 4.4 and Sect. 5.1.2) on a cubic instead of a close-packed lattice.
   * ``ensemble``: independent boxes with N_b = round(exp(U(ln 2048, ln 262144))), side
     round(N_b^(1/3)), sigma ~ U[0.01, 0.3], gamma in {5/3, 7/5}; box b uses seed + 1000 b.
+  * ``sod_tube``: the Sod tube of the paper's validation (Sect. 4): periodic box x in [-0.5, 1.5),
+    left state rho = 1, P = 1 on a close-packed (face-centred cubic) lattice in x < 0.5, right state
+    rho = 1/8, P = 0.1 on the same lattice with twice the spacing in x >= 0.5, equal masses, v = 0,
+    gamma = 1.4 (u = P / ((gamma-1) rho)).  (On simple cubic lattices the contact sustains a spurious
+    pressure jump: the left star density comes out 18% high.)
+  * ``advection_step``: the density step of the paper's advection test: rho = 1 for
+    0.25 <= x < 0.75 (lattice spacing dx) and 1/8 elsewhere (spacing 2 dx), uniform P, v_x = 1.
+  * ``fcc_lattice``: face-centred cubic (close-packed) lattice of n^3 cells x 4 particles in the
+    periodic unit box, v = 0, u = 1; the paper's validation runs use close-packed lattices, which,
+    unlike the simple cubic one, are stable SPH equilibria.
 """
 from __future__ import annotations
 
@@ -90,3 +100,77 @@ def perfect_lattice(n_side: int, hfact: float = 1.2, h_scale: float = 1.0) -> di
     s = lattice(n_side, sigma_v=0.0, u0=1.0, jitter=0.0, hfact=hfact)
     s["h"] = s["h"] * h_scale
     return s
+
+
+def _block(nx: int, ny: int, x0: float, dx: float) -> list:
+    """Cubic lattice of nx x ny x ny points, spacing dx, starting at x0 along x and 0 along y, z."""
+    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(ny), indexing="ij")
+    return [x0 + (ix.reshape(-1) + 0.5) * dx, (iy.reshape(-1) + 0.5) * dx, (iz.reshape(-1) + 0.5) * dx]
+
+
+def _fcc_block(ncx: int, ncy: int, x0: float, a: float) -> list:
+    """Face-centred cubic lattice of ncx x ncy x ncy cells of side a (4 particles per cell), from x0
+    along x and 0 along y, z."""
+    base = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]]) + 0.25
+    ix, iy, iz = np.meshgrid(np.arange(ncx), np.arange(ncy), np.arange(ncy), indexing="ij")
+    cells = np.stack([ix.reshape(-1), iy.reshape(-1), iz.reshape(-1)], axis=1).astype(np.float64)
+    pos = ((cells[:, None, :] + base[None, :, :]) * a).reshape(-1, 3)
+    return [pos[:, 0] + x0, pos[:, 1].copy(), pos[:, 2].copy()]
+
+
+def sod_tube(nc: int = 64, ncy: int = 6, gamma: float = 1.4, hfact: float = 1.0) -> dict:
+    """Sod shock tube in the periodic box [-0.5, 1.5) x [0, ncy/nc)^2 on close-packed (face-centred
+    cubic) lattices: nc x ncy x ncy cells of side 1/nc on the left (2 nc particle planes per unit
+    length), cells of twice the side on the right (ncy even); equal masses."""
+    a = 1.0 / nc
+    left = _fcc_block(nc, ncy, -0.5, a)
+    right = _fcc_block(nc // 2, ncy // 2, 0.5, 2 * a)
+    out = {k: np.concatenate([p, q]) for k, p, q in zip(("x", "y", "z"), left, right)}
+    nl, nr = len(left[0]), len(right[0])
+    n = nl + nr
+    spacing = a / 4 ** (1.0 / 3.0)
+    out["u"] = np.concatenate([np.full(nl, 1.0 / ((gamma - 1.0) * 1.0)), np.full(nr, 0.1 / ((gamma - 1.0) * 0.125))])
+    out["h"] = np.concatenate([np.full(nl, hfact * spacing), np.full(nr, 2 * hfact * spacing)])
+    for k in ("vx", "vy", "vz"):
+        out[k] = np.zeros(n)
+    out.update(mass=a ** 3 / 4, n=n, dx=spacing, gamma=gamma, box_lo=(-0.5, 0.0, 0.0),
+               box_hi=(1.5, ncy * a, ncy * a))
+    return out
+
+
+def advection_step(nx: int = 32, ny: int = 8, hfact: float = 1.2, vx: float = 1.0) -> dict:
+    """Density step advected through the periodic box [0, 1) x [0, ny/nx)^2 (uniform pressure)."""
+    dx = 1.0 / nx
+    a = _block(nx // 8, ny // 2, 0.0, 2 * dx)          # x in [0, 0.25): rho = 1/8
+    b = _block(nx // 2, ny, 0.25, dx)                  # x in [0.25, 0.75): rho = 1
+    c = _block(nx // 8, ny // 2, 0.75, 2 * dx)         # x in [0.75, 1): rho = 1/8
+    out = {k: np.concatenate([p, q, r]) for k, p, q, r in zip(("x", "y", "z"), a, b, c)}
+    na, nb, nc = len(a[0]), len(b[0]), len(c[0])
+    n = na + nb + nc
+    out["u"] = np.concatenate([np.full(na, 8.0), np.full(nb, 1.0), np.full(nc, 8.0)])   # P = (gamma-1) rho u uniform
+    out["h"] = np.concatenate([np.full(na, 2 * hfact * dx), np.full(nb, hfact * dx), np.full(nc, 2 * hfact * dx)])
+    out["vx"] = np.full(n, vx)
+    out["vy"] = np.zeros(n)
+    out["vz"] = np.zeros(n)
+    out.update(mass=dx ** 3, n=n, dx=dx, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, ny * dx, ny * dx))
+    return out
+
+
+def fcc_lattice(n_cells: int, hfact: float = 1.2, u0: float = 1.0) -> dict:
+    """Close-packed (face-centred cubic) lattice: cell side a = 1/n_cells, 4 particles per cell at
+    (0,0,0), (1/2,1/2,0), (1/2,0,1/2), (0,1/2,1/2) a (+ a/4 to keep them off the box faces)."""
+    a = 1.0 / n_cells
+    base = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]]) + 0.25
+    ix, iy, iz = np.meshgrid(np.arange(n_cells), np.arange(n_cells), np.arange(n_cells), indexing="ij")
+    cells = np.stack([ix.reshape(-1), iy.reshape(-1), iz.reshape(-1)], axis=1).astype(np.float64)
+    pos = ((cells[:, None, :] + base[None, :, :]) * a).reshape(-1, 3)
+    n = len(pos)
+    spacing = a / 4 ** (1.0 / 3.0)   # (volume per particle)^(1/3)
+    out = {"x": pos[:, 0].copy(), "y": pos[:, 1].copy(), "z": pos[:, 2].copy()}
+    for k in ("vx", "vy", "vz"):
+        out[k] = np.zeros(n)
+    out["u"] = np.full(n, float(u0))
+    out["h"] = np.full(n, hfact * spacing)
+    out.update(mass=1.0 / n, n=n, dx=spacing)
+    return out
+
