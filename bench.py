@@ -141,10 +141,11 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------------- GPU arm
 def run_precision(torch, sph, w, precision: int, steps: int, warmup: int, dist, timing_pass: bool,
-                  clocks: ClockSampler | None, morton_bits: int = 21):
+                  clocks: ClockSampler | None, morton_bits: int = 21, graph: bool = True):
     p = sph.default_params(precision=precision, morton_bits=morton_bits)
     s = sph.DeviceState.from_numpy(w)
     solver = sph.Solver(p, w["n"])
+    solver.set_graph(graph)           # each step replayed as one captured graph after the first
     solver.converge(s)
     shape, _ = solver.autotune(s)     # launch shapes and reduction level, before the warm-up
     for _ in range(warmup):
@@ -171,6 +172,8 @@ def run_precision(torch, sph, w, precision: int, steps: int, warmup: int, dist, 
     ms = e0.elapsed_time(e1) / steps
     st = solver.stats()
     launches = (st["kernel_launches"] - launches0) / steps
+    if graph and st["graph_replays"] < steps:
+        raise RuntimeError(f"graph replay expected in the timed steps: {st}")
     out = {"ms_per_step": ms, "wall_ms_per_step": 1e3 * t_wall / steps, "launches_per_step": launches,
            "clocks": clk, "stats": st, "launch": shape}
     if timing_pass:
@@ -188,7 +191,7 @@ def run_precision(torch, sph, w, precision: int, steps: int, warmup: int, dist, 
     return out
 
 
-def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349) -> dict:
+def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349, graph: bool = True) -> dict:
     """Ensemble workload: 256 independent periodic boxes, N_b log-uniform in [2048, 262144], sigma_v
     U[0.01, 0.3], gamma in {5/3, 7/5}, mixed precision, one context for all boxes (one launch per
     stage), every box advanced by its own CFL step."""
@@ -202,6 +205,7 @@ def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349) -> dict
     gam = np.array([b["gamma"] for b in boxes])
     s = sph.DeviceState.from_numpy(cat)
     solver = sph.Solver.batch(sph.default_params(precision=sph.SPH_MIXED), off, mass, gam)
+    solver.set_graph(graph)
     solver.converge(s)
     shape, _ = solver.autotune(s)
     for _ in range(warmup):
@@ -218,6 +222,7 @@ def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349) -> dict
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     st = solver.stats()
+    replays, fallbacks = st["graph_replays"], st["graph_fallbacks"]
     solver.set_timing(True)
     solver.reset_timing()
     solver.step(s)
@@ -227,7 +232,9 @@ def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349) -> dict
     return {"value": n / (ms * 1e-3), "unit": "particles/s", "ms_per_step": ms, "boxes": len(boxes), "particles": n,
             "smallest_box": int(min(b["n"] for b in boxes)), "largest_box": int(max(b["n"] for b in boxes)),
             "dtype": "f32 pair sums (Kahan) / f64 state", "launches_per_step": (st["kernel_launches"] - l0) / steps,
-            "timing": "per-box CFL steps, one context, one launch per stage for all boxes", "stage_ms": stage,
+            "timing": "per-box CFL steps, one context, one launch per stage for all boxes"
+                      + (", each step replayed as one captured CUDA graph" if graph else ""), "stage_ms": stage,
+            "graph": graph, "graph_replays": replays, "graph_fallbacks": fallbacks,
             "density_iters_max": st["density_iters_max"], "outer_passes": st["outer_passes"],
             "cache_pairs": st["n_pairs"], "stage2_chunks": st["cand_chunks"], "launch": shape}
 
@@ -296,6 +303,8 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--morton-bits", type=int, default=21,
                     help="bits per axis of the Morton codes (21: 63-bit codes; 10: the 30-bit u32 variant)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="run every step stage by stage instead of replaying it as one captured CUDA graph")
     ap.add_argument("--only", choices=["fp64", "mixed", "ensemble"], default=None,
                     help="run one precision only (profiling); the headline needs both")
     args = ap.parse_args()
@@ -345,16 +354,20 @@ def main():
     w = make_workload(args.workload, rank)
     n = w["n"]
     clocks = ClockSampler(local)
+    graph = not args.no_graph
     if args.only == "ensemble":
-        print(json.dumps({"workload": "ensemble", **run_ensemble(torch, sph, args.steps, max(args.warmup, 3))}))
+        print(json.dumps({"workload": "ensemble", **run_ensemble(torch, sph, args.steps, max(args.warmup, 3),
+                                                                 graph=graph)}))
         return
     if args.only == "mixed":
-        r = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, clocks, args.morton_bits)
+        r = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, clocks, args.morton_bits,
+                          graph)
         print(json.dumps({"workload": args.workload, "precision": "mixed", "ms_per_step": r["ms_per_step"],
                           "particles_per_s": n / (r["ms_per_step"] * 1e-3), "stage_ms": r["stage_ms"]}))
         r["solver"].close()
         return
-    r64 = run_precision(torch, sph, w, 0, args.steps, max(args.warmup, 3), dist, True, clocks, args.morton_bits)
+    r64 = run_precision(torch, sph, w, 0, args.steps, max(args.warmup, 3), dist, True, clocks, args.morton_bits,
+                        graph)
     from paper_2503_09713_gb300 import replicas
     ms = replicas.max_over_ranks(r64["ms_per_step"], dist, "cuda")
     value = replicas.sum_over_ranks(n, dist, "cuda") / (ms * 1e-3)
@@ -382,6 +395,7 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "particles": n,
                        "parallelism": f"replicas x{world}" if world > 1 else "single box",
+                       "graph": "each step replayed as one captured CUDA graph" if graph else "stage by stage",
                        "l2": f"inputs larger than L2 (state {16 * 8 * n / 1e9:.1f} GB, neighbour cache "
                              f"{4 * st['cache_slots'] / 1e9:.1f} GB per replica; L2 0.13 GB)",
                        "leaves": st["n_leaves"], "cache_pairs": st["n_pairs"],
@@ -392,7 +406,8 @@ def main():
             "roofline": roofline, "launch": r64["launch"]}
 
     if not args.no_mixed and args.only != "fp64":
-        r32 = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, None, args.morton_bits)
+        r32 = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, None, args.morton_bits,
+                            graph)
         ms32 = r32["ms_per_step"]
         st32 = r32["timing_stats"]
         f32 = st32["n_pairs"] * FLOP_FORCE32_CAND + st32["force_pairs"] * FLOP_FORCE32_PAIR
@@ -409,7 +424,7 @@ def main():
         r32["solver"].close()
 
     if not args.no_ensemble and args.only is None:
-        line["ensemble"] = run_ensemble(torch, sph, args.steps, max(args.warmup, 3))
+        line["ensemble"] = run_ensemble(torch, sph, args.steps, max(args.warmup, 3), graph=graph)
 
     if not args.no_e2e:
         t, h2d, d2h = e2e_run(torch, sph, r64["solver"], r64["state"], args.steps)

@@ -142,6 +142,9 @@ typedef struct {
                                 preparation, force loop, corrector, shock switch */
     double cfl_multiplier;   /* lambda_CFL after the last sph_step (1 while eps_v = 0) */
     int corrector_passes;    /* corrector passes of the last sph_step */
+    int64_t graph_replays;   /* sph_step calls replayed as a captured graph (sph_set_graph) */
+    int64_t graph_captures;  /* graphs captured */
+    int64_t graph_fallbacks; /* replays finished stage by stage (a capacity grew or h left the cache) */
 } sph_stats;
 
 /* Launch shapes of the pair kernels and the tree reduction level, chosen by sph_autotune or set by
@@ -270,6 +273,19 @@ int sph_set_timing(sph_ctx *ctx, int enable);
 
 /* Zero the accumulated stage times. */
 int sph_reset_timing(sph_ctx *ctx);
+
+/* Enable (1) or disable (0) graph replay of sph_step.  When enabled, a step whose context and state
+ * are unchanged since the last step that ran stage by stage (same state pointers, n, parameters,
+ * launch shapes and array capacities) is recorded once into a CUDA graph (captured on a private
+ * stream) and then replayed on the context stream: every stage is one launch with its grid sized by
+ * the capacity of the leaf- and group-indexed arrays, the leaf, group, candidate-chunk and cache
+ * counts stay on the device, and the host reads the step's scalars back once, at the end.  A stage
+ * whose input an earlier stage left incomplete (a count above its capacity, a full candidate list or
+ * cache, h at the cache limit) does nothing; the host then finishes that step stage by stage (the
+ * arrays grow, the outer density loop runs) and the next step captures again
+ * (sph_stats.graph_fallbacks).  Results are bit-identical to the stage-by-stage step.  Ignored while
+ * per-stage timing is on.  Errors: INVALID_ARG (ctx NULL). */
+int sph_set_graph(sph_ctx *ctx, int enable);
 
 /* Morton codes and stable sort without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc/cudaFree -- an application whose device

@@ -13,6 +13,7 @@ int64_t scan_scratch_elems(int64_t n);
 
 // Grow a set of device arrays to new byte sizes (contents not kept); on failure all are freed.
 static int regrow(sph_ctx *c, void **const *ptrs, const size_t *bytes, size_t count, const char *what) {
+    ++c->gen;   // a captured step holds the old pointers
     for (size_t k = 0; k < count; k++) {
         if (*ptrs[k]) SPH_CUDA(c, cudaFree(*ptrs[k]));
         *ptrs[k] = nullptr;
@@ -33,7 +34,7 @@ static int regrow(sph_ctx *c, void **const *ptrs, const size_t *bytes, size_t co
 // Arrays indexed by leaf or node (their number L is known only after the compaction of A4).
 int ensure_tree(sph_ctx *c, int64_t L) {
     if (L <= c->l_cap) return SPH_OK;
-    const int64_t cap = L + L / 4 + 64;
+    const int64_t cap = std::min(L + L / 4 + 64, c->n_cap);   // L <= n
     void **ptrs[] = {(void **)&c->lchild, (void **)&c->rchild, (void **)&c->endrange, (void **)&c->lflag,
                      (void **)&c->rflag, (void **)&c->child, (void **)&c->node_parent, (void **)&c->leaf_parent,
                      (void **)&c->visit, (void **)&c->nodes, (void **)&c->nodesf};
@@ -106,7 +107,7 @@ Groups make_groups(const sph_ctx *c) {
 // margin, contents not kept.
 int ensure_groups(sph_ctx *c, int64_t G) {
     if (G <= c->g_cap) return SPH_OK;
-    const int64_t cap = G + G / 4 + 64;
+    const int64_t cap = std::min(G + G / 4 + 64, c->n_cap);   // G <= n
     void **ptrs[] = {(void **)&c->gboxf, (void **)&c->grp_chunks, (void **)&c->chunk_off,
                      (void **)&c->cand, (void **)&c->cand_cnt, (void **)&c->grp_slots, (void **)&c->grp_off,
                      (void **)&c->gstart, (void **)&c->group_box};
@@ -123,9 +124,15 @@ int ensure_groups(sph_ctx *c, int64_t G) {
 
 int read_scalars(sph_ctx *c) {
     SPH_CUDA(c, cudaMemcpyAsync(c->hscal, c->dscal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    if (c->batch)   // per-box CFL minima of the last force pass, in the same synchronisation
+        SPH_CUDA(c, cudaMemcpyAsync(c->h_dt_bits, c->box_dt_next, (size_t)c->n_boxes * 8, cudaMemcpyDeviceToHost,
+                                    c->stream));
     SPH_CUDA(c, cudaStreamSynchronize(c->stream));
     return SPH_OK;
 }
+
+Count leaf_count(sph_ctx *c) { return Count{&c->dscal->n_leaves, c->l_cap, &c->dscal->flags, abort_word(c)}; }
+Count group_count(sph_ctx *c) { return Count{&c->dscal->n_groups, c->g_cap, &c->dscal->flags, abort_word(c)}; }
 
 }  // namespace sph
 
@@ -157,6 +164,10 @@ void free_all(sph_ctx *c) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hscal) cudaFreeHost(c->hscal);
+    if (c->h_dt) cudaFreeHost(c->h_dt);
+    if (c->h_dt_bits) cudaFreeHost(c->h_dt_bits);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
 }
@@ -197,35 +208,41 @@ int check_state(sph_ctx *c, const sph_state *s, bool need_vel) {
     return SPH_OK;
 }
 
-int finish_forces(sph_ctx *c) {
-    int r = read_scalars(c);
-    if (r) return r;
+// Host side of a finished force pass, from the scalars read back: CFL step (per box in a batch),
+// pair count, timeout flag.
+int absorb_forces(sph_ctx *c) {
     double dt;
     unsigned long long b = c->hscal->dt_min_bits;
     std::memcpy(&dt, &b, sizeof dt);
     c->dt_next = dt;
     c->stats.dt_next = dt;
     c->stats.force_pairs = (int64_t)c->hscal->inrange_pairs;
-    if (c->batch) {
-        std::vector<unsigned long long> bits((size_t)c->n_boxes);
-        SPH_CUDA(c, cudaMemcpy(bits.data(), c->box_dt_next, bits.size() * 8, cudaMemcpyDeviceToHost));
-        for (int b = 0; b < c->n_boxes; b++) std::memcpy(&c->h_box_dt[(size_t)b], &bits[(size_t)b], 8);
-    }
-    if (c->hscal->flags & kErrTimeout) return fail(c, SPH_ERR_TIMEOUT, "device wait ran out");
+    if (c->batch)
+        for (int b = 0; b < c->n_boxes; b++) std::memcpy(&c->h_box_dt[(size_t)b], &c->h_dt_bits[b], 8);
+    if (c->hscal->flags & (kErrTimeout | kErrTimeoutS2)) return fail(c, SPH_ERR_TIMEOUT, "device wait ran out");
     return SPH_OK;
 }
 
+int finish_forces(sph_ctx *c) {
+    int r = read_scalars(c);
+    if (r) return r;
+    return absorb_forces(c);
+}
+
 // Density with the outer loop of App. F: while some h leaves cache_tol * h^n, refresh the cell
-// h_max and rebuild the cache around the current h, then iterate again.
-int density_with_restarts(sph_ctx *c, sph_state *s, int *iters, int max_outer) {
+// h_max and rebuild the cache around the current h, then iterate again.  stale: the first density
+// pass has already run (in a captured step) and left some h at the cache limit.
+int density_with_restarts(sph_ctx *c, sph_state *s, int *iters, int max_outer, bool stale = false) {
     int passes = 1;
     for (;;) {
-        bool stale = false;
         int r;
-        if ((r = stage_begin(c, kStDensity)) || (r = density_run(c, s, iters, &stale)) ||
-            (r = stage_end(c, kStDensity)))
-            return r;
-        if (!stale) break;
+        if (!stale) {
+            if ((r = stage_begin(c, kStDensity)) || (r = density_run(c, s, iters, &stale)) ||
+                (r = stage_end(c, kStDensity)))
+                return r;
+            if (!stale) break;
+        }
+        stale = false;
         if (passes >= max_outer)
             return fail(c, SPH_ERR_CACHE_STALE, "h left the cache tolerance after %d cache builds", passes);
         if ((r = stage_begin(c, kStNeigh)) || (r = tree_boxes(c, s)) || (r = neighbours_build(c, s)) ||
@@ -235,6 +252,149 @@ int density_with_restarts(sph_ctx *c, sph_state *s, int *iters, int max_outer) {
     }
     c->stats.outer_passes = passes;
     return SPH_OK;
+}
+
+// ------------------------------------------------------------------------------------ sph_step
+// Shock switch, the saves for the corrector re-runs and the first force pass with its corrector:
+// the part of a step after the density.
+int step_tail(sph_ctx *c, sph_state *s, double dt) {
+    int r;
+    if (c->p.av_switch &&
+        ((r = stage_begin(c, kStSwitch)) || (r = switch_run(c, s, dt)) || (r = stage_end(c, kStSwitch))))
+        return r;
+    const int64_t st = c->n_cap;
+    if (c->p.eps_v > 0.0 && (r = integrate_save(c, s))) return r;   // v*, u*, a^n, du^n for the re-runs
+    if ((r = forces_run(c, s, c->a_new, c->a_new + st, c->a_new + 2 * st, c->a_new + 3 * st))) return r;
+    if ((r = stage_begin(c, kStCorrect)) || (r = integrate_correct(c, s, dt)) || (r = stage_end(c, kStCorrect)))
+        return r;
+    return SPH_OK;
+}
+
+// A0 predictor, A1-A6 tree, A7 cache, A8 density / h, then step_tail.  Stage by stage: with the host
+// checks, the capacity growth and the outer restart of the density.  While capturing: one density
+// pass; every check is left to the error word read back after the replay.
+int step_body(sph_ctx *c, sph_state *s, double dt) {
+    int r;
+    if (c->p.eps_v > 0.0 && !c->rerun) {
+        ++c->gen;
+        if ((r = alloc(c, &c->rerun, (size_t)8 * c->n_cap))) return r;
+    }
+    if ((r = stage_begin(c, kStPredict)) || (r = integrate_predict(c, s, dt, c->dhdt_valid ? c->dhdt : nullptr)) ||
+        (r = stage_end(c, kStPredict)))
+        return r;
+    // tree (reorders the state; outputs are recomputed below)
+    if ((r = stage_begin(c, kStTree)) || (r = tree_build(c, s, false)) || (r = stage_end(c, kStTree))) return r;
+    // cache at h^n
+    if ((r = stage_begin(c, kStNeigh)) || (r = neighbours_build(c, s)) || (r = stage_end(c, kStNeigh))) return r;
+    int iters = 0;
+    if (c->capturing) {
+        bool stale = false;
+        if ((r = density_run(c, s, &iters, &stale))) return r;
+    } else if ((r = density_with_restarts(c, s, &iters, c->p.max_outer))) {
+        return r;
+    }
+    return step_tail(c, s, dt);
+}
+
+bool graph_matches(const sph_ctx *c, const sph_state *s) {
+    return c->gexec && c->graph_gen == c->gen && c->graph_dhdt == c->dhdt_valid &&
+           std::memcmp(&c->graph_state, s, sizeof *s) == 0;
+}
+
+// Records step_body into an executable graph.  The capture runs on a private stream (a capture
+// cannot start on the legacy default stream); nothing executes until the replay.
+int graph_capture(sph_ctx *c, sph_state *s, double dt) {
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (!c->cap_stream) SPH_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    const int64_t launches0 = c->launches;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        c->stream = user;
+        return cuda_fail(c, e, "cudaStreamBeginCapture");
+    }
+    c->capturing = true;
+    int r = SPH_OK;
+    e = cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream);   // the step's error word
+    if (e != cudaSuccess) r = cuda_fail(c, e, "cudaMemsetAsync");
+    if (!r) r = step_body(c, s, dt);
+    c->capturing = false;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->stream, &g);
+    c->stream = user;
+    c->graph_launches = c->launches - launches0;
+    c->launches = launches0;
+    if (r || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return r ? r : cuda_fail(c, e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        cudaGetLastError();
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    c->graph_gen = c->gen;
+    c->graph_state = *s;
+    c->graph_dhdt = c->dhdt_valid;
+    ++c->graph_captures;
+    return SPH_OK;
+}
+
+// One replay and the single read-back of the step's scalars.  A failed stage skipped everything
+// after it on the device; the host then finishes the step stage by stage: from the tree when a
+// count outgrew its arrays (they grow, and the next step captures again), from the cache rebuild
+// of the outer density loop when some h reached the cache limit.
+int graph_replay(sph_ctx *c, sph_state *s, double dt) {
+    SPH_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+    c->launches += c->graph_launches;
+    ++c->graph_replays;
+    int r = read_scalars(c);
+    if (r) return r;
+    const DevScalars &h = *c->hscal;
+    const uint32_t fl = h.flags;
+    if (fl & kErrNonFinite) return fail(c, SPH_ERR_NONFINITE, "non-finite position or h <= 0");
+    if (fl & (kErrTimeout | kErrTimeoutS2)) return fail(c, SPH_ERR_TIMEOUT, "device wait ran out");
+    if (fl & kErrStack) return fail(c, SPH_ERR_CAPACITY, "tree walk stack overflow");
+    if (fl & kErrNotConverged) return fail(c, SPH_ERR_H_NOT_CONVERGED, "h iteration exceeded %d", c->p.h_max_iter);
+    int iters = 0;
+    if (fl & (kErrCapacity | kErrCandOverflow | kErrCacheOverflow)) {
+        ++c->graph_fallbacks;
+        if ((r = tree_build(c, s, false)) || (r = neighbours_build(c, s)) ||
+            (r = density_with_restarts(c, s, &iters, c->p.max_outer)) || (r = step_tail(c, s, dt)))
+            return r;
+        return finish_forces(c);
+    }
+    // tree and cache as built on the device
+    c->n_leaves = h.n_leaves;
+    c->n_groups = h.n_groups;
+    c->total_slots = h.total_slots;
+    c->n_pairs = h.n_pairs;
+    c->tree_valid = c->cache_valid = true;
+    c->stats.n = s->n;
+    c->stats.n_leaves = h.n_leaves;
+    c->stats.n_red = c->p.reduction_level;
+    c->stats.n_groups = h.n_groups;
+    c->stats.n_pairs = h.n_pairs;
+    c->stats.cache_slots = h.total_slots;
+    c->stats.cand_chunks = h.total_chunks;
+    c->stats.density_iters_max = (int)h.max_iters;
+    c->stats.density_pair_evals = (int64_t)h.pair_evals;
+    c->stats.density_inrange = (int64_t)h.dens_inrange;
+    if (fl & kErrStale) {
+        ++c->graph_fallbacks;
+        if ((r = density_with_restarts(c, s, &iters, c->p.max_outer, true)) || (r = step_tail(c, s, dt))) return r;
+        return finish_forces(c);
+    }
+    c->stats.outer_passes = 1;
+    c->density_valid = true;
+    return absorb_forces(c);
 }
 
 }  // namespace
@@ -319,12 +479,14 @@ int create_ctx(const sph_params *p, int64_t n_cap, int n_boxes, int64_t neigh_ca
         (r = alloc(c, &c->nb_cnt, N)) || (r = alloc(c, &c->nb_ptr, N)) || (r = alloc(c, &c->nb_ids, c->nb_cap)) ||
         (r = alloc(c, &c->a_new, (size_t)4 * N)) || (r = alloc(c, &c->dhdt, N)) ||
         (r = alloc(c, &c->block_part, (size_t)(N / 256 + 2))) || (r = alloc(c, &c->dscal, 1)) ||
-        (r = alloc(c, &c->box_root, n_boxes))) {
+        (r = alloc(c, &c->box_root, n_boxes)) || (r = alloc(c, &c->box_dt, n_boxes))) {
         free_all(c);
         delete c;
         return r;
     }
-    if (cudaMallocHost((void **)&c->hscal, sizeof(DevScalars)) != cudaSuccess) {
+    if (cudaMallocHost((void **)&c->hscal, sizeof(DevScalars)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->h_dt, (size_t)n_boxes * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->h_dt_bits, (size_t)n_boxes * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         free_all(c);
         delete c;
@@ -391,8 +553,7 @@ int sph_batch_create(const sph_params *p, int n_boxes, const int64_t *box_offset
         return SPH_OK;
     };
     if ((r = alloc(c, &c->box_of, total)) || (r = alloc(c, &c->box_mass, n_boxes)) ||
-        (r = alloc(c, &c->box_gamma, n_boxes)) || (r = alloc(c, &c->box_dt, n_boxes)) ||
-        (r = alloc(c, &c->box_dt_next, n_boxes)) || (r = up(c->box_of, box_of.data(), box_of.size() * 2)) ||
+        (r = alloc(c, &c->box_gamma, n_boxes)) || (r = alloc(c, &c->box_dt_next, n_boxes)) || (r = up(c->box_of, box_of.data(), box_of.size() * 2)) ||
         (r = up(c->box_mass, box_mass, (size_t)n_boxes * 8)) || (r = up(c->box_gamma, gam.data(), gam.size() * 8))) {
         sph_destroy(c);
         return r;
@@ -426,6 +587,7 @@ int sph_set_params(sph_ctx *c, const sph_params *p) {
     int r = check_params(c, p);
     if (r) return r;
     c->p = *p;
+    ++c->gen;   // parameters are baked into a captured step
     c->launch.reduction_level = p->reduction_level;
     c->morton_bits = c->batch ? std::min(p->morton_bits, (63 - c->box_bits) / 3) : p->morton_bits;
     c->tree_valid = c->cache_valid = c->density_valid = c->forces_valid = false;
@@ -486,71 +648,59 @@ int sph_compute_forces(sph_ctx *c, sph_state *s) {
 int sph_step(sph_ctx *c, sph_state *s, double dt, double *dt_used, double *dt_next) {
     int r = check_state(c, s, true);
     if (r) return r;
+    // time step of every box, on the device for the predictor, switch and corrector
     if (c->batch) {
         if (s->n != c->n_cap) return fail(c, SPH_ERR_INVALID_ARG, "a batch state holds every box");
-        std::vector<double> &bd = c->h_step_dt;
-        bd.assign((size_t)c->n_boxes, dt);
+        for (int b = 0; b < c->n_boxes; b++) c->h_dt[b] = dt;
         if (!(dt > 0)) {
             for (int b = 0; b < c->n_boxes; b++) {
                 if (!(c->h_box_dt[(size_t)b] > 0) && c->h_box_off[b + 1] > c->h_box_off[b])
                     return fail(c, SPH_ERR_ORDER, "dt <= 0 needs a previous force evaluation");
-                bd[(size_t)b] = c->h_box_dt[(size_t)b] > 0 ? c->h_box_dt[(size_t)b] : 0.0;
+                c->h_dt[b] = c->h_box_dt[(size_t)b] > 0 ? c->h_box_dt[(size_t)b] : 0.0;
             }
         }
-        SPH_CUDA(c, cudaMemcpyAsync(c->box_dt, bd.data(), bd.size() * 8, cudaMemcpyHostToDevice, c->stream));
-        dt = *std::min_element(bd.begin(), bd.end());
-    } else if (!(dt > 0)) {
-        if (!(c->dt_next > 0)) return fail(c, SPH_ERR_ORDER, "dt <= 0 needs a previous force evaluation");
-        dt = c->dt_next;
+        dt = *std::min_element(c->h_dt, c->h_dt + c->n_boxes);
+    } else {
+        if (!(dt > 0)) {
+            if (!(c->dt_next > 0)) return fail(c, SPH_ERR_ORDER, "dt <= 0 needs a previous force evaluation");
+            dt = c->dt_next;
+        }
+        c->h_dt[0] = dt;
     }
+    SPH_CUDA(c, cudaMemcpyAsync(c->box_dt, c->h_dt, (size_t)c->n_boxes * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream));
     c->n = s->n;
-    // A0 predictor
-    if ((r = stage_begin(c, kStPredict)) || (r = integrate_predict(c, s, dt, c->dhdt_valid ? c->dhdt : nullptr)) ||
-        (r = stage_end(c, kStPredict)))
-        return r;
-    // A1-A6 tree (reorders the state; outputs are recomputed below)
-    if ((r = stage_begin(c, kStTree)) || (r = tree_build(c, s, false)) || (r = stage_end(c, kStTree))) return r;
-    // A7 cache at h^n
-    if ((r = stage_begin(c, kStNeigh)) || (r = neighbours_build(c, s)) || (r = stage_end(c, kStNeigh))) return r;
-    // A8 density / h with the outer restart
-    int iters = 0;
-    if ((r = density_with_restarts(c, s, &iters, c->p.max_outer))) return r;
-    // shock switch: alpha^{n+1} from v*, grad v*, grad a^n at the new positions and h (App. G)
-    if (c->p.av_switch &&
-        ((r = stage_begin(c, kStSwitch)) || (r = switch_run(c, s, dt)) || (r = stage_end(c, kStSwitch))))
-        return r;
-    const int64_t st = c->n_cap;
-    const bool check = c->p.eps_v > 0.0;
-    if (check) {   // v*, u*, a^n, du^n for the corrector re-runs
-        if (!c->rerun && (r = alloc(c, &c->rerun, (size_t)8 * st))) return r;
-        double *src[8] = {s->vx, s->vy, s->vz, s->u, s->ax, s->ay, s->az, s->du};
-        for (int f = 0; f < 8; f++)
-            SPH_CUDA(c, cudaMemcpyAsync(c->rerun + (size_t)f * st, src[f], (size_t)s->n * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, c->stream));
+    // A0-A10 up to the first corrector pass: replayed as one graph, or stage by stage
+    bool replay = false;
+    if (c->graph_on && !c->timing) {
+        if (!graph_matches(c, s) && c->eager_gen == c->gen && (r = graph_capture(c, s, dt))) return r;
+        replay = graph_matches(c, s);
     }
-    // A9 forces into a_new, A10 corrector; re-runs with v* <- v^{n+1} while Eq. cvleapfrog fails
-    double ratio = 0.0;
-    bool failed = false;
-    int pass = 0;
-    for (;;) {
-        ++pass;
-        if ((r = forces_run(c, s, c->a_new, c->a_new + st, c->a_new + 2 * st, c->a_new + 3 * st))) return r;
-        if ((r = stage_begin(c, kStCorrect)) ||
-            (r = (pass == 1 ? integrate_correct(c, s, dt) : integrate_correct_again(c, s, dt))) ||
-            (r = stage_end(c, kStCorrect)))
-            return r;
-        if ((r = finish_forces(c))) return r;
+    if (replay) r = graph_replay(c, s, dt);
+    else if (!(r = step_body(c, s, dt))) r = finish_forces(c);
+    if (r) return r;
+    c->eager_gen = c->gen;   // capacities fit the current particle distribution
+    // corrector re-runs with v* <- v^{n+1} while Eq. cvleapfrog fails
+    const bool check = c->p.eps_v > 0.0;
+    auto ratio_now = [&]() {
         double dvm;
-        unsigned long long b = c->hscal->dv_max_bits;
+        const unsigned long long b = c->hscal->dv_max_bits;
         std::memcpy(&dvm, &b, sizeof dvm);
         const double v2 = c->hscal->v2_sum;
-        ratio = v2 > 0 ? dvm / std::sqrt(v2 / (double)s->n) : 0.0;
-        const bool fails = check && !(ratio < c->p.eps_v);
-        if (pass == 1) {
-            c->stats.dv_ratio = ratio;
-            failed = fails;
-        }
-        if (!fails || pass >= c->p.max_corr) break;
+        return v2 > 0 ? dvm / std::sqrt(v2 / (double)s->n) : 0.0;
+    };
+    c->stats.dv_ratio = ratio_now();
+    const bool failed = check && !(c->stats.dv_ratio < c->p.eps_v);
+    bool fails = failed;
+    int pass = 1;
+    while (fails && pass < c->p.max_corr) {
+        ++pass;
+        const int64_t st = c->n_cap;
+        if ((r = forces_run(c, s, c->a_new, c->a_new + st, c->a_new + 2 * st, c->a_new + 3 * st)) ||
+            (r = stage_begin(c, kStCorrect)) || (r = integrate_correct_again(c, s, dt)) ||
+            (r = stage_end(c, kStCorrect)) || (r = finish_forces(c)))
+            return r;
+        fails = check && !(ratio_now() < c->p.eps_v);
     }
     c->corr_passes = pass;
     // CFL multiplier: halved in a step whose first pass failed, else relaxed towards 1
@@ -570,6 +720,16 @@ int sph_step(sph_ctx *c, sph_state *s, double dt, double *dt_used, double *dt_ne
     c->dhdt_valid = true;
     if (dt_used) *dt_used = dt;
     if (dt_next) *dt_next = c->dt_next;
+    return SPH_OK;
+}
+
+int sph_set_graph(sph_ctx *c, int enable) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    c->graph_on = enable != 0;
+    if (!c->graph_on && c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
     return SPH_OK;
 }
 
@@ -677,6 +837,9 @@ int sph_export_neighbours(sph_ctx *c, int64_t *off, uint32_t *ids) {
 int sph_get_stats(sph_ctx *c, sph_stats *st) {
     if (!c || !st) return SPH_ERR_INVALID_ARG;
     c->stats.kernel_launches = c->launches;
+    c->stats.graph_replays = c->graph_replays;
+    c->stats.graph_captures = c->graph_captures;
+    c->stats.graph_fallbacks = c->graph_fallbacks;
     *st = c->stats;
     return SPH_OK;
 }
@@ -697,6 +860,7 @@ int sph_set_launch(sph_ctx *c, const sph_launch *in) {
         c->p.reduction_level = in->reduction_level;
         c->tree_valid = c->cache_valid = false;
     }
+    if (std::memcmp(&c->launch, in, sizeof *in) != 0) ++c->gen;   // shapes are baked into a captured step
     c->launch = *in;
     return SPH_OK;
 }

@@ -128,9 +128,11 @@ __global__ void __launch_bounds__(256, kMixed ? 3 : 1) k_density(int64_t n, cons
                                                  const uint32_t *__restrict__ nb_cnt,
                                                  const unsigned long long *__restrict__ nb_ptr,
                                                  const uint32_t *__restrict__ nb_ids, DensParams dp,
-                                                 double *__restrict__ rho, double *__restrict__ omega, DevScalars *sc) {
+                                                 double *__restrict__ rho, double *__restrict__ omega, DevScalars *sc,
+                                                 const uint32_t *abort) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one thread per particle
     if (a - (threadIdx.x & 31) >= n) return;   // whole warp past the end
+    if (aborted(abort, kAbortDensity)) return;   // captured step: the cache is incomplete
     int it = 0;
     uint32_t nin = 0, evals = 0, flag = 0;
     if (a < n) {
@@ -206,7 +208,7 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
     dp.box_mass = c->batch ? c->box_mass : nullptr;
     dp.box_of = c->batch ? c->box_of : nullptr;
     const int blk = c->launch.density_block;
-    SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
+    if (!c->capturing) SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->max_iters, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->pair_evals, 0, 2 * sizeof(unsigned long long), c->stream));
     with_kernel(c->p.kernel, [&](auto kern) {
@@ -214,14 +216,18 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
         if (c->p.precision == SPH_MIXED)
             k_density<K, true><<<grid_for(n, blk), blk, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
                                                                         c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
-                                                                        s->omega, c->dscal);
+                                                                        s->omega, c->dscal, abort_word(c));
         else
             k_density<K, false><<<grid_for(n, blk), blk, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
                                                                          c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
-                                                                         s->omega, c->dscal);
+                                                                         s->omega, c->dscal, abort_word(c));
         return 0;
     });
     SPH_LAUNCH_CHECK(c, "k_density");
+    if (c->capturing) {   // iterations, stale and convergence flags are read back after the step
+        *stale = false;
+        return SPH_OK;
+    }
     static_assert(offsetof(DevScalars, flags) == offsetof(DevScalars, max_iters) + sizeof(uint32_t), "layout");
     SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->max_iters, &c->dscal->max_iters, 2 * sizeof(uint32_t),
                                 cudaMemcpyDeviceToHost, c->stream));

@@ -21,6 +21,7 @@ struct ForceParams {
     const double *box_gamma;   // per-box adiabatic index (batch) or nullptr
     const uint16_t *box_of;    // box of each particle (batch) or nullptr
     unsigned long long *box_dt_next;   // per-box CFL minimum (bits) or nullptr
+    const uint32_t *abort;     // captured step: skip when an earlier stage failed
 };
 
 // Per-particle FP64 record of the force loop: 128 bytes, read as 8 double2.
@@ -40,7 +41,7 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
                              const double *__restrict__ alpha, ForceParams fp, int mixed, FRec *__restrict__ rec, float4 *__restrict__ m_v, float4 *__restrict__ m_t,
                              float4 *__restrict__ m_r, float *__restrict__ h32) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || aborted(fp.abort, kAbortStep)) return;
     const double gam = fp.box_gamma ? fp.box_gamma[fp.box_of[i]] : fp.gamma;
     if (mixed) {
         // FP32 records for the FP32 pair sums: P = (gamma-1) rho u, c_s = sqrt(gamma (gamma-1) u),
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
                                                      DevScalars *sc) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one thread per particle
     if (a - (threadIdx.x & 31) >= n) return;   // whole warp past the end
+    if (aborted(fp.abort, kAbortStep)) return;
     const int box = (a < n && fp.box_of) ? fp.box_of[a] : 0;
     double tdt = INFINITY;
     unsigned long long npair = 0;
@@ -225,6 +227,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *_
                                                       ForceOut out, DevScalars *sc) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one thread per particle
     if (a - (threadIdx.x & 31) >= n) return;   // whole warp past the end
+    if (aborted(fp.abort, kAbortStep)) return;
     const int box = (a < n && fp.box_of) ? fp.box_of[a] : 0;
     double tdt = INFINITY;
     unsigned long long npair = 0;
@@ -340,6 +343,7 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     fp.box_gamma = c->batch ? c->box_gamma : nullptr;
     fp.box_of = c->batch ? c->box_of : nullptr;
     fp.box_dt_next = c->batch ? c->box_dt_next : nullptr;
+    fp.abort = abort_word(c);
     const int mixed = c->p.precision == SPH_MIXED;
     int r = ensure_force_records(c);
     if (r) return r;

@@ -11,7 +11,7 @@ namespace sph {
 struct IntParams {
     double dt;
     double h_clamp, inv_h_clamp;
-    const double *box_dt;      // per-box time step (batch) or nullptr
+    const double *box_dt;      // time step per box on the device (box_of nullptr: one box) or nullptr
     const uint16_t *box_of;
     double lo[3], hi[3];
     int periodic;
@@ -39,7 +39,7 @@ __global__ void k_predict(int64_t n, double *__restrict__ x, double *__restrict_
                           const double *__restrict__ dhdt, IntParams ip) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double dt = ip.box_dt ? ip.box_dt[ip.box_of[i]] : ip.dt;
+    const double dt = ip.box_dt ? ip.box_dt[ip.box_of ? ip.box_of[i] : 0] : ip.dt;
     const double hdt = 0.5 * dt;
     const double kx = hdt * ax[i], ky = hdt * ay[i], kz = hdt * az[i], ku = hdt * du[i];
     const double hvx = vx[i] + kx, hvy = vy[i] + ky, hvz = vz[i] + kz;
@@ -68,11 +68,12 @@ __global__ void k_correct(int64_t n, double *__restrict__ vx, double *__restrict
                           double *__restrict__ u, double *__restrict__ ax, double *__restrict__ ay,
                           double *__restrict__ az, double *__restrict__ du, const double *__restrict__ anew,
                           int64_t stride, double dt, const double *__restrict__ box_dt,
-                          const uint16_t *__restrict__ box_of, DevScalars *sc, double *__restrict__ block_part) {
+                          const uint16_t *__restrict__ box_of, DevScalars *sc, double *__restrict__ block_part,
+                          const uint32_t *abort) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float dv = 0.f, v2 = 0.f;
-    if (i < n) {
-        const double hdt = 0.5 * (box_dt ? box_dt[box_of[i]] : dt);
+    if (i < n && !aborted(abort, kAbortStep)) {
+        const double hdt = 0.5 * (box_dt ? box_dt[box_of ? box_of[i] : 0] : dt);
         const double nax = anew[i], nay = anew[stride + i], naz = anew[2 * stride + i], ndu = anew[3 * stride + i];
         const double dvx = hdt * (nax - ax[i]), dvy = hdt * (nay - ay[i]), dvz = hdt * (naz - az[i]);
         const double wx = vx[i] + dvx, wy = vy[i] + dvy, wz = vz[i] + dvz;
@@ -117,11 +118,11 @@ __global__ void k_correct_again(int64_t n, double *__restrict__ vx, double *__re
                                 double *__restrict__ ay, double *__restrict__ az, double *__restrict__ du,
                                 const double *__restrict__ anew, int64_t stride, const double *__restrict__ save,
                                 double dt, const double *__restrict__ box_dt, const uint16_t *__restrict__ box_of,
-                                DevScalars *sc, double *__restrict__ block_part) {
+                                DevScalars *sc, double *__restrict__ block_part, const uint32_t *abort) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float dv = 0.f, v2 = 0.f;
-    if (i < n) {
-        const double hdt = 0.5 * (box_dt ? box_dt[box_of[i]] : dt);
+    if (i < n && !aborted(abort, kAbortStep)) {
+        const double hdt = 0.5 * (box_dt ? box_dt[box_of ? box_of[i] : 0] : dt);
         const double nax = anew[i], nay = anew[stride + i], naz = anew[2 * stride + i], ndu = anew[3 * stride + i];
         const double ex = hdt * (nax - ax[i]), ey = hdt * (nay - ay[i]), ez = hdt * (naz - az[i]);
         const double wx = save[i] + hdt * (nax - save[4 * stride + i]);
@@ -174,12 +175,30 @@ __global__ void k_sum_parts(const double *__restrict__ part, int64_t m, double *
 
 __global__ void k_reset_dv(DevScalars *sc) { sc->dv_max_bits = 0ULL; }
 
+// v*, u*, a^n, du^n of the step into save[8][stride] for the corrector re-runs.
+struct SaveArgs {
+    const double *src[8];
+};
+__global__ void k_save(int64_t n, SaveArgs a, int64_t stride, double *__restrict__ save) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int f = 0; f < 8; f++) save[f * stride + i] = a.src[f][i];
+}
+
+int integrate_save(sph_ctx *c, sph_state *s) {
+    SaveArgs a{{s->vx, s->vy, s->vz, s->u, s->ax, s->ay, s->az, s->du}};
+    k_save<<<grid_for(s->n, 256), 256, 0, c->stream>>>(s->n, a, c->n_cap, c->rerun);
+    SPH_LAUNCH_CHECK(c, "k_save");
+    return SPH_OK;
+}
+
 int integrate_predict(sph_ctx *c, sph_state *s, double dt, const double *dhdt) {
     IntParams ip;
     ip.dt = dt;
     ip.h_clamp = c->p.h_clamp;
     ip.inv_h_clamp = 1.0 / c->p.h_clamp;
-    ip.box_dt = c->batch ? c->box_dt : nullptr;
+    ip.box_dt = c->box_dt;   // written by sph_step before the step
     ip.box_of = c->batch ? c->box_of : nullptr;
     for (int k = 0; k < 3; k++) {
         ip.lo[k] = c->p.box_lo[k];
@@ -198,8 +217,8 @@ int integrate_correct(sph_ctx *c, sph_state *s, double dt) {
     k_reset_dv<<<1, 1, 0, c->stream>>>(c->dscal);
     SPH_LAUNCH_CHECK(c, "k_reset_dv");
     k_correct<<<blocks, 256, 0, c->stream>>>(n, s->vx, s->vy, s->vz, s->u, s->ax, s->ay, s->az, s->du, c->a_new,
-                                             c->n_cap, dt, c->batch ? c->box_dt : nullptr,
-                                             c->batch ? c->box_of : nullptr, c->dscal, c->block_part);
+                                             c->n_cap, dt, c->box_dt, c->batch ? c->box_of : nullptr, c->dscal,
+                                             c->block_part, abort_word(c));
     SPH_LAUNCH_CHECK(c, "k_correct");
     k_sum_parts<<<1, 256, 0, c->stream>>>(c->block_part, blocks, &c->dscal->v2_sum);
     SPH_LAUNCH_CHECK(c, "k_sum_parts");
@@ -212,9 +231,9 @@ int integrate_correct_again(sph_ctx *c, sph_state *s, double dt) {
     k_reset_dv<<<1, 1, 0, c->stream>>>(c->dscal);
     SPH_LAUNCH_CHECK(c, "k_reset_dv");
     k_correct_again<<<blocks, 256, 0, c->stream>>>(n, s->vx, s->vy, s->vz, s->u, s->ax, s->ay, s->az, s->du,
-                                                   c->a_new, c->n_cap, c->rerun, dt,
-                                                   c->batch ? c->box_dt : nullptr, c->batch ? c->box_of : nullptr,
-                                                   c->dscal, c->block_part);
+                                                   c->a_new, c->n_cap, c->rerun, dt, c->box_dt,
+                                                   c->batch ? c->box_of : nullptr, c->dscal, c->block_part,
+                                                   abort_word(c));
     SPH_LAUNCH_CHECK(c, "k_correct_again");
     k_sum_parts<<<1, 256, 0, c->stream>>>(c->block_part, blocks, &c->dscal->v2_sum);
     SPH_LAUNCH_CHECK(c, "k_sum_parts");

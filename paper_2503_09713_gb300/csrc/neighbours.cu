@@ -42,11 +42,11 @@ static Geo make_geo(const sph_params &p) {
 // ------------------------------------------------------------------ group boxes (warp per group)
 // FP32 box of each group, rounded outwards from the FP64 positions (min/max in FP32 on the ALU
 // pipe: the walk and the stage-2 extent only need a box that contains the group).
-__global__ void k_group_boxes(Groups gr, int64_t G, const double *__restrict__ x, const double *__restrict__ y,
+__global__ void k_group_boxes(Groups gr, Count Gc, const double *__restrict__ x, const double *__restrict__ y,
                               const double *__restrict__ z, const double *__restrict__ h, NodeF *__restrict__ gboxf) {
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (g >= G) return;
+    if (g >= read_count(Gc, kAbortTree)) return;
     const int64_t a = group_first(gr, g) + lane;
     const bool va = a < group_end(gr, g);
     const double p[3] = {va ? x[a] : 0.0, va ? y[a] : 0.0, va ? z[a] : 0.0};
@@ -85,14 +85,15 @@ __device__ __forceinline__ float walk_radius(float s, float h1, float h2) {
     return __fmul_ru(__fmul_ru(s, fmaxf(h1, h2)), 1.0f + 1.0f / 65536.0f);
 }
 
-__global__ void __launch_bounds__(256) k_walk(Groups gr, int64_t G, int64_t L, const NodeF *__restrict__ gboxf,
+__global__ void __launch_bounds__(256) k_walk(Groups gr, Count Gc, Count Lc, const NodeF *__restrict__ gboxf,
                                              const NodeF *__restrict__ nodesf, const int32_t *__restrict__ child,
                                              const int64_t *__restrict__ leaf_first,
                                              const int32_t *__restrict__ box_root, float s, Geo geo,
                                              uint2 *__restrict__ cand, uint32_t *__restrict__ cand_cnt, int cap,
                                              int64_t *__restrict__ grp_chunks, uint32_t *flags) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G) return;
+    if (g >= read_count(Gc, kAbortTree)) return;
+    const int64_t L = read_count(Lc, kAbortTree);
     const int32_t rootc = box_root[group_box_of(gr, g)];   // the walk stays inside the group's box
     const NodeF q = load_nodef(&gboxf[g]);
     const NodeF root = load_nodef(&nodesf[rootc]);
@@ -224,8 +225,8 @@ constexpr uint32_t kGrpSpinLimit = 1u << 22;
 // a box; the kernel asks for a quarter box (warp-uniform), otherwise every separation is wrapped on
 // its own.  Pairs within a relative 2^-10 of the radius are decided in FP64 (exact_pair).
 __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
-    Groups gr, const int32_t *__restrict__ box_root, int64_t G, const uint2 *__restrict__ cand, const uint32_t *__restrict__ cand_cnt, int cap,
-    const int64_t *__restrict__ chunk_off, const NodeF *__restrict__ gboxf, const Node *__restrict__ nodes,
+    Groups gr, const int32_t *__restrict__ box_root, Count Gc, const uint2 *__restrict__ cand, const uint32_t *__restrict__ cand_cnt, int cap,
+    const int64_t *__restrict__ chunk_off, int64_t masks_cap, const NodeF *__restrict__ gboxf, const Node *__restrict__ nodes,
     const float4 *__restrict__ rel, const float *__restrict__ h32, const double *__restrict__ x,
     const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h, double s,
     float quarter_box, Geo geo, uint32_t *__restrict__ masks, uint32_t *__restrict__ nb_cnt,
@@ -236,10 +237,18 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4 *s_posw = s2_smem + warp * 32;
     float2 *s_tw = reinterpret_cast<float2 *>(s2_smem + (blockDim.x >> 5) * 32) + warp * 32;
+    // group count and the mask capacity: the same decision in every block, taken before any ticket
+    const int64_t G = read_count(Gc, kAbortStage2);
+    if (G == 0) return;
+    if (chunk_off[G] * 32 > masks_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&sc->flags, kErrCapacity);
+        return;
+    }
     int64_t g = 0;
     if (lane == 0) g = atomicAdd(ticket, 1u);
     g = __shfl_sync(0xffffffffu, g, 0);
     if (g >= G) return;
+    if (g == 0 && lane == 0) sc->total_chunks = chunk_off[G];
     const int64_t first = group_first(gr, g);
     const int64_t a = first + lane;
     const int64_t gsize = group_end(gr, g) - first;
@@ -367,7 +376,7 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
             const unsigned need = inc ? (((inc & (0u - inc)) << 1) - 1u) : 0xffffffffu;
             if (notready & need) {
                 if (++spins > kGrpSpinLimit) {
-                    if (lane == 0) atomicOr(&sc->flags, kErrTimeout);
+                    if (lane == 0) atomicOr(&sc->flags, kErrTimeoutS2);
                     break;
                 }
                 __nanosleep(32);
@@ -388,11 +397,14 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     if (va) nb_ptr[a] = pack_nb_ptr(off_g + lane, gsize);
     if (lane == 0) {
         grp_off[g] = off_g;
-        if (g == G - 1) grp_off[G] = off_g + (int64_t)slots;
+        if (g == G - 1) {
+            grp_off[G] = off_g + (int64_t)slots;
+            sc->total_slots = off_g + (int64_t)slots;
+        }
         atomicAdd((unsigned long long *)&sc->n_pairs, (unsigned long long)sum);
     }
     if (off_g + (int64_t)slots > nb_cap) {   // cache too small: the host grows it and runs again
-        if (lane == 0) atomicOr(&sc->flags, kErrCandOverflow);
+        if (lane == 0) atomicOr(&sc->flags, kErrCacheOverflow);
         return;
     }
     // ---- (3) expand the masks into the cache
@@ -424,6 +436,7 @@ __global__ void k_h32(int64_t n, const double *__restrict__ h, float *__restrict
 template <typename T>
 static int ensure(sph_ctx *c, T **p, int64_t &cap, int64_t need, const char *what) {
     if (need <= cap) return SPH_OK;
+    ++c->gen;   // a captured step holds the old pointer
     const int64_t newcap = need + need / 4 + 1024;
     SPH_CUDA(c, cudaFree(*p));
     *p = nullptr;
@@ -439,27 +452,28 @@ static int ensure(sph_ctx *c, T **p, int64_t &cap, int64_t need, const char *wha
 int neighbours_build(sph_ctx *c, const sph_state *s) {
     if (!c->tree_valid) return fail(c, SPH_ERR_ORDER, "sph_find_neighbours before sph_build_tree");
     const int64_t n = s->n;
-    const int64_t G = c->n_groups;
+    const int64_t G = launch_groups(c);   // the group count, or the capacity in a captured step
     const Groups gr = make_groups(c);
-    const int64_t L = c->n_leaves;
     const Geo geo = make_geo(c->p);
     const double sc = kernel_radius(c->p.kernel) * c->p.cache_tol;   // R_kern * chi
     c->cache_valid = false;
 
     k_h32<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->h, c->h32, c->h_base);
     SPH_LAUNCH_CHECK(c, "k_h32");
-    k_group_boxes<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, G, s->x, s->y, s->z, s->h, c->gboxf);
+    k_group_boxes<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, group_count(c), s->x, s->y, s->z, s->h,
+                                                                c->gboxf);
     SPH_LAUNCH_CHECK(c, "k_group_boxes");
 
     // stage 1, growing the candidate capacity while a list overflows
     for (int attempt = 0;; attempt++) {
-        SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
-        k_walk<<<grid_for(G, c->launch.walk_block), c->launch.walk_block, 0, c->stream>>>(gr, G, L, c->gboxf, c->nodesf, c->child, c->leaf_first,
-                                                        c->box_root, (float)sc, geo, c->cand, c->cand_cnt,
-                                                        c->cand_cap, c->grp_chunks, &c->dscal->flags);
+        if (!c->capturing) SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
+        k_walk<<<grid_for(G, c->launch.walk_block), c->launch.walk_block, 0, c->stream>>>(
+            gr, group_count(c), leaf_count(c), c->gboxf, c->nodesf, c->child, c->leaf_first, c->box_root, (float)sc,
+            geo, c->cand, c->cand_cnt, c->cand_cap, c->grp_chunks, &c->dscal->flags);
         SPH_LAUNCH_CHECK(c, "k_walk");
-        int r = exclusive_scan_i64(c, c->grp_chunks, c->chunk_off, G);
+        int r = exclusive_scan_i64_dev(c, c->grp_chunks, c->chunk_off, &c->dscal->n_groups, G);
         if (r) return r;
+        if (c->capturing) break;   // overflow is flagged on the device and the host redoes the step
         SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->flags, &c->dscal->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                     c->stream));
         SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->total_chunks, &c->chunk_off[G], sizeof(int64_t),
@@ -470,6 +484,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         if (!(fl & kErrCandOverflow)) break;
         if (attempt >= 6) return fail(c, SPH_ERR_CAPACITY, "candidate range list overflow (cap %d)", c->cand_cap);
         const int newcap = c->cand_cap * 2;
+        ++c->gen;
         uint2 *nc = nullptr;
         if (cudaMalloc(&nc, (size_t)c->g_cap * newcap * sizeof(uint2)) != cudaSuccess) {
             cudaGetLastError();
@@ -479,7 +494,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         c->cand = nc;
         c->cand_cap = newcap;
     }
-    const int64_t chunks = c->hscal->total_chunks;
+    const int64_t chunks = c->capturing ? 0 : c->hscal->total_chunks;
     int r = ensure(c, &c->masks, c->masks_cap, chunks * 32, "candidate masks");
     if (r) return r;
 
@@ -491,14 +506,18 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
     int64_t total = 0;
     for (int attempt = 0;; attempt++) {
         SPH_CUDA(c, cudaMemsetAsync(&c->dscal->n_pairs, 0, sizeof(int64_t), c->stream));
-        SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
+        if (!c->capturing) SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
         SPH_CUDA(c, cudaMemsetAsync(&c->dscal->s2_ticket, 0, sizeof(uint32_t), c->stream));
         SPH_CUDA(c, cudaMemsetAsync(c->grp_slots, 0, (size_t)G * sizeof(int64_t), c->stream));
         k_stage2<<<blocks, s2w * 32, s2_smem, c->stream>>>(
-            gr, c->box_root, G, c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->gboxf, c->nodes, c->rel, c->h32, s->x, s->y,
-            s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->nb_ptr, (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket,
-            c->grp_off, c->nb_ids, c->nb_cap, c->dscal);
+            gr, c->box_root, group_count(c), c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->masks_cap, c->gboxf,
+            c->nodes, c->rel, c->h32, s->x, s->y, s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->nb_ptr,
+            (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket, c->grp_off, c->nb_ids, c->nb_cap, c->dscal);
         SPH_LAUNCH_CHECK(c, "k_stage2");
+        if (c->capturing) {   // counts and overflow stay on the device until the step is read back
+            c->cache_valid = true;
+            return SPH_OK;
+        }
         SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->total_slots, &c->grp_off[G], sizeof(int64_t), cudaMemcpyDeviceToHost,
                                     c->stream));
         SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->n_pairs, &c->dscal->n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost,
@@ -506,9 +525,9 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->flags, &c->dscal->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                     c->stream));
         SPH_CUDA(c, cudaStreamSynchronize(c->stream));
-        if (c->hscal->flags & kErrTimeout) return fail(c, SPH_ERR_TIMEOUT, "stage-2 look-back wait ran out");
+        if (c->hscal->flags & kErrTimeoutS2) return fail(c, SPH_ERR_TIMEOUT, "stage-2 look-back wait ran out");
         total = c->hscal->total_slots;
-        if (!(c->hscal->flags & kErrCandOverflow) && total <= c->nb_cap) break;
+        if (!(c->hscal->flags & kErrCacheOverflow) && total <= c->nb_cap) break;
         if (attempt >= 2) return fail(c, SPH_ERR_CAPACITY, "neighbour cache does not fit");
         r = ensure(c, &c->nb_ids, c->nb_cap, total, "neighbour cache");
         if (r) return r;

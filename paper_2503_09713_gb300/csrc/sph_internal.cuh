@@ -27,7 +27,45 @@ enum : uint32_t {
     kErrNonFinite = 1u << 3,    // NaN/Inf position or h
     kErrNotConverged = 1u << 4, // Newton iteration hit h_max_iter
     kErrStale = 1u << 5,        // an h was clamped at cache_tol * h^n
+    kErrCapacity = 1u << 6,     // a count (leaves, groups, candidate chunks) above its arrays (captured step)
+    kErrCacheOverflow = 1u << 7,// the neighbour cache is smaller than the kept pairs (host grows and retries)
+    kErrTimeoutS2 = 1u << 8,    // the stage-2 look-back wait ran out
 };
+
+// A captured step (sph_set_graph) runs every stage without the host in between: a stage whose
+// inputs an earlier stage left incomplete returns without writing.  Each mask holds the bits that
+// the stages before the kernel set (never a bit the kernel itself sets, so all its blocks agree).
+constexpr uint32_t kAbortTree = kErrNonFinite | kErrTimeout | kErrCapacity;
+constexpr uint32_t kAbortStage2 = kAbortTree | kErrCandOverflow | kErrStack;
+constexpr uint32_t kAbortDensity = kAbortStage2 | kErrCacheOverflow | kErrTimeoutS2;
+constexpr uint32_t kAbortStep = kAbortDensity | kErrStale | kErrNotConverged;
+
+// Error word as an abort source: nullptr outside a captured step.  A plain (L1-cached) load: the
+// bits that matter were set by earlier kernels, and every warp of a launch reads the same word, so
+// an uncached load per warp would queue hundreds of thousands of requests on one L2 slice.
+__device__ __forceinline__ bool aborted(const uint32_t *abort, uint32_t mask) {
+    return abort && (*abort & mask);
+}
+
+// A data-dependent count (leaves, groups) read on the device.  Arrays indexed by it hold cap
+// entries; a count above cap flags kErrCapacity and reads as 0, as does any count in a captured step
+// after an earlier stage failed (abort bits).  Outside a captured step the host has sized the arrays
+// and the launch from the same count.
+struct Count {
+    const int64_t *n;
+    int64_t cap;
+    uint32_t *flags;
+    const uint32_t *abort;
+};
+__device__ __forceinline__ int64_t read_count(const Count &c, uint32_t mask) {
+    if (aborted(c.abort, mask)) return 0;
+    const int64_t v = __ldg(c.n);   // written by an earlier kernel, read-only here
+    if (v > c.cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(c.flags, kErrCapacity);
+        return 0;
+    }
+    return v;
+}
 
 // One tree node: tight box and largest smoothing length; 64 bytes, two 32-byte sectors.
 struct __align__(16) Node {
@@ -96,6 +134,7 @@ struct DevScalars {
     double v2_sum;                    // sum |v|^2 after the corrector
     int64_t n_groups;                 // groups of the last tree build
 };
+static_assert(sizeof(DevScalars) % 8 == 0, "DevScalars is copied as a whole");
 
 struct Buffer {
     void *p = nullptr;
@@ -227,10 +266,9 @@ struct sph_ctx {
     double *box_mass = nullptr;        // [n_boxes] (batch)
     double *box_gamma = nullptr;       // [n_boxes] (batch)
     int32_t *box_root = nullptr;       // [n_boxes] node at the root of each box's subtree
-    double *box_dt = nullptr;          // [n_boxes] time step of the current step (batch)
+    double *box_dt = nullptr;          // [n_boxes] time step of the current step (one entry for one box)
     unsigned long long *box_dt_next = nullptr;  // [n_boxes] CFL minimum (bits) of the last force pass
     std::vector<double> h_box_dt;      // host copy of the last CFL step per box
-    std::vector<double> h_step_dt;     // time step of each box in the current step
     int64_t *gstart = nullptr;         // [groups + 1] first particle of each group
     uint16_t *group_box = nullptr;     // [groups] box of each group (batch)
 
@@ -243,6 +281,21 @@ struct sph_ctx {
     int64_t launches = 0;              // kernels launched by this context
     bool timing = false;               // per-stage CUDA-event timing (sph_set_timing)
     cudaEvent_t ev[2] = {nullptr, nullptr};
+
+    // ---- captured step (sph_set_graph) ----
+    bool graph_on = false;             // replay sph_step as one CUDA graph
+    bool capturing = false;            // recording: no host reads, grids from the capacities
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr; // private stream the step is captured on
+    uint64_t eager_gen = 0;            // gen after the last step that ran (or finished) stage by stage
+    uint64_t gen = 1;                  // bumped by every reallocation and setting change
+    uint64_t graph_gen = 0;            // gen the graph was captured at
+    sph_state graph_state{};           // state the graph was captured for
+    bool graph_dhdt = false;           // dh/dt gathered with the state in the captured step
+    double *h_dt = nullptr;            // [n_boxes] pinned: time step of the next step, copied to box_dt
+    unsigned long long *h_dt_bits = nullptr;  // [n_boxes] pinned: box_dt_next read back (batch)
+    int64_t graph_launches = 0;        // kernels in the captured step
+    int64_t graph_replays = 0, graph_captures = 0, graph_fallbacks = 0;
 };
 
 namespace sph {
@@ -274,6 +327,7 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
 int integrate_predict(sph_ctx *c, sph_state *s, double dt, const double *dhdt);
 int integrate_correct(sph_ctx *c, sph_state *s, double dt);
 int integrate_correct_again(sph_ctx *c, sph_state *s, double dt);   // corrector re-run from v*, u*
+int integrate_save(sph_ctx *c, sph_state *s);                       // v*, u*, a^n, du^n -> rerun
 int switch_run(sph_ctx *c, sph_state *s, double dt);               // shock-switch step of alpha
 int read_scalars(sph_ctx *c);
 Groups make_groups(const sph_ctx *c);
@@ -287,6 +341,16 @@ enum Stage { kStPredict = 0, kStTree, kStNeigh, kStDensity, kStForcePrep, kStFor
 int stage_begin(sph_ctx *c, int k);
 int stage_end(sph_ctx *c, int k);
 int exclusive_scan_i64(sph_ctx *c, const int64_t *in, int64_t *out, int64_t n);  // out[n] = total
+// The same over the first min(*dn, cap) elements of in, for a count known only on the device (out
+// needs cap + 1 entries; out[count] = total).
+int exclusive_scan_i64_dev(sph_ctx *c, const int64_t *in, int64_t *out, const int64_t *dn, int64_t cap);
+// Launch extents of the leaf- and group-indexed kernels: the counts, or in a captured step the
+// capacities (the kernels read the counts on the device).
+inline int64_t launch_leaves(const sph_ctx *c) { return c->capturing ? c->l_cap : c->n_leaves; }
+inline int64_t launch_groups(const sph_ctx *c) { return c->capturing ? c->g_cap : c->n_groups; }
+inline const uint32_t *abort_word(const sph_ctx *c) { return c->capturing ? &c->dscal->flags : nullptr; }
+Count leaf_count(sph_ctx *c);
+Count group_count(sph_ctx *c);
 
 // ---------------------------------------------------------------- device helpers
 

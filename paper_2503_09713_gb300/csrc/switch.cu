@@ -18,6 +18,7 @@ struct SwitchParams {
     const double *box_mass, *box_gamma, *box_dt;
     const uint16_t *box_of;
     PairGeo geo;
+    const uint32_t *abort;     // captured step: skip when an earlier stage failed
 };
 
 template <typename K, bool kMixed>
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(128) k_alpha(int64_t n, const double *__restri
                                                double *__restrict__ alpha) {
     using T = typename std::conditional<kMixed, float, double>::type;
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= n) return;
+    if (a >= n || aborted(sp.abort, kAbortStep)) return;
     const int box = sp.box_of ? sp.box_of[a] : 0;
     const double m = sp.box_mass ? sp.box_mass[box] : sp.mass;
     const double gam = sp.box_gamma ? sp.box_gamma[box] : sp.gamma;
@@ -116,9 +117,10 @@ int switch_run(sph_ctx *c, sph_state *s, double dt) {
     sp.dt = dt;
     sp.box_mass = c->batch ? c->box_mass : nullptr;
     sp.box_gamma = c->batch ? c->box_gamma : nullptr;
-    sp.box_dt = c->batch ? c->box_dt : nullptr;
+    sp.box_dt = c->box_dt;   // written by sph_step before the step
     sp.box_of = c->batch ? c->box_of : nullptr;
     sp.geo = make_pair_geo(c->p);
+    sp.abort = abort_word(c);
     with_kernel(c->p.kernel, [&](auto kern) {
         using K = decltype(kern);
         if (c->p.precision == SPH_MIXED)

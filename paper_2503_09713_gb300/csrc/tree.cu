@@ -268,6 +268,15 @@ __global__ void k_gather(int64_t n, const uint32_t *__restrict__ perm, GatherArg
     if (g.id_dst) g.id_dst[i] = g.id_src ? g.id_src[p] : p;
 }
 
+// Copy of the gathered block back into the state arrays (and id): a kernel, not a device-to-device
+// memcpy, so the copy runs on the SMs at HBM speed in a captured step as well.
+__global__ void k_copy_back(int64_t n, GatherArgs g) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int f = 0; f < g.nf; f++) g.dst[f][i] = g.src[f][i];
+    if (g.id_dst) g.id_dst[i] = g.id_src[i];
+}
+
 // FP32 cell-relative coordinates: cell index on a 2^10 grid per axis and the FP32 offset from the
 // cell corner; packed cell index in .w (x<<20 | y<<10 | z).
 __global__ void k_rel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
@@ -374,11 +383,12 @@ __device__ __forceinline__ int kdelta(const uint64_t *mu, int64_t L, int64_t i, 
     return __clzll((long long)(mu[i] ^ mu[j]));
 }
 
-__global__ void k_karras(int64_t L, const uint64_t *__restrict__ mu, int32_t *__restrict__ lchild,
+__global__ void k_karras(Count Lc, const uint64_t *__restrict__ mu, int32_t *__restrict__ lchild,
                          int32_t *__restrict__ rchild, uint8_t *__restrict__ lflag, uint8_t *__restrict__ rflag,
                          int32_t *__restrict__ endrange, int32_t *__restrict__ child,
                          int32_t *__restrict__ node_parent, int32_t *__restrict__ leaf_parent) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t L = read_count(Lc, kAbortTree);
     if (i >= L - 1) return;
     const int dir = (kdelta(mu, L, i, i + 1) - kdelta(mu, L, i, i - 1)) >= 0 ? 1 : -1;
     const int dmin = kdelta(mu, L, i, i - dir);
@@ -423,11 +433,12 @@ __device__ __forceinline__ void load_node(const Node *nd, Node &o) {
     o.hi[0] = cc.x; o.hi[1] = cc.y; o.hi[2] = dd.x; o.pad = dd.y;
 }
 
-__global__ void k_boxes(int64_t L, const int64_t *__restrict__ leaf_first, const double *__restrict__ x,
+__global__ void k_boxes(Count Lc, const int64_t *__restrict__ leaf_first, const double *__restrict__ x,
                         const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h,
                         const int32_t *__restrict__ child, const int32_t *__restrict__ node_parent,
                         const int32_t *__restrict__ leaf_parent, uint32_t *visit, Node *nodes, NodeF *nodesf) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t L = read_count(Lc, kAbortTree);
     if (j >= L) return;
     Node b;
     for (int k = 0; k < 3; k++) { b.lo[k] = INFINITY; b.hi[k] = -INFINITY; }
@@ -469,10 +480,11 @@ __global__ void k_boxes(int64_t L, const int64_t *__restrict__ leaf_first, const
 
 // Root of each box's subtree (batch): the node whose leaves all carry the box index and whose parent
 // mixes boxes; a box with one leaf has that leaf as its root.
-__global__ void k_box_roots(int64_t L, const uint64_t *__restrict__ mu_leaf, const int32_t *__restrict__ endrange,
+__global__ void k_box_roots(Count Lc, const uint64_t *__restrict__ mu_leaf, const int32_t *__restrict__ endrange,
                             const int32_t *__restrict__ node_parent, const int32_t *__restrict__ leaf_parent,
                             int shift, int32_t *__restrict__ box_root) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t L = read_count(Lc, kAbortTree);
     const int64_t nin = L - 1;
     if (t >= nin + L) return;
     auto range_box = [&](int64_t node, uint64_t &b_lo, uint64_t &b_hi) {
@@ -504,11 +516,12 @@ __global__ void k_box_roots(int64_t L, const uint64_t *__restrict__ mu_leaf, con
 // Node t marks the first particle of its range when it qualifies and its parent does not; a leaf
 // with more than kGroup particles marks every kGroup-th particle; in a batch every box start is
 // marked too.  An exclusive scan of the marks numbers the groups in particle order.
-__global__ void k_group_marks(int64_t L, int64_t n, const int64_t *__restrict__ leaf_first,
+__global__ void k_group_marks(Count Lc, int64_t n, const int64_t *__restrict__ leaf_first,
                               const uint64_t *__restrict__ mu_leaf, const int32_t *__restrict__ endrange,
                               const int32_t *__restrict__ node_parent, const int32_t *__restrict__ leaf_parent,
                               int shift, const uint16_t *__restrict__ box_of, int64_t *__restrict__ marks) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t L = read_count(Lc, kAbortTree);
     const int64_t nin = L - 1;
     if (t < n && (t == 0 || (box_of && box_of[t] != box_of[t - 1]))) marks[t] = 1;
     if (t >= nin + L) return;
@@ -537,42 +550,55 @@ __global__ void k_group_marks(int64_t L, int64_t n, const int64_t *__restrict__ 
     }
 }
 
+// Group table from the scanned marks; the group count pos[n] goes to sc->n_groups (checked against
+// the capacity g_cap of the per-group arrays).
 __global__ void k_group_table(int64_t n, const int64_t *__restrict__ marks, const int64_t *__restrict__ pos,
                               const uint16_t *__restrict__ box_of, int64_t *__restrict__ gstart,
-                              uint16_t *__restrict__ group_box) {
+                              uint16_t *__restrict__ group_box, int64_t g_cap, DevScalars *sc,
+                              const uint32_t *abort) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    if (t >= n || aborted(abort, kAbortTree)) return;
+    const int64_t G = pos[n];
+    if (t == n - 1) sc->n_groups = G;
+    if (G > g_cap) {
+        if (t == 0) atomicOr(&sc->flags, kErrCapacity);
+        return;
+    }
     if (marks[t]) {
         const int64_t g = pos[t];
         gstart[g] = t;
         if (box_of) group_box[g] = box_of[t];
     }
-    if (t == n - 1) gstart[pos[n]] = n;
+    if (t == n - 1) gstart[G] = n;
 }
 
 static int make_group_table(sph_ctx *c, int64_t n) {
-    const int64_t L = c->n_leaves;
+    const int64_t L = launch_leaves(c);
     int64_t *marks = reinterpret_cast<int64_t *>(c->gather_tmp);   // free after the reorder
     int64_t *pos = marks + c->n_cap;                                // [n + 1]
     SPH_CUDA(c, cudaMemsetAsync(marks, 0, (size_t)n * sizeof(int64_t), c->stream));
     const int64_t threads = std::max<int64_t>(n, 2 * L - 1);
     k_group_marks<<<grid_for(threads, 256), 256, 0, c->stream>>>(
-        L, n, c->leaf_first, c->mu_leaf, c->endrange, c->node_parent, c->leaf_parent, 3 * c->morton_bits,
-        c->batch ? c->box_of : nullptr, marks);
+        leaf_count(c), n, c->leaf_first, c->mu_leaf, c->endrange, c->node_parent, c->leaf_parent,
+        3 * c->morton_bits, c->batch ? c->box_of : nullptr, marks);
     SPH_LAUNCH_CHECK(c, "k_group_marks");
     int r = exclusive_scan_i64(c, marks, pos, n);
     if (r) return r;
-    SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->n_groups, &pos[n], sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
-    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
-    const int64_t G = c->hscal->n_groups;
-    if (G < 1 || G > n) return fail(c, SPH_ERR_CUDA, "bad group count %lld", (long long)G);
-    r = ensure_groups(c, G);
-    if (r) return r;
+    if (!c->capturing) {   // a captured step keeps the group count on the device
+        SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->n_groups, &pos[n], sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+        const int64_t G = c->hscal->n_groups;
+        if (G < 1 || G > n) return fail(c, SPH_ERR_CUDA, "bad group count %lld", (long long)G);
+        r = ensure_groups(c, G);
+        if (r) return r;
+        c->n_groups = G;
+        c->stats.n_groups = G;
+    }
     k_group_table<<<grid_for(n, 256), 256, 0, c->stream>>>(n, marks, pos, c->batch ? c->box_of : nullptr,
-                                                           c->gstart, c->group_box);
+                                                           c->gstart, c->group_box, c->g_cap, c->dscal,
+                                                           abort_word(c));
     SPH_LAUNCH_CHECK(c, "k_group_table");
-    c->n_groups = G;
-    c->stats.n_groups = G;
     return SPH_OK;
 }
 
@@ -593,9 +619,9 @@ static Box3 make_box(const sph_params &p) {
 }
 
 static int boxes(sph_ctx *c, const sph_state *s) {
-    const int64_t L = c->n_leaves;
+    const int64_t L = launch_leaves(c);
     if (L > 1) SPH_CUDA(c, cudaMemsetAsync(c->visit, 0, (size_t)(L - 1) * sizeof(uint32_t), c->stream));
-    k_boxes<<<grid_for(L, 128), 128, 0, c->stream>>>(L, c->leaf_first, s->x, s->y, s->z, s->h, c->child,
+    k_boxes<<<grid_for(L, 128), 128, 0, c->stream>>>(leaf_count(c), c->leaf_first, s->x, s->y, s->z, s->h, c->child,
                                                      c->node_parent, c->leaf_parent, c->visit, c->nodes,
                                                      c->nodesf);
     SPH_LAUNCH_CHECK(c, "k_boxes");
@@ -646,13 +672,17 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
         g.id_dst = (f0 == 0 && s->id) ? c->id_tmp : nullptr;
         k_gather<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->perm, g);
         SPH_LAUNCH_CHECK(c, "k_gather");
-        for (int k = 0; k < g.nf; k++)
-            SPH_CUDA(c, cudaMemcpyAsync(fields_dst[f0 + k], g.dst[k], (size_t)n * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, c->stream));
+        GatherArgs b{};
+        b.nf = g.nf;
+        for (int k = 0; k < g.nf; k++) {
+            b.src[k] = g.dst[k];
+            b.dst[k] = fields_dst[f0 + k];
+        }
+        b.id_src = g.id_dst ? c->id_tmp : nullptr;   // the id is complete after the first block
+        b.id_dst = g.id_dst ? s->id : nullptr;
+        k_copy_back<<<grid_for(n, 256), 256, 0, c->stream>>>(n, b);
+        SPH_LAUNCH_CHECK(c, "k_copy_back");
     }
-    if (s->id)
-        SPH_CUDA(c, cudaMemcpyAsync(s->id, c->id_tmp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
-                                    c->stream));
     k_rel<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, bx, c->rel);
     SPH_LAUNCH_CHECK(c, "k_rel");
 
@@ -682,29 +712,32 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
     k_compact<<<(unsigned)nb, kCpThreads, 0, c->stream>>>(n, c->mask[cur], c->mu, boff, c->leaf_first, c->mu_leaf,
                                                          c->dscal);
     SPH_LAUNCH_CHECK(c, "k_compact");
-    SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->n_leaves, &c->dscal->n_leaves, sizeof(int64_t), cudaMemcpyDeviceToHost,
-                                c->stream));
-    SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->flags, &c->dscal->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                                c->stream));
-    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (c->hscal->flags & kErrNonFinite) return fail(c, SPH_ERR_NONFINITE, "non-finite position or h <= 0");
-    if (c->hscal->flags & kErrTimeout) return fail(c, SPH_ERR_TIMEOUT, "radix sort look-back wait ran out");
-    const int64_t L = c->hscal->n_leaves;
-    if (L < 1 || L > n) return fail(c, SPH_ERR_CUDA, "bad leaf count %lld", (long long)L);
-    c->n_leaves = L;
-    r = ensure_tree(c, L);
-    if (r) return r;
+    if (!c->capturing) {   // a captured step keeps the leaf count on the device
+        SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->n_leaves, &c->dscal->n_leaves, sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, c->stream));
+        SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->flags, &c->dscal->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (c->hscal->flags & kErrNonFinite) return fail(c, SPH_ERR_NONFINITE, "non-finite position or h <= 0");
+        if (c->hscal->flags & kErrTimeout) return fail(c, SPH_ERR_TIMEOUT, "radix sort look-back wait ran out");
+        const int64_t L = c->hscal->n_leaves;
+        if (L < 1 || L > n) return fail(c, SPH_ERR_CUDA, "bad leaf count %lld", (long long)L);
+        c->n_leaves = L;
+        r = ensure_tree(c, L);
+        if (r) return r;
+    }
+    const int64_t L = launch_leaves(c);
 
     // A5 Karras
     if (L > 1) {
-        k_karras<<<grid_for(L - 1, 256), 256, 0, c->stream>>>(L, c->mu_leaf, c->lchild, c->rchild, c->lflag,
+        k_karras<<<grid_for(L - 1, 256), 256, 0, c->stream>>>(leaf_count(c), c->mu_leaf, c->lchild, c->rchild, c->lflag,
                                                                c->rflag, c->endrange, c->child, c->node_parent,
                                                                c->leaf_parent);
         SPH_LAUNCH_CHECK(c, "k_karras");
     }
     // subtree root of every box
     if (c->batch) {
-        k_box_roots<<<grid_for(2 * L - 1, 256), 256, 0, c->stream>>>(L, c->mu_leaf, c->endrange, c->node_parent,
+        k_box_roots<<<grid_for(2 * L - 1, 256), 256, 0, c->stream>>>(leaf_count(c), c->mu_leaf, c->endrange, c->node_parent,
                                                                      c->leaf_parent, 3 * c->morton_bits, c->box_root);
         SPH_LAUNCH_CHECK(c, "k_box_roots");
     }
@@ -716,7 +749,7 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
     if (r) return r;
     c->tree_valid = true;
     c->stats.n = n;
-    c->stats.n_leaves = L;
+    c->stats.n_leaves = c->n_leaves;
     c->stats.n_red = c->p.reduction_level;
     return SPH_OK;
 }

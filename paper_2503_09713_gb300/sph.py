@@ -66,7 +66,8 @@ class sph_stats(ctypes.Structure):
                 ("cand_chunks", _i64),
                 ("density_iters_max", _i), ("outer_passes", _i), ("n_red", _i), ("dt_next", _d), ("dv_ratio", _d),
                 ("kernel_launches", _i64), ("density_pair_evals", _i64), ("density_inrange", _i64), ("force_pairs", _i64), ("stage_ms", _d * 8),
-                ("cfl_multiplier", _d), ("corrector_passes", _i)]
+                ("cfl_multiplier", _d), ("corrector_passes", _i), ("graph_replays", _i64),
+                ("graph_captures", _i64), ("graph_fallbacks", _i64)]
 
 class sph_launch(ctypes.Structure):
     _fields_ = [("density_block", _i), ("forces_block", _i), ("walk_block", _i), ("stage2_warps", _i),
@@ -113,6 +114,7 @@ def load():
         "sph_export_neighbours": (_i, [_p, _p, _p]),
         "sph_get_stats": (_i, [_p, P(sph_stats)]),
         "sph_set_timing": (_i, [_p, _i]),
+        "sph_set_graph": (_i, [_p, _i]),
         "sph_reset_timing": (_i, [_p]),
         "sph_get_launch": (_i, [_p, P(sph_launch)]),
         "sph_set_launch": (_i, [_p, P(sph_launch)]),
@@ -226,6 +228,10 @@ def sph_get_stats(ctx) -> dict:
 
 def sph_set_timing(ctx, on: bool):
     _check(ctx, load().sph_set_timing(ctx, 1 if on else 0))
+
+
+def sph_set_graph(ctx, on: bool):
+    _check(ctx, load().sph_set_graph(ctx, 1 if on else 0))
 
 
 def sph_reset_timing(ctx):
@@ -418,6 +424,10 @@ class Solver:
 
     def set_timing(self, on: bool):
         sph_set_timing(self.ctx, on)
+
+    def set_graph(self, on: bool):
+        """Replay sph_step as one captured CUDA graph (see sph_set_graph)."""
+        sph_set_graph(self.ctx, on)
 
     def reset_timing(self):
         sph_reset_timing(self.ctx)
