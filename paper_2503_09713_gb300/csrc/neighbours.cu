@@ -1,13 +1,17 @@
 // Neighbour cache (App. C "Two-stages neighbour cache", App. D interaction criteria).
 //
 // Stage 1: every group (a tree node of at most 32 particles, see Groups) walks the radix tree once with
-// the group-group criterion  AABB_g  intersects  AABB_c (+) s*max(h_max,g, h_max,c),  s = R_kern*chi,
-// shifting the group box by the periodic images it can reach.  The walk runs on FP32 copies of the
-// boxes rounded outwards, so it keeps every cell the FP64 test keeps.  Leaves found one after the
-// other are merged into particle ranges (leaves are contiguous runs of the Morton order).
+// a group-cell criterion: dist(AABB_g, AABB_c) <= s*max(h_max,g, h_max,c),  s = R_kern*chi (the
+// Euclidean distance between the boxes: the cell box grown by a ball rather than the per-axis
+// expansion, so corner cells that hold no possible pair are not visited), shifting the group box by
+// the periodic images it can reach.  The walk runs on FP32 copies of the boxes rounded outwards, with
+// the distance rounded down and the radius up, so it keeps every cell that can hold a pair of the
+// object-object criterion.  Leaves found one after the other are merged into particle ranges
+// (leaves are contiguous runs of the Morton order).
 // Stage 2: one warp per group, lane = particle a, tests the candidates of the ranges, 32 at a time
 // from shared memory, against  |r_ab|^2 < (s*max(h_a,h_b))^2  (object-object criterion with the cache
-// tolerance of App. F).  The test runs in FP32 on coordinates relative to the group; pairs within a
+// tolerance of App. F); candidates farther from the group's box than any threshold of the group are
+// dropped first, one test per candidate.  The test runs in FP32 on coordinates relative to the group; pairs within a
 // relative 2^-10 of the radius are decided in FP64 exactly as the definition states, so the kept set
 // is the FP64 set.  The count pass stores, per 32-candidate chunk and lane, the bit mask of kept
 // candidates; after a scan over groups the fill pass only expands those masks.  Layout of the cache:
@@ -127,9 +131,14 @@ __global__ void __launch_bounds__(256) k_walk(Groups gr, Count Gc, Count Lc, con
                     const int32_t c = stack[--sp];
                     const NodeF nd = load_nodef(&nodesf[c]);
                     const float r = walk_radius(s, q.hmax, nd.hmax);
-                    const bool hit = (qlo[0] <= __fadd_ru(nd.hi[0], r)) && (__fadd_rd(nd.lo[0], -r) <= qhi[0]) &&
-                                     (qlo[1] <= __fadd_ru(nd.hi[1], r)) && (__fadd_rd(nd.lo[1], -r) <= qhi[1]) &&
-                                     (qlo[2] <= __fadd_ru(nd.hi[2], r)) && (__fadd_rd(nd.lo[2], -r) <= qhi[2]);
+                    // squared distance between the two boxes, rounded down, against r^2 rounded up
+                    float d2 = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        const float gap = fmaxf(fmaxf(__fsub_rd(nd.lo[k], qhi[k]), __fsub_rd(qlo[k], nd.hi[k])), 0.f);
+                        d2 = __fmaf_rd(gap, gap, d2);
+                    }
+                    const bool hit = d2 <= __fmul_ru(r, r);
                     if (!hit) continue;
                     if (c >= nin) {
                         const int64_t j = c - nin;
@@ -282,6 +291,12 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     const float hA = va ? h32[a] : 0.f;
     const float tA = (s32 * hA) * (s32 * hA);
     const float tAhi = tA * kBandHi, tAlo = tA * kBandLo;
+    // the group's box in the same relative FP32 coordinates, and its largest h (candidate filter)
+    const float glo[3] = {warp_min_f(va ? ax : INFINITY), warp_min_f(va ? ay : INFINITY),
+                          warp_min_f(va ? az : INFINITY)};
+    const float ghi[3] = {warp_max_f(va ? ax : -INFINITY), warp_max_f(va ? ay : -INFINITY),
+                          warp_max_f(va ? az : -INFINITY)};
+    const float hmax_g = warp_max_f(hA);
     const NodeF q = gboxf[g];
     const double hroot = nodes[box_root[group_box_of(gr, g)]].hmax;
     const float ext = fmaxf(fmaxf(__fsub_ru(q.hi[0], q.lo[0]), __fsub_ru(q.hi[1], q.lo[1])), __fsub_ru(q.hi[2], q.lo[2]));
@@ -314,8 +329,19 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
             __syncwarp();
             uint32_t hi = 0, lo = 0;
             if (compact) {
-#pragma unroll
-                for (int jj = 0; jj < 32; jj++) {
+                // Candidate filter (lane = candidate): drop a candidate farther from the group's box
+                // than (s max(h_max,g, h_b))^2 (1 + 2^-10).  Per axis |B - A| >= the gap to the box
+                // in FP32 too (rounding is monotone), and the squared sums below are formed in the
+                // same order as the pair test, so no particle of the group would keep a dropped one.
+                const float gx = fmaxf(fmaxf(glo[0] - P.x, P.x - ghi[0]), 0.f);
+                const float gy = fmaxf(fmaxf(glo[1] - P.y, P.y - ghi[1]), 0.f);
+                const float gz = fmaxf(fmaxf(glo[2] - P.z, P.z - ghi[2]), 0.f);
+                const float hm = fmaxf(hmax_g, hb);
+                const bool need = fmaf(gz, gz, fmaf(gy, gy, gx * gx)) <= (s32 * hm) * (s32 * hm) * kBandHi;
+                uint32_t todo = __ballot_sync(0xffffffffu, need);
+                while (todo) {   // warp-uniform
+                    const int jj = __ffs(todo) - 1;
+                    todo &= todo - 1;
                     const float4 B = s_posw[jj];
                     const float r2 = sep2(B, true, ax, ay, az, ca);
                     if (r2 <= fmaxf(tAhi, B.w)) hi |= 1u << jj;
