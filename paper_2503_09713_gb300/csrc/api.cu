@@ -825,9 +825,10 @@ int sph_export_neighbours(sph_ctx *c, int64_t *off, uint32_t *ids) {
     if (ids) {
         for (int64_t g = 0; g < G; g++) {
             const int64_t first = gst[(size_t)g], end = gst[(size_t)g + 1], size = end - first;
-            for (int64_t a = first; a < end; a++) {
-                const int64_t base = goff[g] + (a - first);
-                for (uint32_t k = 0; k < cnt[a]; k++) ids[off[a] + k] = raw[base + (int64_t)k * size];
+            for (int64_t a = first; a < end; a++) {   // entry k at off_g + 4 size (k/4) + 4 lane + k%4
+                const int64_t base = goff[g] + 4 * (a - first);
+                for (uint32_t k = 0; k < cnt[a]; k++)
+                    ids[off[a] + k] = raw[base + (int64_t)(k >> 2) * 4 * size + (k & 3)];
             }
         }
     }

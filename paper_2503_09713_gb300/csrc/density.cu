@@ -45,7 +45,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         const float lim = (float)(K::R * K::R) * kPreBand / ((float)hinv2);
         double f0 = K::F0, g0 = 3.0 * K::F0, k0 = 12.0 * K::F0;
         for (uint32_t k = 0; k < cnt; k++) {
-            const uint32_t b = ids[k * st];
+            const uint32_t b = nb_at(ids, k, st);
             float fx, fy, fz;
             int sx, sy, sz;
             rel_sep_shift(A, rel[b], geo, fx, fy, fz, sx, sy, sz);
@@ -93,28 +93,18 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         // software pipeline: the indices of the next four neighbours are loaded while the current
         // four are gathered and summed
         uint32_t k = 0;
-        uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
-        if (cnt >= 4) {
-            n0 = ids[0];
-            n1 = ids[st];
-            n2 = ids[2 * st];
-            n3 = ids[3 * st];
-        }
+        uint4 nq = make_uint4(0u, 0u, 0u, 0u);
+        if (cnt >= 4) nq = nb_quad(ids, 0, st);
         for (; k + 4 <= cnt; k += 4) {
-            const uint32_t b0 = n0, b1 = n1, b2 = n2, b3 = n3;
-            if (k + 8 <= cnt) {
-                n0 = ids[(k + 4) * st];
-                n1 = ids[(k + 5) * st];
-                n2 = ids[(k + 6) * st];
-                n3 = ids[(k + 7) * st];
-            }
-            const float4 B0 = rel[b0], B1 = rel[b1], B2 = rel[b2], B3 = rel[b3];
+            const uint4 bq = nq;
+            if (k + 8 <= cnt) nq = nb_quad(ids, (k >> 2) + 1, st);
+            const float4 B0 = rel[bq.x], B1 = rel[bq.y], B2 = rel[bq.z], B3 = rel[bq.w];
             acc(B0);
             acc(B1);
             acc(B2);
             acc(B3);
         }
-        for (; k < cnt; k++) acc(rel[ids[k * st]]);
+        for (; k < cnt; k++) acc(rel[nb_at(ids, k, st)]);
         sf = kahan_value(s0, c0);
         sg = kahan_value(s1, c1);
         sk = (double)s2;

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
     uint32_t st;
     const uint32_t *ids = nb_list(nb_ids, pw, st);
     const int64_t lbeg = ids - nb_ids;
-    prefetch_lists_l2(nb_ids, lbeg, cnt ? lbeg + (int64_t)(cnt - 1) * st + 1 : lbeg);
+    prefetch_lists_l2(nb_ids, lbeg, lbeg + nb_span(cnt, st));
     if (a < n) {
     FRec A;
     load_rec(&rec[a], A);
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
     double axs = 0.0, ays = 0.0, azs = 0.0, dus = 0.0, divs = 0.0;
     double vs = A.acs;
     for (uint32_t k = 0; k < cnt; k++) {
-        const uint32_t b = ids[k * st];
+        const uint32_t b = nb_at(ids, k, st);
         float fx, fy, fz;
         int sx, sy, sz;
         rel_sep_shift(PA, rel[b], geo, fx, fy, fz, sx, sy, sz);
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *_
     uint32_t st;
     const uint32_t *ids = nb_list(nb_ids, pw, st);
     const int64_t lbeg = ids - nb_ids;
-    prefetch_lists_l2(nb_ids, lbeg, cnt ? lbeg + (int64_t)(cnt - 1) * st + 1 : lbeg);
+    prefetch_lists_l2(nb_ids, lbeg, lbeg + nb_span(cnt, st));
     if (a < n) {
     const float4 PA = rel[a], VA = m_v[a], TA = m_t[a], RA = m_r[a];
     const double mass_d = fp.box_mass ? fp.box_mass[box] : fp.mass;
@@ -289,14 +289,15 @@ __global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *_
     // two neighbours per iteration: their gathers are issued together
     uint32_t k = 0;
     for (; k + 2 <= cnt; k += 2) {
-        const uint32_t b0 = ids[k * st], b1 = ids[(k + 1) * st];
+        const uint2 bp = nb_pair(ids, k, st);
+        const uint32_t b0 = bp.x, b1 = bp.y;
         const float4 P0 = rel[b0], P1 = rel[b1];
         const float4 V0 = m_v[b0], V1 = m_v[b1];
         pair(b0, P0, V0);
         pair(b1, P1, V1);
     }
     if (k < cnt) {
-        const uint32_t b = ids[k * st];
+        const uint32_t b = nb_at(ids, k, st);
         pair(b, rel[b], m_v[b]);
     }
     const double axs = mass_d * kahan_value(sx, cx), ays = mass_d * kahan_value(sy, cy),

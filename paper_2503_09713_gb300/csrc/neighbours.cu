@@ -11,12 +11,12 @@
 // Stage 2: one warp per group, lane = particle a, tests the candidates of the ranges, 32 at a time
 // from shared memory, against  |r_ab|^2 < (s*max(h_a,h_b))^2  (object-object criterion with the cache
 // tolerance of App. F); candidates farther from the group's box than any threshold of the group are
-// dropped first, one test per candidate.  The test runs in FP32 on coordinates relative to the group; pairs within a
-// relative 2^-10 of the radius are decided in FP64 exactly as the definition states, so the kept set
-// is the FP64 set.  The count pass stores, per 32-candidate chunk and lane, the bit mask of kept
-// candidates; after a scan over groups the fill pass only expands those masks.  Layout of the cache:
-// particle a = start_g + lane of a group of size_g particles owns entries off_g + size_g k + lane,
-// k < count_a.
+// dropped first, one test per candidate.  The test runs in FP32 on coordinates relative to the
+// group; pairs within a relative 2^-10 of the radius are decided in FP64 exactly as the definition
+// states, so the kept set is the FP64 set.  The count pass stores, per 32-candidate chunk and lane,
+// the bit mask of kept candidates; after a scan over groups the fill pass only expands those masks.
+// Layout of the cache: particle a = start_g + lane of a group of size_g particles owns entries
+// k = 4 r + j, k < count_a, at off_g + 4 size_g r + 4 lane + j (16-byte quads, see nb_list).
 #include <cuda/atomic>
 
 #include "physics.cuh"
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         sum += __shfl_xor_sync(0xffffffffu, sum, o);
     }
-    const unsigned long long slots = (unsigned long long)mx * (unsigned long long)gsize;
+    const unsigned long long slots = (((unsigned long long)mx + 3ULL) & ~3ULL) * (unsigned long long)gsize;
     // ---- (2) decoupled look-back over the preceding groups (lane k reads group g-1-k)
     if (lane == 0) {
         cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> mine(lookback[g]);
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
         }
     }
     const int64_t off_g = (int64_t)excl;
-    if (va) nb_ptr[a] = pack_nb_ptr(off_g + lane, gsize);
+    if (va) nb_ptr[a] = pack_nb_ptr(off_g + 4 * lane, gsize);
     if (lane == 0) {
         grp_off[g] = off_g;
         if (g == G - 1) {
@@ -433,8 +433,10 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
         if (lane == 0) atomicOr(&sc->flags, kErrCacheOverflow);
         return;
     }
-    // ---- (3) expand the masks into the cache
-    const int64_t off = off_g + lane;
+    // ---- (3) expand the masks into the cache, one 16-byte quad per four entries
+    uint32_t *dst = nb_ids + off_g + 4 * lane;
+    const int64_t row = 4 * gsize;
+    uint4 quad = make_uint4(0u, 0u, 0u, 0u);
     uint32_t k = 0;
     chunk = 0;
     for (int ci = 0; ci < ncand; ci++) {
@@ -444,11 +446,17 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
             while (m) {
                 const int jj = __ffs(m) - 1;
                 m &= m - 1;
-                nb_ids[off + (int64_t)k * gsize] = (uint32_t)(base + jj);
+                const uint32_t v = (uint32_t)(base + jj), j = k & 3u;
+                quad.x = j == 0u ? v : quad.x;
+                quad.y = j == 1u ? v : quad.y;
+                quad.z = j == 2u ? v : quad.z;
+                quad.w = v;
+                if (j == 3u) *reinterpret_cast<uint4 *>(dst + (int64_t)(k >> 2) * row) = quad;
                 ++k;
             }
         }
     }
+    if (k & 3u) *reinterpret_cast<uint4 *>(dst + (int64_t)(k >> 2) * row) = quad;   // last, partial quad
 }
 
 __global__ void k_h32(int64_t n, const double *__restrict__ h, float *__restrict__ h32, double *__restrict__ hb) {

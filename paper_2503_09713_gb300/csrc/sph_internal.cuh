@@ -105,8 +105,11 @@ __device__ __forceinline__ int64_t group_first(const Groups &gr, int64_t g) { re
 __device__ __forceinline__ int64_t group_end(const Groups &gr, int64_t g) { return gr.start[g + 1]; }
 __device__ __forceinline__ int group_box_of(const Groups &gr, int64_t g) { return gr.box ? gr.box[g] : 0; }
 
-// Where a particle's neighbour list starts in the cache and its stride (the size of its group):
-// offset in the low 58 bits, stride above.  Entry k of the list is ids[offset + k * stride].
+// Cache layout: group g of S particles owns rows of 4 S entries from off_g (a multiple of 4); the
+// particle in lane l of the group keeps its entries k = 4 r + j at off_g + 4 S r + 4 l + j.  Each
+// particle's entries come in aligned 16-byte quads, and one row of a group is contiguous, so a
+// warp reads a row with one 16-byte load per lane and stage 2 writes whole quads.
+// List head of a particle: off_g + 4 l in the low 58 bits, the stride S above.
 constexpr int kNbStrideShift = 58;
 __device__ __forceinline__ unsigned long long pack_nb_ptr(int64_t off, int64_t stride) {
     return ((unsigned long long)stride << kNbStrideShift) | (unsigned long long)off;
@@ -114,6 +117,20 @@ __device__ __forceinline__ unsigned long long pack_nb_ptr(int64_t off, int64_t s
 __device__ __forceinline__ const uint32_t *nb_list(const uint32_t *nb_ids, unsigned long long w, uint32_t &stride) {
     stride = (uint32_t)(w >> kNbStrideShift);
     return nb_ids + (int64_t)(w & ((1ULL << kNbStrideShift) - 1));
+}
+// Entry k of a list; quad r (entries 4r .. 4r+3); pair of entries k, k+1 for even k; the extent of
+// a list of cnt entries from its head (for prefetches).
+__device__ __forceinline__ uint32_t nb_at(const uint32_t *ids, uint32_t k, uint32_t st) {
+    return ids[(int64_t)(k >> 2) * 4 * st + (k & 3)];
+}
+__device__ __forceinline__ uint4 nb_quad(const uint32_t *ids, uint32_t r, uint32_t st) {
+    return *reinterpret_cast<const uint4 *>(ids + (int64_t)r * 4 * st);
+}
+__device__ __forceinline__ uint2 nb_pair(const uint32_t *ids, uint32_t k, uint32_t st) {
+    return *reinterpret_cast<const uint2 *>(ids + (int64_t)(k >> 2) * 4 * st + (k & 3));
+}
+__device__ __forceinline__ int64_t nb_span(uint32_t cnt, uint32_t st) {
+    return cnt ? (int64_t)((cnt - 1) >> 2) * 4 * st + 4 : 0;
 }
 
 // Device scalars written by kernels and read back by the host in one copy.
@@ -232,7 +249,7 @@ struct sph_ctx {
     unsigned long long *nb_ptr = nullptr;  // [n_cap] list start and stride (pack_nb_ptr)
     int64_t *grp_slots = nullptr;      // [groups + 1] stage-2 look-back words
     int64_t *grp_off = nullptr;        // [groups + 1]
-    uint32_t *nb_ids = nullptr;        // cache entries, group-interleaved: off_g + k*size_g + lane
+    uint32_t *nb_ids = nullptr;        // cache entries in quads: off_g + 4 size_g (k/4) + 4 lane + k%4
     int64_t nb_cap = 0;
     int64_t n_pairs = 0, total_slots = 0;
     bool cache_valid = false;

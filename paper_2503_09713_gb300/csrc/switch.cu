@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(128) k_alpha(int64_t n, const double *__restri
     const float4 A = rel[a];
     const double xa = x[a], ya = y[a], za = z[a];
     for (uint32_t k = 0; k < cnt; k++) {
-        const uint32_t b = ids[k * st];
+        const uint32_t b = nb_at(ids, k, st);
         T dx, dy, dz;
         if (kMixed) {
             float fx, fy, fz;
