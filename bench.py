@@ -48,8 +48,8 @@ FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan)
 TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
                    "paper_2503_09713_gb300/csrc/sph_internal.cuh")
 TRAFFIC = {
-    "k_forces_fp64": {"bytes": 1073115392 + 95789056, "src_sha256": "e3c025842a31808b68612c42723860a2bb3d83aa645ac0f5688478dc9472d132"},
-    "k_forces_mixed": {"bytes": 892540928 + 92871424, "src_sha256": "e3c025842a31808b68612c42723860a2bb3d83aa645ac0f5688478dc9472d132"},
+    "k_forces_fp64": {"bytes": 1073009664 + 95242496, "src_sha256": "6717f0e4c11a58969547e6bea737b5623bb5f2812ac06e59aeca531b1d4f4f74"},
+    "k_forces_mixed": {"bytes": 888898304 + 92820736, "src_sha256": "6717f0e4c11a58969547e6bea737b5623bb5f2812ac06e59aeca531b1d4f4f74"},
 }
 
 
@@ -293,7 +293,7 @@ def peaks():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="sedov128", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
