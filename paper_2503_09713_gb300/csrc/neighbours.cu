@@ -125,11 +125,10 @@ __global__ void __launch_bounds__(256) k_walk(Groups gr, Count Gc, Count Lc, con
                                       __fadd_rd(q.lo[2], sh[2][iz])};
                 const float qhi[3] = {__fadd_ru(q.hi[0], sh[0][ix]), __fadd_ru(q.hi[1], sh[1][iy]),
                                       __fadd_ru(q.hi[2], sh[2][iz])};
-                int sp = 0;
-                stack[sp++] = rootc;
-                while (sp > 0) {
-                    const int32_t c = stack[--sp];
-                    const NodeF nd = load_nodef(&nodesf[c]);
+                // Depth-first walk over hit nodes: a node's two children are loaded and tested
+                // together when the node is popped, and only hits are pushed (right, then left, so
+                // leaves come out in Morton order).
+                auto hits = [&](const NodeF &nd) {
                     const float r = walk_radius(s, q.hmax, nd.hmax);
                     // squared distance between the two boxes, rounded down, against r^2 rounded up
                     float d2 = 0.f;
@@ -138,20 +137,27 @@ __global__ void __launch_bounds__(256) k_walk(Groups gr, Count Gc, Count Lc, con
                         const float gap = fmaxf(fmaxf(__fsub_rd(nd.lo[k], qhi[k]), __fsub_rd(qlo[k], nd.hi[k])), 0.f);
                         d2 = __fmaf_rd(gap, gap, d2);
                     }
-                    const bool hit = d2 <= __fmul_ru(r, r);
-                    if (!hit) continue;
+                    return d2 <= __fmul_ru(r, r);
+                };
+                int sp = 0;
+                if (hits(root)) stack[sp++] = rootc;
+                while (sp > 0) {
+                    const int32_t c = stack[--sp];
                     if (c >= nin) {
                         const int64_t j = c - nin;
                         push_leaf(out, cap, count, (uint32_t)leaf_first[j], (uint32_t)leaf_first[j + 1]);
-                    } else {
-                        if (sp + 2 > kStackDepth) {
-                            atomicOr(flags, kErrStack);
-                            sp = 0;
-                            break;
-                        }
-                        stack[sp++] = child[2 * c + 1];
-                        stack[sp++] = child[2 * c];
+                        continue;
                     }
+                    const int2 ch = *reinterpret_cast<const int2 *>(&child[2 * c]);
+                    const NodeF nl = load_nodef(&nodesf[ch.x]), nr = load_nodef(&nodesf[ch.y]);
+                    const bool hl = hits(nl), hr = hits(nr);
+                    if (sp + 2 > kStackDepth) {
+                        atomicOr(flags, kErrStack);
+                        sp = 0;
+                        break;
+                    }
+                    if (hr) stack[sp++] = ch.y;
+                    if (hl) stack[sp++] = ch.x;
                 }
             }
     if (count > cap) {
