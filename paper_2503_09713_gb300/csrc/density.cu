@@ -112,7 +112,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
 }
 
 template <typename K, bool kMixed>
-__global__ void __launch_bounds__(256, kMixed ? 3 : 1) k_density(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+__global__ void __launch_bounds__(256, kMixed ? 4 : 1) k_density(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                                                  const double *__restrict__ z, const float4 *__restrict__ rel,
                                                  double *__restrict__ h, const double *__restrict__ h_base,
                                                  const uint32_t *__restrict__ nb_cnt,
