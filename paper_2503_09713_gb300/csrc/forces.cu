@@ -286,11 +286,14 @@ __global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *_
         }
         kahan_add(su, cu, dut);
     };
-    // two neighbours per iteration: their gathers are issued together
+    // two neighbours per iteration, their gathers issued together; the next pair of indices is
+    // loaded one iteration ahead
     uint32_t k = 0;
+    uint2 nbp = make_uint2(0u, 0u);
+    if (cnt >= 2) nbp = nb_pair(ids, 0, st);
     for (; k + 2 <= cnt; k += 2) {
-        const uint2 bp = nb_pair(ids, k, st);
-        const uint32_t b0 = bp.x, b1 = bp.y;
+        const uint32_t b0 = nbp.x, b1 = nbp.y;
+        if (k + 4 <= cnt) nbp = nb_pair(ids, k + 2, st);
         const float4 P0 = rel[b0], P1 = rel[b1];
         const float4 V0 = m_v[b0], V1 = m_v[b1];
         pair(b0, P0, V0);
