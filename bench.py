@@ -405,6 +405,11 @@ def main():
             "clocks": r64["clocks"], "gpu_launches": int(round(r64["launches_per_step"] * args.steps)),
             "roofline": roofline, "launch": r64["launch"]}
 
+    if args.no_e2e:   # free the FP64 context before the next one (the largest workload needs the room)
+        r64["solver"].close()
+        r64.pop("state")
+        torch.cuda.empty_cache()
+
     if not args.no_mixed and args.only != "fp64":
         r32 = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, None, args.morton_bits,
                             graph)
@@ -422,6 +427,8 @@ def main():
                                       "peak_source": "nominal FP32 rate (unit counts x 2.07 GHz)",
                                       "kernel_ms": kms32, "flops_per_launch": f32}}
         r32["solver"].close()
+        r32.pop("state")
+        torch.cuda.empty_cache()
 
     if not args.no_ensemble and args.only is None:
         line["ensemble"] = run_ensemble(torch, sph, args.steps, max(args.warmup, 3), graph=graph)

@@ -223,6 +223,8 @@ __device__ __forceinline__ bool exact_pair(int64_t a, int64_t b, const double *_
 constexpr int kS2MaxWarps = 8;   // stage-2 warps per block: 1 .. 8 (sph_launch.stage2_warps)
 constexpr float kBandLo = 1.0f - 1.0f / 1024.0f;
 constexpr float kBandHi = 1.0f + 1.0f / 1024.0f;
+constexpr float kInvHi = 1.0f / kBandHi, kInvLo = 1.0f / kBandLo;   // the band applied to r^2 instead
+constexpr float kPreHi = 1.0f + 1.0f / 512.0f;   // candidate filter: wider than the band and its rounding
 
 constexpr unsigned long long kGrpAgg = 1ULL << 62;
 constexpr unsigned long long kGrpInc = 2ULL << 62;
@@ -296,7 +298,6 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     grel(Araw, ax, ay, az);
     const float hA = va ? h32[a] : 0.f;
     const float tA = (s32 * hA) * (s32 * hA);
-    const float tAhi = tA * kBandHi, tAlo = tA * kBandLo;
     // the group's box in the same relative FP32 coordinates, and its largest h (candidate filter)
     const float glo[3] = {warp_min_f(va ? ax : INFINITY), warp_min_f(va ? ay : INFINITY),
                           warp_min_f(va ? az : INFINITY)};
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
                 if (compact) {
                     float px, py, pz;
                     grel(P, px, py, pz);
-                    P = make_float4(px, py, pz, (s32 * hb) * (s32 * hb) * kBandHi);
+                    P = make_float4(px, py, pz, (s32 * hb) * (s32 * hb));
                 }
             }
             s_posw[lane] = P;
@@ -336,22 +337,24 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
             uint32_t hi = 0, lo = 0;
             if (compact) {
                 // Candidate filter (lane = candidate): drop a candidate farther from the group's box
-                // than (s max(h_max,g, h_b))^2 (1 + 2^-10).  Per axis |B - A| >= the gap to the box
-                // in FP32 too (rounding is monotone), and the squared sums below are formed in the
-                // same order as the pair test, so no particle of the group would keep a dropped one.
+                // than (s max(h_max,g, h_b))^2 (1 + 2^-9).  Per axis |B - A| >= the gap to the box
+                // in FP32 too (rounding is monotone), the squared sums below are formed in the same
+                // order as the pair test, and a kept pair has r^2 <= max(t_a, t_b) (1 + 2^-10) up to
+                // one rounding, so no particle of the group would keep a dropped candidate.
                 const float gx = fmaxf(fmaxf(glo[0] - P.x, P.x - ghi[0]), 0.f);
                 const float gy = fmaxf(fmaxf(glo[1] - P.y, P.y - ghi[1]), 0.f);
                 const float gz = fmaxf(fmaxf(glo[2] - P.z, P.z - ghi[2]), 0.f);
                 const float hm = fmaxf(hmax_g, hb);
-                const bool need = fmaf(gz, gz, fmaf(gy, gy, gx * gx)) <= (s32 * hm) * (s32 * hm) * kBandHi;
+                const bool need = fmaf(gz, gz, fmaf(gy, gy, gx * gx)) <= (s32 * hm) * (s32 * hm) * kPreHi;
                 uint32_t todo = __ballot_sync(0xffffffffu, need);
                 while (todo) {   // warp-uniform
                     const int jj = __ffs(todo) - 1;
                     todo &= todo - 1;
-                    const float4 B = s_posw[jj];
+                    const float4 B = s_posw[jj];   // .w = (s h_b)^2
                     const float r2 = sep2(B, true, ax, ay, az, ca);
-                    if (r2 <= fmaxf(tAhi, B.w)) hi |= 1u << jj;
-                    if (r2 < fmaxf(tAlo, s_tw[jj].x)) lo |= 1u << jj;
+                    const float T = fmaxf(tA, B.w);
+                    if (r2 * kInvHi <= T) hi |= 1u << jj;   // possibly inside: r^2 <= T (1 + 2^-10)
+                    if (r2 * kInvLo < T) lo |= 1u << jj;    // surely inside:   r^2 < T (1 - 2^-10)
                 }
             } else {
                 const int m = (rg.y - base) < 32 ? (int)(rg.y - base) : 32;
