@@ -3,6 +3,7 @@
 // into leaves, Karras radix tree (Table arrays_fig_karras) and bottom-up tight boxes + h_max.
 #include <cuda/atomic>
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <mutex>
 
@@ -22,17 +23,28 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v) {
     return v;
 }
 
+// min(floor(g), top) for g >= 0, 0 for g < 0 or NaN, read from the bits of g: exact, and on the
+// integer pipe (FP64 floor and conversion would take the FP64 pipe, which is 1/64 of FP32 here).
+__device__ __forceinline__ uint64_t floor_clamped(double g, uint64_t top) {
+    const long long b = __double_as_longlong(g);
+    if (b < 0) return 0;                                    // negative or -0.0
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    const uint64_t frac = (uint64_t)b & ((1ULL << 52) - 1);
+    if (e < 0) return 0;                                    // [0, 1)
+    if (e == 1024) return frac ? 0 : top;                   // NaN, +inf
+    if (e >= 52) return top;
+    const uint64_t f = (frac | (1ULL << 52)) >> (52 - e);
+    return f > top ? top : f;
+}
+
 // App. B "Morton codes": remap to [0,1) by (x-lo)/(hi-lo), integer grid of 2^21 per axis,
 // interleave X0 Y0 Z0 X1 ... with x most significant.  inv_span is 1/span when span is a power of
-// two (then the product equals the quotient bit for bit) and 0 otherwise (divide).
+// two (then the product equals the quotient bit for bit, and one product by inv_span 2^bits equals
+// the two exact scalings) and 0 otherwise (divide).
 __device__ __forceinline__ uint64_t quantise(double x, double lo, double span, double inv_span, int bits = 21) {
-    double s = inv_span != 0.0 ? (x - lo) * inv_span : (x - lo) / span;
     const double scale = (double)(1ULL << bits);   // exact power of two
-    double g = s * scale;
-    const double top = scale - 1.0;
-    if (!(g >= 0.0)) g = 0.0;
-    if (g > top) g = top;
-    return (uint64_t)floor(g);
+    const double g = inv_span != 0.0 ? (x - lo) * (inv_span * scale) : ((x - lo) / span) * scale;
+    return floor_clamped(g, (1ULL << bits) - 1);
 }
 
 struct Box3 {
@@ -289,11 +301,10 @@ __global__ void k_rel(int64_t n, const double *__restrict__ x, const double *__r
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         const double cell = b.span[k] * (1.0 / 1024.0);
-        double g = floor(b.inv_span[k] != 0.0 ? (p[k] - b.lo[k]) * (1024.0 * b.inv_span[k]) : (p[k] - b.lo[k]) / cell);
-        if (!(g >= 0.0)) g = 0.0;
-        if (g > 1023.0) g = 1023.0;
-        ci[k] = (uint32_t)g;
-        off[k] = (float)(p[k] - (b.lo[k] + g * cell));
+        const uint32_t g = (uint32_t)floor_clamped(
+            b.inv_span[k] != 0.0 ? (p[k] - b.lo[k]) * (1024.0 * b.inv_span[k]) : (p[k] - b.lo[k]) / cell, 1023);
+        ci[k] = g;
+        off[k] = (float)(p[k] - fma((double)g, cell, b.lo[k]));
     }
     rel[i] = make_float4(off[0], off[1], off[2], __uint_as_float((ci[0] << 20) | (ci[1] << 10) | ci[2]));
 }
@@ -433,6 +444,15 @@ __device__ __forceinline__ void load_node(const Node *nd, Node &o) {
     o.hi[0] = cc.x; o.hi[1] = cc.y; o.hi[2] = dd.x; o.pad = dd.y;
 }
 
+// Signed-integer key with the order of the double (finite values; -0.0 sorts below +0.0).
+__device__ __forceinline__ long long order_key(double v) {
+    const long long b = __double_as_longlong(v);
+    return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
+}
+__device__ __forceinline__ double from_order_key(long long k) {
+    return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffLL : k);
+}
+
 __global__ void k_boxes(Count Lc, const int64_t *__restrict__ leaf_first, const double *__restrict__ x,
                         const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h,
                         const int32_t *__restrict__ child, const int32_t *__restrict__ node_parent,
@@ -440,18 +460,24 @@ __global__ void k_boxes(Count Lc, const int64_t *__restrict__ leaf_first, const 
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t L = read_count(Lc, kAbortTree);
     if (j >= L) return;
-    Node b;
-    for (int k = 0; k < 3; k++) { b.lo[k] = INFINITY; b.hi[k] = -INFINITY; }
-    b.hmax = 0.0;
-    b.pad = 0.0;
+    // min / max over the leaf's particles as signed integers that order like the doubles (exact, on
+    // the integer pipe)
+    long long klo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, khi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN}, kh = 0;
     for (int64_t p = leaf_first[j]; p < leaf_first[j + 1]; p++) {
-        const double r[3] = {x[p], y[p], z[p]};
+        const long long r[3] = {order_key(x[p]), order_key(y[p]), order_key(z[p])};
         for (int k = 0; k < 3; k++) {
-            b.lo[k] = fmin(b.lo[k], r[k]);
-            b.hi[k] = fmax(b.hi[k], r[k]);
+            klo[k] = min(klo[k], r[k]);
+            khi[k] = max(khi[k], r[k]);
         }
-        b.hmax = fmax(b.hmax, h[p]);
+        kh = max(kh, __double_as_longlong(h[p]));   // h > 0: its bits order like its value
     }
+    Node b;
+    for (int k = 0; k < 3; k++) {
+        b.lo[k] = from_order_key(klo[k]);
+        b.hi[k] = from_order_key(khi[k]);
+    }
+    b.hmax = __longlong_as_double(kh);
+    b.pad = 0.0;
     const int64_t nin = L - 1;
     nodes[nin + j] = b;
     nodesf[nin + j] = to_float_outward(b);
