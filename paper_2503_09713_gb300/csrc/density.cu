@@ -43,7 +43,9 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         const double hinv2 = hinv * hinv;
         const float4 A = rel[a];
         const float lim = (float)(K::R * K::R) * kPreBand / ((float)hinv2);
-        double f0 = K::F0, g0 = 3.0 * K::F0, k0 = 12.0 * K::F0;
+        const float hinv2f = (float)hinv2;
+        double f0 = K::F0, g0 = 3.0 * K::F0;
+        float k0 = (float)(12.0 * K::F0);
         for (uint32_t k = 0; k < cnt; k++) {
             const uint32_t b = nb_at(ids, k, st);
             float fx, fy, fz;
@@ -62,12 +64,19 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 const double qdf = q * df;
                 f0 += f;
                 g0 += 3.0 * f + qdf;
-                k0 += 12.0 * f + 8.0 * qdf + q2 * K::d2(q);
+                // sum m d2W/dh2 only carries Omega over the last Newton step (below eps_c h^n, reading
+                // of Eq. sphomega): FP32 terms from the FP32 separation are far more accurate than
+                // that and keep the FP64 pipe free
+                const float q2f = (fx * fx + fy * fy + fz * fz) * hinv2f;
+                const float qf = sqrtf(q2f);
+                float ff, dff;
+                K::eval(qf, ff, dff);
+                k0 += 12.f * ff + 8.f * qf * dff + q2f * K::d2(qf);
             }
         }
         sf = f0;
         sg = g0;
-        sk = k0;
+        sk = (double)k0;
     } else {
         // FP32 path: four neighbours per iteration so that four independent gathers are in flight
         const float4 A = rel[a];

@@ -21,9 +21,10 @@ struct IntParams {
 // A particle moves less than a box length per step, so the floor is -1, 0 or 1: taken by compares
 // (the same values as the quotient form), with the quotient form kept for anything further out.
 __device__ __forceinline__ double wrap(double x, double lo, double hi) {
+    const long long kx = order_key(x);
+    if (kx >= order_key(lo) && kx < order_key(hi)) return x;   // inside (integer compares; NaN fails)
     const double L = hi - lo;
     double w;
-    if (x >= lo && x < hi) return x;
     if (x >= hi && x < hi + L) w = x - L;
     else if (x < lo && x >= lo - L) w = x + L;
     else w = x - L * floor((x - lo) / L);
@@ -58,9 +59,11 @@ __global__ void k_predict(int64_t n, double *__restrict__ x, double *__restrict_
     u[i] = (u[i] + ku) + ku;
     if (dhdt) {
         const double h0 = h[i];
-        double hp = h0 + dt * dhdt[i];
-        hp = fmin(fmax(hp, h0 * ip.inv_h_clamp), h0 * ip.h_clamp);
-        h[i] = hp;
+        const double hp = h0 + dt * dhdt[i];
+        const double hlo = h0 * ip.inv_h_clamp, hhi = h0 * ip.h_clamp;
+        // fmin(fmax(hp, hlo), hhi) by integer compares (NaN gives hlo, as fmax does)
+        const long long k = order_key(hp);
+        h[i] = (nan_bits(hp) || k < order_key(hlo)) ? hlo : (k > order_key(hhi) ? hhi : hp);
     }
 }
 

@@ -383,6 +383,19 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
     return (unsigned long long)__double_as_longlong(v);
 }
 
+// Signed-integer key with the order of the double (non-NaN values; -0.0 sorts below +0.0): compares
+// and min / max of doubles on the integer pipe (the FP64 pipe is 1/64 of FP32 on this GPU).
+__device__ __forceinline__ long long order_key(double v) {
+    const long long b = __double_as_longlong(v);
+    return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
+}
+__device__ __forceinline__ double from_order_key(long long k) {
+    return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffLL : k);
+}
+__device__ __forceinline__ bool nan_bits(double v) {
+    return ((unsigned long long)__double_as_longlong(v) << 1) > 0xffe0000000000000ULL;
+}
+
 // Warp-wide FP32 min / max (all 32 lanes).
 __device__ __forceinline__ float warp_min_f(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));

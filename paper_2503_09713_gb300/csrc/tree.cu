@@ -444,15 +444,6 @@ __device__ __forceinline__ void load_node(const Node *nd, Node &o) {
     o.hi[0] = cc.x; o.hi[1] = cc.y; o.hi[2] = dd.x; o.pad = dd.y;
 }
 
-// Signed-integer key with the order of the double (finite values; -0.0 sorts below +0.0).
-__device__ __forceinline__ long long order_key(double v) {
-    const long long b = __double_as_longlong(v);
-    return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
-}
-__device__ __forceinline__ double from_order_key(long long k) {
-    return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffLL : k);
-}
-
 __global__ void k_boxes(Count Lc, const int64_t *__restrict__ leaf_first, const double *__restrict__ x,
                         const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h,
                         const int32_t *__restrict__ child, const int32_t *__restrict__ node_parent,
