@@ -48,8 +48,8 @@ FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan)
 TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
                    "paper_2503_09713_gb300/csrc/sph_internal.cuh")
 TRAFFIC = {
-    "k_forces_fp64": {"bytes": 1073009664 + 95242496, "src_sha256": "6717f0e4c11a58969547e6bea737b5623bb5f2812ac06e59aeca531b1d4f4f74"},
-    "k_forces_mixed": {"bytes": 888898304 + 92820736, "src_sha256": "6717f0e4c11a58969547e6bea737b5623bb5f2812ac06e59aeca531b1d4f4f74"},
+    "k_forces_fp64": {"bytes": 1073750272 + 95486208, "src_sha256": "7d78f5527c4a37dccab8308d93c1cdd166cc2b4b29856812035098a9ed8892ed"},
+    "k_forces_mixed": {"bytes": 874337280 + 93192704, "src_sha256": "7d78f5527c4a37dccab8308d93c1cdd166cc2b4b29856812035098a9ed8892ed"},
 }
 
 
@@ -141,13 +141,16 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------------- GPU arm
 def run_precision(torch, sph, w, precision: int, steps: int, warmup: int, dist, timing_pass: bool,
-                  clocks: ClockSampler | None, morton_bits: int = 21, graph: bool = True):
+                  clocks: ClockSampler | None, morton_bits: int = 21, graph: bool = True, shape=None):
     p = sph.default_params(precision=precision, morton_bits=morton_bits)
     s = sph.DeviceState.from_numpy(w)
     solver = sph.Solver(p, w["n"])
     solver.set_graph(graph)           # each step replayed as one captured graph after the first
     solver.converge(s)
-    shape, _ = solver.autotune(s)     # launch shapes and reduction level, before the warm-up
+    if shape:                         # shapes pinned (e.g. a profile of the shapes a bench line chose)
+        solver.set_launch(**shape)
+    else:                             # launch shapes and reduction level, before the warm-up
+        shape, _ = solver.autotune(s)
     for _ in range(warmup):
         solver.step(s)
     stream = torch.cuda.current_stream()
@@ -191,7 +194,7 @@ def run_precision(torch, sph, w, precision: int, steps: int, warmup: int, dist, 
     return out
 
 
-def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349, graph: bool = True) -> dict:
+def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349, graph: bool = True, shape=None) -> dict:
     """Ensemble workload: 256 independent periodic boxes, N_b log-uniform in [2048, 262144], sigma_v
     U[0.01, 0.3], gamma in {5/3, 7/5}, mixed precision, one context for all boxes (one launch per
     stage), every box advanced by its own CFL step."""
@@ -207,7 +210,10 @@ def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349, graph: 
     solver = sph.Solver.batch(sph.default_params(precision=sph.SPH_MIXED), off, mass, gam)
     solver.set_graph(graph)
     solver.converge(s)
-    shape, _ = solver.autotune(s)
+    if shape:
+        solver.set_launch(**shape)
+    else:
+        shape, _ = solver.autotune(s)
     for _ in range(warmup):
         solver.step(s)
     stream = torch.cuda.current_stream()
@@ -305,6 +311,9 @@ def main():
                     help="bits per axis of the Morton codes (21: 63-bit codes; 10: the 30-bit u32 variant)")
     ap.add_argument("--no-graph", action="store_true",
                     help="run every step stage by stage instead of replaying it as one captured CUDA graph")
+    ap.add_argument("--shapes", default=None,
+                    help='JSON {"fp64": {...}, "mixed": {...}, "ensemble": {...}} of sph_launch fields used instead '
+                         'of the autotuner (to profile the shapes a bench line reports under "launch")')
     ap.add_argument("--only", choices=["fp64", "mixed", "ensemble"], default=None,
                     help="run one precision only (profiling); the headline needs both")
     args = ap.parse_args()
@@ -355,19 +364,20 @@ def main():
     n = w["n"]
     clocks = ClockSampler(local)
     graph = not args.no_graph
+    shapes = json.loads(args.shapes) if args.shapes else {}
     if args.only == "ensemble":
         print(json.dumps({"workload": "ensemble", **run_ensemble(torch, sph, args.steps, max(args.warmup, 3),
-                                                                 graph=graph)}))
+                                                                 graph=graph, shape=shapes.get("ensemble"))}))
         return
     if args.only == "mixed":
         r = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, clocks, args.morton_bits,
-                          graph)
+                          graph, shapes.get("mixed"))
         print(json.dumps({"workload": args.workload, "precision": "mixed", "ms_per_step": r["ms_per_step"],
                           "particles_per_s": n / (r["ms_per_step"] * 1e-3), "stage_ms": r["stage_ms"]}))
         r["solver"].close()
         return
     r64 = run_precision(torch, sph, w, 0, args.steps, max(args.warmup, 3), dist, True, clocks, args.morton_bits,
-                        graph)
+                        graph, shapes.get("fp64"))
     from paper_2503_09713_gb300 import replicas
     ms = replicas.max_over_ranks(r64["ms_per_step"], dist, "cuda")
     value = replicas.sum_over_ranks(n, dist, "cuda") / (ms * 1e-3)
@@ -412,7 +422,7 @@ def main():
 
     if not args.no_mixed and args.only != "fp64":
         r32 = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, None, args.morton_bits,
-                            graph)
+                            graph, shapes.get("mixed"))
         ms32 = r32["ms_per_step"]
         st32 = r32["timing_stats"]
         f32 = st32["n_pairs"] * FLOP_FORCE32_CAND + st32["force_pairs"] * FLOP_FORCE32_PAIR
@@ -431,7 +441,8 @@ def main():
         torch.cuda.empty_cache()
 
     if not args.no_ensemble and args.only is None:
-        line["ensemble"] = run_ensemble(torch, sph, args.steps, max(args.warmup, 3), graph=graph)
+        line["ensemble"] = run_ensemble(torch, sph, args.steps, max(args.warmup, 3), graph=graph,
+                                        shape=shapes.get("ensemble"))
 
     if not args.no_e2e:
         t, h2d, d2h = e2e_run(torch, sph, r64["solver"], r64["state"], args.steps)
