@@ -16,6 +16,7 @@ namespace sph {
 struct ForceParams {
     double mass, gamma, alpha_av, beta_av, alpha_u, c_cour, c_force;
     double kern_c;             // C_norm of the smoothing kernel
+    double kern_r;             // its support radius R_kern (in units of h)
     PairGeo geo;
     const double *box_mass;    // per-box particle mass (batch) or nullptr
     const double *box_gamma;   // per-box adiabatic index (batch) or nullptr
@@ -25,12 +26,13 @@ struct ForceParams {
 };
 
 // Per-particle FP64 record of the force loop: 128 bytes, read as 8 double2.
-// pre = P/(rho^2 Omega), qf = 1/(rho Omega), fn = C_norm/h^4, acs = alpha_AV c_s.
+// pre = P/(rho^2 Omega), hqf = 1/(2 rho Omega), fn = C_norm/h^4, acs = alpha_AV c_s,
+// rh2 = (R_kern h)^2 (a pair interacts when r^2 < max(rh2_a, rh2_b), the same bits as (R max h)^2).
 struct __align__(16) FRec {
     double x, y, z, h;
     double vx, vy, vz, u;
-    double pre, qf, acs, P;
-    double rho, hinv, fn, pad;
+    double pre, hqf, acs, P;
+    double rho, hinv, fn, rh2;
 };
 
 __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
@@ -62,10 +64,12 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
         FRec f;
         f.x = x[i]; f.y = y[i]; f.z = z[i]; f.h = hi;
         f.vx = vx[i]; f.vy = vy[i]; f.vz = vz[i]; f.u = ui;
-        f.pre = (gam - 1.0) * ui * qf; f.qf = qf;
+        f.pre = (gam - 1.0) * ui * qf; f.hqf = 0.5 * qf;
         f.acs = (alpha ? alpha[i] : fp.alpha_av) * sqrt(gam * (gam - 1.0) * ui);
         f.P = (gam - 1.0) * r * ui;
-        f.rho = r; f.hinv = hinv; f.fn = hinv * hinv * hinv * hinv * fp.kern_c; f.pad = 0.0;
+        f.rho = r; f.hinv = hinv; f.fn = hinv * hinv * hinv * hinv * fp.kern_c;
+        const double rad = __dmul_rn(fp.kern_r, hi);
+        f.rh2 = __dmul_rn(rad, rad);
         rec[i] = f;
         h32[i] = (float)hi;
     }
@@ -78,10 +82,10 @@ __device__ __forceinline__ void load_rec(const FRec *p, FRec &o) {
     t = __ldg(q + 1); o.z = t.x; o.h = t.y;
     t = __ldg(q + 2); o.vx = t.x; o.vy = t.y;
     t = __ldg(q + 3); o.vz = t.x; o.u = t.y;
-    t = __ldg(q + 4); o.pre = t.x; o.qf = t.y;
+    t = __ldg(q + 4); o.pre = t.x; o.hqf = t.y;
     t = __ldg(q + 5); o.acs = t.x; o.P = t.y;
     t = __ldg(q + 6); o.rho = t.x; o.hinv = t.y;
-    t = __ldg(q + 7); o.fn = t.x; o.pad = t.y;
+    t = __ldg(q + 7); o.fn = t.x; o.rh2 = t.y;
 }
 
 struct ForceOut {
@@ -167,10 +171,10 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
         const double dx = image_diff(A.x, B.x, sx, geo.L[0]);
         const double dy = image_diff(A.y, B.y, sy, geo.L[1]);
         const double dz = image_diff(A.z, B.z, sz, geo.L[2]);
-        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        const double hm = nonneg_max(A.h, B.h);
-        const double rad = __dmul_rn(K::R, hm);
-        if (!nonneg_lt(r2, __dmul_rn(rad, rad))) continue;
+        // r < R max(h_a, h_b); both kernels and their derivatives vanish at R, so the rounding of r^2
+        // (fused here) only decides pairs whose terms are zero
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        if (!nonneg_lt(r2, nonneg_max(A.rh2, B.rh2))) continue;
         ++npair;
         const double rinv = rsqrt(r2);
         const double r = r2 * rinv;
@@ -183,8 +187,8 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
         double Aa = A.pre, Ab = B.pre;
         if (__double_as_longlong(vdotr) < 0) {   // sign bit: approaching (-0 changes nothing below)
             const double w = fp.beta_av * vdotr;   // = -beta |v.rhat|
-            Aa -= 0.5 * (A.acs - w) * vdotr * A.qf;
-            Ab -= 0.5 * (B.acs - w) * vdotr * B.qf;
+            Aa -= (A.acs - w) * vdotr * A.hqf;
+            Ab -= (B.acs - w) * vdotr * B.hqf;
             vs = nonneg_max(vs, A.acs - w);
         }
         const double sc_ = (Aa * Fa + Ab * Fb) * rinv;
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
             const double t = 2.0 * fabs(A.P - B.P);   // v_sig^u = sqrt(t / (rho_a + rho_b))
             if (__double_as_longlong(t) > 0) {
                 const double vsu = t * rsqrt(t * (A.rho + B.rho));
-                dus += fp.alpha_u * vsu * (A.u - B.u) * 0.5 * (Fa * A.qf + Fb * B.qf);
+                dus += fp.alpha_u * vsu * (A.u - B.u) * (Fa * A.hqf + Fb * B.hqf);
             }
         }
     }
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
     out.az[a] = azs;
     out.du[a] = dus;
     out.vsig[a] = vs;
-    out.dhdt[a] = -A.h * A.qf * (1.0 / 3.0) * m * divs;
+    out.dhdt[a] = -A.h * (2.0 * A.hqf) * (1.0 / 3.0) * m * divs;
     tdt = dt_candidate(A.h, vs, axs, ays, azs, fp);
     }
     dt_reduce(tdt, npair, sc, fp.box_dt_next, box);
@@ -342,6 +346,7 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     fp.c_cour = c->p.c_cour;
     fp.c_force = c->p.c_force;
     fp.kern_c = with_kernel(c->p.kernel, [](auto kern) { return decltype(kern)::C; });
+    fp.kern_r = kernel_radius(c->p.kernel);
     fp.geo = make_pair_geo(c->p);
     fp.box_mass = c->batch ? c->box_mass : nullptr;
     fp.box_gamma = c->batch ? c->box_gamma : nullptr;
