@@ -58,7 +58,12 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
             const double q2 = (dx * dx + dy * dy + dz * dz) * hinv2;
             if (nonneg_lt(q2, K::R * K::R)) {
                 ++nin;
-                const double q = sqrt(q2);
+                const float q2f = (fx * fx + fy * fy + fz * fz) * hinv2f;
+                const float qf = sqrtf(q2f);
+                // q = sqrt(q2) by one Newton-Raphson step from the FP32 root of the FP32 separation
+                // (relative error below 1e-13)
+                const double qd = (double)qf;
+                const double q = qf > 0.f ? fma(fma(-qd, qd, q2), (double)(0.5f / qf), qd) : sqrt(q2);
                 double f, df;
                 K::eval(q, f, df);
                 const double qdf = q * df;
@@ -67,8 +72,6 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 // sum m d2W/dh2 only carries Omega over the last Newton step (below eps_c h^n, reading
                 // of Eq. sphomega): FP32 terms from the FP32 separation are far more accurate than
                 // that and keep the FP64 pipe free
-                const float q2f = (fx * fx + fy * fy + fz * fz) * hinv2f;
-                const float qf = sqrtf(q2f);
                 float ff, dff;
                 K::eval(qf, ff, dff);
                 k0 += 12.f * ff + 8.f * qf * dff + q2f * K::d2(qf);
