@@ -181,23 +181,41 @@ __global__ void __launch_bounds__(kRsThreads) k_onesweep(const uint64_t *__restr
 
     uint32_t excl = 0;
     if (tile > 0) {
+        // look-back over the preceding tiles, kLbBatch words per round trip (tile 0 is inclusive, so
+        // the walk never passes it)
+        constexpr int kLbBatch = 8;
         int64_t j = tile - 1;
         uint32_t spins = 0;
-        while (j >= 0) {
-            cuda::atomic_ref<uint32_t, cuda::thread_scope_device> other(lookback[j * 256 + d]);
-            const uint32_t w = other.load(cuda::memory_order_relaxed);
-            const uint32_t fl = w & ~kLbMask;
-            if (fl == 0u) {
+        bool done = false;
+        while (!done && j >= 0) {
+            uint32_t w[kLbBatch];
+#pragma unroll
+            for (int q = 0; q < kLbBatch; q++) {
+                w[q] = kLbInc;
+                if (j - q >= 0) {
+                    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> other(lookback[(j - q) * 256 + d]);
+                    w[q] = other.load(cuda::memory_order_relaxed);
+                }
+            }
+            int q = 0;
+            for (; q < kLbBatch; q++) {
+                const uint32_t fl = w[q] & ~kLbMask;
+                if (fl == 0u) break;   // not published yet: read again from here
+                excl += w[q] & kLbMask;
+                if (fl == kLbInc) {
+                    done = true;
+                    break;
+                }
+            }
+            if (done) break;
+            j -= q;
+            if (q < kLbBatch) {
                 if (++spins > kSpinLimit) {
                     atomicOr(flags, kErrTimeout);
                     break;
                 }
                 __nanosleep(32);
-                continue;
             }
-            excl += w & kLbMask;
-            if (fl == kLbInc) break;
-            --j;
         }
         mine.store(kLbInc | (excl + total), cuda::memory_order_relaxed);
     }
@@ -291,11 +309,8 @@ __global__ void k_copy_back(int64_t n, GatherArgs g) {
 
 // FP32 cell-relative coordinates: cell index on a 2^10 grid per axis and the FP32 offset from the
 // cell corner; packed cell index in .w (x<<20 | y<<10 | z).
-__global__ void k_rel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
-                      const double *__restrict__ z, Box3 b, float4 *__restrict__ rel) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double p[3] = {x[i], y[i], z[i]};
+__device__ __forceinline__ float4 rel_coords(double px, double py, double pz, const Box3 &b) {
+    const double p[3] = {px, py, pz};
     uint32_t ci[3];
     float off[3];
 #pragma unroll
@@ -306,7 +321,25 @@ __global__ void k_rel(int64_t n, const double *__restrict__ x, const double *__r
         ci[k] = g;
         off[k] = (float)(p[k] - fma((double)g, cell, b.lo[k]));
     }
-    rel[i] = make_float4(off[0], off[1], off[2], __uint_as_float((ci[0] << 20) | (ci[1] << 10) | ci[2]));
+    return make_float4(off[0], off[1], off[2], __uint_as_float((ci[0] << 20) | (ci[1] << 10) | ci[2]));
+}
+
+__global__ void k_rel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                      const double *__restrict__ z, Box3 b, float4 *__restrict__ rel) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    rel[i] = rel_coords(x[i], y[i], z[i], b);
+}
+
+// The copy back of the first gathered block (x, y, z in its first three fields) with the relative
+// coordinates of the reordered positions computed on the way.
+__global__ void k_copy_back_rel(int64_t n, GatherArgs g, Box3 b, float4 *__restrict__ rel) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double px = g.src[0][i], py = g.src[1][i], pz = g.src[2][i];
+    for (int f = 0; f < g.nf; f++) g.dst[f][i] = g.src[f][i];
+    if (g.id_dst) g.id_dst[i] = g.id_src[i];
+    rel[i] = rel_coords(px, py, pz, b);
 }
 
 // ====================================================================================== mask
@@ -697,11 +730,19 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
         }
         b.id_src = g.id_dst ? c->id_tmp : nullptr;   // the id is complete after the first block
         b.id_dst = g.id_dst ? s->id : nullptr;
-        k_copy_back<<<grid_for(n, 256), 256, 0, c->stream>>>(n, b);
-        SPH_LAUNCH_CHECK(c, "k_copy_back");
+        if (f0 == 0 && g.nf >= 3) {   // fields[0..2] are x, y, z
+            k_copy_back_rel<<<grid_for(n, 256), 256, 0, c->stream>>>(n, b, bx, c->rel);
+            SPH_LAUNCH_CHECK(c, "k_copy_back_rel");
+        } else {
+            k_copy_back<<<grid_for(n, 256), 256, 0, c->stream>>>(n, b);
+            SPH_LAUNCH_CHECK(c, "k_copy_back");
+        }
     }
-    k_rel<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, bx, c->rel);
-    SPH_LAUNCH_CHECK(c, "k_rel");
+    const bool rel_done = nf >= 3;
+    if (!rel_done) {
+        k_rel<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, bx, c->rel);
+        SPH_LAUNCH_CHECK(c, "k_rel");
+    }
 
     // A3 mask + reduction
     k_mask_init<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->mu, c->mask[0]);
