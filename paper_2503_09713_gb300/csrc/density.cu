@@ -17,7 +17,7 @@
 namespace sph {
 
 struct DensParams {
-    double mass, hfact, h_tol, h_clamp, chi;
+    double mass, hfact, h_tol, h_clamp, inv_h_clamp, chi;
     int max_iter;
     PairGeo geo;
     const double *box_mass;   // per-box particle mass (batch) or nullptr
@@ -151,25 +151,33 @@ __global__ void __launch_bounds__(256, kMixed ? 4 : 1) k_density(int64_t n, cons
         ++it;
         double sf, sg, sk;
         density_sums<K, kMixed>(a, ha, cnt, ids, st, x, y, z, rel, dp.geo, sf, sg, sk, nin);
+        // one division for 1/h and one for the Newton step; the clamps and tests compare the
+        // bits of the doubles (integer pipe) and |dh| <= eps_c h^n needs no quotient
         const double hinv = 1.0 / ha;
         const double hinv3 = hinv * hinv * hinv;
-        const double rho_sum = m * sf * hinv3 * K::C;
-        const double dsum = -m * sg * hinv3 * hinv * K::C;   // sum_b m dW/dh
+        const double mch3 = m * K::C * hinv3;
+        const double rho_sum = mch3 * sf;
+        const double dsum = -mch3 * sg * hinv;   // sum_b m dW/dh
         const double rho_h = m * hf3 * hinv3;
         double hnew = ha - (rho_sum - rho_h) / (dsum + 3.0 * rho_h * hinv);
-        if (hnew > ha * dp.h_clamp) hnew = ha * dp.h_clamp;
-        else if (hnew < ha / dp.h_clamp) hnew = ha / dp.h_clamp;
-        const double eps = fabs(hnew - ha) / hn;
-        if (hnew > hn * dp.chi) {
+        if (!nan_bits(hnew)) {   // step clamped to [h / lambda, h lambda]
+            const double hi_c = ha * dp.h_clamp, lo_c = ha * dp.inv_h_clamp;
+            const long long kn = order_key(hnew);
+            if (kn > order_key(hi_c)) hnew = hi_c;
+            else if (kn < order_key(lo_c)) hnew = lo_c;
+        }
+        const double dh = hnew - ha;
+        const bool small = !nonneg_lt(dp.h_tol * hn, fabs(dh));   // |dh| <= eps_c h^n (NaN: no)
+        if (!nan_bits(hnew) && nonneg_lt(hn * dp.chi, hnew)) {
             hnew = hn * dp.chi;
             stale = true;
         }
         // sum m dW/dh at the new h, to first order in the step (|dh| <= eps_c h^n at convergence,
         // so the neglected term is O(eps_c^2))
-        dsum_new = dsum + m * sk * hinv3 * hinv * hinv * K::C * (hnew - ha);
+        dsum_new = dsum + mch3 * sk * hinv * hinv * (hnew - ha);
         ha = hnew;
         if (stale) break;
-        if (eps <= dp.h_tol) {
+        if (small) {
             conv = true;
             break;
         }
@@ -204,6 +212,7 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
     dp.hfact = c->p.hfact;
     dp.h_tol = c->p.h_tol;
     dp.h_clamp = c->p.h_clamp;
+    dp.inv_h_clamp = 1.0 / c->p.h_clamp;
     dp.chi = c->p.cache_tol;
     dp.max_iter = c->p.h_max_iter;
     dp.geo = make_pair_geo(c->p);
