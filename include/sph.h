@@ -199,11 +199,13 @@ int sph_set_params(sph_ctx *ctx, const sph_params *p);
  * the tree is kept in the context.  Errors: INVALID_ARG (n > n_cap), NONFINITE, TIMEOUT, CUDA. */
 int sph_build_tree(sph_ctx *ctx, sph_state *s);
 
-/* A7 (App. C two-stage neighbour cache, App. D criteria): stage 1 walks the tree once per group of
- * 32 consecutive particles with the group-group criterion at radius 2*cache_tol*max(h); stage 2
- * keeps, for every particle a, each b != a with |r_ab|^2 < (2*cache_tol*max(h_a,h_b))^2 (nearest
- * periodic image, FP64 decision).  h = state->h is recorded as h^n.  *n_pairs (may be NULL)
- * receives the number of cached pairs.  Requires sph_build_tree.  Errors: ORDER, CAPACITY, OOM, CUDA. */
+/* A7 (App. C two-stage neighbour cache, App. D criteria): stage 1 walks the tree once per group (the
+ * largest tree nodes of at most 32 particles of one box, sph_tree_view.group_start), keeping every
+ * cell whose box lies within R_kern*cache_tol*max(h_max) of the group's box; stage 2 keeps, for
+ * every particle a, each b != a with |r_ab|^2 < (R_kern*cache_tol*max(h_a,h_b))^2 (nearest periodic
+ * image, FP64 decision), R_kern = 2 for M4.  h = state->h is recorded as h^n.  *n_pairs (may be
+ * NULL) receives the number of cached pairs.  Requires sph_build_tree.  Errors: ORDER, CAPACITY,
+ * OOM, CUDA. */
 int sph_find_neighbours(sph_ctx *ctx, const sph_state *s, int64_t *n_pairs);
 
 /* A8 (App. F): per particle, Newton-Raphson on rho_sum(h) - m (hfact/h)^3 over the cached
@@ -244,7 +246,7 @@ int sph_tree_sizes(sph_ctx *ctx, int64_t *n, int64_t *n_leaves);
 int sph_export_tree(sph_ctx *ctx, sph_tree_view *view);
 
 /* Copy the neighbour cache as CSR to host arrays: off[n+1] (int64) and ids[n_pairs] (indices in
- * the current, Morton, order; each list in the cache's walk order). */
+ * the current, Morton, order; each list in increasing index order). */
 int sph_export_neighbours(sph_ctx *ctx, int64_t *off, uint32_t *ids);
 
 /* Statistics of the last calls. */
