@@ -178,9 +178,7 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
         ++npair;
         const double rinv = rsqrt(r2);
         const double r = r2 * rinv;
-        double f, dfa, dfb;
-        K::eval(r * A.hinv, f, dfa);
-        K::eval(r * B.hinv, f, dfb);
+        const double dfa = kernel_df<K>(r * A.hinv), dfb = kernel_df<K>(r * B.hinv);
         const double Fa = dfa * A.fn;
         const double Fb = dfb * B.fn;
         const double vdotr = ((A.vx - B.vx) * dx + (A.vy - B.vy) * dy + (A.vz - B.vz) * dz) * rinv;
@@ -262,9 +260,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *_
         const float4 RB = m_r[b];
         const float rinv = rsqrtf(r2);
         const float r = r2 * rinv;
-        float f_, dfa, dfb;
-        K::eval(r * hia, f_, dfa);
-        K::eval(r * VB.w, f_, dfb);
+        const float dfa = kernel_df<K>(r * hia), dfb = kernel_df<K>(r * VB.w);
         const float Fa = dfa * Fa_n;
         const float Fb = dfb * RB.z;
         const float vdotr = fmaf(VA.z - VB.z, dz, fmaf(VA.y - VB.y, dy, (VA.x - VB.x) * dx)) * rinv;

@@ -2,6 +2,7 @@
 // Kahan summation for the FP32 pair sums of the mixed-precision path.
 #pragma once
 #include <climits>
+#include <type_traits>
 
 #include "sph_internal.cuh"
 
@@ -41,6 +42,25 @@ struct Kernel<SPH_KERNEL_M4> {
     template <typename T>
     __device__ static T d2(T q) { return T(1.5) * posp(T(2), q) - T(6) * posp(T(1), q); }
 };
+
+// f'(q) alone (the force loops need no f): from eval, except for M4, where the two pieces
+// q (9/4 q - 3) (q < 1) and -3/4 (2-q)^2 (1 <= q < 2) take one operation fewer than the truncated
+// powers.
+__device__ __forceinline__ bool below_one(double q) { return nonneg_lt(q, 1.0); }
+__device__ __forceinline__ bool below_one(float q) { return q < 1.f; }
+template <typename K, typename T>
+__device__ __forceinline__ T kernel_df(T q) {
+    if constexpr (std::is_same<K, Kernel<SPH_KERNEL_M4>>::value) {
+        const T t2 = posp(T(2), q);
+        const T outer = T(-0.75) * t2 * t2;
+        const T inner = q * (T(2.25) * q - T(3));
+        return below_one(q) ? inner : outer;
+    } else {
+        T f, df;
+        K::eval(q, f, df);
+        return df;
+    }
+}
 
 template <>
 struct Kernel<SPH_KERNEL_M5> {
