@@ -6,7 +6,7 @@ Tolerances (derived from the arithmetic):
     order (1e-6)^2, so |h_gpu/h_ref - 1| <= 1e-9.
   * forces, FP64, on the same h and Omega: sums of ~60 terms in a different order, each term at most
     c_s^2/h per unit mass: |da| <= 1e-12 * 64 * c_s^2/h_min (about 1e-10 of max|a| here).
-  * mixed precision against FP64 (spec bar): rho relative <= 1e-5, a <= 1e-4 of max|a|.
+  * mixed precision against FP64 (the mixed path's tolerance): rho relative <= 1e-5, a <= 1e-4 of max|a|.
 """
 import numpy as np
 import pytest
