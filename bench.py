@@ -48,8 +48,8 @@ FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan)
 TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
                    "paper_2503_09713_gb300/csrc/sph_internal.cuh")
 TRAFFIC = {
-    "k_forces_fp64": {"bytes": 1073566976 + 95490816, "src_sha256": "0925f8d0602493cf922678f9ef58f8c7e99d1ec986f797ccdda98eb20a754791"},
-    "k_forces_mixed": {"bytes": 873945088 + 93592064, "src_sha256": "0925f8d0602493cf922678f9ef58f8c7e99d1ec986f797ccdda98eb20a754791"},
+    "k_forces_fp64": {"bytes": 1073871616 + 95938560, "src_sha256": "359194fbb3643f353261396a8df7c4dcbe9b3f04f3e97ac4a726084568c7c0cd"},
+    "k_forces_mixed": {"bytes": 874044160 + 93720576, "src_sha256": "359194fbb3643f353261396a8df7c4dcbe9b3f04f3e97ac4a726084568c7c0cd"},
 }
 
 
