@@ -44,7 +44,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         const float4 A = rel[a];
         const float lim = (float)(K::R * K::R) * kPreBand / ((float)hinv2);
         const float hinv2f = (float)hinv2;
-        double f0 = K::F0, g0 = 3.0 * K::F0;
+        double f0 = K::F0, gq = 0.0;   // sum f and sum q f' (sum (3 f + q f') = 3 sum f + sum q f')
         float k0 = (float)(12.0 * K::F0);
         for (uint32_t k = 0; k < cnt; k++) {
             const uint32_t b = nb_at(ids, k, st);
@@ -66,9 +66,8 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 const double q = qf > 0.f ? fma(fma(-qd, qd, q2), (double)(0.5f / qf), qd) : sqrt(q2);
                 double f, df;
                 K::eval(q, f, df);
-                const double qdf = q * df;
                 f0 += f;
-                g0 += 3.0 * f + qdf;
+                gq = fma(q, df, gq);
                 // sum m d2W/dh2 only carries Omega over the last Newton step (below eps_c h^n, reading
                 // of Eq. sphomega): FP32 terms from the FP32 separation are far more accurate than
                 // that and keep the FP64 pipe free
@@ -78,7 +77,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
             }
         }
         sf = f0;
-        sg = g0;
+        sg = fma(3.0, f0, gq);
         sk = (double)k0;
     } else {
         // FP32 path: four neighbours per iteration so that four independent gathers are in flight
