@@ -43,20 +43,20 @@ FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan)
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the roofline kernels,
 # from one ncu capture of the Sedov 128^3 step (profiles/forces_sedov128_traffic.md), valid only for
-# the kernel sources it was taken on: the SHA-256 of those files is stored beside each figure and a
-# mismatch reports null.
+# that workload and for the kernel sources it was taken on: the workload and the SHA-256 of those
+# files are stored beside each figure, and any other workload or a changed source reports null.
 TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
                    "paper_2503_09713_gb300/csrc/sph_internal.cuh")
 TRAFFIC = {
-    "k_forces_fp64": {"bytes": 1073871616 + 95938560, "src_sha256": "359194fbb3643f353261396a8df7c4dcbe9b3f04f3e97ac4a726084568c7c0cd"},
-    "k_forces_mixed": {"bytes": 874044160 + 93720576, "src_sha256": "359194fbb3643f353261396a8df7c4dcbe9b3f04f3e97ac4a726084568c7c0cd"},
+    "k_forces_fp64": {"workload": "sedov128", "bytes": 1073871616 + 95938560, "src_sha256": "359194fbb3643f353261396a8df7c4dcbe9b3f04f3e97ac4a726084568c7c0cd"},
+    "k_forces_mixed": {"workload": "sedov128", "bytes": 874044160 + 93720576, "src_sha256": "359194fbb3643f353261396a8df7c4dcbe9b3f04f3e97ac4a726084568c7c0cd"},
 }
 
 
-def kernel_traffic(name):
+def kernel_traffic(name, workload):
     import hashlib
     t = TRAFFIC.get(name)
-    if not t:
+    if not t or t["workload"] != workload:
         return None
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
@@ -396,7 +396,7 @@ def main():
     kms = stage[dominant]
     achieved = flops / (kms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": kernel_traffic(kname),
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": kernel_traffic(kname, args.workload),
                 "peak_source": "nominal FP64 rate (unit counts x 2.07 GHz)", "kernel_ms": kms,
                 "flops_per_launch": flops, "stage_ms": stage}
 
@@ -433,7 +433,7 @@ def main():
                          "stage_ms": r32["stage_ms"], "launch": r32["launch"],
                          "roofline": {"bound": "alu", "kernel": "k_forces_mixed", "achieved": ach32,
                                       "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach32 / FP32_PEAK_TFLOPS,
-                                      "traffic": kernel_traffic("k_forces_mixed"),
+                                      "traffic": kernel_traffic("k_forces_mixed", args.workload),
                                       "peak_source": "nominal FP32 rate (unit counts x 2.07 GHz)",
                                       "kernel_ms": kms32, "flops_per_launch": f32}}
         r32["solver"].close()
