@@ -48,8 +48,8 @@ FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan)
 TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
                    "paper_2503_09713_gb300/csrc/sph_internal.cuh")
 TRAFFIC = {
-    "k_forces_fp64": {"workload": "sedov128", "bytes": 1073871616 + 95938560, "src_sha256": "359194fbb3643f353261396a8df7c4dcbe9b3f04f3e97ac4a726084568c7c0cd"},
-    "k_forces_mixed": {"workload": "sedov128", "bytes": 874044160 + 93720576, "src_sha256": "359194fbb3643f353261396a8df7c4dcbe9b3f04f3e97ac4a726084568c7c0cd"},
+    "k_forces_fp64": {"workload": "sedov128", "bytes": 1074084352 + 95674368, "src_sha256": "41719363cf4180bf10302f0226082239e2db6fafe141c933c9283e9e372dcb32"},
+    "k_forces_mixed": {"workload": "sedov128", "bytes": 874375168 + 93700096, "src_sha256": "41719363cf4180bf10302f0226082239e2db6fafe141c933c9283e9e372dcb32"},
 }
 
 

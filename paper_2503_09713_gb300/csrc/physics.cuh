@@ -39,18 +39,37 @@ struct Kernel<SPH_KERNEL_M4> {
         f = T(0.25) * t2 * t2 * t2 - t1 * t1 * t1;
         df = T(-0.75) * t2 * t2 + T(3) * t1 * t1;
     }
+    // FP64: the same function as one polynomial per piece in Horner form, the piece chosen by integer
+    // compares of q's bits, so f and f' cost 3 + 2 fused multiply-adds on the FP64 pipe instead of
+    // the 11 FP64 operations of the truncated powers (near q = 2 the expanded form loses the relative
+    // accuracy of the small value, not the absolute one: |error| <= a few ulp(2) = 1e-15):
+    //   q < 1:      f = 1 - 3/2 q^2 + 3/4 q^3,        f' = -3 q + 9/4 q^2
+    //   1 <= q < 2: f = 2 - 3 q + 3/2 q^2 - 1/4 q^3,  f' = -3 + 3 q - 3/4 q^2
+    __device__ static void eval(double q, double &f, double &df) {
+        const bool in1 = nonneg_lt(q, 1.0), in2 = nonneg_lt(q, 2.0);
+        const double c3 = in1 ? 0.75 : -0.25, c2 = in1 ? -1.5 : 1.5, c1 = in1 ? 0.0 : -3.0, c0 = in1 ? 1.0 : 2.0;
+        f = in2 ? fma(fma(fma(c3, q, c2), q, c1), q, c0) : 0.0;
+        df = in2 ? dfdq_piece(q, in1) : 0.0;
+    }
+    __device__ static double dfdq(double q) { return nonneg_lt(q, 2.0) ? dfdq_piece(q, nonneg_lt(q, 1.0)) : 0.0; }
+    __device__ static double dfdq_piece(double q, bool in1) {
+        const double d2 = in1 ? 2.25 : -0.75, d1 = in1 ? -3.0 : 3.0, d0 = in1 ? 0.0 : -3.0;
+        return fma(fma(d2, q, d1), q, d0);
+    }
     template <typename T>
     __device__ static T d2(T q) { return T(1.5) * posp(T(2), q) - T(6) * posp(T(1), q); }
 };
 
-// f'(q) alone (the force loops need no f): from eval, except for M4, where the two pieces
-// q (9/4 q - 3) (q < 1) and -3/4 (2-q)^2 (1 <= q < 2) take one operation fewer than the truncated
-// powers.
+// f'(q) alone (the force loops need no f): from eval, except for M4, where the FP64 loop takes the
+// Horner form above and the FP32 loop the two pieces q (9/4 q - 3) (q < 1) and -3/4 (2-q)^2
+// (1 <= q < 2), one operation fewer than the truncated powers.
 __device__ __forceinline__ bool below_one(double q) { return nonneg_lt(q, 1.0); }
 __device__ __forceinline__ bool below_one(float q) { return q < 1.f; }
 template <typename K, typename T>
 __device__ __forceinline__ T kernel_df(T q) {
-    if constexpr (std::is_same<K, Kernel<SPH_KERNEL_M4>>::value) {
+    if constexpr (std::is_same<K, Kernel<SPH_KERNEL_M4>>::value && std::is_same<T, double>::value) {
+        return K::dfdq(q);
+    } else if constexpr (std::is_same<K, Kernel<SPH_KERNEL_M4>>::value) {
         const T t2 = posp(T(2), q);
         const T outer = T(-0.75) * t2 * t2;
         const T inner = q * (T(2.25) * q - T(3));
