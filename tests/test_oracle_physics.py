@@ -103,6 +103,57 @@ def test_lattice_density_continuum_limit():
         assert abs(rs[0] / rho0 - 1.0) < tol
 
 
+def _lattice_shell_counts(smax):
+    """Number of integer vectors k with |k|^2 = s, for s <= smax (enumerated)."""
+    r = math.isqrt(smax) + 1
+    c = {}
+    for i in range(-r, r + 1):
+        for j in range(-r, r + 1):
+            for k in range(-r, r + 1):
+                s = i * i + j * j + k * k
+                if s <= smax:
+                    c[s] = c.get(s, 0) + 1
+    return c
+
+
+def test_lattice_density_root_by_shell_sums():
+    """Perfect cubic lattice (dx = 1, m = 1), M4 (C = 1/pi), hfact 1.2: rho_sum(h) is the finite sum
+    over lattice shells sum_s N_s W(sqrt(s), h), so the root of rho_sum(h) = (hfact/h)^3 (Eq. rhoh)
+    and Omega = 1 + h/(3 rho) sum m dW/dh (Eq. sphomega) follow by bisection on that sum, without the
+    oracle's neighbour search or iteration: h/dx = 1.199670052480, rho/rho_0 = 1.000825322613,
+    Omega = 0.9808953172, with the 56 points of the shells |k|^2 = 1..5 inside 2h.  The oracle on a
+    10^3 periodic lattice must give the same values to rounding."""
+    shells = _lattice_shell_counts(16)   # 2h < 4 dx for every h tried
+
+    def f(q):
+        return 1 - 1.5 * q * q + 0.75 * q ** 3 if q < 1 else (0.25 * (2 - q) ** 3 if q < 2 else 0.0)
+
+    def df(q):
+        return -3 * q + 2.25 * q * q if q < 1 else (-0.75 * (2 - q) ** 2 if q < 2 else 0.0)
+
+    def g(h):
+        return sum(n * f(math.sqrt(s) / h) for s, n in shells.items()) - math.pi * 1.2 ** 3
+
+    lo, hi = 1.1, 1.3
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (lo, mid) if g(lo) * g(mid) <= 0 else (mid, hi)
+    h = 0.5 * (lo + hi)
+    rho = sum(n * f(math.sqrt(s) / h) for s, n in shells.items()) / (math.pi * h ** 3)
+    dwdh = -sum(n * (3 * f(math.sqrt(s) / h) + math.sqrt(s) / h * df(math.sqrt(s) / h))
+                for s, n in shells.items()) / (math.pi * h ** 4)
+    om = 1 + h / (3 * rho) * dwdh
+    assert abs(h - 1.199670052480) < 1e-12 and abs(rho - 1.000825322613) < 1e-12
+    assert abs(om - 0.9808953172) < 1e-10
+    assert sum(n for s, n in shells.items() if 0 < s < (2 * h) ** 2) == 56
+    w = WL.perfect_lattice(10)
+    hr = O.density_root(w["x"], w["y"], w["z"], 1.2, 2.0 * w["dx"])
+    assert np.max(np.abs(hr / w["dx"] - h)) < 1e-12
+    rs, omo = O.density_at(w["x"], w["y"], w["z"], hr, w["mass"], 1.2)
+    assert np.max(np.abs(rs * w["dx"] ** 3 / w["mass"] - rho)) < 1e-12
+    assert np.max(np.abs(omo - om)) < 1e-12
+
+
 def test_root_satisfies_density_equation_jittered():
     """Invariant h_a (rho_sum,a / m)^(1/3) = hfact at the root, and Alg. F agrees with the root to its
     tolerance."""
