@@ -40,6 +40,37 @@ def test_host_only_entry_points(lib):
     assert lib.sph_destroy(None) == sph.SPH_OK
 
 
+def test_degenerate_sizes_are_refused_before_any_device_call(lib):
+    """An empty particle set, an empty or oversized batch and malformed box tables are argument
+    errors found on the host (the context pointer stays NULL)."""
+    import numpy as np
+    p = sph.default_params()
+    ctx = ctypes.c_void_p(1)
+    assert lib.sph_create(ctypes.byref(p), 0, 0, None, ctypes.byref(ctx)) == sph.SPH_ERR_INVALID_ARG
+    assert ctx.value is None
+    assert lib.sph_create(ctypes.byref(p), (1 << 30) + 1, 0, None, ctypes.byref(ctx)) == sph.SPH_ERR_INVALID_ARG
+
+    def batch(off, mass, gamma=None, n_boxes=None):
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        mass = np.ascontiguousarray(mass, dtype=np.float64)
+        g = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.float64)
+        out = ctypes.c_void_p(1)
+        nb = len(off) - 1 if n_boxes is None else n_boxes
+        r = lib.sph_batch_create(ctypes.byref(p), nb, off.ctypes.data, mass.ctypes.data,
+                                 None if g is None else g.ctypes.data, 0, None, ctypes.byref(out))
+        assert out.value is None
+        return r
+
+    bad = sph.SPH_ERR_INVALID_ARG
+    assert batch([0, 0, 0], [1.0, 1.0]) == bad                 # every box empty
+    assert batch([5, 10], [1.0]) == bad                        # offsets do not start at 0
+    assert batch([0, 10, 5], [1.0, 1.0]) == bad                # negative box size
+    assert batch([0, 10], [0.0]) == bad                        # mass not positive
+    assert batch([0, 10], [1.0], gamma=[1.0]) == bad           # gamma not above 1
+    assert batch([0, 10], [1.0], n_boxes=0) == bad             # no box
+    assert batch(np.arange(4098) * 4, np.ones(4097)) == bad    # more than 4096 boxes
+
+
 def _c_layout(struct, fields):
     """sizeof and offsetof of a struct of include/sph.h, from the C compiler (gcc, host)."""
     import os
