@@ -42,7 +42,7 @@ FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan)
                              # conductivity (Kahan), divergence
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the roofline kernels,
-# from one ncu capture of the Sedov 128^3 step (profiles/forces_sedov128_traffic.md), valid only for
+# from one ncu capture of the Sedov 128^3 step (summarised under profiles/), valid only for
 # that workload and for the kernel sources it was taken on: the workload and the SHA-256 of those
 # files are stored beside each figure, and any other workload or a changed source reports null.
 TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
@@ -194,18 +194,19 @@ def run_precision(torch, sph, w, precision: int, steps: int, warmup: int, dist, 
     return out
 
 
-def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349, graph: bool = True, shape=None) -> dict:
+def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349, graph: bool = True, shape=None,
+                 dist=None) -> dict:
     """Ensemble workload: 256 independent periodic boxes, N_b log-uniform in [2048, 262144], sigma_v
     U[0.01, 0.3], gamma in {5/3, 7/5}, mixed precision, one context for all boxes (one launch per
-    stage), every box advanced by its own CFL step."""
-    import numpy as np
-    from paper_2503_09713_gb300 import workloads
+    stage), every box advanced by its own CFL step.  Under torchrun the boxes are shared out over the
+    ranks (longest-processing-time by particle count, no data exchange); the step time is the
+    largest over ranks and the particles the sum over ranks."""
+    from paper_2503_09713_gb300 import replicas, workloads
     boxes = workloads.ensemble(256, seed=seed)
-    off = np.concatenate([[0], np.cumsum([b["n"] for b in boxes])]).astype(np.int64)
-    cat = {k: np.concatenate([b[k] for b in boxes]) for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h")}
-    cat["mass"] = 1.0
-    mass = np.array([b["mass"] for b in boxes])
-    gam = np.array([b["gamma"] for b in boxes])
+    world = dist.get_world_size() if dist else 1
+    rank = dist.get_rank() if dist else 0
+    part = replicas.ensemble_shard(boxes, world, rank)
+    off, mass, gam, cat = part["offsets"], part["mass"], part["gamma"], part["state"]
     s = sph.DeviceState.from_numpy(cat)
     solver = sph.Solver.batch(sph.default_params(precision=sph.SPH_MIXED), off, mass, gam)
     solver.set_graph(graph)
@@ -218,6 +219,8 @@ def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349, graph: 
         solver.step(s)
     stream = torch.cuda.current_stream()
     l0 = solver.stats()["kernel_launches"]
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -226,7 +229,9 @@ def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349, graph: 
         solver.step(s)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+    if dist:
+        dist.barrier()
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / steps, dist, "cuda")
     st = solver.stats()
     replays, fallbacks = st["graph_replays"], st["graph_fallbacks"]
     solver.set_timing(True)
@@ -234,8 +239,9 @@ def run_ensemble(torch, sph, steps: int, warmup: int, seed: int = 12349, graph: 
     solver.step(s)
     stage = solver.stats()["stage_ms"]
     solver.close()
-    n = int(off[-1])
+    n = int(replicas.sum_over_ranks(int(off[-1]), dist, "cuda"))
     return {"value": n / (ms * 1e-3), "unit": "particles/s", "ms_per_step": ms, "boxes": len(boxes), "particles": n,
+            "boxes_per_rank": len(part["boxes"]) if world == 1 else f"{len(part['boxes'])} on rank 0 of {world}",
             "smallest_box": int(min(b["n"] for b in boxes)), "largest_box": int(max(b["n"] for b in boxes)),
             "dtype": "f32 pair sums (Kahan) / f64 state", "launches_per_step": (st["kernel_launches"] - l0) / steps,
             "timing": "per-box CFL steps, one context, one launch per stage for all boxes"
@@ -367,7 +373,8 @@ def main():
     shapes = json.loads(args.shapes) if args.shapes else {}
     if args.only == "ensemble":
         print(json.dumps({"workload": "ensemble", **run_ensemble(torch, sph, args.steps, max(args.warmup, 3),
-                                                                 graph=graph, shape=shapes.get("ensemble"))}))
+                                                                 graph=graph, shape=shapes.get("ensemble"),
+                                                                 dist=dist)}))
         return
     if args.only == "mixed":
         r = run_precision(torch, sph, w, 1, args.steps, max(args.warmup, 3), dist, True, clocks, args.morton_bits,
@@ -442,7 +449,7 @@ def main():
 
     if not args.no_ensemble and args.only is None:
         line["ensemble"] = run_ensemble(torch, sph, args.steps, max(args.warmup, 3), graph=graph,
-                                        shape=shapes.get("ensemble"))
+                                        shape=shapes.get("ensemble"), dist=dist)
 
     if not args.no_e2e:
         t, h2d, d2h = e2e_run(torch, sph, r64["solver"], r64["state"], args.steps)

@@ -299,8 +299,9 @@ int sph_set_graph(sph_ctx *ctx, int enable);
  * original order.  x, y, z: DEVICE float64[n]; box_lo, box_hi: HOST double[3]; codes_out (uint64[n])
  * and perm_out (uint32[n]): DEVICE, caller-owned, must not alias the inputs.  Work is issued on
  * `stream` (a cudaStream_t, NULL = legacy default) and the call returns after it has finished.
- * Limit: n <= 262144 (SPH_ERR_CAPACITY beyond; SPH_ERR_INVALID_ARG for NULL pointers or an empty
- * box).  Scratch: a fixed 3.5 MiB device array inside the library, one per GPU, created by the CUDA
+ * Limit: n <= 262144 (SPH_ERR_CAPACITY beyond); n = 0 returns SPH_OK without touching the outputs;
+ * SPH_ERR_INVALID_ARG for n < 0, NULL pointers or an empty box.  An error left pending by an earlier,
+ * unrelated CUDA runtime call is cleared on entry, so SPH_ERR_CUDA always means this call failed.  Scratch: a fixed 3.5 MiB device array inside the library, one per GPU, created by the CUDA
  * runtime when the library's device code is loaded on that GPU and held until the process exits;
  * its device address is looked up on the first call made on each device, so make that first call
  * outside any stream capture.  Every call on a
@@ -310,6 +311,20 @@ int sph_set_graph(sph_ctx *ctx, int enable);
  * TIMEOUT (a bounded look-back wait ran out), CUDA. */
 int sph_sort_morton_noalloc(int64_t n, const double *x, const double *y, const double *z, const double *box_lo,
                             const double *box_hi, uint64_t *codes_out, uint32_t *perm_out, void *stream);
+
+/* Failure-detection probe (no counterpart in the paper; for tests).  Makes one of the library's
+ * bounded device-side waits run out on purpose, without a fault or a hang, and reports it the way
+ * a real stall would be reported.  which = 0: one radix-sort pass over two tiles of scratch keys
+ * (buffers allocated and freed by the call) launched so that the first tile is never processed; the
+ * second tile's decoupled look-back waits `spins` rounds for it.  which = 1: stage 2 of the current
+ * neighbour cache run again as one warp that starts at the second group, whose look-back waits for
+ * the first group; the cache is marked invalid afterwards (call sph_find_neighbours again); s must
+ * be the state of the last cache build.  spins: rounds of the wait, 1 .. 2^20 (the library's own
+ * limits are 2^22).  Returns SPH_ERR_TIMEOUT when the wait ran out as designed (the expected
+ * result), SPH_OK if it did not, SPH_ERR_ORDER without a cache of at least two groups (which = 1)
+ * or inside a captured step, SPH_ERR_INVALID_ARG, SPH_ERR_OOM, SPH_ERR_CUDA.  The context stays
+ * usable. */
+int sph_debug_wait_timeout(sph_ctx *ctx, const sph_state *s, int which, uint32_t spins);
 
 /* Message of the last error of ctx (never NULL; "" when none). */
 const char *sph_last_error(sph_ctx *ctx);

@@ -114,34 +114,39 @@ void orc_sort_by_key(int64_t n, const uint64_t *keys, uint64_t *sorted, uint32_t
 }
 
 /* ====================================================================================== */
-/* Keep mask and reduction: Alg. "Removal mask initialisation and reduction algorithm"      */
-/* (App. C).  Reading: each pass reads the mask of the previous pass and writes a new one    */
-/* (the in-place parallel update of the paper is a race); a neighbour index that runs off    */
-/* either end gives delta = -1.                                                              */
+/* Keep mask and reduction (App. C, "Reduction").  Written from the criterion the appendix    */
+/* states in words, not from its listing: duplicates are masked first (only the first of a    */
+/* run of equal codes stays); then each reduction pass looks at the binary radix tree of the   */
+/* codes kept so far and, for every internal node whose two children are both leaves, drops    */
+/* the second (right) one of the two, so that pair of leaves becomes a single leaf.  The tree  */
+/* is this file's own top-down construction (orc_radix_tree), a pass reads the tree of the     */
+/* previous pass's result only (the paper's in-place parallel update is a race; reading: one   */
+/* pass after the other), and the first code is never dropped (it is always a left child).    */
 /* ====================================================================================== */
+void orc_radix_tree(int64_t L, const uint64_t *mu_leaf, int nbits, int32_t *lchild, int32_t *rchild,
+                    uint8_t *lflag, uint8_t *rflag, int32_t *endrange);
+
 void orc_keep_mask(int64_t n, const uint64_t *mu, int nbits, int n_red, uint8_t *xi)
 {
     if (n <= 0) return;
-    /* duplicates: keep the first of every run of equal codes */
     for (int64_t i = 0; i < n; i++) xi[i] = (i == 0) ? 1 : (mu[i] != mu[i - 1]);
-    uint8_t *nxt = (uint8_t *)malloc((size_t)n);
+    int64_t *kept = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    uint64_t *codes = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    int32_t *lc = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *rc = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *er = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    uint8_t *lf = (uint8_t *)malloc((size_t)n);
+    uint8_t *rf = (uint8_t *)malloc((size_t)n);
     for (int pass = 0; pass < n_red; pass++) {
-        for (int64_t i = 0; i < n; i++) {
-            if (!xi[i]) { nxt[i] = 0; continue; }
-            int64_t im1 = i - 1;
-            while (im1 >= 0 && !xi[im1]) im1--;
-            int64_t im2 = im1 - 1;
-            while (im2 >= 0 && !xi[im2]) im2--;
-            int64_t ip1 = i + 1;
-            while (ip1 < n && !xi[ip1]) ip1++;
-            int d0 = (ip1 < n) ? orc_delta(mu[i], mu[ip1], nbits) : -1;
-            int dm1 = (im1 >= 0) ? orc_delta(mu[im1], mu[i], nbits) : -1;
-            int dm2 = (im2 >= 0 && im1 >= 0) ? orc_delta(mu[im2], mu[im1], nbits) : -1;
-            nxt[i] = !(d0 < dm1 && dm2 < dm1);
-        }
-        memcpy(xi, nxt, (size_t)n);
+        int64_t L = 0;
+        for (int64_t i = 0; i < n; i++)
+            if (xi[i]) { kept[L] = i; codes[L] = mu[i]; L++; }
+        if (L < 2) break;
+        orc_radix_tree(L, codes, nbits, lc, rc, lf, rf, er);
+        for (int64_t c = 0; c < L - 1; c++)
+            if (lf[c] && rf[c]) xi[kept[rc[c]]] = 0;   /* the second leaf of a leaf-leaf pair */
     }
-    free(nxt);
+    free(kept); free(codes); free(lc); free(rc); free(er); free(lf); free(rf);
 }
 
 /* Stream compaction (App. C, "Reduction"; Fig. mortonlistbuild): id[j] = index of the j-th kept

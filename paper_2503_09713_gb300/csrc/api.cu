@@ -616,6 +616,20 @@ int sph_find_neighbours(sph_ctx *c, const sph_state *s, int64_t *n_pairs) {
     return SPH_OK;
 }
 
+int sph_debug_wait_timeout(sph_ctx *c, const sph_state *s, int which, uint32_t spins) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    if (spins < 1 || spins > (1u << 20)) return fail(c, SPH_ERR_INVALID_ARG, "spins outside [1, 2^20]");
+    if (c->capturing) return fail(c, SPH_ERR_ORDER, "not inside a captured step");
+    if (which == 0) return debug_sort_timeout(c, spins);
+    if (which == 1) {
+        int r = check_state(c, s, false);
+        if (r) return r;
+        if (s->n != c->n) return fail(c, SPH_ERR_ORDER, "the probe needs the state of the last cache build");
+        return debug_stage2_timeout(c, s, spins);
+    }
+    return fail(c, SPH_ERR_INVALID_ARG, "which must be 0 (sort) or 1 (stage 2)");
+}
+
 int sph_compute_density_h(sph_ctx *c, sph_state *s, int *iters) {
     int r = check_state(c, s, false);
     if (r) return r;

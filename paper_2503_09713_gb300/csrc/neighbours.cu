@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h, double s,
     float quarter_box, Geo geo, uint32_t *__restrict__ masks, uint32_t *__restrict__ nb_cnt,
     unsigned long long *__restrict__ nb_ptr, unsigned long long *lookback, uint32_t *ticket, int64_t *__restrict__ grp_off, uint32_t *__restrict__ nb_ids,
-    int64_t nb_cap, DevScalars *sc) {
+    int64_t nb_cap, DevScalars *sc, uint32_t spin_limit) {
     // per warp: 32 candidates (FP32 position + threshold) and (s h_b)^2 (1 - 2^-10), h_b
     extern __shared__ float4 s2_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
             const unsigned notready = __ballot_sync(0xffffffffu, fl == 0ULL);
             const unsigned need = inc ? (((inc & (0u - inc)) << 1) - 1u) : 0xffffffffu;
             if (notready & need) {
-                if (++spins > kGrpSpinLimit) {
+                if (++spins > spin_limit) {
                     if (lane == 0) atomicOr(&sc->flags, kErrTimeoutS2);
                     break;
                 }
@@ -492,6 +492,32 @@ static int ensure(sph_ctx *c, T **p, int64_t &cap, int64_t need, const char *wha
     return SPH_OK;
 }
 
+// Failure-detection hook: stage 2 run again on the current candidates as one block of one warp
+// whose group ticket starts at 1, so group 0 never publishes its look-back word and the bounded
+// wait of group 1 runs out after `spins` rounds.  Group 1's tests, masks and (partial) cache rows
+// stay inside the arrays sized for all groups by the last cache build; the cache is marked invalid.
+int debug_stage2_timeout(sph_ctx *c, const sph_state *s, uint32_t spins) {
+    if (!c->cache_valid || c->n_groups < 2) return fail(c, SPH_ERR_ORDER, "the probe needs a cache of two groups");
+    const Geo geo = make_geo(c->p);
+    const double sc = kernel_radius(c->p.kernel) * c->p.cache_tol;
+    const float qbox = (float)(0.25 * fmin(fmin(geo.L[0], geo.L[1]), geo.L[2]));
+    const uint32_t one = 1;
+    c->cache_valid = false;
+    SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
+    SPH_CUDA(c, cudaMemcpyAsync(&c->dscal->s2_ticket, &one, sizeof one, cudaMemcpyHostToDevice, c->stream));
+    SPH_CUDA(c, cudaMemsetAsync(c->grp_slots, 0, (size_t)c->n_groups * sizeof(int64_t), c->stream));
+    k_stage2<<<1, 32, 32 * (sizeof(float4) + sizeof(float2)), c->stream>>>(
+        make_groups(c), c->box_root, group_count(c), c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->masks_cap,
+        c->gboxf, c->nodes, c->rel, c->h32, s->x, s->y, s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->nb_ptr,
+        (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket, c->grp_off, c->nb_ids, c->nb_cap, c->dscal, spins);
+    SPH_LAUNCH_CHECK(c, "k_stage2 (probe)");
+    SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->flags, &c->dscal->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                c->stream));
+    SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->hscal->flags & kErrTimeoutS2) return fail(c, SPH_ERR_TIMEOUT, "stage-2 look-back wait ran out (probe)");
+    return SPH_OK;
+}
+
 int neighbours_build(sph_ctx *c, const sph_state *s) {
     if (!c->tree_valid) return fail(c, SPH_ERR_ORDER, "sph_find_neighbours before sph_build_tree");
     const int64_t n = s->n;
@@ -555,7 +581,8 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         k_stage2<<<blocks, s2w * 32, s2_smem, c->stream>>>(
             gr, c->box_root, group_count(c), c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->masks_cap, c->gboxf,
             c->nodes, c->rel, c->h32, s->x, s->y, s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->nb_ptr,
-            (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket, c->grp_off, c->nb_ids, c->nb_cap, c->dscal);
+            (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket, c->grp_off, c->nb_ids, c->nb_cap, c->dscal,
+            kGrpSpinLimit);
         SPH_LAUNCH_CHECK(c, "k_stage2");
         if (c->capturing) {   // counts and overflow stay on the device until the step is read back
             c->cache_valid = true;

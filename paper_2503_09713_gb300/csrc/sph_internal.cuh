@@ -339,6 +339,8 @@ inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + thread
 int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs);
 int tree_boxes(sph_ctx *c, const sph_state *s);   // A6 again with the current h
 int neighbours_build(sph_ctx *c, const sph_state *s);
+int debug_sort_timeout(sph_ctx *c, uint32_t spins);                          // failure-detection probes
+int debug_stage2_timeout(sph_ctx *c, const sph_state *s, uint32_t spins);
 int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale);
 int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, double *du);
 int integrate_predict(sph_ctx *c, sph_state *s, double dt, const double *dhdt);

@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(kRsThreads) k_onesweep(const uint64_t *__restr
                                                          const uint32_t *__restrict__ vin,
                                                          uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                          int64_t n, int shift, const uint32_t *__restrict__ digit_off,
-                                                         uint32_t *lookback, uint32_t *tile_ctr, uint32_t *flags) {
+                                                         uint32_t *lookback, uint32_t *tile_ctr, uint32_t *flags,
+                                                         uint32_t spin_limit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);                 // [kRsTile]
     uint32_t *sv = reinterpret_cast<uint32_t *>(sk + kRsTile);             // [kRsTile]
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kRsThreads) k_onesweep(const uint64_t *__restr
             if (done) break;
             j -= q;
             if (q < kLbBatch) {
-                if (++spins > kSpinLimit) {
+                if (++spins > spin_limit) {
                     atomicOr(flags, kErrTimeout);
                     break;
                 }
@@ -249,6 +250,26 @@ static size_t onesweep_smem() {
     return (size_t)kRsTile * 8 + (size_t)kRsTile * 4 + (size_t)kRsWarps * 256 * 4 + 256 * 4 * 2 + 16;
 }
 
+// k_onesweep needs more than the default 48 KiB of dynamic shared memory.  The opt-in
+// (cudaFuncSetAttribute) applies to the current device only, so it is made once per device (a
+// process may drive contexts on several GPUs), on the device current at the launch.
+constexpr int kMaxDevices = 64;
+static std::mutex g_optin_mutex;
+static bool g_optin_done[kMaxDevices] = {};
+
+static cudaError_t onesweep_opt_in(size_t sm) {
+    int dev = 0;
+    const cudaError_t ge = cudaGetDevice(&dev);
+    if (ge != cudaSuccess) return ge;
+    if (dev < 0 || dev >= kMaxDevices)
+        return cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    std::lock_guard<std::mutex> lock(g_optin_mutex);
+    if (g_optin_done[dev]) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) g_optin_done[dev] = true;
+    return e;
+}
+
 // keys[0], vals[0] hold the input; one pass per 8-bit digit of the key_bits significant bits; the
 // result is in keys[passes & 1], vals[passes & 1] (returned).
 static int radix_sort(sph_ctx *c, int64_t n, int key_bits, int *out_buf) {
@@ -264,16 +285,12 @@ static int radix_sort(sph_ctx *c, int64_t n, int key_bits, int *out_buf) {
     k_digit_scan<<<8, 256, 0, c->stream>>>(c->digit_hist);
     SPH_LAUNCH_CHECK(c, "k_digit_scan");
     const size_t sm = onesweep_smem();
-    static bool attr_set = false;
-    if (!attr_set) {
-        SPH_CUDA(c, cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr_set = true;
-    }
+    SPH_CUDA(c, onesweep_opt_in(sm));
     for (int p = 0; p < passes; p++) {
         const int src = p & 1, dst = src ^ 1;
         k_onesweep<<<(unsigned)tiles, kRsThreads, sm, c->stream>>>(
             c->keys[src], c->vals[src], c->keys[dst], c->vals[dst], n, 8 * p, c->digit_hist + 256 * p,
-            c->lookback + (size_t)p * tiles * 256, c->tile_ctr + p, &c->dscal->flags);
+            c->lookback + (size_t)p * tiles * 256, c->tile_ctr + p, &c->dscal->flags, kSpinLimit);
         SPH_LAUNCH_CHECK(c, "k_onesweep");
     }
     *out_buf = passes & 1;
@@ -680,6 +697,46 @@ static int boxes(sph_ctx *c, const sph_state *s) {
 
 int tree_boxes(sph_ctx *c, const sph_state *s) { return boxes(c, s); }
 
+// Failure-detection hook: one onesweep pass over two tiles of keys, launched as a single block
+// whose tile ticket starts at 1, so tile 0 never publishes its look-back word and the block's
+// bounded wait runs out after `spins` rounds.  Every access stays inside the two-tile buffers (the
+// output is written only at positions below n).  Own buffers; the context's tree is not touched.
+int debug_sort_timeout(sph_ctx *c, uint32_t spins) {
+    const int64_t n = 2 * kRsTile;
+    uint64_t *k = nullptr;
+    uint32_t *v = nullptr, *words = nullptr;
+    const size_t nwords = 2 * 256 + 256 + 8;   // look-back words of 2 tiles, digit offsets, counter + flags
+    if (cudaMalloc(&k, (size_t)2 * n * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&v, (size_t)2 * n * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&words, nwords * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(k); cudaFree(v); cudaFree(words);
+        return fail(c, SPH_ERR_OOM, "timeout probe buffers");
+    }
+    uint32_t *lookback = words, *digit_off = words + 512, *tile_ctr = words + 768, *flags = words + 769;
+    const uint32_t one = 1;
+    int r = SPH_OK;
+    uint32_t fl = 0;
+    if (cudaMemsetAsync(k, 0, (size_t)2 * n * sizeof(uint64_t), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(v, 0, (size_t)2 * n * sizeof(uint32_t), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(words, 0, nwords * sizeof(uint32_t), c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(tile_ctr, &one, sizeof one, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        onesweep_opt_in(onesweep_smem()) != cudaSuccess) {
+        r = SPH_ERR_CUDA;
+    } else {
+        k_onesweep<<<1, kRsThreads, onesweep_smem(), c->stream>>>(k, v, k + n, v + n, n, 0, digit_off, lookback,
+                                                                   tile_ctr, flags, spins);
+        ++c->launches;
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&fl, flags, sizeof fl, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            r = SPH_ERR_CUDA;
+    }
+    cudaFree(k); cudaFree(v); cudaFree(words);
+    if (r) return fail(c, r, "timeout probe launch");
+    return (fl & kErrTimeout) ? fail(c, SPH_ERR_TIMEOUT, "radix sort look-back wait ran out (probe)") : SPH_OK;
+}
+
 int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
     const int64_t n = s->n;
     const Box3 bx = make_box(c->p);
@@ -882,8 +939,12 @@ extern "C" int sph_sort_morton_noalloc(int64_t n, const double *x, const double 
                                        const double *box_lo, const double *box_hi, uint64_t *codes_out,
                                        uint32_t *perm_out, void *stream) {
     using namespace sph;
-    if (n < 1 || n > kNoAllocMaxN) return SPH_ERR_CAPACITY;
+    if (n < 0) return SPH_ERR_INVALID_ARG;
+    if (n > kNoAllocMaxN) return SPH_ERR_CAPACITY;
+    if (n == 0) return SPH_OK;   // nothing to sort; the outputs are not touched
     if (!x || !y || !z || !box_lo || !box_hi || !codes_out || !perm_out) return SPH_ERR_INVALID_ARG;
+    // an error left by an earlier, unrelated runtime call must not be reported as this call's
+    cudaGetLastError();
     Box3 b;
     for (int k = 0; k < 3; k++) {
         if (!(box_hi[k] > box_lo[k])) return SPH_ERR_INVALID_ARG;
@@ -901,7 +962,7 @@ extern "C" int sph_sort_morton_noalloc(int64_t n, const double *x, const double 
     if (cudaMemsetAsync(sc->hist, 0, sizeof(sc->hist), st) != cudaSuccess ||
         cudaMemsetAsync(sc->lookback, 0, sizeof(sc->lookback), st) != cudaSuccess ||
         cudaMemsetAsync(sc->tile_ctr, 0, sizeof(sc->tile_ctr) + sizeof(sc->flags), st) != cudaSuccess ||
-        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+        onesweep_opt_in(sm) != cudaSuccess) {
         cudaGetLastError();
         return SPH_ERR_CUDA;
     }
@@ -916,7 +977,7 @@ extern "C" int sph_sort_morton_noalloc(int64_t n, const double *x, const double 
         k_onesweep<<<(unsigned)tiles, kRsThreads, sm, st>>>(
             even ? codes_out : sc->keys, even ? perm_out : sc->vals, even ? sc->keys : codes_out,
             even ? sc->vals : perm_out, n, 8 * p, sc->hist + 256 * p, sc->lookback + (size_t)p * tiles * 256,
-            sc->tile_ctr + p, &sc->flags);
+            sc->tile_ctr + p, &sc->flags, kSpinLimit);
     }
     if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
     uint32_t flags = 0;

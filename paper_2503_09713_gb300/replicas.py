@@ -39,3 +39,21 @@ def sum_over_ranks(value: float, dist=None, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device or "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+ENSEMBLE_FIELDS = ("x", "y", "z", "vx", "vy", "vz", "u", "h")
+
+
+def ensemble_shard(boxes, world: int = 1, rank: int = 0) -> dict:
+    """This rank's part of an ensemble of independent boxes (dicts of per-particle arrays with "n",
+    "mass" and "gamma"), as the arguments of a batch context: the boxes shard_boxes assigns to the
+    rank, in ascending box order, concatenated.  Returns {"boxes": box indices, "offsets":
+    int64[k+1], "mass": float64[k], "gamma": float64[k], "state": concatenated arrays}."""
+    import numpy as np
+    plan = shard_boxes([b["n"] for b in boxes], world)[rank]
+    mine = [boxes[b] for b in plan]
+    off = np.concatenate([[0], np.cumsum([b["n"] for b in mine])]).astype(np.int64)
+    state = {k: np.concatenate([b[k] for b in mine]) if mine else np.zeros(0) for k in ENSEMBLE_FIELDS}
+    state["mass"] = 1.0
+    return {"boxes": plan, "offsets": off, "mass": np.array([b["mass"] for b in mine], dtype=np.float64),
+            "gamma": np.array([b["gamma"] for b in mine], dtype=np.float64), "state": state}

@@ -120,6 +120,7 @@ def load():
         "sph_set_launch": (_i, [_p, P(sph_launch)]),
         "sph_autotune": (_i, [_p, P(sph_state), P(sph_launch), P(_d)]),
         "sph_sort_morton_noalloc": (_i, [_i64, _p, _p, _p, P(_d * 3), P(_d * 3), _p, _p, _p]),
+        "sph_debug_wait_timeout": (_i, [_p, P(sph_state), _i, ctypes.c_uint32]),
         "sph_last_error": (ctypes.c_char_p, [_p]),
         "sph_error_string": (ctypes.c_char_p, [_i]),
     }
@@ -236,6 +237,12 @@ def sph_set_graph(ctx, on: bool):
 
 def sph_reset_timing(ctx):
     _check(ctx, load().sph_reset_timing(ctx))
+
+
+def sph_debug_wait_timeout(ctx, st, which: int, spins: int) -> int:
+    """Failure-detection probe: returns the status code (SPH_ERR_TIMEOUT is the expected result)."""
+    return int(load().sph_debug_wait_timeout(ctx, ctypes.byref(st) if st is not None else None, int(which),
+                                             int(spins)))
 
 
 def sph_sort_morton_noalloc(n: int, x_ptr: int, y_ptr: int, z_ptr: int, box_lo, box_hi, codes_ptr: int,

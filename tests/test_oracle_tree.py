@@ -113,37 +113,57 @@ def test_radix_tree_random_invariants(seed):
     _tree_invariants(codes, 20, t)
 
 
-def _siblings(codes, nbits):
-    """Set of j such that leaves j and j+1 are the two leaf children of one internal node."""
-    t = O.radix_tree(codes, nbits)
-    out = set()
-    for i in range(len(codes) - 1):
-        if t.lflag[i] and t.rflag[i]:
-            out.add(int(t.lchild[i]))
-    return out
+def _delta_rule_pass(codes, nbits):
+    """One reduction pass stated through prefix lengths of neighbouring kept codes (the comparison
+    form of App. C's listing, written here independently of the oracle, which works on the radix
+    tree): code j is dropped when delta(j-1, j) exceeds both delta(j-2, j-1) and delta(j, j+1), a
+    neighbour missing at either end counting as -1.  Returns the kept flags."""
+    L = len(codes)
+    c = [int(v) for v in codes]
+
+    def d(i, j):
+        if i < 0 or j >= L:
+            return -1
+        return nbits - (c[i] ^ c[j]).bit_length()
+
+    return [not (j >= 1 and d(j - 1, j) > d(j - 2, j - 1) and d(j - 1, j) > d(j, j + 1)) for j in range(L)]
 
 
 @pytest.mark.parametrize("seed", [3, 4])
-def test_reduction_removes_second_leaf_of_leaf_pairs(seed):
-    """App. C 'Reduction': a pass removes code i exactly when i is the second leaf of a parent whose
-    two children are leaves, in the radix tree of the codes kept by the previous pass."""
+def test_reduction_matches_prefix_comparison_rule(seed):
+    """App. C 'Reduction': the oracle removes the second leaf of every leaf-leaf sibling pair of the
+    radix tree; the same passes stated as comparisons of neighbouring prefix lengths must agree,
+    level by level, on random codes with duplicates."""
     rng = np.random.default_rng(seed)
     nbits = 30
     raw = np.sort(rng.integers(0, 1 << nbits, size=2000, dtype=np.uint64))
     raw = np.concatenate([raw, raw[::17]])           # add duplicates
     mu = np.sort(raw)
     prev = O.keep_mask(mu, nbits, 0)
-    for level in range(1, 5):
+    assert np.array_equal(prev, np.concatenate([[1], (mu[1:] != mu[:-1]).astype(np.uint8)]))
+    for level in range(1, 6):
         cur = O.keep_mask(mu, nbits, level)
         kept_prev = np.nonzero(prev)[0]
-        codes_prev = mu[kept_prev]
-        sib = _siblings(codes_prev, nbits)
-        expect_removed = {int(kept_prev[j + 1]) for j in sib}
-        removed = set(np.nonzero(prev & (1 - cur))[0].tolist())
-        assert removed == expect_removed
+        keep = _delta_rule_pass(mu[kept_prev], nbits)
+        expect = np.zeros_like(prev)
+        expect[kept_prev[np.array(keep, dtype=bool)]] = 1
+        assert np.array_equal(cur, expect), level
         assert cur[0] == 1
         assert np.all(cur <= prev)                      # leaves only merge
         prev = cur
+
+
+@pytest.mark.parametrize("side", [8, 16])
+def test_reduction_halves_leaves_on_power_of_two_lattice(side):
+    """Closed form: on a side^3 lattice with side = 2^k and jitter well inside a cell, the top 3k
+    bits of the 63-bit codes enumerate every lattice cell exactly once, so the radix tree of the
+    codes is a perfect binary tree of depth 3k; every pass pairs all leaves with their siblings and
+    removes one of each pair, leaving again a perfect tree: the leaf counts are side^3 / 2^level."""
+    from paper_2503_09713_gb300 import workloads
+    w = workloads.lattice(side, seed=12345)
+    mu, _ = O.sort_by_key(O.morton(w["x"], w["y"], w["z"], bits=21))
+    counts = [int(O.keep_mask(mu, 63, level).sum()) for level in range(7)]
+    assert counts == [side ** 3 >> level for level in range(7)]
 
 
 def _prefix_box(c1, c2, nbits_axis):
