@@ -24,6 +24,13 @@ struct DensParams {
     const uint16_t *box_of;   // box of each particle (batch) or nullptr
 };
 
+constexpr int kDensQueue = 32;   // FP64 path: queued candidates per thread (8 bytes each in shared memory)
+
+__device__ __forceinline__ double nearest_image(double d, double L, double halfL, int periodic) {
+    if (periodic && nonneg_lt(halfL, fabs(d))) d -= copysign(L, d);   // |d| > L/2 (integer compare)
+    return d;
+}
+
 // Sums over the neighbours of a at smoothing length h (kernel K):  sf = sum f(q),
 // sg = sum (3 f + q f'),  sk = sum (12 f + 8 q f' + q^2 f'')  (self term included: f(0) times 1, 3
 // and 12), so that rho_sum = m C sf / h^3,  sum m dW/dh = -m C sg / h^4,
@@ -34,11 +41,14 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                                              const double *__restrict__ x, const double *__restrict__ y,
                                              const double *__restrict__ z, const float4 *__restrict__ rel,
                                              const PairGeo &geo, double &sf, double &sg, double &sk,
-                                             uint32_t &nin) {
+                                             uint32_t &nin, uint2 *queue) {
     const double hinv = 1.0 / ha;
     if (!kMixed) {
-        // FP32 pre-test on the cell-relative offsets skips the candidates that are clearly outside
-        // R h; the others are evaluated in FP64 with the image shift taken from the cell indices.
+        // Two phases per chunk so that the FP64 work runs with converged lanes: an FP32 pre-test on the
+        // cell-relative offsets queues (up to kDensQueue) the candidates that may lie inside R h (the
+        // others are clearly outside); then every lane of the warp evaluates its queued candidates in
+        // FP64 together, the nearest image taken by |d| > L/2.  All 32 lanes call this function (a lane
+        // without a particle passes cnt = 0).
         const double xa = x[a], ya = y[a], za = z[a];
         const double hinv2 = hinv * hinv;
         const float4 A = rel[a];
@@ -46,19 +56,31 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         const float hinv2f = (float)hinv2;
         double f0 = K::F0, gq = 0.0;   // sum f and sum q f' (sum (3 f + q f') = 3 sum f + sum q f')
         float k0 = (float)(12.0 * K::F0);
-        for (uint32_t k = 0; k < cnt; k++) {
-            const uint32_t b = nb_at(ids, k, st);
-            float fx, fy, fz;
-            int sx, sy, sz;
-            rel_sep_shift(A, rel[b], geo, fx, fy, fz, sx, sy, sz);
-            if (fx * fx + fy * fy + fz * fz > lim) continue;
-            const double dx = image_diff(xa, x[b], sx, geo.L[0]);
-            const double dy = image_diff(ya, y[b], sy, geo.L[1]);
-            const double dz = image_diff(za, z[b], sz, geo.L[2]);
-            const double q2 = (dx * dx + dy * dy + dz * dz) * hinv2;
-            if (nonneg_lt(q2, K::R * K::R)) {
+        const int qs = blockDim.x;
+        uint32_t k = 0;
+        for (;;) {
+            int nq = 0;
+            while (nq < kDensQueue && k < cnt) {
+                const uint32_t b = nb_at(ids, k, st);
+                ++k;
+                float fx, fy, fz;
+                rel_sep(A, rel[b], geo, fx, fy, fz);
+                const float r2f = fx * fx + fy * fy + fz * fz;
+                if (r2f > lim) continue;
+                queue[(nq++) * qs] = make_uint2(b, __float_as_uint(r2f));
+            }
+            const int nq_max = __reduce_max_sync(0xffffffffu, (unsigned)nq);
+            for (int j = 0; j < nq_max; j++) {
+                if (j >= nq) continue;
+                const uint2 e = queue[j * qs];
+                const uint32_t b = e.x;
+                const double dx = nearest_image(xa - x[b], geo.L[0], geo.halfL[0], geo.periodic);
+                const double dy = nearest_image(ya - y[b], geo.L[1], geo.halfL[1], geo.periodic);
+                const double dz = nearest_image(za - z[b], geo.L[2], geo.halfL[2], geo.periodic);
+                const double q2 = (dx * dx + dy * dy + dz * dz) * hinv2;
+                if (!nonneg_lt(q2, K::R * K::R)) continue;
                 ++nin;
-                const float q2f = (fx * fx + fy * fy + fz * fz) * hinv2f;
+                const float q2f = __uint_as_float(e.y) * hinv2f;
                 const float qf = sqrtf(q2f);
                 // q = sqrt(q2) by one Newton-Raphson step from the FP32 root of the FP32 separation
                 // (relative error below 1e-13)
@@ -75,6 +97,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 K::eval(qf, ff, dff);
                 k0 += 12.f * ff + 8.f * qf * dff + q2f * K::d2(qf);
             }
+            if (!__any_sync(0xffffffffu, k < cnt)) break;
         }
         sf = f0;
         sg = fma(3.0, f0, gq);
@@ -131,25 +154,31 @@ __global__ void __launch_bounds__(256, kMixed ? 4 : 1) k_density(int64_t n, cons
                                                  const uint32_t *__restrict__ nb_ids, DensParams dp,
                                                  double *__restrict__ rho, double *__restrict__ omega, DevScalars *sc,
                                                  const uint32_t *abort) {
+    extern __shared__ uint2 dq[];   // FP64 path: [kDensQueue][blockDim.x], thread t's queue is column t
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one thread per particle
     if (a - (threadIdx.x & 31) >= n) return;   // whole warp past the end
     if (aborted(abort, kAbortDensity)) return;   // captured step: the cache is incomplete
     int it = 0;
     uint32_t nin = 0, evals = 0, flag = 0;
-    if (a < n) {
-    const uint32_t cnt = nb_cnt[a];
+    // The Newton loop runs while any lane of the warp iterates (the FP64 sums are warp-collective); a
+    // lane whose particle has converged, gone stale or hit the cap takes part with no candidates.
+    bool active = a < n;
+    const int64_t ai = active ? a : 0;
+    const uint32_t cnt = active ? nb_cnt[a] : 0u;
     uint32_t st;
-    const uint32_t *ids = nb_list(nb_ids, nb_ptr[a], st);
-    double ha = h[a];
-    const double hn = h_base[a];
-    const double m = dp.box_mass ? dp.box_mass[dp.box_of[a]] : dp.mass;
+    const uint32_t *ids = nb_list(nb_ids, active ? nb_ptr[a] : 0ULL, st);
+    double ha = h[ai];
+    const double hn = h_base[ai];
+    const double m = dp.box_mass ? dp.box_mass[dp.box_of[ai]] : dp.mass;
     const double hf3 = dp.hfact * dp.hfact * dp.hfact;
     bool stale = false, conv = false;
     double dsum_new = 0.0;
-    while (it < dp.max_iter) {
-        ++it;
+    while (__any_sync(0xffffffffu, active)) {
+        if (active) ++it;
         double sf, sg, sk;
-        density_sums<K, kMixed>(a, ha, cnt, ids, st, x, y, z, rel, dp.geo, sf, sg, sk, nin);
+        density_sums<K, kMixed>(ai, ha, active ? cnt : 0u, ids, st, x, y, z, rel, dp.geo, sf, sg, sk, nin,
+                                dq + threadIdx.x);
+        if (!active) continue;
         // one division for 1/h and one for the Newton step; the clamps and tests compare the
         // bits of the doubles (integer pipe) and |dh| <= eps_c h^n needs no quotient
         const double hinv = 1.0 / ha;
@@ -175,20 +204,19 @@ __global__ void __launch_bounds__(256, kMixed ? 4 : 1) k_density(int64_t n, cons
         // so the neglected term is O(eps_c^2))
         dsum_new = dsum + mch3 * sk * hinv * hinv * (hnew - ha);
         ha = hnew;
-        if (stale) break;
-        if (small) {
-            conv = true;
-            break;
-        }
+        if (stale) active = false;
+        else if (small) conv = true, active = false;
+        else if (it >= dp.max_iter) active = false;
     }
-    h[a] = ha;
-    flag = stale ? kErrStale : (conv ? 0u : kErrNotConverged);
-    // rho = rho(h) (Eq. rhoh) and Omega (Eq. sphomega) at the final h
-    const double hinv = 1.0 / ha;
-    const double rho_h = m * hf3 * hinv * hinv * hinv;
-    rho[a] = rho_h;
-    omega[a] = 1.0 + ha / (3.0 * rho_h) * dsum_new;
-    evals = cnt * (uint32_t)it;
+    if (a < n) {
+        h[a] = ha;
+        flag = stale ? kErrStale : (conv ? 0u : kErrNotConverged);
+        // rho = rho(h) (Eq. rhoh) and Omega (Eq. sphomega) at the final h
+        const double hinv = 1.0 / ha;
+        const double rho_h = m * hf3 * hinv * hinv * hinv;
+        rho[a] = rho_h;
+        omega[a] = 1.0 + ha / (3.0 * rho_h) * dsum_new;
+        evals = cnt * (uint32_t)it;
     }
     // counters: one atomic per warp (same-address atomics from every thread serialise in L2)
     const uint32_t wit = __reduce_max_sync(0xffffffffu, (uint32_t)it);
@@ -221,6 +249,14 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
     if (!c->capturing) SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->max_iters, 0, sizeof(uint32_t), c->stream));
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->pair_evals, 0, 2 * sizeof(unsigned long long), c->stream));
+    const size_t dsm = (size_t)kDensQueue * blk * sizeof(uint2);
+    cudaError_t oe = cudaSuccess;
+    with_kernel(c->p.kernel, [&](auto kern) {
+        using K = decltype(kern);
+        if (c->p.precision != SPH_MIXED) oe = smem_opt_in<k_density<K, false>>(dsm);
+        return 0;
+    });
+    SPH_CUDA(c, oe);
     with_kernel(c->p.kernel, [&](auto kern) {
         using K = decltype(kern);
         if (c->p.precision == SPH_MIXED)
@@ -228,7 +264,8 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
                                                                         c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
                                                                         s->omega, c->dscal, abort_word(c));
         else
-            k_density<K, false><<<grid_for(n, blk), blk, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+            k_density<K, false><<<grid_for(n, blk), blk, dsm, c->stream>>>(
+                n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
                                                                          c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
                                                                          s->omega, c->dscal, abort_word(c));
         return 0;

@@ -130,9 +130,22 @@ __device__ __forceinline__ void dt_reduce(double t, unsigned long long npair, De
     }
 }
 
-// FP64 pair loop.  A candidate is first tested in FP32 on the cell-relative offsets against the
-// current h (kPreBand margin); the survivors are decided and evaluated in FP64 with the nearest
-// image from the cell indices.  The mass factor is applied once per particle.
+// FP64 pair loop in two phases per chunk, so that the FP64 work runs with converged lanes.  Phase 1
+// walks the particle's cached candidates and keeps those that pass an FP32 test on the cell-relative
+// offsets against the current h (kPreBand margin: every pair inside R max(h_a, h_b) passes), up to
+// kForceQueue of them, in a per-thread queue in shared memory; phase 2 evaluates the queued pairs in
+// FP64, all lanes of the warp stepping through their queues together.  (Tested and evaluated in one
+// loop, ~30% of the candidates fail while other lanes of the warp evaluate, and the FP64 pipe, this
+// loop's bound, runs for every candidate of the warp.)  The FP64 separation takes the nearest image
+// by |d| > L/2, which for every queued pair is the image of the cell-relative test.  The mass factor is
+// applied once per particle.
+constexpr int kForceQueue = 32;   // queued candidates per thread: 4 bytes each in shared memory
+
+__device__ __forceinline__ double nearest_image(double d, double L, double halfL, int periodic) {
+    if (periodic && nonneg_lt(halfL, fabs(d))) d -= copysign(L, d);   // |d| > L/2 (integer compare)
+    return d;
+}
+
 template <typename K>
 __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__restrict__ rec,
                                                      const float4 *__restrict__ rel, const float *__restrict__ h32,
@@ -140,83 +153,99 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
                                                      const unsigned long long *__restrict__ nb_ptr,
                                                      const uint32_t *__restrict__ nb_ids, ForceParams fp, ForceOut out,
                                                      DevScalars *sc) {
+    extern __shared__ uint32_t fq[];   // [kForceQueue][blockDim.x]: thread t's queue is column t
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one thread per particle
     if (a - (threadIdx.x & 31) >= n) return;   // whole warp past the end
     if (aborted(fp.abort, kAbortStep)) return;
-    const int box = (a < n && fp.box_of) ? fp.box_of[a] : 0;
+    const bool va = a < n;
+    const int box = (va && fp.box_of) ? fp.box_of[a] : 0;
     double tdt = INFINITY;
     unsigned long long npair = 0;
-    const uint32_t cnt = a < n ? nb_cnt[a] : 0u;
-    const unsigned long long pw = a < n ? nb_ptr[a] : 0ULL;
+    const uint32_t cnt = va ? nb_cnt[a] : 0u;
+    const unsigned long long pw = va ? nb_ptr[a] : 0ULL;
     uint32_t st;
     const uint32_t *ids = nb_list(nb_ids, pw, st);
     const int64_t lbeg = ids - nb_ids;
     prefetch_lists_l2(nb_ids, lbeg, lbeg + nb_span(cnt, st));
-    if (a < n) {
     FRec A;
-    load_rec(&rec[a], A);
-    const float4 PA = rel[a];
-    const float hA = h32[a];
+    load_rec(&rec[va ? a : 0], A);
+    const float4 PA = rel[va ? a : 0];
+    const float hA = va ? h32[a] : 0.f;
     const PairGeo &geo = fp.geo;
     double axs = 0.0, ays = 0.0, azs = 0.0, dus = 0.0, divs = 0.0;
     double vs = A.acs;
-    for (uint32_t k = 0; k < cnt; k++) {
-        const uint32_t b = nb_at(ids, k, st);
-        float fx, fy, fz;
-        int sx, sy, sz;
-        rel_sep_shift(PA, rel[b], geo, fx, fy, fz, sx, sy, sz);
-        const float hmf = fmaxf(hA, h32[b]);
-        if (fx * fx + fy * fy + fz * fz > (float)(K::R * K::R) * kPreBand * hmf * hmf) continue;
-        FRec B;
-        load_rec(&rec[b], B);
-        const double dx = image_diff(A.x, B.x, sx, geo.L[0]);
-        const double dy = image_diff(A.y, B.y, sy, geo.L[1]);
-        const double dz = image_diff(A.z, B.z, sz, geo.L[2]);
-        // r < R max(h_a, h_b); both kernels and their derivatives vanish at R, so the rounding of r^2
-        // (fused here) only decides pairs whose terms are zero
-        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-        if (!nonneg_lt(r2, nonneg_max(A.rh2, B.rh2))) continue;
-        ++npair;
-        const double rinv = rsqrt(r2);
-        const double r = r2 * rinv;
-        const double dfa = kernel_df<K>(r * A.hinv), dfb = kernel_df<K>(r * B.hinv);
-        const double Fa = dfa * A.fn;
-        const double Fb = dfb * B.fn;
-        const double vdotr = ((A.vx - B.vx) * dx + (A.vy - B.vy) * dy + (A.vz - B.vz) * dz) * rinv;
-        double Aa = A.pre, Ab = B.pre;
-        if (__double_as_longlong(vdotr) < 0) {   // sign bit: approaching (-0 changes nothing below)
-            const double w = fp.beta_av * vdotr;   // = -beta |v.rhat|
-            Aa -= (A.acs - w) * vdotr * A.hqf;
-            Ab -= (B.acs - w) * vdotr * B.hqf;
-            vs = nonneg_max(vs, A.acs - w);
+    uint32_t *q = fq + threadIdx.x;
+    const int qs = blockDim.x;
+    uint32_t k = 0;
+    for (;;) {
+        // phase 1: FP32 pre-test, queue the survivors
+        int nq = 0;
+        while (nq < kForceQueue && k < cnt) {
+            const uint32_t b = nb_at(ids, k, st);
+            ++k;
+            float fx, fy, fz;
+            rel_sep(PA, rel[b], geo, fx, fy, fz);
+            const float hmf = fmaxf(hA, h32[b]);
+            if (!(fx * fx + fy * fy + fz * fz > (float)(K::R * K::R) * kPreBand * hmf * hmf)) q[(nq++) * qs] = b;
         }
-        const double sc_ = (Aa * Fa + Ab * Fb) * rinv;
-        axs -= sc_ * dx;
-        ays -= sc_ * dy;
-        azs -= sc_ * dz;
-        const double vfa = vdotr * Fa;
-        dus = fma(Aa, vfa, dus);
-        divs += vfa;
-        if (fp.alpha_u != 0.0) {
-            const double t = fabs(A.P2 - B.P2);   // 2 |P_a - P_b|; v_sig^u = sqrt(t / (rho_a + rho_b))
-            if (__double_as_longlong(t) > 0) {
-                const double vsu = t * rsqrt(t * (A.rho + B.rho));
-                dus += vsu * (A.au - B.au) * (Fa * A.hqf + Fb * B.hqf);
+        const int nq_max = __reduce_max_sync(0xffffffffu, (unsigned)nq);
+        // phase 2: the queued pairs in FP64
+        for (int j = 0; j < nq_max; j++) {
+            if (j >= nq) continue;
+            const uint32_t b = q[j * qs];
+            FRec B;
+            load_rec(&rec[b], B);
+            const double dx = nearest_image(A.x - B.x, geo.L[0], geo.halfL[0], geo.periodic);
+            const double dy = nearest_image(A.y - B.y, geo.L[1], geo.halfL[1], geo.periodic);
+            const double dz = nearest_image(A.z - B.z, geo.L[2], geo.halfL[2], geo.periodic);
+            // r < R max(h_a, h_b); both kernels and their derivatives vanish at R, so the rounding of
+            // r^2 (fused here) only decides pairs whose terms are zero
+            const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            if (!nonneg_lt(r2, nonneg_max(A.rh2, B.rh2))) continue;
+            ++npair;
+            const double rinv = rsqrt(r2);
+            const double r = r2 * rinv;
+            const double dfa = kernel_df<K>(r * A.hinv), dfb = kernel_df<K>(r * B.hinv);
+            const double Fa = dfa * A.fn;
+            const double Fb = dfb * B.fn;
+            const double vdotr = ((A.vx - B.vx) * dx + (A.vy - B.vy) * dy + (A.vz - B.vz) * dz) * rinv;
+            double Aa = A.pre, Ab = B.pre;
+            if (__double_as_longlong(vdotr) < 0) {   // sign bit: approaching (-0 changes nothing below)
+                const double w = fp.beta_av * vdotr;   // = -beta |v.rhat|
+                Aa -= (A.acs - w) * vdotr * A.hqf;
+                Ab -= (B.acs - w) * vdotr * B.hqf;
+                vs = nonneg_max(vs, A.acs - w);
+            }
+            const double sc_ = (Aa * Fa + Ab * Fb) * rinv;
+            axs -= sc_ * dx;
+            ays -= sc_ * dy;
+            azs -= sc_ * dz;
+            const double vfa = vdotr * Fa;
+            dus = fma(Aa, vfa, dus);
+            divs += vfa;
+            if (fp.alpha_u != 0.0) {
+                const double t = fabs(A.P2 - B.P2);   // 2 |P_a - P_b|; v_sig^u = sqrt(t / (rho_a + rho_b))
+                if (__double_as_longlong(t) > 0) {
+                    const double vsu = t * rsqrt(t * (A.rho + B.rho));
+                    dus += vsu * (A.au - B.au) * (Fa * A.hqf + Fb * B.hqf);
+                }
             }
         }
+        if (!__any_sync(0xffffffffu, k < cnt)) break;
     }
-    const double m = fp.box_mass ? fp.box_mass[box] : fp.mass;
-    axs *= m;
-    ays *= m;
-    azs *= m;
-    dus *= m;
-    out.ax[a] = axs;
-    out.ay[a] = ays;
-    out.az[a] = azs;
-    out.du[a] = dus;
-    out.vsig[a] = vs;
-    out.dhdt[a] = -A.h * (2.0 * A.hqf) * (1.0 / 3.0) * m * divs;
-    tdt = dt_candidate(A.h, vs, axs, ays, azs, fp);
+    if (va) {
+        const double m = fp.box_mass ? fp.box_mass[box] : fp.mass;
+        axs *= m;
+        ays *= m;
+        azs *= m;
+        dus *= m;
+        out.ax[a] = axs;
+        out.ay[a] = ays;
+        out.az[a] = azs;
+        out.du[a] = dus;
+        out.vsig[a] = vs;
+        out.dhdt[a] = -A.h * (2.0 * A.hqf) * (1.0 / 3.0) * m * divs;
+        tdt = dt_candidate(A.h, vs, axs, ays, azs, fp);
     }
     dt_reduce(tdt, npair, sc, fp.box_dt_next, box);
 }
@@ -365,6 +394,14 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     if ((r = stage_end(c, kStForcePrep)) || (r = stage_begin(c, kStForces))) return r;
     ForceOut out{ax, ay, az, du, s->vsig, c->dhdt};
     const int blk = c->launch.forces_block;
+    const size_t fsm = (size_t)kForceQueue * blk * sizeof(uint32_t);
+    cudaError_t oe = cudaSuccess;
+    with_kernel(c->p.kernel, [&](auto kern) {
+        using K = decltype(kern);
+        if (!mixed) oe = smem_opt_in<k_forces_fp64<K>>(fsm);
+        return 0;
+    });
+    SPH_CUDA(c, oe);
     with_kernel(c->p.kernel, [&](auto kern) {
         using K = decltype(kern);
         if (mixed)
@@ -372,7 +409,8 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
                                                                        c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out,
                                                                        c->dscal);
         else
-            k_forces_fp64<K><<<grid_for(n, blk), blk, 0, c->stream>>>(n, (const FRec *)c->frec, c->rel, c->h32,
+            k_forces_fp64<K><<<grid_for(n, blk), blk, fsm, c->stream>>>(
+                n, (const FRec *)c->frec, c->rel, c->h32,
                                                                       c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out,
                                                                       c->dscal);
         return 0;

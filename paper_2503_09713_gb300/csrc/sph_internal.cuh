@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 #include <cuda_runtime.h>
@@ -321,6 +322,25 @@ namespace sph {
 int fail(sph_ctx *c, int code, const char *fmt, ...);
 int cuda_fail(sph_ctx *c, cudaError_t e, const char *where);
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// Opt a kernel into `bytes` of dynamic shared memory (above the 48 KiB default) on the current device.
+// The attribute is per device, so it is set once per device and kernel (a process may drive contexts
+// on several GPUs).
+template <auto Kernel>
+cudaError_t smem_opt_in(size_t bytes) {
+    constexpr int kDevices = 64;
+    static std::mutex mu;
+    static size_t done[kDevices] = {};
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    const cudaError_t ge = cudaGetDevice(&dev);
+    if (ge != cudaSuccess) return ge;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < kDevices && done[dev] >= bytes) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && dev >= 0 && dev < kDevices) done[dev] = bytes;
+    return e;
+}
 
 #define SPH_CUDA(ctx, call)                                        \
     do {                                                           \

@@ -250,25 +250,8 @@ static size_t onesweep_smem() {
     return (size_t)kRsTile * 8 + (size_t)kRsTile * 4 + (size_t)kRsWarps * 256 * 4 + 256 * 4 * 2 + 16;
 }
 
-// k_onesweep needs more than the default 48 KiB of dynamic shared memory.  The opt-in
-// (cudaFuncSetAttribute) applies to the current device only, so it is made once per device (a
-// process may drive contexts on several GPUs), on the device current at the launch.
-constexpr int kMaxDevices = 64;
-static std::mutex g_optin_mutex;
-static bool g_optin_done[kMaxDevices] = {};
-
-static cudaError_t onesweep_opt_in(size_t sm) {
-    int dev = 0;
-    const cudaError_t ge = cudaGetDevice(&dev);
-    if (ge != cudaSuccess) return ge;
-    if (dev < 0 || dev >= kMaxDevices)
-        return cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    std::lock_guard<std::mutex> lock(g_optin_mutex);
-    if (g_optin_done[dev]) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess) g_optin_done[dev] = true;
-    return e;
-}
+// k_onesweep needs more than the default 48 KiB of dynamic shared memory (opted in once per device).
+static cudaError_t onesweep_opt_in(size_t sm) { return smem_opt_in<k_onesweep>(sm); }
 
 // keys[0], vals[0] hold the input; one pass per 8-bit digit of the key_bits significant bits; the
 // result is in keys[passes & 1], vals[passes & 1] (returned).
