@@ -364,7 +364,7 @@ int graph_replay(sph_ctx *c, sph_state *s, double dt) {
     if (fl & kErrStack) return fail(c, SPH_ERR_CAPACITY, "tree walk stack overflow");
     if (fl & kErrNotConverged) return fail(c, SPH_ERR_H_NOT_CONVERGED, "h iteration exceeded %d", c->p.h_max_iter);
     int iters = 0;
-    if (fl & (kErrCapacity | kErrCandOverflow | kErrCacheOverflow)) {
+    if (fl & (kErrCapacity | kErrCandOverflow | kErrCacheOverflow | kErrHalo)) {
         ++c->graph_fallbacks;
         if ((r = tree_build(c, s, false)) || (r = neighbours_build(c, s)) ||
             (r = density_with_restarts(c, s, &iters, c->p.max_outer)) || (r = step_tail(c, s, dt)))

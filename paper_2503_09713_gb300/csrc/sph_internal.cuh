@@ -31,12 +31,13 @@ enum : uint32_t {
     kErrCapacity = 1u << 6,     // a count (leaves, groups, candidate chunks) above its arrays (captured step)
     kErrCacheOverflow = 1u << 7,// the neighbour cache is smaller than the kept pairs (host grows and retries)
     kErrTimeoutS2 = 1u << 8,    // the stage-2 look-back wait ran out
+    kErrHalo = 1u << 9,         // a tile of the fused reduction needs more halo (host runs the passes one by one)
 };
 
 // A captured step (sph_set_graph) runs every stage without the host in between: a stage whose
 // inputs an earlier stage left incomplete returns without writing.  Each mask holds the bits that
 // the stages before the kernel set (never a bit the kernel itself sets, so all its blocks agree).
-constexpr uint32_t kAbortTree = kErrNonFinite | kErrTimeout | kErrCapacity;
+constexpr uint32_t kAbortTree = kErrNonFinite | kErrTimeout | kErrCapacity | kErrHalo;
 constexpr uint32_t kAbortStage2 = kAbortTree | kErrCandOverflow | kErrStack;
 constexpr uint32_t kAbortDensity = kAbortStage2 | kErrCacheOverflow | kErrTimeoutS2;
 constexpr uint32_t kAbortStep = kAbortDensity | kErrStale | kErrNotConverged;

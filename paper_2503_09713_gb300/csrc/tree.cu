@@ -375,6 +375,81 @@ __global__ void k_reduce_pass(int64_t n, const uint64_t *__restrict__ mu, const 
     out[i] = !(d0 < dm1 && dm2 < dm1);
 }
 
+// All reduction passes in one launch: a tile of kRdTile codes is loaded with kRdHalo codes on either
+// side into shared memory, duplicates are masked, and each pass lists the kept positions of the
+// extended range (block scan) and applies the rule above to every listed code, a neighbour beyond
+// the extended range counting as missing.  Such decisions are exact only where the neighbours they
+// read have exact states, so after each pass the range of exact states shrinks from either end by
+// the kept codes next to it (two on the left, one on the right); a tile whose own codes do not all
+// stay inside that range (long runs of removed codes near its ends, e.g. many particles at one
+// position) raises kErrHalo and the host runs the passes one launch each instead.  Results are the
+// same bits as the pass-by-pass kernels.
+constexpr int kRdTile = 4096;
+constexpr int kRdHalo = 512;
+constexpr int kRdExt = kRdTile + 2 * kRdHalo;
+constexpr int kRdThreads = 256;
+constexpr int kRdPer = kRdExt / kRdThreads;
+static_assert(kRdExt % kRdThreads == 0 && kRdExt <= 65535, "list positions are 16-bit");
+constexpr size_t kRdSmem = (size_t)kRdExt * (sizeof(uint64_t) + sizeof(uint8_t) + sizeof(uint16_t));
+
+__global__ void __launch_bounds__(kRdThreads) k_reduce_fused(int64_t n, const uint64_t *__restrict__ mu, int n_red,
+                                                             uint8_t *__restrict__ xi, uint32_t *flags) {
+    extern __shared__ __align__(16) unsigned char rd_smem[];
+    uint64_t *code = reinterpret_cast<uint64_t *>(rd_smem);                      // [kRdExt]
+    uint16_t *list = reinterpret_cast<uint16_t *>(code + kRdExt);                // [kRdExt]
+    uint8_t *kept = reinterpret_cast<uint8_t *>(list + kRdExt);                  // [kRdExt]
+    __shared__ int s_j0, s_j1;
+    const int64_t t0 = (int64_t)blockIdx.x * kRdTile;
+    const int64_t ext_lo = t0 > kRdHalo ? t0 - kRdHalo : 0;
+    const int64_t ext_hi = t0 + kRdTile + kRdHalo < n ? t0 + kRdTile + kRdHalo : n;
+    const int m = (int)(ext_hi - ext_lo);
+    for (int i = threadIdx.x; i < m; i += kRdThreads) code[i] = mu[ext_lo + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kRdThreads) {
+        const int64_t g = ext_lo + i;
+        kept[i] = g == 0 ? 1 : (i > 0 ? code[i] != code[i - 1] : mu[g] != mu[g - 1]);
+    }
+    const bool lo_end = ext_lo == 0, hi_end = ext_hi == n;
+    int64_t lo = ext_lo, hi = ext_hi;   // the states of positions in [lo, hi) are exact
+    __syncthreads();
+    for (int p = 0; p < n_red; p++) {
+        const int b0 = threadIdx.x * kRdPer;
+        int cnt = 0;
+        for (int i = 0; i < kRdPer; i++) cnt += (b0 + i < m) ? kept[b0 + i] : 0;
+        int64_t tot;
+        int pos = (int)block_exclusive_scan<kRdThreads>((int64_t)cnt, tot);
+        for (int i = 0; i < kRdPer; i++)
+            if (b0 + i < m && kept[b0 + i]) list[pos++] = (uint16_t)(b0 + i);
+        const int len = (int)tot;
+        if (threadIdx.x == 0) {
+            s_j0 = len;   // first listed position >= lo
+            s_j1 = -1;    // last listed position < hi
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < len; j += kRdThreads) {
+            const int64_t x = ext_lo + list[j];
+            if (x >= lo && (j == 0 || ext_lo + list[j - 1] < lo)) s_j0 = j;
+            if (x < hi && (j == len - 1 || ext_lo + list[j + 1] >= hi)) s_j1 = j;
+            const uint64_t cx = code[list[j]];
+            const int d0 = j + 1 < len ? dlt(cx, code[list[j + 1]]) : -1;
+            const int dm1 = j >= 1 ? dlt(code[list[j - 1]], cx) : -1;
+            const int dm2 = j >= 2 ? dlt(code[list[j - 2]], code[list[j - 1]]) : -1;
+            kept[list[j]] = !(d0 < dm1 && dm2 < dm1);
+        }
+        __syncthreads();
+        const int j0 = s_j0, j1 = s_j1;
+        if (!lo_end) lo = (j0 + 2 < len) ? ext_lo + list[j0 + 2] : hi;
+        if (!hi_end) hi = (j1 >= 0 && j1 < len) ? ext_lo + list[j1] : lo;
+        __syncthreads();
+    }
+    const int64_t t1 = t0 + kRdTile < n ? t0 + kRdTile : n;
+    if (t0 < lo || t1 > hi) {
+        if (threadIdx.x == 0) atomicOr(flags, kErrHalo);
+        return;
+    }
+    for (int64_t i = t0 + threadIdx.x; i < t1; i += kRdThreads) xi[i] = kept[i - ext_lo];
+}
+
 // ====================================================================================== compaction
 constexpr int kCpThreads = 256;
 constexpr int kCpItems = 8;
@@ -652,6 +727,27 @@ static int make_group_table(sph_ctx *c, int64_t n) {
     return SPH_OK;
 }
 
+// A4: exclusive scan of the keep flags and compaction into leaf_first / mu_leaf (leaf count to the
+// device scalars).
+static int compact_leaves(sph_ctx *c, int64_t n, const uint8_t *keep) {
+    const int64_t nb = (n + kCpChunk - 1) / kCpChunk;
+    int64_t *bsum = c->scan_tmp;                       // [nb]
+    int64_t *boff = c->scan_tmp + nb + 1;              // [nb + 1]
+    int64_t *rest = c->scan_tmp + 2 * (nb + 1);
+    k_flag_sums<<<(unsigned)nb, kCpThreads, 0, c->stream>>>(n, keep, bsum);
+    SPH_LAUNCH_CHECK(c, "k_flag_sums");
+    {
+        int64_t *save = c->scan_tmp;
+        c->scan_tmp = rest;
+        const int r = exclusive_scan_i64(c, bsum, boff, nb);
+        c->scan_tmp = save;
+        if (r) return r;
+    }
+    k_compact<<<(unsigned)nb, kCpThreads, 0, c->stream>>>(n, keep, c->mu, boff, c->leaf_first, c->mu_leaf, c->dscal);
+    SPH_LAUNCH_CHECK(c, "k_compact");
+    return SPH_OK;
+}
+
 static double pow2_reciprocal(double v) {
     int e = 0;
     const double m = std::frexp(v, &e);
@@ -784,38 +880,36 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
         SPH_LAUNCH_CHECK(c, "k_rel");
     }
 
-    // A3 mask + reduction
-    k_mask_init<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->mu, c->mask[0]);
-    SPH_LAUNCH_CHECK(c, "k_mask_init");
-    int cur = 0;
-    for (int pass = 0; pass < c->p.reduction_level; pass++) {
-        k_reduce_pass<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->mu, c->mask[cur], c->mask[cur ^ 1]);
-        SPH_LAUNCH_CHECK(c, "k_reduce_pass");
-        cur ^= 1;
-    }
-    // A4 scan + compaction
-    const int64_t nb = (n + kCpChunk - 1) / kCpChunk;
-    int64_t *bsum = c->scan_tmp;                       // [nb]
-    int64_t *boff = c->scan_tmp + nb + 1;              // [nb + 1]
-    int64_t *rest = c->scan_tmp + 2 * (nb + 1);
-    k_flag_sums<<<(unsigned)nb, kCpThreads, 0, c->stream>>>(n, c->mask[cur], bsum);
-    SPH_LAUNCH_CHECK(c, "k_flag_sums");
-    {
-        int64_t *save = c->scan_tmp;
-        c->scan_tmp = rest;
-        r = exclusive_scan_i64(c, bsum, boff, nb);
-        c->scan_tmp = save;
-        if (r) return r;
-    }
-    k_compact<<<(unsigned)nb, kCpThreads, 0, c->stream>>>(n, c->mask[cur], c->mu, boff, c->leaf_first, c->mu_leaf,
-                                                         c->dscal);
-    SPH_LAUNCH_CHECK(c, "k_compact");
+    // A3 mask + reduction (all passes in one launch; pass by pass where a tile's halo is too short)
+    // and A4 scan + compaction
+    SPH_CUDA(c, smem_opt_in<k_reduce_fused>(kRdSmem));
+    k_reduce_fused<<<(unsigned)((n + kRdTile - 1) / kRdTile), kRdThreads, kRdSmem, c->stream>>>(
+        n, c->mu, c->p.reduction_level, c->mask[0], &c->dscal->flags);
+    SPH_LAUNCH_CHECK(c, "k_reduce_fused");
+    r = compact_leaves(c, n, c->mask[0]);
+    if (r) return r;
     if (!c->capturing) {   // a captured step keeps the leaf count on the device
         SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->n_leaves, &c->dscal->n_leaves, sizeof(int64_t),
                                     cudaMemcpyDeviceToHost, c->stream));
         SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->flags, &c->dscal->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                     c->stream));
         SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (c->hscal->flags & kErrHalo) {   // pass by pass, double-buffered
+            k_mask_init<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->mu, c->mask[0]);
+            SPH_LAUNCH_CHECK(c, "k_mask_init");
+            int cur = 0;
+            for (int pass = 0; pass < c->p.reduction_level; pass++) {
+                k_reduce_pass<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->mu, c->mask[cur], c->mask[cur ^ 1]);
+                SPH_LAUNCH_CHECK(c, "k_reduce_pass");
+                cur ^= 1;
+            }
+            if ((r = compact_leaves(c, n, c->mask[cur]))) return r;
+            SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->n_leaves, &c->dscal->n_leaves, sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, c->stream));
+            SPH_CUDA(c, cudaStreamSynchronize(c->stream));
+            c->hscal->flags &= ~kErrHalo;
+            SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
+        }
         if (c->hscal->flags & kErrNonFinite) return fail(c, SPH_ERR_NONFINITE, "non-finite position or h <= 0");
         if (c->hscal->flags & kErrTimeout) return fail(c, SPH_ERR_TIMEOUT, "radix sort look-back wait ran out");
         const int64_t L = c->hscal->n_leaves;

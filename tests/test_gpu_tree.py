@@ -152,3 +152,21 @@ def test_mortonlistbuild_through_gpu(golden):
     assert [int(m >> np.uint64(60)) for m in t["mu_leaf"]] == [int(c, 2) for c in g["mu_leaf"]]
     m = np.array(codes)
     assert np.array_equal(m[t["perm"]], np.array([int(c, 2) for c in g["mu"]]))
+
+
+@pytest.mark.parametrize("n_red", [5, 7])
+def test_tree_reduction_across_tiles(n_red):
+    """Many reduction passes over many 4096-code tiles of the one-launch reduction (each tile decides
+    its codes from a halo of neighbouring codes): leaves bit-exact against the oracle."""
+    x, y, z = random_positions(50000, 40 + n_red, "uniform")
+    _check_against_oracle(x, y, z, np.full(50000, 0.01), n_red)
+
+
+def test_tree_reduction_long_duplicate_runs():
+    """Two runs of 2500 particles on one point each, inside a 30,000-particle set: the removed codes
+    around them exceed any tile's halo, so those tiles take the pass-by-pass kernels; leaves stay
+    bit-exact against the oracle."""
+    x, y, z = random_positions(30000, 77, "uniform")
+    x[:2500], y[:2500], z[:2500] = 0.31, 0.62, 0.93
+    x[2500:5000], y[2500:5000], z[2500:5000] = 0.71, 0.22, 0.43
+    _check_against_oracle(x, y, z, np.full(30000, 0.01), 4)
