@@ -70,17 +70,31 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 queue[(nq++) * qs] = make_uint2(b, __float_as_uint(r2f));
             }
             const int nq_max = __reduce_max_sync(0xffffffffu, (unsigned)nq);
+            // the next queued neighbour's position is loaded while the current one is evaluated
+            uint2 e = queue[0];
+            double bx = 0.0, by = 0.0, bz = 0.0;
+            if (nq > 0) {
+                bx = x[e.x];
+                by = y[e.x];
+                bz = z[e.x];
+            }
             for (int j = 0; j < nq_max; j++) {
                 if (j >= nq) continue;
-                const uint2 e = queue[j * qs];
-                const uint32_t b = e.x;
-                const double dx = nearest_image(xa - x[b], geo.L[0], geo.halfL[0], geo.periodic);
-                const double dy = nearest_image(ya - y[b], geo.L[1], geo.halfL[1], geo.periodic);
-                const double dz = nearest_image(za - z[b], geo.L[2], geo.halfL[2], geo.periodic);
+                const uint2 ec = e;
+                const double cx = bx, cy = by, cz = bz;
+                if (j + 1 < nq) {
+                    e = queue[(j + 1) * qs];
+                    bx = x[e.x];
+                    by = y[e.x];
+                    bz = z[e.x];
+                }
+                const double dx = nearest_image(xa - cx, geo.L[0], geo.halfL[0], geo.periodic);
+                const double dy = nearest_image(ya - cy, geo.L[1], geo.halfL[1], geo.periodic);
+                const double dz = nearest_image(za - cz, geo.L[2], geo.halfL[2], geo.periodic);
                 const double q2 = (dx * dx + dy * dy + dz * dz) * hinv2;
                 if (!nonneg_lt(q2, K::R * K::R)) continue;
                 ++nin;
-                const float q2f = __uint_as_float(e.y) * hinv2f;
+                const float q2f = __uint_as_float(ec.y) * hinv2f;
                 const float qf = sqrtf(q2f);
                 // q = sqrt(q2) by one Newton-Raphson step from the FP32 root of the FP32 separation
                 // (relative error below 1e-13)
