@@ -59,7 +59,7 @@ int ensure_force_records(sph_ctx *c) {
     }
     if (c->frec) return SPH_OK;
     void **ptrs[] = {(void **)&c->frec};
-    const size_t bytes[] = {N * 128};
+    const size_t bytes[] = {N * 160};
     return regrow(c, ptrs, bytes, 1, "FP64 force records");
 }
 

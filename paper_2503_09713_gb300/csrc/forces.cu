@@ -15,6 +15,7 @@ namespace sph {
 
 struct ForceParams {
     double mass, gamma, alpha_av, beta_av, alpha_u, c_cour, c_force;
+    int m4_poly;               // FP64 records carry the M4 gradient as polynomials (FRec)
     double kern_c;             // C_norm of the smoothing kernel
     double kern_r;             // its support radius R_kern (in units of h)
     PairGeo geo;
@@ -25,16 +26,24 @@ struct ForceParams {
     const uint32_t *abort;     // captured step: skip when an earlier stage failed
 };
 
-// Per-particle FP64 record of the force loop: 128 bytes, read as 8 double2.
-// pre = P/(rho^2 Omega), hqf = 1/(2 rho Omega), fn = C_norm/h^4, acs = alpha_AV c_s,
-// rh2 = (R_kern h)^2 (a pair interacts when r^2 < max(rh2_a, rh2_b), the same bits as (R max h)^2),
-// and for the conductivity term au = alpha_u u and P2 = 2 P (one FP64 product fewer per pair each).
+// Per-particle FP64 record of the force loop: 160 bytes, read as double2.
+// pre = P/(rho^2 Omega), hqf = 1/(2 rho Omega), acs = alpha_AV c_s, rh2 = (R_kern h)^2 (a pair
+// interacts when r^2 < max(rh2_a, rh2_b), the same bits as (R max h)^2), and for the conductivity
+// term au = alpha_u u and P2 = 2 P (one FP64 product fewer per pair each).  k[]: the smoothing
+// kernel's gradient.  In general k0 = 1/h and k1 = C_norm/h^4, so F_ab(h) = k1 f'(r k0).  For M4
+// the loop needs F(r)/r only, which on each piece is a polynomial in r^2 and 1/r:
+//   r < h:      F/r = g2i r^2 (1/r) + g1i,          g2i = 9/4 k h^-2,  g1i = -3 k h^-1
+//   h <= r < 2h: F/r = (g2o r^2 + g0o) (1/r) + g1o,  g2o = -3/4 k h^-2, g1o = 3 k h^-1, g0o = -3 k
+// with k = C_norm/h^4 (from f'(q) = -3q + 9/4 q^2 and -3 + 3q - 3/4 q^2); then k0 = h^2 (the piece
+// boundary, compared with r^2), k1 = g0o, k2 = g1i, k3 = g1o, k4 = g2i, k5 = g2o.
 struct __align__(16) FRec {
     double x, y, z, h;
     double vx, vy, vz, au;
     double pre, hqf, acs, P2;
-    double rho, hinv, fn, rh2;
+    double rho, rh2, k0, k1;
+    double k2, k3, k4, k5;
 };
+static_assert(sizeof(FRec) == 160, "FP64 force record");
 
 __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                              const double *__restrict__ z, const double *__restrict__ vx,
@@ -68,14 +77,28 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
         f.pre = (gam - 1.0) * ui * qf; f.hqf = 0.5 * qf;
         f.acs = (alpha ? alpha[i] : fp.alpha_av) * sqrt(gam * (gam - 1.0) * ui);
         f.P2 = 2.0 * ((gam - 1.0) * r * ui);
-        f.rho = r; f.hinv = hinv; f.fn = hinv * hinv * hinv * hinv * fp.kern_c;
+        f.rho = r;
+        const double fn = hinv * hinv * hinv * hinv * fp.kern_c;
         const double rad = __dmul_rn(fp.kern_r, hi);
         f.rh2 = __dmul_rn(rad, rad);
+        if (fp.m4_poly) {
+            f.k0 = hi * hi;
+            f.k1 = -3.0 * fn;
+            f.k2 = -3.0 * fn * hinv;
+            f.k3 = 3.0 * fn * hinv;
+            f.k4 = 2.25 * fn * hinv * hinv;
+            f.k5 = -0.75 * fn * hinv * hinv;
+        } else {
+            f.k0 = hinv;
+            f.k1 = fn;
+            f.k2 = f.k3 = f.k4 = f.k5 = 0.0;
+        }
         rec[i] = f;
         h32[i] = (float)hi;
     }
 }
 
+template <bool kPoly>
 __device__ __forceinline__ void load_rec(const FRec *p, FRec &o) {
     const double2 *q = reinterpret_cast<const double2 *>(p);
     double2 t;
@@ -85,8 +108,25 @@ __device__ __forceinline__ void load_rec(const FRec *p, FRec &o) {
     t = __ldg(q + 3); o.vz = t.x; o.au = t.y;
     t = __ldg(q + 4); o.pre = t.x; o.hqf = t.y;
     t = __ldg(q + 5); o.acs = t.x; o.P2 = t.y;
-    t = __ldg(q + 6); o.rho = t.x; o.hinv = t.y;
-    t = __ldg(q + 7); o.fn = t.x; o.rh2 = t.y;
+    t = __ldg(q + 6); o.rho = t.x; o.rh2 = t.y;
+    t = __ldg(q + 7); o.k0 = t.x; o.k1 = t.y;
+    if (kPoly) {
+        t = __ldg(q + 8); o.k2 = t.x; o.k3 = t.y;
+        t = __ldg(q + 9); o.k4 = t.x; o.k5 = t.y;
+    }
+}
+
+// F_ab(h)/r of one side of a pair from its record (see FRec), r2 = r^2, rinv = 1/r, inside the
+// interaction range of that side (r^2 < rh2) or zero.
+template <typename K>
+__device__ __forceinline__ double grad_over_r(const FRec &R, double r2, double rinv) {
+    if constexpr (std::is_same<K, Kernel<SPH_KERNEL_M4>>::value) {
+        const bool in1 = nonneg_lt(r2, R.k0), in2 = nonneg_lt(r2, R.rh2);
+        const double g2 = in1 ? R.k4 : R.k5, g0 = in1 ? 0.0 : R.k1, g1 = in1 ? R.k2 : R.k3;
+        return in2 ? fma(fma(g2, r2, g0), rinv, g1) : 0.0;
+    } else {
+        return kernel_df<K>(r2 * rinv * R.k0) * R.k1 * rinv;
+    }
 }
 
 struct ForceOut {
@@ -167,8 +207,9 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
     const uint32_t *ids = nb_list(nb_ids, pw, st);
     const int64_t lbeg = ids - nb_ids;
     prefetch_lists_l2(nb_ids, lbeg, lbeg + nb_span(cnt, st));
+    constexpr bool kPoly = std::is_same<K, Kernel<SPH_KERNEL_M4>>::value;
     FRec A;
-    load_rec(&rec[va ? a : 0], A);
+    load_rec<kPoly>(&rec[va ? a : 0], A);
     const float4 PA = rel[va ? a : 0];
     const float hA = va ? h32[a] : 0.f;
     const PairGeo &geo = fp.geo;
@@ -194,7 +235,7 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
             if (j >= nq) continue;
             const uint32_t b = q[j * qs];
             FRec B;
-            load_rec(&rec[b], B);
+            load_rec<kPoly>(&rec[b], B);
             const double dx = nearest_image(A.x - B.x, geo.L[0], geo.halfL[0], geo.periodic);
             const double dy = nearest_image(A.y - B.y, geo.L[1], geo.halfL[1], geo.periodic);
             const double dz = nearest_image(A.z - B.z, geo.L[2], geo.halfL[2], geo.periodic);
@@ -204,11 +245,10 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
             if (!nonneg_lt(r2, nonneg_max(A.rh2, B.rh2))) continue;
             ++npair;
             const double rinv = rsqrt(r2);
-            const double r = r2 * rinv;
-            const double dfa = kernel_df<K>(r * A.hinv), dfb = kernel_df<K>(r * B.hinv);
-            const double Fa = dfa * A.fn;
-            const double Fb = dfb * B.fn;
-            const double vdotr = ((A.vx - B.vx) * dx + (A.vy - B.vy) * dy + (A.vz - B.vz) * dz) * rinv;
+            // G = F_ab/r of both sides: F rhat = G (r_a - r_b), v_ab . rhat F = (v_ab . (r_a - r_b)) G
+            const double Ga = grad_over_r<K>(A, r2, rinv), Gb = grad_over_r<K>(B, r2, rinv);
+            const double vd = (A.vx - B.vx) * dx + (A.vy - B.vy) * dy + (A.vz - B.vz) * dz;
+            const double vdotr = vd * rinv;
             double Aa = A.pre, Ab = B.pre;
             if (__double_as_longlong(vdotr) < 0) {   // sign bit: approaching (-0 changes nothing below)
                 const double w = fp.beta_av * vdotr;   // = -beta |v.rhat|
@@ -216,18 +256,19 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
                 Ab -= (B.acs - w) * vdotr * B.hqf;
                 vs = nonneg_max(vs, A.acs - w);
             }
-            const double sc_ = (Aa * Fa + Ab * Fb) * rinv;
+            const double sc_ = Aa * Ga + Ab * Gb;
             axs -= sc_ * dx;
             ays -= sc_ * dy;
             azs -= sc_ * dz;
-            const double vfa = vdotr * Fa;
+            const double vfa = vd * Ga;   // (v_ab . rhat) F_ab(h_a)
             dus = fma(Aa, vfa, dus);
             divs += vfa;
             if (fp.alpha_u != 0.0) {
                 const double t = fabs(A.P2 - B.P2);   // 2 |P_a - P_b|; v_sig^u = sqrt(t / (rho_a + rho_b))
                 if (__double_as_longlong(t) > 0) {
                     const double vsu = t * rsqrt(t * (A.rho + B.rho));
-                    dus += vsu * (A.au - B.au) * (Fa * A.hqf + Fb * B.hqf);
+                    // F_a hqf_a + F_b hqf_b = r (G_a hqf_a + G_b hqf_b)
+                    dus += vsu * (A.au - B.au) * ((r2 * rinv) * (Ga * A.hqf + Gb * B.hqf));
                 }
             }
         }
@@ -374,6 +415,7 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     fp.c_force = c->p.c_force;
     fp.kern_c = with_kernel(c->p.kernel, [](auto kern) { return decltype(kern)::C; });
     fp.kern_r = kernel_radius(c->p.kernel);
+    fp.m4_poly = c->p.kernel == SPH_KERNEL_M4;
     fp.geo = make_pair_geo(c->p);
     fp.box_mass = c->batch ? c->box_mass : nullptr;
     fp.box_gamma = c->batch ? c->box_gamma : nullptr;
