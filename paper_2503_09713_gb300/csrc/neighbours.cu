@@ -18,6 +18,7 @@
 // Layout of the cache: particle a = start_g + lane of a group of size_g particles owns entries
 // k = 4 r + j, k < count_a, at off_g + 4 size_g r + 4 lane + j (16-byte quads, see nb_list).
 #include <cuda/atomic>
+#include <cmath>
 
 #include "physics.cuh"
 
@@ -29,6 +30,17 @@ struct Geo {
     float Lf[3];     // box side in FP32
     int periodic;
 };
+
+// Stage 2 tests in the frame of a group's first cell when the group's extent plus the largest
+// search radius stays below this: half the smallest box side less two cells, rounded down.
+static float frame_limit(const Geo &geo) {
+    const double lmin = fmin(fmin(geo.L[0], geo.L[1]), geo.L[2]);
+    const double cmax = fmax(fmax(geo.L[0], geo.L[1]), geo.L[2]) / 1024.0;
+    const double v = 0.5 * lmin - 2.0 * cmax;
+    float f = (float)v;
+    if ((double)f > v) f = std::nextafter(f, -INFINITY);
+    return f;
+}
 
 static Geo make_geo(const sph_params &p) {
     Geo g;
@@ -238,15 +250,17 @@ constexpr uint32_t kGrpSpinLimit = 1u << 22;
 // are still in L2, into the cache.  Tests run in FP32 relative to the cell of the group's first
 // particle, the periodic wrap done once per particle on the integer cell index.  A true neighbour
 // b of a group particle lies within ext + s*h_max of that cell (ext: group extent, h_max: largest h
-// in the tree), so its wrapped coordinate is its nearest image whenever ext + s*h_max is below half
-// a box; the kernel asks for a quarter box (warp-uniform), otherwise every separation is wrapped on
-// its own.  Pairs within a relative 2^-10 of the radius are decided in FP64 (exact_pair).
+// in the box), so its wrapped coordinate is its nearest image whenever ext + s*h_max stays below half
+// a box by two cells (the wrap works on whole cells); a wrongly wrapped candidate that is not a true
+// neighbour is never nearer than its nearest image, so it is rejected either way.  The condition is
+// warp-uniform; a group that fails it wraps every separation on its own.  Pairs within a relative
+// 2^-10 of the radius are decided in FP64 (exact_pair).
 __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     Groups gr, const int32_t *__restrict__ box_root, Count Gc, const uint2 *__restrict__ cand, const uint32_t *__restrict__ cand_cnt, int cap,
     const int64_t *__restrict__ chunk_off, int64_t masks_cap, const NodeF *__restrict__ gboxf, const Node *__restrict__ nodes,
     const float4 *__restrict__ rel, const float *__restrict__ h32, const double *__restrict__ x,
     const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h, double s,
-    float quarter_box, Geo geo, uint32_t *__restrict__ masks, uint32_t *__restrict__ nb_cnt,
+    float frame_lim, Geo geo, uint32_t *__restrict__ masks, uint32_t *__restrict__ nb_cnt,
     unsigned long long *__restrict__ nb_ptr, unsigned long long *lookback, uint32_t *ticket, int64_t *__restrict__ grp_off, uint32_t *__restrict__ nb_ids,
     int64_t nb_cap, DevScalars *sc, uint32_t spin_limit) {
     // per warp: 32 candidates (FP32 position + threshold) and (s h_b)^2 (1 - 2^-10), h_b
@@ -307,7 +321,7 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     const NodeF q = gboxf[g];
     const double hroot = nodes[box_root[group_box_of(gr, g)]].hmax;
     const float ext = fmaxf(fmaxf(__fsub_ru(q.hi[0], q.lo[0]), __fsub_ru(q.hi[1], q.lo[1])), __fsub_ru(q.hi[2], q.lo[2]));
-    const bool compact = ext + (float)(s * hroot) < quarter_box;   // warp-uniform
+    const bool compact = ext + (float)(s * hroot) < frame_lim;   // warp-uniform
     int ca[3];
     unpack_cell(Araw, ca[0], ca[1], ca[2]);
     const uint2 *cl = cand + (size_t)g * cap;
@@ -500,7 +514,7 @@ int debug_stage2_timeout(sph_ctx *c, const sph_state *s, uint32_t spins) {
     if (!c->cache_valid || c->n_groups < 2) return fail(c, SPH_ERR_ORDER, "the probe needs a cache of two groups");
     const Geo geo = make_geo(c->p);
     const double sc = kernel_radius(c->p.kernel) * c->p.cache_tol;
-    const float qbox = (float)(0.25 * fmin(fmin(geo.L[0], geo.L[1]), geo.L[2]));
+    const float qbox = frame_limit(geo);
     const uint32_t one = 1;
     c->cache_valid = false;
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
@@ -571,7 +585,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
     const int s2w = c->launch.stage2_warps;
     const unsigned blocks = grid_for(G, s2w);
     const size_t s2_smem = (size_t)s2w * 32 * (sizeof(float4) + sizeof(float2));
-    const float qbox = (float)(0.25 * fmin(fmin(geo.L[0], geo.L[1]), geo.L[2]));
+    const float qbox = frame_limit(geo);
     int64_t total = 0;
     for (int attempt = 0;; attempt++) {
         SPH_CUDA(c, cudaMemsetAsync(&c->dscal->n_pairs, 0, sizeof(int64_t), c->stream));
