@@ -48,8 +48,8 @@ FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan)
 TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
                    "paper_2503_09713_gb300/csrc/sph_internal.cuh")
 TRAFFIC = {
-    "k_forces_fp64": {"workload": "sedov128", "bytes": 1074084352 + 95674368, "src_sha256": "41719363cf4180bf10302f0226082239e2db6fafe141c933c9283e9e372dcb32"},
-    "k_forces_mixed": {"workload": "sedov128", "bytes": 874375168 + 93700096, "src_sha256": "41719363cf4180bf10302f0226082239e2db6fafe141c933c9283e9e372dcb32"},
+    "k_forces_fp64": {"workload": "sedov128", "bytes": 1153067264 + 95765248, "src_sha256": "2464d595d01863f115e1f4536397b36e4f6416ba8f88272ffd4bad055e090408"},
+    "k_forces_mixed": {"workload": "sedov128", "bytes": 875627008 + 94093824, "src_sha256": "2464d595d01863f115e1f4536397b36e4f6416ba8f88272ffd4bad055e090408"},
 }
 
 
