@@ -301,14 +301,14 @@ int sph_set_graph(sph_ctx *ctx, int enable);
  * `stream` (a cudaStream_t, NULL = legacy default) and the call returns after it has finished.
  * Limit: n <= 262144 (SPH_ERR_CAPACITY beyond); n = 0 returns SPH_OK without touching the outputs;
  * SPH_ERR_INVALID_ARG for n < 0, NULL pointers or an empty box.  An error left pending by an earlier,
- * unrelated CUDA runtime call is cleared on entry, so SPH_ERR_CUDA always means this call failed.  Scratch: a fixed 3.5 MiB device array inside the library, one per GPU, created by the CUDA
- * runtime when the library's device code is loaded on that GPU and held until the process exits;
- * its device address is looked up on the first call made on each device, so make that first call
- * outside any stream capture.  Every call on a
- * device shares that array and leaves its last contents there (the parts that must start at zero
- * are cleared by each call); calls whose work overlaps on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller.  Errors: CAPACITY, INVALID_ARG,
- * TIMEOUT (a bounded look-back wait ran out), CUDA. */
+ * unrelated CUDA runtime call is cleared on entry, so SPH_ERR_CUDA always means this call failed.
+ * Scratch: a fixed 4 MiB device array inside the library, one per GPU, created by the CUDA runtime
+ * when the library's device code is loaded on that GPU and held until the process exits; its device
+ * address is looked up on the first call made on each device, so make that first call outside any
+ * stream capture.  Every call on a device shares that array and leaves its last contents there (the
+ * parts that must start at zero are cleared by each call); calls whose work overlaps on the GPU
+ * (other streams, other host threads) race on it and must be serialised by the caller.  Errors:
+ * CAPACITY, INVALID_ARG, TIMEOUT (a bounded look-back wait ran out), CUDA. */
 int sph_sort_morton_noalloc(int64_t n, const double *x, const double *y, const double *z, const double *box_lo,
                             const double *box_hi, uint64_t *codes_out, uint32_t *perm_out, void *stream);
 

@@ -460,7 +460,7 @@ int create_ctx(const sph_params *p, int64_t n_cap, int n_boxes, int64_t neigh_ca
     }
     const int64_t N = n_cap;
     const int64_t G = (N + 31) / 32 + n_boxes;   // per-group arrays: first guess, grown by ensure_groups
-    const int64_t tiles = (N + 4095) / 4096;
+    const int64_t tiles = (N + kSortTile - 1) / kSortTile;
     const int64_t chunks = (N + 2047) / 2048;
     c->sort_tiles = tiles;
     c->cand_cap = 128;

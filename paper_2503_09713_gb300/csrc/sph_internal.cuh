@@ -19,6 +19,7 @@ constexpr int kCellBits = 10;            // cell grid of the FP32 relative coord
 constexpr int kStackDepth = 66;          // tree-walk stack (tree depth <= 63 for distinct 63-bit codes)
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kGatherBatch = 4;          // state fields reordered per gather pass (scratch: 4 x n_cap doubles)
+constexpr int kSortTile = 2048;          // keys per tile of a radix-sort pass (256 threads x 8 keys)
 
 // Device error word bits (ctx->d_flags[0]).
 enum : uint32_t {

@@ -52,20 +52,41 @@ struct Box3 {
     double inv_span[3];   // exact reciprocal when span is a power of two, else 0
 };
 
+// Grid scale of the box for k_morton: k = 2^bits / span on every axis when all spans are powers of
+// two (an exact product, so (x - lo) k equals ((x - lo) / span) 2^bits bit for bit), else 0.
+struct Quant {
+    double lo[3], span[3], k[3];
+    int pow2;
+};
+
+// The finiteness of a double (exponent field not all ones) and h > 0 from the bits (integer pipe).
+__device__ __forceinline__ bool finite_bits(double v) {
+    return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ULL) != 0x7ff0000000000000ULL;
+}
+
 // In a batch the key is (box index << 3*bits) | Morton code with `bits` bits per axis, so that the
 // sort keeps each box's particles together and every box is a subtree of the radix tree.
 __global__ void k_morton(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
-                         const double *__restrict__ z, const double *__restrict__ h, Box3 b,
+                         const double *__restrict__ z, const double *__restrict__ h, Quant b,
                          uint64_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t *flags,
                          const uint16_t *__restrict__ box_of, int bits) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double px = x[i], py = y[i], pz = z[i], ph = h[i];
-    if (!isfinite(px) || !isfinite(py) || !isfinite(pz) || !isfinite(ph) || !(ph > 0.0))
+    if (!finite_bits(px) || !finite_bits(py) || !finite_bits(pz) || !finite_bits(ph) || __double_as_longlong(ph) <= 0)
         atomicOr(flags, kErrNonFinite);
-    const uint64_t X = quantise(px, b.lo[0], b.span[0], b.inv_span[0], bits);
-    const uint64_t Y = quantise(py, b.lo[1], b.span[1], b.inv_span[1], bits);
-    const uint64_t Z = quantise(pz, b.lo[2], b.span[2], b.inv_span[2], bits);
+    const uint64_t top = (1ULL << bits) - 1;
+    uint64_t X, Y, Z;
+    if (b.pow2) {
+        X = floor_clamped((px - b.lo[0]) * b.k[0], top);
+        Y = floor_clamped((py - b.lo[1]) * b.k[1], top);
+        Z = floor_clamped((pz - b.lo[2]) * b.k[2], top);
+    } else {
+        const double scale = (double)(1ULL << bits);
+        X = floor_clamped(((px - b.lo[0]) / b.span[0]) * scale, top);
+        Y = floor_clamped(((py - b.lo[1]) / b.span[1]) * scale, top);
+        Z = floor_clamped(((pz - b.lo[2]) / b.span[2]) * scale, top);
+    }
     uint64_t key = (spread3(X) << 2) | (spread3(Y) << 1) | spread3(Z);
     if (box_of) key |= (uint64_t)box_of[i] << (3 * bits);
     keys[i] = key;
@@ -79,7 +100,8 @@ __global__ void k_morton(int64_t n, const double *__restrict__ x, const double *
 // contiguously.
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 16;
+constexpr int kRsItems = kSortTile / kRsThreads;
+static_assert(kRsItems * kRsThreads == kSortTile, "tile = threads x keys per thread");
 constexpr int kRsTile = kRsThreads * kRsItems;
 constexpr int kRsWarpKeys = 32 * kRsItems;
 constexpr uint32_t kLbAgg = 1u << 30;
@@ -824,7 +846,15 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
     SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
 
     // A1 Morton codes
-    k_morton<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, s->h, bx, c->keys[0], c->vals[0],
+    Quant qb;
+    qb.pow2 = 1;
+    for (int k = 0; k < 3; k++) {
+        qb.lo[k] = bx.lo[k];
+        qb.span[k] = bx.span[k];
+        qb.k[k] = bx.inv_span[k] * (double)(1ULL << c->morton_bits);   // exact: powers of two
+        if (bx.inv_span[k] == 0.0) qb.pow2 = 0;
+    }
+    k_morton<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, s->h, qb, c->keys[0], c->vals[0],
                                                       &c->dscal->flags, c->batch ? c->box_of : nullptr,
                                                       c->morton_bits);
     SPH_LAUNCH_CHECK(c, "k_morton");
@@ -959,18 +989,18 @@ namespace sph {
 namespace {
 
 constexpr int64_t kNoAllocMaxN = 262144;                       // largest n accepted (64^3 particles)
-constexpr int64_t kNoAllocTiles = kNoAllocMaxN / kRsTile;      // 64 sort tiles
+constexpr int64_t kNoAllocTiles = kNoAllocMaxN / kRsTile;      // sort tiles at the largest n
 
 struct NoAllocScratch {
     uint64_t keys[kNoAllocMaxN];                  // ping-pong side of the sort (2 MiB)
     uint32_t vals[kNoAllocMaxN];                  // (1 MiB)
-    uint32_t lookback[8 * kNoAllocTiles * 256];   // decoupled look-back words (512 KiB)
+    uint32_t lookback[8 * kNoAllocTiles * 256];   // decoupled look-back words (1 MiB)
     uint32_t hist[8 * 256];                       // digit histograms -> offsets
     uint32_t tile_ctr[8];
     uint32_t flags;
 };
 
-// Shared by every call on a device: it keeps the last call's contents.  3.5 MiB per device, held by
+// Shared by every call on a device: it keeps the last call's contents.  4 MiB per device, held by
 // every GPU that loads the library until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
