@@ -311,22 +311,64 @@ struct GatherArgs {
     uint32_t *id_dst;
 };
 
-__global__ void k_gather(int64_t n, const uint32_t *__restrict__ perm, GatherArgs g) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t p = perm[i];
-    if (p >= (uint64_t)n) p = 0;   // only after a flagged sort failure
-    for (int f = 0; f < g.nf; f++) g.dst[f][i] = g.src[f][p];
-    if (g.id_dst) g.id_dst[i] = g.id_src ? g.id_src[p] : p;
+// The reorder touches only the particles whose index changes (perm[i] != i): from one step to the
+// next a particle keeps its rank in Morton order unless its code passes a neighbour's, so the
+// permutation is mostly the identity.  Marks, an exclusive scan and a compaction list those
+// positions (the count stays on the device, at pos[n]); the gather and the copy back run over the
+// list.  Pure data movement: the same bits as gathering every particle.
+// Moved positions, counted per 2048-position chunk (flags from perm on the fly), then listed after
+// a scan of the chunk counts; the count goes to moved_n.
+constexpr int kMvThreads = 256;
+constexpr int kMvItems = 8;
+constexpr int kMvChunk = kMvThreads * kMvItems;
+
+__global__ void k_moved_sums(int64_t n, const uint32_t *__restrict__ perm, int64_t *__restrict__ bsum) {
+    const int64_t base = (int64_t)blockIdx.x * kMvChunk + (int64_t)threadIdx.x * kMvItems;
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kMvItems; k++)
+        if (base + k < n) s += perm[base + k] != (uint32_t)(base + k);
+    int64_t tot;
+    block_exclusive_scan<kMvThreads>(s, tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-// Copy of the gathered block back into the state arrays (and id): a kernel, not a device-to-device
-// memcpy, so the copy runs on the SMs at HBM speed in a captured step as well.
-__global__ void k_copy_back(int64_t n, GatherArgs g) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int f = 0; f < g.nf; f++) g.dst[f][i] = g.src[f][i];
-    if (g.id_dst) g.id_dst[i] = g.id_src[i];
+__global__ void k_moved_list(int64_t n, const uint32_t *__restrict__ perm, const int64_t *__restrict__ boff,
+                             uint32_t *__restrict__ moved, int64_t *__restrict__ moved_n) {
+    const int64_t base = (int64_t)blockIdx.x * kMvChunk + (int64_t)threadIdx.x * kMvItems;
+    bool f[kMvItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kMvItems; k++) {
+        f[k] = base + k < n && perm[base + k] != (uint32_t)(base + k);
+        s += f[k];
+    }
+    int64_t tot;
+    int64_t pos = boff[blockIdx.x] + block_exclusive_scan<kMvThreads>(s, tot);
+#pragma unroll
+    for (int k = 0; k < kMvItems; k++)
+        if (f[k]) moved[pos++] = (uint32_t)(base + k);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *moved_n = boff[blockIdx.x] + tot;
+}
+
+__global__ void k_gather_moved(const int64_t *__restrict__ count, const uint32_t *__restrict__ moved,
+                               const uint32_t *__restrict__ perm, GatherArgs g, int64_t n) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= __ldg(count)) return;
+    const uint32_t i = moved[j];
+    uint32_t p = perm[i];
+    if (p >= (uint64_t)n) p = 0;   // only after a flagged sort failure
+    for (int f = 0; f < g.nf; f++) g.dst[f][j] = g.src[f][p];
+    if (g.id_dst) g.id_dst[j] = g.id_src ? g.id_src[p] : p;
+}
+
+__global__ void k_copy_back_moved(const int64_t *__restrict__ count, const uint32_t *__restrict__ moved,
+                                  GatherArgs g) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= __ldg(count)) return;
+    const uint32_t i = moved[j];
+    for (int f = 0; f < g.nf; f++) g.dst[f][i] = g.src[f][j];
+    if (g.id_dst) g.id_dst[i] = g.id_src[j];
 }
 
 // FP32 cell-relative coordinates: cell index on a 2^10 grid per axis and the FP32 offset from the
@@ -351,17 +393,6 @@ __global__ void k_rel(int64_t n, const double *__restrict__ x, const double *__r
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     rel[i] = rel_coords(x[i], y[i], z[i], b);
-}
-
-// The copy back of the first gathered block (x, y, z in its first three fields) with the relative
-// coordinates of the reordered positions computed on the way.
-__global__ void k_copy_back_rel(int64_t n, GatherArgs g, Box3 b, float4 *__restrict__ rel) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double px = g.src[0][i], py = g.src[1][i], pz = g.src[2][i];
-    for (int f = 0; f < g.nf; f++) g.dst[f][i] = g.src[f][i];
-    if (g.id_dst) g.id_dst[i] = g.id_src[i];
-    rel[i] = rel_coords(px, py, pz, b);
 }
 
 // ====================================================================================== mask
@@ -877,6 +908,27 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
     if (c->dhdt_valid) fields[nf++] = c->dhdt;   // dh/dt of the last force pass travels with its particles
     if (s->alpha) fields[nf++] = s->alpha;       // per-particle alpha of the shock switch
     for (int f = 0; f < nf; f++) fields_dst[f] = const_cast<double *>(fields[f]);
+    // positions that change: chunk counts and their scan in the scan scratch (laid out as the leaf
+    // compaction lays it out; it is free until then), the list in the free half of the value buffers,
+    // the count after the chunk offsets
+    static_assert(kMvChunk == kCpChunk, "the scan scratch is sized for chunks of kCpChunk");
+    const int64_t mv_nb = (n + kMvChunk - 1) / kMvChunk;
+    int64_t *mv_boff = c->scan_tmp + mv_nb + 1;   // [mv_nb + 1]
+    {
+        int64_t *bsum = c->scan_tmp;              // [mv_nb]
+        k_moved_sums<<<(unsigned)mv_nb, kMvThreads, 0, c->stream>>>(n, c->perm, bsum);
+        SPH_LAUNCH_CHECK(c, "k_moved_sums");
+        int64_t *save = c->scan_tmp;
+        c->scan_tmp = c->scan_tmp + 2 * (mv_nb + 1);
+        r = exclusive_scan_i64(c, bsum, mv_boff, mv_nb);
+        c->scan_tmp = save;
+        if (r) return r;
+        k_moved_list<<<(unsigned)mv_nb, kMvThreads, 0, c->stream>>>(n, c->perm, mv_boff, c->vals[buf ^ 1],
+                                                                    mv_boff + mv_nb);
+        SPH_LAUNCH_CHECK(c, "k_moved_list");
+    }
+    uint32_t *moved = c->vals[buf ^ 1];
+    const int64_t *n_moved = mv_boff + mv_nb;
     for (int f0 = 0; f0 < nf || (f0 == 0 && s->id); f0 += kGatherBatch) {
         GatherArgs g{};
         g.nf = std::min(kGatherBatch, nf - f0);
@@ -886,8 +938,8 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
         }
         g.id_src = s->id;
         g.id_dst = (f0 == 0 && s->id) ? c->id_tmp : nullptr;
-        k_gather<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->perm, g);
-        SPH_LAUNCH_CHECK(c, "k_gather");
+        k_gather_moved<<<grid_for(n, 256), 256, 0, c->stream>>>(n_moved, moved, c->perm, g, n);
+        SPH_LAUNCH_CHECK(c, "k_gather_moved");
         GatherArgs b{};
         b.nf = g.nf;
         for (int k = 0; k < g.nf; k++) {
@@ -896,19 +948,11 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
         }
         b.id_src = g.id_dst ? c->id_tmp : nullptr;   // the id is complete after the first block
         b.id_dst = g.id_dst ? s->id : nullptr;
-        if (f0 == 0 && g.nf >= 3) {   // fields[0..2] are x, y, z
-            k_copy_back_rel<<<grid_for(n, 256), 256, 0, c->stream>>>(n, b, bx, c->rel);
-            SPH_LAUNCH_CHECK(c, "k_copy_back_rel");
-        } else {
-            k_copy_back<<<grid_for(n, 256), 256, 0, c->stream>>>(n, b);
-            SPH_LAUNCH_CHECK(c, "k_copy_back");
-        }
+        k_copy_back_moved<<<grid_for(n, 256), 256, 0, c->stream>>>(n_moved, moved, b);
+        SPH_LAUNCH_CHECK(c, "k_copy_back_moved");
     }
-    const bool rel_done = nf >= 3;
-    if (!rel_done) {
-        k_rel<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, bx, c->rel);
-        SPH_LAUNCH_CHECK(c, "k_rel");
-    }
+    k_rel<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, bx, c->rel);
+    SPH_LAUNCH_CHECK(c, "k_rel");
 
     // A3 mask + reduction (all passes in one launch; pass by pass where a tile's halo is too short)
     // and A4 scan + compaction
