@@ -56,8 +56,8 @@ typedef struct {
     int kernel;           /* SPH_KERNEL_*; M4 by default (the paper's tests use M4 with hfact 1.2
                              and M6 with hfact 1.0) */
     int precision;        /* SPH_FP64: all pair arithmetic in FP64.  SPH_MIXED: FP64 positions, h
-                             iteration and integration; FP32 pair sums on cell-relative offsets with
-                             Kahan-compensated accumulation */
+                             iteration and integration; FP32 pair sums on separations taken from
+                             32-bit fixed-point positions, with Kahan-compensated accumulation */
     double hfact;         /* rho(h) = m (hfact/h)^3 (Eq. rhoh); 1.2 */
     double gamma;         /* P = (gamma-1) rho u; 5/3 */
     double alpha_av;      /* alpha^AV of v_sig; 1 */

@@ -157,7 +157,7 @@ void free_all(sph_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->digit_hist, c->lookback, c->tile_ctr,
                     c->mask[0], c->mask[1], c->scan_tmp, c->leaf_first, c->mu_leaf, c->lchild, c->rchild,
                     c->endrange, c->lflag, c->rflag, c->child, c->node_parent, c->leaf_parent, c->visit, c->nodes, c->nodesf,
-                    c->gather_tmp, c->id_tmp, c->rel, c->h32, c->h_base, c->gboxf, c->grp_chunks, c->chunk_off, c->masks, c->cand, c->cand_cnt, c->nb_cnt, c->nb_ptr,
+                    c->gather_tmp, c->id_tmp, c->qpos, c->h_base, c->gboxf, c->grp_chunks, c->chunk_off, c->masks, c->cand, c->cand_cnt, c->nb_cnt, c->nb_ptr,
                     c->grp_slots, c->grp_off, c->nb_ids, c->frec, c->m_v, c->m_t, c->m_r, c->a_new, c->dhdt, c->block_part, c->rerun,
                     c->hs_fields, c->hs_id, c->dscal, c->box_of, c->box_mass, c->box_gamma, c->box_root,
                     c->box_dt, c->box_dt_next, c->gstart, c->group_box};
@@ -474,7 +474,7 @@ int create_ctx(const sph_params *p, int64_t n_cap, int n_boxes, int64_t neigh_ca
         (r = alloc(c, &c->leaf_first, N + 1)) || (r = alloc(c, &c->mu_leaf, N)) ||
         (r = ensure_tree(c, std::max<int64_t>(N / 6, 1))) ||
         (r = alloc(c, &c->gather_tmp, (size_t)kGatherBatch * N)) || (r = alloc(c, &c->id_tmp, N)) ||
-        (r = alloc(c, &c->rel, N)) || (r = alloc(c, &c->h32, N)) || (r = alloc(c, &c->h_base, N)) ||
+        (r = alloc(c, &c->qpos, N)) || (r = alloc(c, &c->h_base, N)) ||
         (r = ensure_groups(c, G)) || (r = alloc(c, &c->masks, (size_t)c->masks_cap)) ||
         (r = alloc(c, &c->nb_cnt, N)) || (r = alloc(c, &c->nb_ptr, N)) || (r = alloc(c, &c->nb_ids, c->nb_cap)) ||
         (r = alloc(c, &c->a_new, (size_t)4 * N)) || (r = alloc(c, &c->dhdt, N)) ||

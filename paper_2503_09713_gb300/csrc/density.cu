@@ -8,8 +8,8 @@
 // convergence rho = rho(h) (Eq. rhoh) and Omega = 1 + h/(3 rho) sum_b m dW/dh at the final h, the
 // sum carried from the last Newton evaluation to the final h by its h-derivative (second-order
 // error in a step below eps_c h^n), so no further pass over the neighbours is needed.
-// FP64 path: all pair arithmetic in FP64.  Mixed path: pair sums in FP32 (Kahan) on cell-relative
-// offsets; Newton update, h, rho and Omega in FP64.
+// FP64 path: all pair arithmetic in FP64.  Mixed path: pair sums in FP32 (Kahan) on separations
+// from fixed-point positions; Newton update, h, rho and Omega in FP64.
 #include <cstddef>
 
 #include "physics.cuh"
@@ -26,11 +26,6 @@ struct DensParams {
 
 constexpr int kDensQueue = 32;   // FP64 path: queued candidates per thread (8 bytes each in shared memory)
 
-__device__ __forceinline__ double nearest_image(double d, double L, double halfL, int periodic) {
-    if (periodic && nonneg_lt(halfL, fabs(d))) d -= copysign(L, d);   // |d| > L/2 (integer compare)
-    return d;
-}
-
 // Sums over the neighbours of a at smoothing length h (kernel K):  sf = sum f(q),
 // sg = sum (3 f + q f'),  sk = sum (12 f + 8 q f' + q^2 f'')  (self term included: f(0) times 1, 3
 // and 12), so that rho_sum = m C sf / h^3,  sum m dW/dh = -m C sg / h^4,
@@ -39,19 +34,19 @@ template <typename K, bool kMixed>
 __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt, const uint32_t *__restrict__ ids,
                                              uint32_t st,
                                              const double *__restrict__ x, const double *__restrict__ y,
-                                             const double *__restrict__ z, const float4 *__restrict__ rel,
+                                             const double *__restrict__ z, const uint4 *__restrict__ qpos,
                                              const PairGeo &geo, double &sf, double &sg, double &sk,
                                              uint32_t &nin, uint2 *queue) {
     const double hinv = 1.0 / ha;
     if (!kMixed) {
         // Two phases per chunk so that the FP64 work runs with converged lanes: an FP32 pre-test on the
-        // cell-relative offsets queues (up to kDensQueue) the candidates that may lie inside R h (the
+        // fixed-point positions queues (up to kDensQueue) the candidates that may lie inside R h (the
         // others are clearly outside); then every lane of the warp evaluates its queued candidates in
         // FP64 together, the nearest image taken by |d| > L/2.  All 32 lanes call this function (a lane
         // without a particle passes cnt = 0).
         const double xa = x[a], ya = y[a], za = z[a];
         const double hinv2 = hinv * hinv;
-        const float4 A = rel[a];
+        const uint4 A = qpos[a];
         const float lim = (float)(K::R * K::R) * kPreBand / ((float)hinv2);
         const float hinv2f = (float)hinv2;
         double f0 = K::F0, gq = 0.0;   // sum f and sum q f' (sum (3 f + q f') = 3 sum f + sum q f')
@@ -64,7 +59,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 const uint32_t b = nb_at(ids, k, st);
                 ++k;
                 float fx, fy, fz;
-                rel_sep(A, rel[b], geo, fx, fy, fz);
+                rel_sep(A, qpos[b], geo, fx, fy, fz);
                 const float r2f = fx * fx + fy * fy + fz * fz;
                 if (r2f > lim) continue;
                 queue[(nq++) * qs] = make_uint2(b, __float_as_uint(r2f));
@@ -118,12 +113,12 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         sk = (double)k0;
     } else {
         // FP32 path: four neighbours per iteration so that four independent gathers are in flight
-        const float4 A = rel[a];
+        const uint4 A = qpos[a];
         const float hi = (float)hinv;
         const float hi2 = hi * hi;
         constexpr float R2 = (float)(K::R * K::R);
         float s0 = (float)K::F0, c0 = 0.f, s1 = (float)(3.0 * K::F0), c1 = 0.f, s2 = (float)(12.0 * K::F0);
-        auto acc = [&](const float4 B) {
+        auto acc = [&](const uint4 B) {
             float dx, dy, dz;
             rel_sep(A, B, geo, dx, dy, dz);
             const float q2 = (dx * dx + dy * dy + dz * dz) * hi2;
@@ -146,13 +141,13 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         for (; k + 4 <= cnt; k += 4) {
             const uint4 bq = nq;
             if (k + 8 <= cnt) nq = nb_quad(ids, (k >> 2) + 1, st);
-            const float4 B0 = rel[bq.x], B1 = rel[bq.y], B2 = rel[bq.z], B3 = rel[bq.w];
+            const uint4 B0 = qpos[bq.x], B1 = qpos[bq.y], B2 = qpos[bq.z], B3 = qpos[bq.w];
             acc(B0);
             acc(B1);
             acc(B2);
             acc(B3);
         }
-        for (; k < cnt; k++) acc(rel[nb_at(ids, k, st)]);
+        for (; k < cnt; k++) acc(qpos[nb_at(ids, k, st)]);
         sf = kahan_value(s0, c0);
         sg = kahan_value(s1, c1);
         sk = (double)s2;
@@ -161,7 +156,7 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
 
 template <typename K, bool kMixed>
 __global__ void __launch_bounds__(256, kMixed ? 4 : 1) k_density(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
-                                                 const double *__restrict__ z, const float4 *__restrict__ rel,
+                                                 const double *__restrict__ z, const uint4 *__restrict__ qpos,
                                                  double *__restrict__ h, const double *__restrict__ h_base,
                                                  const uint32_t *__restrict__ nb_cnt,
                                                  const unsigned long long *__restrict__ nb_ptr,
@@ -190,7 +185,7 @@ __global__ void __launch_bounds__(256, kMixed ? 4 : 1) k_density(int64_t n, cons
     while (__any_sync(0xffffffffu, active)) {
         if (active) ++it;
         double sf, sg, sk;
-        density_sums<K, kMixed>(ai, ha, active ? cnt : 0u, ids, st, x, y, z, rel, dp.geo, sf, sg, sk, nin,
+        density_sums<K, kMixed>(ai, ha, active ? cnt : 0u, ids, st, x, y, z, qpos, dp.geo, sf, sg, sk, nin,
                                 dq + threadIdx.x);
         if (!active) continue;
         // one division for 1/h and one for the Newton step; the clamps and tests compare the
@@ -274,12 +269,12 @@ int density_run(sph_ctx *c, sph_state *s, int *iters, bool *stale) {
     with_kernel(c->p.kernel, [&](auto kern) {
         using K = decltype(kern);
         if (c->p.precision == SPH_MIXED)
-            k_density<K, true><<<grid_for(n, blk), blk, 0, c->stream>>>(n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+            k_density<K, true><<<grid_for(n, blk), blk, 0, c->stream>>>(n, s->x, s->y, s->z, c->qpos, s->h, c->h_base,
                                                                         c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
                                                                         s->omega, c->dscal, abort_word(c));
         else
             k_density<K, false><<<grid_for(n, blk), blk, dsm, c->stream>>>(
-                n, s->x, s->y, s->z, c->rel, s->h, c->h_base,
+                n, s->x, s->y, s->z, c->qpos, s->h, c->h_base,
                                                                          c->nb_cnt, c->nb_ptr, c->nb_ids, dp, s->rho,
                                                                          s->omega, c->dscal, abort_word(c));
         return 0;

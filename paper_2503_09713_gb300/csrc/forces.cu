@@ -8,7 +8,7 @@
 //   v_sig^dt_a = max_b (alpha c_s,a + beta max(0, -v_ab.rhat)),  alpha c_s,a without neighbours
 // over pairs with r_ab < R_kern max(h_a, h_b).  Per-particle factors (P/(rho^2 Omega), 1/(rho Omega), c_s,
 // P, rho, 1/h) are computed once per particle by a preparation kernel.  The mixed path evaluates
-// each pair in FP32 from cell-relative offsets and accumulates with Kahan compensation.
+// each pair in FP32 from fixed-point positions and accumulates with Kahan compensation.
 #include "physics.cuh"
 
 namespace sph {
@@ -51,7 +51,7 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
                              const double *__restrict__ u, const double *__restrict__ h,
                              const double *__restrict__ rho, const double *__restrict__ omega,
                              const double *__restrict__ alpha, ForceParams fp, int mixed, FRec *__restrict__ rec, float4 *__restrict__ m_v, float4 *__restrict__ m_t,
-                             float4 *__restrict__ m_r, float *__restrict__ h32) {
+                             float4 *__restrict__ m_r, uint4 *__restrict__ qpos) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || aborted(fp.abort, kAbortStep)) return;
     const double gam = fp.box_gamma ? fp.box_gamma[fp.box_of[i]] : fp.gamma;
@@ -94,7 +94,7 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
             f.k2 = f.k3 = f.k4 = f.k5 = 0.0;
         }
         rec[i] = f;
-        h32[i] = (float)hi;
+        qpos[i].w = __float_as_uint((float)hi);   // the FP32 h of the pre-test
     }
 }
 
@@ -171,24 +171,19 @@ __device__ __forceinline__ void dt_reduce(double t, unsigned long long npair, De
 }
 
 // FP64 pair loop in two phases per chunk, so that the FP64 work runs with converged lanes.  Phase 1
-// walks the particle's cached candidates and keeps those that pass an FP32 test on the cell-relative
-// offsets against the current h (kPreBand margin: every pair inside R max(h_a, h_b) passes), up to
+// walks the particle's cached candidates and keeps those that pass an FP32 test on the fixed-point
+// separations against the current h (kPreBand margin: every pair inside R max(h_a, h_b) passes), up to
 // kForceQueue of them, in a per-thread queue in shared memory; phase 2 evaluates the queued pairs in
 // FP64, all lanes of the warp stepping through their queues together.  (Tested and evaluated in one
 // loop, ~30% of the candidates fail while other lanes of the warp evaluate, and the FP64 pipe, this
 // loop's bound, runs for every candidate of the warp.)  The FP64 separation takes the nearest image
-// by |d| > L/2, which for every queued pair is the image of the cell-relative test.  The mass factor is
+// by |d| > L/2, which for every queued pair is the image of the fixed-point test.  The mass factor is
 // applied once per particle.
 constexpr int kForceQueue = 32;   // queued candidates per thread: 4 bytes each in shared memory
 
-__device__ __forceinline__ double nearest_image(double d, double L, double halfL, int periodic) {
-    if (periodic && nonneg_lt(halfL, fabs(d))) d -= copysign(L, d);   // |d| > L/2 (integer compare)
-    return d;
-}
-
 template <typename K>
 __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__restrict__ rec,
-                                                     const float4 *__restrict__ rel, const float *__restrict__ h32,
+                                                     const uint4 *__restrict__ qpos,
                                                      const uint32_t *__restrict__ nb_cnt,
                                                      const unsigned long long *__restrict__ nb_ptr,
                                                      const uint32_t *__restrict__ nb_ids, ForceParams fp, ForceOut out,
@@ -210,8 +205,8 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
     constexpr bool kPoly = std::is_same<K, Kernel<SPH_KERNEL_M4>>::value;
     FRec A;
     load_rec<kPoly>(&rec[va ? a : 0], A);
-    const float4 PA = rel[va ? a : 0];
-    const float hA = va ? h32[a] : 0.f;
+    const uint4 PA = qpos[va ? a : 0];
+    const float hA = va ? __uint_as_float(PA.w) : 0.f;
     const PairGeo &geo = fp.geo;
     double axs = 0.0, ays = 0.0, azs = 0.0, dus = 0.0, divs = 0.0;
     double vs = A.acs;
@@ -225,8 +220,9 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
             const uint32_t b = nb_at(ids, k, st);
             ++k;
             float fx, fy, fz;
-            rel_sep(PA, rel[b], geo, fx, fy, fz);
-            const float hmf = fmaxf(hA, h32[b]);
+            const uint4 PB = qpos[b];
+            rel_sep(PA, PB, geo, fx, fy, fz);
+            const float hmf = fmaxf(hA, __uint_as_float(PB.w));
             if (!(fx * fx + fy * fy + fz * fz > (float)(K::R * K::R) * kPreBand * hmf * hmf)) q[(nq++) * qs] = b;
         }
         const int nq_max = __reduce_max_sync(0xffffffffu, (unsigned)nq);
@@ -292,7 +288,7 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
 }
 
 template <typename K>
-__global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *__restrict__ rel,
+__global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const uint4 *__restrict__ qpos,
                                                       const float4 *__restrict__ m_v, const float4 *__restrict__ m_t,
                                                       const float4 *__restrict__ m_r, const double *__restrict__ h,
                                                       const uint32_t *__restrict__ nb_cnt,
@@ -312,7 +308,8 @@ __global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *_
     const int64_t lbeg = ids - nb_ids;
     prefetch_lists_l2(nb_ids, lbeg, lbeg + nb_span(cnt, st));
     if (a < n) {
-    const float4 PA = rel[a], VA = m_v[a], TA = m_t[a], RA = m_r[a];
+    const uint4 PA = qpos[a];
+    const float4 VA = m_v[a], TA = m_t[a], RA = m_r[a];
     const double mass_d = fp.box_mass ? fp.box_mass[box] : fp.mass;
     const float mass = (float)mass_d, beta = (float)fp.beta_av, au = (float)fp.alpha_u;
     // the mass factor is applied once per particle; the sums are the pair terms divided by m
@@ -321,7 +318,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *_
     const float hia = VA.w;
     const float Fa_n = RA.z;   // C_norm/h_a^4
     // one pair; B's position and velocity are already loaded
-    auto pair = [&](uint32_t b, const float4 PB, const float4 VB) {
+    auto pair = [&](uint32_t b, const uint4 PB, const float4 VB) {
         float dx, dy, dz;
         rel_sep(PA, PB, fp.geo, dx, dy, dz);
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -366,14 +363,14 @@ __global__ void __launch_bounds__(256) k_forces_mixed(int64_t n, const float4 *_
     for (; k + 2 <= cnt; k += 2) {
         const uint32_t b0 = nbp.x, b1 = nbp.y;
         if (k + 4 <= cnt) nbp = nb_pair(ids, k + 2, st);
-        const float4 P0 = rel[b0], P1 = rel[b1];
+        const uint4 P0 = qpos[b0], P1 = qpos[b1];
         const float4 V0 = m_v[b0], V1 = m_v[b1];
         pair(b0, P0, V0);
         pair(b1, P1, V1);
     }
     if (k < cnt) {
         const uint32_t b = nb_at(ids, k, st);
-        pair(b, rel[b], m_v[b]);
+        pair(b, qpos[b], m_v[b]);
     }
     const double axs = mass_d * kahan_value(sx, cx), ays = mass_d * kahan_value(sy, cy),
                  azs = mass_d * kahan_value(sz, cz);
@@ -429,7 +426,7 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     k_force_prep<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, s->vx, s->vy, s->vz, s->u, s->h,
                                                            s->rho, s->omega, c->p.av_switch ? s->alpha : nullptr,
                                                            fp, mixed, (FRec *)c->frec, c->m_v,
-                                                           c->m_t, c->m_r, c->h32);
+                                                           c->m_t, c->m_r, c->qpos);
     SPH_LAUNCH_CHECK(c, "k_force_prep");
     k_reset_dt<<<1, 32, 0, c->stream>>>(c->dscal, fp.box_dt_next, c->n_boxes);
     SPH_LAUNCH_CHECK(c, "k_reset_dt");
@@ -447,12 +444,12 @@ int forces_run(sph_ctx *c, sph_state *s, double *ax, double *ay, double *az, dou
     with_kernel(c->p.kernel, [&](auto kern) {
         using K = decltype(kern);
         if (mixed)
-            k_forces_mixed<K><<<grid_for(n, blk), blk, 0, c->stream>>>(n, c->rel, c->m_v, c->m_t, c->m_r, s->h,
+            k_forces_mixed<K><<<grid_for(n, blk), blk, 0, c->stream>>>(n, c->qpos, c->m_v, c->m_t, c->m_r, s->h,
                                                                        c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out,
                                                                        c->dscal);
         else
             k_forces_fp64<K><<<grid_for(n, blk), blk, fsm, c->stream>>>(
-                n, (const FRec *)c->frec, c->rel, c->h32,
+                n, (const FRec *)c->frec, c->qpos,
                                                                       c->nb_cnt, c->nb_ptr, c->nb_ids, fp, out,
                                                                       c->dscal);
         return 0;

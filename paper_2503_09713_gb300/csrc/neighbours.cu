@@ -26,13 +26,14 @@ namespace sph {
 
 struct Geo {
     double lo[3], L[3], halfL[3];
-    float cell[3];   // box side / 1024 in FP32
+    float unit[3];   // length of one step of the fixed-point positions
     float Lf[3];     // box side in FP32
     int periodic;
 };
 
-// Stage 2 tests in the frame of a group's first cell when the group's extent plus the largest
-// search radius stays below this: half the smallest box side less two cells, rounded down.
+// Stage 2 tests in the frame of a group's first particle when the group's extent plus the largest
+// search radius stays below this: half the smallest box side less a margin of 2/1024 of the largest
+// side (far above the rounding of the FP32 sum it is compared with), rounded down.
 static float frame_limit(const Geo &geo) {
     const double lmin = fmin(fmin(geo.L[0], geo.L[1]), geo.L[2]);
     const double cmax = fmax(fmax(geo.L[0], geo.L[1]), geo.L[2]) / 1024.0;
@@ -48,7 +49,7 @@ static Geo make_geo(const sph_params &p) {
         g.lo[k] = p.box_lo[k];
         g.L[k] = p.box_hi[k] - p.box_lo[k];
         g.halfL[k] = 0.5 * g.L[k];
-        g.cell[k] = (float)(g.L[k] / 1024.0);
+        g.unit[k] = (float)(g.L[k] * (p.periodic ? 0x1p-32 : 0x1p-30));
         g.Lf[k] = (float)g.L[k];
     }
     g.periodic = p.periodic;
@@ -207,17 +208,6 @@ __global__ void __launch_bounds__(256) k_walk(Groups gr, Count Gc, Count Lc, con
 }
 
 // ------------------------------------------------------------------ stage 2: per-particle filter
-__device__ __forceinline__ int wrap_cell(int d, int periodic) {
-    return periodic ? (((d + 512) & 1023) - 512) : d;
-}
-
-__device__ __forceinline__ void unpack_cell(const float4 P, int &cx, int &cy, int &cz) {
-    const uint32_t p = __float_as_uint(P.w);
-    cx = (int)((p >> 20) & 1023u);
-    cy = (int)((p >> 10) & 1023u);
-    cz = (int)(p & 1023u);
-}
-
 // The definition, in FP64 and in the order of the oracle: r^2 = (dx*dx + dy*dy) + dz*dz < (s*max h)^2.
 __device__ __forceinline__ bool exact_pair(int64_t a, int64_t b, const double *__restrict__ x,
                                            const double *__restrict__ y, const double *__restrict__ z,
@@ -247,18 +237,19 @@ constexpr uint32_t kGrpSpinLimit = 1u << 22;
 // (1) tests the candidates and keeps, per 32-candidate chunk and lane, the bit mask of kept
 // candidates; (2) obtains the group's offset in the cache by decoupled look-back over the
 // preceding groups (the group needs 32 x its largest count entries); (3) expands its masks, which
-// are still in L2, into the cache.  Tests run in FP32 relative to the cell of the group's first
-// particle, the periodic wrap done once per particle on the integer cell index.  A true neighbour
-// b of a group particle lies within ext + s*h_max of that cell (ext: group extent, h_max: largest h
-// in the box), so its wrapped coordinate is its nearest image whenever ext + s*h_max stays below half
-// a box by two cells (the wrap works on whole cells); a wrongly wrapped candidate that is not a true
-// neighbour is never nearer than its nearest image, so it is rejected either way.  The condition is
+// are still in L2, into the cache.  Tests run in FP32 relative to the group's first particle: the
+// int32 difference of fixed-point counts (one per particle) is the image nearest to that particle.
+// A true neighbour b of a group particle lies within ext + s*h_max of it (ext: group extent, h_max:
+// largest h in the box), so that image is b's nearest image from every particle of the group whenever
+// ext + s*h_max stays below half a box (with a margin, see frame_limit); a candidate taken in another
+// image is not a true neighbour and is never nearer than its nearest image, so it is rejected either
+// way.  The condition is
 // warp-uniform; a group that fails it wraps every separation on its own.  Pairs within a relative
 // 2^-10 of the radius are decided in FP64 (exact_pair).
 __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     Groups gr, const int32_t *__restrict__ box_root, Count Gc, const uint2 *__restrict__ cand, const uint32_t *__restrict__ cand_cnt, int cap,
     const int64_t *__restrict__ chunk_off, int64_t masks_cap, const NodeF *__restrict__ gboxf, const Node *__restrict__ nodes,
-    const float4 *__restrict__ rel, const float *__restrict__ h32, const double *__restrict__ x,
+    const uint4 *__restrict__ qpos, const double *__restrict__ x,
     const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h, double s,
     float frame_lim, Geo geo, uint32_t *__restrict__ masks, uint32_t *__restrict__ nb_cnt,
     unsigned long long *__restrict__ nb_ptr, unsigned long long *lookback, uint32_t *ticket, int64_t *__restrict__ grp_off, uint32_t *__restrict__ nb_ids,
@@ -285,32 +276,17 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     const int64_t gsize = group_end(gr, g) - first;
     const bool va = lane < gsize;
     const float s32 = (float)s;
-    const float4 Araw = rel[va ? a : first];
-    int rcx, rcy, rcz;
-    unpack_cell(rel[first], rcx, rcy, rcz);
-    auto grel = [&](const float4 P, float &px, float &py, float &pz) {
-        int cx, cy, cz;
-        unpack_cell(P, cx, cy, cz);
-        px = fmaf((float)wrap_cell(cx - rcx, geo.periodic), geo.cell[0], P.x);
-        py = fmaf((float)wrap_cell(cy - rcy, geo.periodic), geo.cell[1], P.y);
-        pz = fmaf((float)wrap_cell(cz - rcz, geo.periodic), geo.cell[2], P.z);
-    };
-    auto sep2 = [&](const float4 B, bool compact_path, float axr, float ayr, float azr, const int *ca) {
-        float dx, dy, dz;
-        if (compact_path) {
-            dx = B.x - axr; dy = B.y - ayr; dz = B.z - azr;
-        } else {
-            int cb[3];
-            unpack_cell(B, cb[0], cb[1], cb[2]);
-            dx = fmaf((float)wrap_cell(cb[0] - ca[0], geo.periodic), geo.cell[0], B.x - Araw.x);
-            dy = fmaf((float)wrap_cell(cb[1] - ca[1], geo.periodic), geo.cell[1], B.y - Araw.y);
-            dz = fmaf((float)wrap_cell(cb[2] - ca[2], geo.periodic), geo.cell[2], B.z - Araw.z);
-        }
-        return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const uint4 Araw = qpos[va ? a : first];
+    const uint4 F = qpos[first];
+    // coordinates in the frame of the group's first particle (nearest image of each)
+    auto grel = [&](const uint4 P, float &px, float &py, float &pz) {
+        px = (float)(int)(P.x - F.x) * geo.unit[0];
+        py = (float)(int)(P.y - F.y) * geo.unit[1];
+        pz = (float)(int)(P.z - F.z) * geo.unit[2];
     };
     float ax, ay, az;
     grel(Araw, ax, ay, az);
-    const float hA = va ? h32[a] : 0.f;
+    const float hA = va ? __uint_as_float(Araw.w) : 0.f;
     const float tA = (s32 * hA) * (s32 * hA);
     // the group's box in the same relative FP32 coordinates, and its largest h (candidate filter)
     const float glo[3] = {warp_min_f(va ? ax : INFINITY), warp_min_f(va ? ay : INFINITY),
@@ -322,8 +298,6 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     const double hroot = nodes[box_root[group_box_of(gr, g)]].hmax;
     const float ext = fmaxf(fmaxf(__fsub_ru(q.hi[0], q.lo[0]), __fsub_ru(q.hi[1], q.lo[1])), __fsub_ru(q.hi[2], q.lo[2]));
     const bool compact = ext + (float)(s * hroot) < frame_lim;   // warp-uniform
-    int ca[3];
-    unpack_cell(Araw, ca[0], ca[1], ca[2]);
     const uint2 *cl = cand + (size_t)g * cap;
     const int ncand = (int)min(cand_cnt[g], (uint32_t)cap);
     uint32_t *gm = masks + (size_t)chunk_off[g] * 32 + lane;
@@ -334,15 +308,18 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
         const uint2 rg = cl[ci];
         for (int64_t base = rg.x; base < rg.y; base += 32, ++chunk) {
             const int64_t b = base + lane;
+            // compact: group-frame position and (s h_b)^2; otherwise the fixed-point position
             float4 P = make_float4(1e30f, 1e30f, 1e30f, 0.f);
             float hb = 0.f;
             if (b < rg.y) {
-                P = rel[b];
-                hb = h32[b];
+                const uint4 Q = qpos[b];
+                hb = __uint_as_float(Q.w);
                 if (compact) {
                     float px, py, pz;
-                    grel(P, px, py, pz);
+                    grel(Q, px, py, pz);
                     P = make_float4(px, py, pz, (s32 * hb) * (s32 * hb));
+                } else {
+                    P = make_float4(__uint_as_float(Q.x), __uint_as_float(Q.y), __uint_as_float(Q.z), 0.f);
                 }
             }
             s_posw[lane] = P;
@@ -365,7 +342,8 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
                     const int jj = __ffs(todo) - 1;
                     todo &= todo - 1;
                     const float4 B = s_posw[jj];   // .w = (s h_b)^2
-                    const float r2 = sep2(B, true, ax, ay, az, ca);
+                    const float dx = B.x - ax, dy = B.y - ay, dz = B.z - az;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     const float T = fmaxf(tA, B.w);
                     if (r2 * kInvHi <= T) hi |= 1u << jj;   // possibly inside: r^2 <= T (1 + 2^-10)
                     if (r2 * kInvLo < T) lo |= 1u << jj;    // surely inside:   r^2 < T (1 - 2^-10)
@@ -373,7 +351,11 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
             } else {
                 const int m = (rg.y - base) < 32 ? (int)(rg.y - base) : 32;
                 for (int jj = 0; jj < m; jj++) {
-                    const float r2 = sep2(s_posw[jj], false, ax, ay, az, ca);
+                    const float4 B = s_posw[jj];   // fixed-point counts
+                    const float dx = (float)(int)(__float_as_uint(B.x) - Araw.x) * geo.unit[0];
+                    const float dy = (float)(int)(__float_as_uint(B.y) - Araw.y) * geo.unit[1];
+                    const float dz = (float)(int)(__float_as_uint(B.z) - Araw.z) * geo.unit[2];
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     const float hm = fmaxf(hA, s_tw[jj].y);
                     const float t = (s32 * hm) * (s32 * hm);
                     if (r2 <= t * kBandHi) hi |= 1u << jj;
@@ -482,11 +464,13 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     if (k & 3u) *reinterpret_cast<uint4 *>(dst + (int64_t)(k >> 2) * row) = quad;   // last, partial quad
 }
 
-__global__ void k_h32(int64_t n, const double *__restrict__ h, float *__restrict__ h32, double *__restrict__ hb) {
+// h^n of the cache (the FP64 copy the density iteration measures its steps against) and the FP32 h
+// in the fixed-point positions' .w, which the stage-2 tests read.
+__global__ void k_h_base(int64_t n, const double *__restrict__ h, uint4 *__restrict__ qpos, double *__restrict__ hb) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double v = h[i];
-    h32[i] = (float)v;
+    qpos[i].w = __float_as_uint((float)v);
     hb[i] = v;
 }
 
@@ -522,7 +506,7 @@ int debug_stage2_timeout(sph_ctx *c, const sph_state *s, uint32_t spins) {
     SPH_CUDA(c, cudaMemsetAsync(c->grp_slots, 0, (size_t)c->n_groups * sizeof(int64_t), c->stream));
     k_stage2<<<1, 32, 32 * (sizeof(float4) + sizeof(float2)), c->stream>>>(
         make_groups(c), c->box_root, group_count(c), c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->masks_cap,
-        c->gboxf, c->nodes, c->rel, c->h32, s->x, s->y, s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->nb_ptr,
+        c->gboxf, c->nodes, c->qpos, s->x, s->y, s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->nb_ptr,
         (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket, c->grp_off, c->nb_ids, c->nb_cap, c->dscal, spins);
     SPH_LAUNCH_CHECK(c, "k_stage2 (probe)");
     SPH_CUDA(c, cudaMemcpyAsync(&c->hscal->flags, &c->dscal->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost,
@@ -541,8 +525,8 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
     const double sc = kernel_radius(c->p.kernel) * c->p.cache_tol;   // R_kern * chi
     c->cache_valid = false;
 
-    k_h32<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->h, c->h32, c->h_base);
-    SPH_LAUNCH_CHECK(c, "k_h32");
+    k_h_base<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->h, c->qpos, c->h_base);
+    SPH_LAUNCH_CHECK(c, "k_h_base");
     k_group_boxes<<<grid_for(G * 32, 128), 128, 0, c->stream>>>(gr, group_count(c), s->x, s->y, s->z, s->h,
                                                                 c->gboxf);
     SPH_LAUNCH_CHECK(c, "k_group_boxes");
@@ -594,7 +578,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         SPH_CUDA(c, cudaMemsetAsync(c->grp_slots, 0, (size_t)G * sizeof(int64_t), c->stream));
         k_stage2<<<blocks, s2w * 32, s2_smem, c->stream>>>(
             gr, c->box_root, group_count(c), c->cand, c->cand_cnt, c->cand_cap, c->chunk_off, c->masks_cap, c->gboxf,
-            c->nodes, c->rel, c->h32, s->x, s->y, s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->nb_ptr,
+            c->nodes, c->qpos, s->x, s->y, s->z, s->h, sc, qbox, geo, c->masks, c->nb_cnt, c->nb_ptr,
             (unsigned long long *)c->grp_slots, &c->dscal->s2_ticket, c->grp_off, c->nb_ids, c->nb_cap, c->dscal,
             kGrpSpinLimit);
         SPH_LAUNCH_CHECK(c, "k_stage2");

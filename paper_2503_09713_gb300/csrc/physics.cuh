@@ -218,7 +218,7 @@ __device__ __forceinline__ double kahan_value(float s, float c) { return (double
 // Geometry shared by the pair loops.
 struct PairGeo {
     double L[3], halfL[3];
-    float cell[3];
+    float unit[3];   // length of one step of the fixed-point positions (see qpos_scale)
     int periodic;
 };
 
@@ -227,57 +227,23 @@ inline PairGeo make_pair_geo(const sph_params &p) {
     for (int k = 0; k < 3; k++) {
         g.L[k] = p.box_hi[k] - p.box_lo[k];
         g.halfL[k] = 0.5 * g.L[k];
-        g.cell[k] = (float)(g.L[k] / 1024.0);
+        g.unit[k] = (float)(g.L[k] * (p.periodic ? 0x1p-32 : 0x1p-30));
     }
     g.periodic = p.periodic;
     return g;
 }
 
-// FP32 separation r_a - r_b from cell-relative coordinates (nearest periodic image).
-__device__ __forceinline__ void rel_sep(const float4 A, const float4 B, const PairGeo &geo, float &dx, float &dy,
+// FP32 separation r_a - r_b (nearest periodic image) from fixed-point positions.
+__device__ __forceinline__ void rel_sep(const uint4 A, const uint4 B, const PairGeo &geo, float &dx, float &dy,
                                         float &dz) {
-    const uint32_t pa = __float_as_uint(A.w), pb = __float_as_uint(B.w);
-    int dix = (int)((pa >> 20) & 1023u) - (int)((pb >> 20) & 1023u);
-    int diy = (int)((pa >> 10) & 1023u) - (int)((pb >> 10) & 1023u);
-    int diz = (int)(pa & 1023u) - (int)(pb & 1023u);
-    if (geo.periodic) {
-        dix = ((dix + 512) & 1023) - 512;
-        diy = ((diy + 512) & 1023) - 512;
-        diz = ((diz + 512) & 1023) - 512;
-    }
-    dx = fmaf((float)dix, geo.cell[0], A.x - B.x);
-    dy = fmaf((float)diy, geo.cell[1], A.y - B.y);
-    dz = fmaf((float)diz, geo.cell[2], A.z - B.z);
+    dx = (float)(int)(A.x - B.x) * geo.unit[0];
+    dy = (float)(int)(A.y - B.y) * geo.unit[1];
+    dz = (float)(int)(A.z - B.z) * geo.unit[2];
 }
 
-// Same separation, plus the periodic image shift (in box lengths, -1/0/+1 per axis) that turns the
-// FP64 difference r_a - r_b into the nearest image: the cell-index difference is wrapped into
-// [-512, 511]; a wrap of +-1024 cells is an image shift of -+1 box.
-__device__ __forceinline__ void rel_sep_shift(const float4 A, const float4 B, const PairGeo &geo, float &dx,
-                                              float &dy, float &dz, int &sx, int &sy, int &sz) {
-    const uint32_t pa = __float_as_uint(A.w), pb = __float_as_uint(B.w);
-    const int rx = (int)((pa >> 20) & 1023u) - (int)((pb >> 20) & 1023u);
-    const int ry = (int)((pa >> 10) & 1023u) - (int)((pb >> 10) & 1023u);
-    const int rz = (int)(pa & 1023u) - (int)(pb & 1023u);
-    int wx = rx, wy = ry, wz = rz;
-    if (geo.periodic) {
-        wx = ((rx + 512) & 1023) - 512;
-        wy = ((ry + 512) & 1023) - 512;
-        wz = ((rz + 512) & 1023) - 512;
-    }
-    sx = (wx - rx) / 1024;
-    sy = (wy - ry) / 1024;
-    sz = (wz - rz) / 1024;
-    dx = fmaf((float)wx, geo.cell[0], A.x - B.x);
-    dy = fmaf((float)wy, geo.cell[1], A.y - B.y);
-    dz = fmaf((float)wz, geo.cell[2], A.z - B.z);
-}
-
-// FP64 nearest-image difference a - b given the shift from rel_sep_shift (the shift is zero for all
-// but boundary-crossing pairs; adding -L gives the same rounding as subtracting L).
-__device__ __forceinline__ double image_diff(double a, double b, int s, double L) {
-    double d = a - b;
-    if (s != 0) d += (double)s * L;
+// FP64 nearest image of a separation: |d| > L/2 moves it by one box length (integer compare).
+__device__ __forceinline__ double nearest_image(double d, double L, double halfL, int periodic) {
+    if (periodic && nonneg_lt(halfL, fabs(d))) d -= copysign(L, d);
     return d;
 }
 

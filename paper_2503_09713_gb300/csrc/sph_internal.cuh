@@ -233,8 +233,7 @@ struct sph_ctx {
     // ---- reorder scratch and per-particle derived arrays ----
     double *gather_tmp = nullptr;      // [kGatherBatch][n_cap]
     uint32_t *id_tmp = nullptr;
-    float4 *rel = nullptr;             // [n_cap] FP32 cell offsets + packed cell index
-    float *h32 = nullptr;              // [n_cap]
+    uint4 *qpos = nullptr;             // [n_cap] fixed-point positions, .w FP32 h (see QScale)
     double *h_base = nullptr;          // [n_cap] h^n of the cache
 
     // ---- neighbour cache ----
@@ -392,6 +391,28 @@ inline int64_t launch_groups(const sph_ctx *c) { return c->capturing ? c->g_cap 
 inline const uint32_t *abort_word(const sph_ctx *c) { return c->capturing ? &c->dscal->flags : nullptr; }
 Count leaf_count(sph_ctx *c);
 Count group_count(sph_ctx *c);
+
+// Fixed-point positions (uint4 per particle: x, y, z counts, .w the FP32 bits of h): per axis the
+// position as an unsigned 32-bit count of steps from an origin.  Periodic box: steps of L 2^-32 from
+// the low corner, the count taken modulo 2^32, so that the int32 difference of two counts is the
+// separation of the nearest periodic image.  Open box: steps of L 2^-30 from lo - L/2, so that
+// differences of positions inside the box stay below 2^31 steps.  A separation is one integer
+// subtraction, one conversion and one product per axis; its error is the conversion's rounding
+// (2^-24 relative) plus under one step (2^-32 L or 2^-30 L) of absolute error.
+struct QScale {
+    double lo[3];   // origin
+    double k[3];    // steps per unit length
+};
+
+inline QScale qpos_scale(const double *box_lo, const double *box_hi, int periodic) {
+    QScale q;
+    for (int k = 0; k < 3; k++) {
+        const double L = box_hi[k] - box_lo[k];
+        q.lo[k] = periodic ? box_lo[k] : box_lo[k] - 0.5 * L;
+        q.k[k] = (periodic ? 0x1p32 : 0x1p30) / L;
+    }
+    return q;
+}
 
 // ---------------------------------------------------------------- device helpers
 

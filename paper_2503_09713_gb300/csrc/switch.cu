@@ -7,7 +7,7 @@
 //   tau_a = h_a / (sigma_decay c_s,a),
 //   alpha^{n+1} = max((alpha^n + alpha_loc dt/tau)/(1 + dt/tau), alpha_loc),
 // alpha_max = alpha_av.  The sums run over the cached neighbours with r < R_kern h_a.  FP64 path:
-// FP64 sums; mixed path: FP32 sums on cell-relative offsets (alpha is a limiter: the paper notes
+// FP64 sums; mixed path: FP32 sums on fixed-point separations (alpha is a limiter: the paper notes
 // that Phantom keeps alpha and div v in single precision).
 #include "physics.cuh"
 
@@ -23,7 +23,7 @@ struct SwitchParams {
 
 template <typename K, bool kMixed>
 __global__ void __launch_bounds__(128) k_alpha(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
-                                               const double *__restrict__ z, const float4 *__restrict__ rel,
+                                               const double *__restrict__ z, const uint4 *__restrict__ qpos,
                                                const double *__restrict__ vx, const double *__restrict__ vy,
                                                const double *__restrict__ vz, const double *__restrict__ ax,
                                                const double *__restrict__ ay, const double *__restrict__ az,
@@ -50,22 +50,19 @@ __global__ void __launch_bounds__(128) k_alpha(int64_t n, const double *__restri
     const T aax = (T)ax[a], aay = (T)ay[a], aaz = (T)az[a];
     T G[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
     T diva = T(0);
-    const float4 A = rel[a];
+    const uint4 A = qpos[a];
     const double xa = x[a], ya = y[a], za = z[a];
     for (uint32_t k = 0; k < cnt; k++) {
         const uint32_t b = nb_at(ids, k, st);
         T dx, dy, dz;
         if (kMixed) {
             float fx, fy, fz;
-            rel_sep(A, rel[b], sp.geo, fx, fy, fz);
+            rel_sep(A, qpos[b], sp.geo, fx, fy, fz);
             dx = (T)fx; dy = (T)fy; dz = (T)fz;
         } else {
-            float fx, fy, fz;
-            int sx, sy, sz;
-            rel_sep_shift(A, rel[b], sp.geo, fx, fy, fz, sx, sy, sz);
-            dx = (T)image_diff(xa, x[b], sx, sp.geo.L[0]);
-            dy = (T)image_diff(ya, y[b], sy, sp.geo.L[1]);
-            dz = (T)image_diff(za, z[b], sz, sp.geo.L[2]);
+            dx = (T)nearest_image(xa - x[b], sp.geo.L[0], sp.geo.halfL[0], sp.geo.periodic);
+            dy = (T)nearest_image(ya - y[b], sp.geo.L[1], sp.geo.halfL[1], sp.geo.periodic);
+            dz = (T)nearest_image(za - z[b], sp.geo.L[2], sp.geo.halfL[2], sp.geo.periodic);
         }
         const T r2 = dx * dx + dy * dy + dz * dz;
         if (!(r2 * hinv * hinv < R2) || !(r2 > T(0))) continue;
@@ -125,11 +122,11 @@ int switch_run(sph_ctx *c, sph_state *s, double dt) {
         using K = decltype(kern);
         if (c->p.precision == SPH_MIXED)
             k_alpha<K, true><<<grid_for(n, 128), 128, 0, c->stream>>>(
-                n, s->x, s->y, s->z, c->rel, s->vx, s->vy, s->vz, s->ax, s->ay, s->az, s->u, s->h, s->omega,
+                n, s->x, s->y, s->z, c->qpos, s->vx, s->vy, s->vz, s->ax, s->ay, s->az, s->u, s->h, s->omega,
                 c->nb_cnt, c->nb_ptr, c->nb_ids, sp, s->alpha);
         else
             k_alpha<K, false><<<grid_for(n, 128), 128, 0, c->stream>>>(
-                n, s->x, s->y, s->z, c->rel, s->vx, s->vy, s->vz, s->ax, s->ay, s->az, s->u, s->h, s->omega,
+                n, s->x, s->y, s->z, c->qpos, s->vx, s->vy, s->vz, s->ax, s->ay, s->az, s->u, s->h, s->omega,
                 c->nb_cnt, c->nb_ptr, c->nb_ids, sp, s->alpha);
         return 0;
     });

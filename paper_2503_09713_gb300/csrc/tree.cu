@@ -371,28 +371,18 @@ __global__ void k_copy_back_moved(const int64_t *__restrict__ count, const uint3
     if (g.id_dst) g.id_dst[i] = g.id_src[j];
 }
 
-// FP32 cell-relative coordinates: cell index on a 2^10 grid per axis and the FP32 offset from the
-// cell corner; packed cell index in .w (x<<20 | y<<10 | z).
-__device__ __forceinline__ float4 rel_coords(double px, double py, double pz, const Box3 &b) {
-    const double p[3] = {px, py, pz};
-    uint32_t ci[3];
-    float off[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const double cell = b.span[k] * (1.0 / 1024.0);
-        const uint32_t g = (uint32_t)floor_clamped(
-            b.inv_span[k] != 0.0 ? (p[k] - b.lo[k]) * (1024.0 * b.inv_span[k]) : (p[k] - b.lo[k]) / cell, 1023);
-        ci[k] = g;
-        off[k] = (float)(p[k] - fma((double)g, cell, b.lo[k]));
-    }
-    return make_float4(off[0], off[1], off[2], __uint_as_float((ci[0] << 20) | (ci[1] << 10) | ci[2]));
+// Fixed-point positions (see QScale): per axis floor((p - lo) k) modulo 2^32; .w is written by the
+// neighbour search (FP32 h).
+__device__ __forceinline__ uint32_t fixed_count(double p, double lo, double k) {
+    return (uint32_t)(unsigned long long)__double2ll_rd((p - lo) * k);
 }
 
-__global__ void k_rel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
-                      const double *__restrict__ z, Box3 b, float4 *__restrict__ rel) {
+__global__ void k_qpos(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                       const double *__restrict__ z, QScale q, uint4 *__restrict__ qpos) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    rel[i] = rel_coords(x[i], y[i], z[i], b);
+    qpos[i] = make_uint4(fixed_count(x[i], q.lo[0], q.k[0]), fixed_count(y[i], q.lo[1], q.k[1]),
+                         fixed_count(z[i], q.lo[2], q.k[2]), 0u);
 }
 
 // ====================================================================================== mask
@@ -951,8 +941,9 @@ int tree_build(sph_ctx *c, sph_state *s, bool gather_outputs) {
         k_copy_back_moved<<<grid_for(n, 256), 256, 0, c->stream>>>(n_moved, moved, b);
         SPH_LAUNCH_CHECK(c, "k_copy_back_moved");
     }
-    k_rel<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z, bx, c->rel);
-    SPH_LAUNCH_CHECK(c, "k_rel");
+    k_qpos<<<grid_for(n, 256), 256, 0, c->stream>>>(n, s->x, s->y, s->z,
+                                                    qpos_scale(c->p.box_lo, c->p.box_hi, c->p.periodic), c->qpos);
+    SPH_LAUNCH_CHECK(c, "k_qpos");
 
     // A3 mask + reduction (all passes in one launch; pass by pass where a tile's halo is too short)
     // and A4 scan + compaction
