@@ -254,11 +254,13 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     float frame_lim, Geo geo, uint32_t *__restrict__ masks, uint32_t *__restrict__ nb_cnt,
     unsigned long long *__restrict__ nb_ptr, unsigned long long *lookback, uint32_t *ticket, int64_t *__restrict__ grp_off, uint32_t *__restrict__ nb_ids,
     int64_t nb_cap, DevScalars *sc, uint32_t spin_limit) {
-    // per warp: 32 candidates (FP32 position + threshold) and (s h_b)^2 (1 - 2^-10), h_b
+    // per warp: 32 candidates (group-frame position and (s h_b)^2, or the fixed-point position), and
+    // h_b (wrapped path) or the chunk position of each compacted candidate (group-frame path)
     extern __shared__ float4 s2_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4 *s_posw = s2_smem + warp * 32;
-    float2 *s_tw = reinterpret_cast<float2 *>(s2_smem + (blockDim.x >> 5) * 32) + warp * 32;
+    float *s_hb = reinterpret_cast<float *>(s2_smem + (blockDim.x >> 5) * 32) + warp * 64;
+    int *s_jj = reinterpret_cast<int *>(s_hb + 32);
     // group count and the mask capacity: the same decision in every block, taken before any ticket
     const int64_t G = read_count(Gc, kAbortStage2);
     if (G == 0) return;
@@ -322,33 +324,57 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
                     P = make_float4(__uint_as_float(Q.x), __uint_as_float(Q.y), __uint_as_float(Q.z), 0.f);
                 }
             }
-            s_posw[lane] = P;
-            s_tw[lane] = make_float2((s32 * hb) * (s32 * hb) * kBandLo, hb);
-            __syncwarp();
-            uint32_t hi = 0, lo = 0;
+            uint32_t hi = 0;
             if (compact) {
                 // Candidate filter (lane = candidate): drop a candidate farther from the group's box
                 // than (s max(h_max,g, h_b))^2 (1 + 2^-9).  Per axis |B - A| >= the gap to the box
                 // in FP32 too (rounding is monotone), the squared sums below are formed in the same
-                // order as the pair test, and a kept pair has r^2 <= max(t_a, t_b) (1 + 2^-10) up to
-                // one rounding, so no particle of the group would keep a dropped candidate.
+                // order as the pair test, and a kept pair has r^2 < max(t_a, t_b) (1 + 2^-10) (up to
+                // one rounding of r^2), so no particle of the group would keep a dropped candidate.
                 const float gx = fmaxf(fmaxf(glo[0] - P.x, P.x - ghi[0]), 0.f);
                 const float gy = fmaxf(fmaxf(glo[1] - P.y, P.y - ghi[1]), 0.f);
                 const float gz = fmaxf(fmaxf(glo[2] - P.z, P.z - ghi[2]), 0.f);
                 const float hm = fmaxf(hmax_g, hb);
                 const bool need = fmaf(gz, gz, fmaf(gy, gy, gx * gx)) <= (s32 * hm) * (s32 * hm) * kPreHi;
-                uint32_t todo = __ballot_sync(0xffffffffu, need);
-                while (todo) {   // warp-uniform
-                    const int jj = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    const float4 B = s_posw[jj];   // .w = (s h_b)^2
+                const uint32_t needm = __ballot_sync(0xffffffffu, need);
+                if (need) {   // compacted: kept candidate k in slot k
+                    const int slot = __popc(needm & ((1u << lane) - 1u));
+                    s_posw[slot] = P;
+                    s_jj[slot] = lane;
+                }
+                __syncwarp();
+                // Every lane tests the kept candidates (warp-uniform loop).  Each decision is the sign
+                // of a fused difference, r^2 (1 -+ 2^-10)^-1 - T rounded once (the exact sign), moved
+                // into bit k of the compacted masks by one funnel shift: possibly inside (hc), surely
+                // inside (lc).
+                const int nk = __popc(needm);
+                uint32_t hc = 0, lc = 0;
+#pragma unroll 4
+                for (int k = nk - 1; k >= 0; --k) {
+                    const float4 B = s_posw[k];   // .w = (s h_b)^2
                     const float dx = B.x - ax, dy = B.y - ay, dz = B.z - az;
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     const float T = fmaxf(tA, B.w);
-                    if (r2 * kInvHi <= T) hi |= 1u << jj;   // possibly inside: r^2 <= T (1 + 2^-10)
-                    if (r2 * kInvLo < T) lo |= 1u << jj;    // surely inside:   r^2 < T (1 - 2^-10)
+                    hc = __funnelshift_l(__float_as_uint(fmaf(r2, kInvHi, -T)), hc, 1);
+                    lc = __funnelshift_l(__float_as_uint(fmaf(r2, kInvLo, -T)), lc, 1);
+                }
+                if (!va) hc = 0;   // lanes past the group keep nothing
+                uint32_t band = hc & ~lc;   // inside the band: FP64 decides
+                while (band) {
+                    const int k = __ffs(band) - 1;
+                    band &= band - 1;
+                    if (!exact_pair(a, base + s_jj[k], x, y, z, h, s, geo)) hc &= ~(1u << k);
+                }
+                while (hc) {   // back to chunk positions
+                    const int k = __ffs(hc) - 1;
+                    hc &= hc - 1;
+                    hi |= 1u << s_jj[k];
                 }
             } else {
+                s_posw[lane] = P;
+                s_hb[lane] = hb;
+                __syncwarp();
+                uint32_t lo = 0;
                 const int m = (rg.y - base) < 32 ? (int)(rg.y - base) : 32;
                 for (int jj = 0; jj < m; jj++) {
                     const float4 B = s_posw[jj];   // fixed-point counts
@@ -356,23 +382,20 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
                     const float dy = (float)(int)(__float_as_uint(B.y) - Araw.y) * geo.unit[1];
                     const float dz = (float)(int)(__float_as_uint(B.z) - Araw.z) * geo.unit[2];
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    const float hm = fmaxf(hA, s_tw[jj].y);
+                    const float hm = fmaxf(hA, s_hb[jj]);
                     const float t = (s32 * hm) * (s32 * hm);
                     if (r2 <= t * kBandHi) hi |= 1u << jj;
                     if (r2 < t * kBandLo) lo |= 1u << jj;
                 }
+                if (!va) hi = lo = 0;   // lanes past the group keep nothing
+                uint32_t band = hi & ~lo;   // inside the band: FP64 decides
+                while (band) {
+                    const int jj = __ffs(band) - 1;
+                    band &= band - 1;
+                    if (!exact_pair(a, base + jj, x, y, z, h, s, geo)) hi &= ~(1u << jj);
+                }
             }
-            if (!va) hi = lo = 0;   // lanes past the group keep nothing
-            if (a >= base && a < base + 32) {   // not its own neighbour
-                hi &= ~(1u << (uint32_t)(a - base));
-                lo &= ~(1u << (uint32_t)(a - base));
-            }
-            uint32_t band = hi & ~lo;   // inside the band: FP64 decides
-            while (band) {
-                const int jj = __ffs(band) - 1;
-                band &= band - 1;
-                if (!exact_pair(a, base + jj, x, y, z, h, s, geo)) hi &= ~(1u << jj);
-            }
+            if (a >= base && a < base + 32) hi &= ~(1u << (uint32_t)(a - base));   // not its own neighbour
             gm[(size_t)chunk * 32] = hi;
             cnt += __popc(hi);
             __syncwarp();
