@@ -465,7 +465,7 @@ int create_ctx(const sph_params *p, int64_t n_cap, int n_boxes, int64_t neigh_ca
     c->sort_tiles = tiles;
     c->cand_cap = 128;
     c->nb_cap = neigh_cap > 0 ? neigh_cap : 96 * N;
-    c->masks_cap = G * 16 * 32;   // grown by the cache build when the candidate chunks need more
+    c->masks_cap = G * 16 * kChunkWords;   // grown by the cache build when the candidate chunks need more
     const int64_t scan_elems = 2 * (chunks + 1) + scan_scratch_elems(chunks) + scan_scratch_elems(G + 1) + 64;
     if ((r = alloc(c, &c->keys[0], N)) || (r = alloc(c, &c->keys[1], N)) || (r = alloc(c, &c->vals[0], N)) ||
         (r = alloc(c, &c->vals[1], N)) || (r = alloc(c, &c->digit_hist, 8 * 256)) ||

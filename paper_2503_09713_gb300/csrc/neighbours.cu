@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(256) k_walk(Groups gr, Count Gc, Count Lc, con
         }
         count = m;
     }
-    int64_t chunks = 0;
-    for (int i = 0; i < count; i++) chunks += (out[i].y - out[i].x + 31) / 32;
+    int64_t total = 0;
+    for (int i = 0; i < count; i++) total += out[i].y - out[i].x;
     cand_cnt[g] = (uint32_t)count;
-    grp_chunks[g] = chunks;
+    grp_chunks[g] = (total + 31) / 32;   // stage 2 takes the concatenated ranges 32 at a time
 }
 
 // ------------------------------------------------------------------ stage 2: per-particle filter
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     // group count and the mask capacity: the same decision in every block, taken before any ticket
     const int64_t G = read_count(Gc, kAbortStage2);
     if (G == 0) return;
-    if (chunk_off[G] * 32 > masks_cap) {
+    if (chunk_off[G] * kChunkWords > masks_cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&sc->flags, kErrCapacity);
         return;
     }
@@ -302,104 +302,129 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     const bool compact = ext + (float)(s * hroot) < frame_lim;   // warp-uniform
     const uint2 *cl = cand + (size_t)g * cap;
     const int ncand = (int)min(cand_cnt[g], (uint32_t)cap);
-    uint32_t *gm = masks + (size_t)chunk_off[g] * 32 + lane;
+    const int64_t nchunks = chunk_off[g + 1] - chunk_off[g];
+    uint32_t *const gbase = masks + (size_t)chunk_off[g] * kChunkWords;
     uint32_t cnt = 0;
-    int64_t chunk = 0;
-    // ---- (1) tests
-    for (int ci = 0; ci < ncand; ci++) {
-        const uint2 rg = cl[ci];
-        for (int64_t base = rg.x; base < rg.y; base += 32, ++chunk) {
-            const int64_t b = base + lane;
-            // compact: group-frame position and (s h_b)^2; otherwise the fixed-point position
-            float4 P = make_float4(1e30f, 1e30f, 1e30f, 0.f);
-            float hb = 0.f;
-            if (b < rg.y) {
-                const uint4 Q = qpos[b];
-                hb = __uint_as_float(Q.w);
-                if (compact) {
-                    float px, py, pz;
-                    grel(Q, px, py, pz);
-                    P = make_float4(px, py, pz, (s32 * hb) * (s32 * hb));
-                } else {
-                    P = make_float4(__uint_as_float(Q.x), __uint_as_float(Q.y), __uint_as_float(Q.z), 0.f);
-                }
+    // cursor over the concatenated candidate ranges (warp-uniform)
+    int ci = 0;
+    int64_t cur = 0, rend = 0;
+    if (ncand > 0) {
+        const uint2 r0 = cl[0];
+        cur = r0.x;
+        rend = r0.y;
+    }
+    // ---- (1) tests, 32 candidates of the concatenated ranges per chunk
+    for (int64_t chunk = 0; chunk < nchunks; ++chunk) {
+        uint32_t *gch = gbase + (size_t)chunk * kChunkWords;   // [0, 32): masks, [32, 64): candidates
+        int64_t b = -1;   // this lane's candidate
+        int filled = 0;
+        while (filled < 32 && ci < ncand) {
+            const int take = (int)min((int64_t)(32 - filled), rend - cur);
+            if (lane >= filled && lane < filled + take) b = cur + (lane - filled);
+            filled += take;
+            cur += take;
+            if (cur == rend && ++ci < ncand) {
+                const uint2 r = cl[ci];
+                cur = r.x;
+                rend = r.y;
             }
-            uint32_t hi = 0;
-            if (compact) {
-                // Candidate filter (lane = candidate): drop a candidate farther from the group's box
-                // than (s max(h_max,g, h_b))^2 (1 + 2^-9).  Per axis |B - A| >= the gap to the box
-                // in FP32 too (rounding is monotone), the squared sums below are formed in the same
-                // order as the pair test, and a kept pair has r^2 < max(t_a, t_b) (1 + 2^-10) (up to
-                // one rounding of r^2), so no particle of the group would keep a dropped candidate.
-                const float gx = fmaxf(fmaxf(glo[0] - P.x, P.x - ghi[0]), 0.f);
-                const float gy = fmaxf(fmaxf(glo[1] - P.y, P.y - ghi[1]), 0.f);
-                const float gz = fmaxf(fmaxf(glo[2] - P.z, P.z - ghi[2]), 0.f);
-                const float hm = fmaxf(hmax_g, hb);
-                const bool need = fmaf(gz, gz, fmaf(gy, gy, gx * gx)) <= (s32 * hm) * (s32 * hm) * kPreHi;
-                const uint32_t needm = __ballot_sync(0xffffffffu, need);
-                if (need) {   // compacted: kept candidate k in slot k
-                    const int slot = __popc(needm & ((1u << lane) - 1u));
-                    s_posw[slot] = P;
-                    s_jj[slot] = lane;
-                }
-                __syncwarp();
-                // Every lane tests the kept candidates (warp-uniform loop).  Each decision is the sign
-                // of a fused difference, r^2 (1 -+ 2^-10)^-1 - T rounded once (the exact sign), moved
-                // into bit k of the compacted masks by one funnel shift: possibly inside (hc), surely
-                // inside (lc).
-                const int nk = __popc(needm);
-                uint32_t hc = 0, lc = 0;
-#pragma unroll 4
-                for (int k = nk - 1; k >= 0; --k) {
-                    const float4 B = s_posw[k];   // .w = (s h_b)^2
-                    const float dx = B.x - ax, dy = B.y - ay, dz = B.z - az;
-                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    const float T = fmaxf(tA, B.w);
-                    hc = __funnelshift_l(__float_as_uint(fmaf(r2, kInvHi, -T)), hc, 1);
-                    lc = __funnelshift_l(__float_as_uint(fmaf(r2, kInvLo, -T)), lc, 1);
-                }
-                if (!va) hc = 0;   // lanes past the group keep nothing
-                uint32_t band = hc & ~lc;   // inside the band: FP64 decides
-                while (band) {
-                    const int k = __ffs(band) - 1;
-                    band &= band - 1;
-                    if (!exact_pair(a, base + s_jj[k], x, y, z, h, s, geo)) hc &= ~(1u << k);
-                }
-                while (hc) {   // back to chunk positions
-                    const int k = __ffs(hc) - 1;
-                    hc &= hc - 1;
-                    hi |= 1u << s_jj[k];
-                }
-            } else {
-                s_posw[lane] = P;
-                s_hb[lane] = hb;
-                __syncwarp();
-                uint32_t lo = 0;
-                const int m = (rg.y - base) < 32 ? (int)(rg.y - base) : 32;
-                for (int jj = 0; jj < m; jj++) {
-                    const float4 B = s_posw[jj];   // fixed-point counts
-                    const float dx = (float)(int)(__float_as_uint(B.x) - Araw.x) * geo.unit[0];
-                    const float dy = (float)(int)(__float_as_uint(B.y) - Araw.y) * geo.unit[1];
-                    const float dz = (float)(int)(__float_as_uint(B.z) - Araw.z) * geo.unit[2];
-                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    const float hm = fmaxf(hA, s_hb[jj]);
-                    const float t = (s32 * hm) * (s32 * hm);
-                    if (r2 <= t * kBandHi) hi |= 1u << jj;
-                    if (r2 < t * kBandLo) lo |= 1u << jj;
-                }
-                if (!va) hi = lo = 0;   // lanes past the group keep nothing
-                uint32_t band = hi & ~lo;   // inside the band: FP64 decides
-                while (band) {
-                    const int jj = __ffs(band) - 1;
-                    band &= band - 1;
-                    if (!exact_pair(a, base + jj, x, y, z, h, s, geo)) hi &= ~(1u << jj);
-                }
-            }
-            if (a >= base && a < base + 32) hi &= ~(1u << (uint32_t)(a - base));   // not its own neighbour
-            gm[(size_t)chunk * 32] = hi;
-            cnt += __popc(hi);
-            __syncwarp();
         }
+        // compact: group-frame position and (s h_b)^2; otherwise the fixed-point position
+        float4 P = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+        float hb = 0.f;
+        if (b >= 0) {
+            const uint4 Q = qpos[b];
+            hb = __uint_as_float(Q.w);
+            if (compact) {
+                float px, py, pz;
+                grel(Q, px, py, pz);
+                P = make_float4(px, py, pz, (s32 * hb) * (s32 * hb));
+            } else {
+                P = make_float4(__uint_as_float(Q.x), __uint_as_float(Q.y), __uint_as_float(Q.z), 0.f);
+            }
+        }
+        // The group's own particles are consecutive in the (sorted, duplicate-free) candidate stream
+        // and pass every filter: lane a's own slot is found from the first of them in this chunk.
+        const uint32_t mg = __ballot_sync(0xffffffffu, b >= first && b < first + gsize);
+        int jself = -1;
+        if (mg) {
+            const int j0 = __ffs(mg) - 1;
+            const int64_t d = a - __shfl_sync(0xffffffffu, b, j0);
+            if (va && d >= 0 && d < __popc(mg)) jself = j0 + (int)d;
+        }
+        uint32_t hi = 0;
+        if (compact) {
+            // Candidate filter (lane = candidate): drop a candidate farther from the group's box
+            // than (s max(h_max,g, h_b))^2 (1 + 2^-9).  Per axis |B - A| >= the gap to the box
+            // in FP32 too (rounding is monotone), the squared sums below are formed in the same
+            // order as the pair test, and a kept pair has r^2 < max(t_a, t_b) (1 + 2^-10) (up to
+            // one rounding of r^2), so no particle of the group would keep a dropped candidate.
+            const float gx = fmaxf(fmaxf(glo[0] - P.x, P.x - ghi[0]), 0.f);
+            const float gy = fmaxf(fmaxf(glo[1] - P.y, P.y - ghi[1]), 0.f);
+            const float gz = fmaxf(fmaxf(glo[2] - P.z, P.z - ghi[2]), 0.f);
+            const float hm = fmaxf(hmax_g, hb);
+            const bool need = fmaf(gz, gz, fmaf(gy, gy, gx * gx)) <= (s32 * hm) * (s32 * hm) * kPreHi;
+            const uint32_t needm = __ballot_sync(0xffffffffu, need);
+            if (need) {   // compacted: kept candidate k in slot k, its index beside the masks
+                const int slot = __popc(needm & ((1u << lane) - 1u));
+                s_posw[slot] = P;
+                s_jj[slot] = (int)b;
+                gch[32 + slot] = (uint32_t)b;
+            }
+            __syncwarp();
+            // Every lane tests the kept candidates (warp-uniform loop).  Each decision is the sign
+            // of a fused difference, r^2 (1 -+ 2^-10)^-1 - T rounded once (the exact sign), moved
+            // into bit k of the masks by one funnel shift: possibly inside (hi), surely inside (lc).
+            const int nk = __popc(needm);
+            uint32_t lc = 0;
+#pragma unroll 4
+            for (int k = nk - 1; k >= 0; --k) {
+                const float4 B = s_posw[k];   // .w = (s h_b)^2
+                const float dx = B.x - ax, dy = B.y - ay, dz = B.z - az;
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const float T = fmaxf(tA, B.w);
+                hi = __funnelshift_l(__float_as_uint(fmaf(r2, kInvHi, -T)), hi, 1);
+                lc = __funnelshift_l(__float_as_uint(fmaf(r2, kInvLo, -T)), lc, 1);
+            }
+            if (!va) hi = 0;   // lanes past the group keep nothing
+            if (jself >= 0 && ((needm >> jself) & 1u))   // not its own neighbour
+                hi &= ~(1u << __popc(needm & ((1u << jself) - 1u)));
+            uint32_t band = hi & ~lc;   // inside the band: FP64 decides
+            while (band) {
+                const int k = __ffs(band) - 1;
+                band &= band - 1;
+                if (!exact_pair(a, s_jj[k], x, y, z, h, s, geo)) hi &= ~(1u << k);
+            }
+        } else {
+            s_posw[lane] = P;
+            s_hb[lane] = hb;
+            s_jj[lane] = (int)b;
+            gch[32 + lane] = (uint32_t)b;
+            __syncwarp();
+            uint32_t lo = 0;
+            for (int jj = 0; jj < filled; jj++) {
+                const float4 B = s_posw[jj];   // fixed-point counts
+                const float dx = (float)(int)(__float_as_uint(B.x) - Araw.x) * geo.unit[0];
+                const float dy = (float)(int)(__float_as_uint(B.y) - Araw.y) * geo.unit[1];
+                const float dz = (float)(int)(__float_as_uint(B.z) - Araw.z) * geo.unit[2];
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const float hm = fmaxf(hA, s_hb[jj]);
+                const float t = (s32 * hm) * (s32 * hm);
+                if (r2 <= t * kBandHi) hi |= 1u << jj;
+                if (r2 < t * kBandLo) lo |= 1u << jj;
+            }
+            if (!va) hi = lo = 0;   // lanes past the group keep nothing
+            if (jself >= 0) hi &= ~(1u << jself);   // not its own neighbour
+            uint32_t band = hi & ~lo;   // inside the band: FP64 decides
+            while (band) {
+                const int jj = __ffs(band) - 1;
+                band &= band - 1;
+                if (!exact_pair(a, s_jj[jj], x, y, z, h, s, geo)) hi &= ~(1u << jj);
+            }
+        }
+        gch[lane] = hi;
+        cnt += __popc(hi);
+        __syncwarp();
     }
     if (va) nb_cnt[a] = cnt;
     uint32_t mx = cnt, sum = cnt;
@@ -466,23 +491,23 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     const int64_t row = 4 * gsize;
     uint4 quad = make_uint4(0u, 0u, 0u, 0u);
     uint32_t k = 0;
-    chunk = 0;
-    for (int ci = 0; ci < ncand; ci++) {
-        const uint2 rg = cl[ci];
-        for (int64_t base = rg.x; base < rg.y; base += 32, ++chunk) {
-            uint32_t m = gm[(size_t)chunk * 32];
-            while (m) {
-                const int jj = __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t v = (uint32_t)(base + jj), j = k & 3u;
-                quad.x = j == 0u ? v : quad.x;
-                quad.y = j == 1u ? v : quad.y;
-                quad.z = j == 2u ? v : quad.z;
-                quad.w = v;
-                if (j == 3u) *reinterpret_cast<uint4 *>(dst + (int64_t)(k >> 2) * row) = quad;
-                ++k;
-            }
+    for (int64_t chunk = 0; chunk < nchunks; ++chunk) {
+        const uint32_t *gch = gbase + (size_t)chunk * kChunkWords;
+        uint32_t m = gch[lane];
+        s_jj[lane] = (int)gch[32 + lane];   // the chunk's candidates (slots without a mask bit unused)
+        __syncwarp();
+        while (m) {
+            const int jj = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t v = (uint32_t)s_jj[jj], j = k & 3u;
+            quad.x = j == 0u ? v : quad.x;
+            quad.y = j == 1u ? v : quad.y;
+            quad.z = j == 2u ? v : quad.z;
+            quad.w = v;
+            if (j == 3u) *reinterpret_cast<uint4 *>(dst + (int64_t)(k >> 2) * row) = quad;
+            ++k;
         }
+        __syncwarp();
     }
     if (k & 3u) *reinterpret_cast<uint4 *>(dst + (int64_t)(k >> 2) * row) = quad;   // last, partial quad
 }
@@ -585,7 +610,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
         c->cand_cap = newcap;
     }
     const int64_t chunks = c->capturing ? 0 : c->hscal->total_chunks;
-    int r = ensure(c, &c->masks, c->masks_cap, chunks * 32, "candidate masks");
+    int r = ensure(c, &c->masks, c->masks_cap, chunks * kChunkWords, "candidate masks");
     if (r) return r;
 
     // stage 2 in one pass; if the cache turns out too small it grows and the pass runs again

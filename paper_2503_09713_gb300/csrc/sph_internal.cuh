@@ -20,6 +20,7 @@ constexpr int kStackDepth = 66;          // tree-walk stack (tree depth <= 63 fo
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kGatherBatch = 4;          // state fields reordered per gather pass (scratch: 4 x n_cap doubles)
 constexpr int kSortTile = 2048;          // keys per tile of a radix-sort pass (256 threads x 8 keys)
+constexpr int kChunkWords = 64;          // stage-2 chunk of 32 candidates: 32 lane masks, 32 candidate ids
 
 // Device error word bits (ctx->d_flags[0]).
 enum : uint32_t {
@@ -242,7 +243,7 @@ struct sph_ctx {
     sph::NodeF *gboxf = nullptr;       // [groups] FP32 group boxes, rounded outwards
     int64_t *grp_chunks = nullptr;     // [groups + 1] candidate chunks per group -> scan
     int64_t *chunk_off = nullptr;      // [groups + 1]
-    uint32_t *masks = nullptr;         // [chunks * 32] stage-2 hit masks
+    uint32_t *masks = nullptr;         // [chunks * kChunkWords] stage-2 hit masks and candidates
     int64_t masks_cap = 0;
     uint2 *cand = nullptr;             // [groups * cand_cap] candidate particle ranges [x, y)
     uint32_t *cand_cnt = nullptr;      // [groups]
