@@ -52,9 +52,11 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
         double f0 = K::F0, gq = 0.0;   // sum f and sum q f' (sum (3 f + q f') = 3 sum f + sum q f')
         float k0 = (float)(12.0 * K::F0);
         const int qs = blockDim.x;
+        const float dface = face_distance(xa, ya, za, geo);
         uint32_t k = 0;
         for (;;) {
             int nq = 0;
+            float reach = 0.f;   // largest |separation| component of a queued candidate
             while (nq < kDensQueue && k < cnt) {
                 const uint32_t b = nb_at(ids, k, st);
                 ++k;
@@ -63,8 +65,10 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 const float r2f = fx * fx + fy * fy + fz * fz;
                 if (r2f > lim) continue;
                 queue[(nq++) * qs] = make_uint2(b, __float_as_uint(r2f));
+                reach = fmaxf(reach, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
             }
             const int nq_max = __reduce_max_sync(0xffffffffu, (unsigned)nq);
+            const bool wrap = __any_sync(0xffffffffu, may_cross_face(reach, dface, geo));
             // the next queued neighbour's position is loaded while the current one is evaluated
             uint2 e = queue[0];
             double bx = 0.0, by = 0.0, bz = 0.0;
@@ -73,6 +77,9 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 by = y[e.x];
                 bz = z[e.x];
             }
+            // the FP64 evaluation, with the nearest-image step only where some lane of the warp may
+            // have a neighbour across a periodic face (warp-uniform)
+            auto evaluate = [&](auto wrap_c) {
             for (int j = 0; j < nq_max; j++) {
                 if (j >= nq) continue;
                 const uint2 ec = e;
@@ -83,9 +90,12 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                     by = y[e.x];
                     bz = z[e.x];
                 }
-                const double dx = nearest_image(xa - cx, geo.L[0], geo.halfL[0], geo.periodic);
-                const double dy = nearest_image(ya - cy, geo.L[1], geo.halfL[1], geo.periodic);
-                const double dz = nearest_image(za - cz, geo.L[2], geo.halfL[2], geo.periodic);
+                double dx = xa - cx, dy = ya - cy, dz = za - cz;
+                if (decltype(wrap_c)::value) {
+                    dx = nearest_image(dx, geo.L[0], geo.halfL[0], geo.periodic);
+                    dy = nearest_image(dy, geo.L[1], geo.halfL[1], geo.periodic);
+                    dz = nearest_image(dz, geo.L[2], geo.halfL[2], geo.periodic);
+                }
                 const double q2 = (dx * dx + dy * dy + dz * dz) * hinv2;
                 if (!nonneg_lt(q2, K::R * K::R)) continue;
                 ++nin;
@@ -106,6 +116,9 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 K::eval(qf, ff, dff);
                 k0 += 12.f * ff + 8.f * qf * dff + q2f * K::d2(qf);
             }
+            };
+            if (wrap) evaluate(std::true_type{});
+            else evaluate(std::false_type{});
             if (!__any_sync(0xffffffffu, k < cnt)) break;
         }
         sf = f0;

@@ -212,10 +212,12 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
     double vs = A.acs;
     uint32_t *q = fq + threadIdx.x;
     const int qs = blockDim.x;
+    const float dface = va ? face_distance(A.x, A.y, A.z, geo) : INFINITY;
     uint32_t k = 0;
     for (;;) {
         // phase 1: FP32 pre-test, queue the survivors
         int nq = 0;
+        float reach = 0.f;   // largest |separation| component of a queued candidate
         while (nq < kForceQueue && k < cnt) {
             const uint32_t b = nb_at(ids, k, st);
             ++k;
@@ -223,18 +225,27 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
             const uint4 PB = qpos[b];
             rel_sep(PA, PB, geo, fx, fy, fz);
             const float hmf = fmaxf(hA, __uint_as_float(PB.w));
-            if (!(fx * fx + fy * fy + fz * fz > (float)(K::R * K::R) * kPreBand * hmf * hmf)) q[(nq++) * qs] = b;
+            if (!(fx * fx + fy * fy + fz * fz > (float)(K::R * K::R) * kPreBand * hmf * hmf)) {
+                q[(nq++) * qs] = b;
+                reach = fmaxf(reach, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
+            }
         }
         const int nq_max = __reduce_max_sync(0xffffffffu, (unsigned)nq);
-        // phase 2: the queued pairs in FP64
+        const bool wrap = __any_sync(0xffffffffu, may_cross_face(reach, dface, geo));
+        // phase 2: the queued pairs in FP64, with the nearest-image step only where some lane of the
+        // warp may have a neighbour across a periodic face (warp-uniform)
+        auto evaluate = [&](auto wrap_c) {
         for (int j = 0; j < nq_max; j++) {
             if (j >= nq) continue;
             const uint32_t b = q[j * qs];
             FRec B;
             load_rec<kPoly>(&rec[b], B);
-            const double dx = nearest_image(A.x - B.x, geo.L[0], geo.halfL[0], geo.periodic);
-            const double dy = nearest_image(A.y - B.y, geo.L[1], geo.halfL[1], geo.periodic);
-            const double dz = nearest_image(A.z - B.z, geo.L[2], geo.halfL[2], geo.periodic);
+            double dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+            if (decltype(wrap_c)::value) {
+                dx = nearest_image(dx, geo.L[0], geo.halfL[0], geo.periodic);
+                dy = nearest_image(dy, geo.L[1], geo.halfL[1], geo.periodic);
+                dz = nearest_image(dz, geo.L[2], geo.halfL[2], geo.periodic);
+            }
             // r < R max(h_a, h_b); both kernels and their derivatives vanish at R, so the rounding of
             // r^2 (fused here) only decides pairs whose terms are zero
             const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
@@ -268,6 +279,9 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
                 }
             }
         }
+        };
+        if (wrap) evaluate(std::true_type{});
+        else evaluate(std::false_type{});
         if (!__any_sync(0xffffffffu, k < cnt)) break;
     }
     if (va) {

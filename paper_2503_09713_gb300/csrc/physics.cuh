@@ -217,20 +217,42 @@ __device__ __forceinline__ double kahan_value(float s, float c) { return (double
 
 // Geometry shared by the pair loops.
 struct PairGeo {
-    double L[3], halfL[3];
+    double lo[3], L[3], halfL[3];
     float unit[3];   // length of one step of the fixed-point positions (see qpos_scale)
+    float wmargin;   // 2^-20 of the largest box side (see may_cross_face)
     int periodic;
 };
 
 inline PairGeo make_pair_geo(const sph_params &p) {
     PairGeo g;
     for (int k = 0; k < 3; k++) {
+        g.lo[k] = p.box_lo[k];
         g.L[k] = p.box_hi[k] - p.box_lo[k];
         g.halfL[k] = 0.5 * g.L[k];
         g.unit[k] = (float)(g.L[k] * (p.periodic ? 0x1p-32 : 0x1p-30));
     }
+    g.wmargin = (float)(0x1p-20 * std::max(g.L[0], std::max(g.L[1], g.L[2])));
     g.periodic = p.periodic;
     return g;
+}
+
+// Distance of a position to the nearest face of a periodic box (FP32; +inf for an open box).
+__device__ __forceinline__ float face_distance(double px, double py, double pz, const PairGeo &geo) {
+    if (!geo.periodic) return INFINITY;
+    const double p[3] = {px, py, pz};
+    double d = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 3; k++) d = fmin(d, fmin(p[k] - geo.lo[k], geo.lo[k] + geo.L[k] - p[k]));
+    return (float)d;
+}
+
+// Whether a neighbour whose separation components are at most `reach` (FP32, nearest image) may lie
+// across a periodic face from a particle `dface` from the nearest face.  If not, the particle's
+// position minus the separation stays inside the box on every axis, so the plain FP64 difference
+// of the stored positions is already the nearest image.  The margins cover the FP32 separation's
+// error (2^-24 relative plus one fixed-point step) and the rounding of dface.
+__device__ __forceinline__ bool may_cross_face(float reach, float dface, const PairGeo &geo) {
+    return geo.periodic && !(reach * 1.001f + geo.wmargin < dface);
 }
 
 // FP32 separation r_a - r_b (nearest periodic image) from fixed-point positions.
