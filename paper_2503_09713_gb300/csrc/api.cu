@@ -59,7 +59,7 @@ int ensure_force_records(sph_ctx *c) {
     }
     if (c->frec) return SPH_OK;
     void **ptrs[] = {(void **)&c->frec};
-    const size_t bytes[] = {N * 160};
+    const size_t bytes[] = {N * 176};   // one FP64 force record (FRec) per particle
     return regrow(c, ptrs, bytes, 1, "FP64 force records");
 }
 

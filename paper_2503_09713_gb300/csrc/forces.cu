@@ -26,7 +26,7 @@ struct ForceParams {
     const uint32_t *abort;     // captured step: skip when an earlier stage failed
 };
 
-// Per-particle FP64 record of the force loop: 160 bytes, read as double2.
+// Per-particle FP64 record of the force loop: 176 bytes, read as double2.
 // pre = P/(rho^2 Omega), hqf = 1/(2 rho Omega), acs = alpha_AV c_s, rh2 = (R_kern h)^2 (a pair
 // interacts when r^2 < max(rh2_a, rh2_b), the same bits as (R max h)^2), and for the conductivity
 // term au = alpha_u u and P2 = 2 P (one FP64 product fewer per pair each).  k[]: the smoothing
@@ -35,15 +35,19 @@ struct ForceParams {
 //   r < h:      F/r = g2i r^2 (1/r) + g1i,          g2i = 9/4 k h^-2,  g1i = -3 k h^-1
 //   h <= r < 2h: F/r = (g2o r^2 + g0o) (1/r) + g1o,  g2o = -3/4 k h^-2, g1o = 3 k h^-1, g0o = -3 k
 // with k = C_norm/h^4 (from f'(q) = -3q + 9/4 q^2 and -3 + 3q - 3/4 q^2); then k0 = h^2 (the piece
-// boundary, compared with r^2), k1 = g0o, k2 = g1i, k3 = g1o, k4 = g2i, k5 = g2o.
+// boundary, compared with r^2), k1 = g0o, k2 = g1i, k3 = g1o, k4 = g2i, k5 = g2o.  av1 = -acs hqf and
+// av2 = beta_AV hqf carry the artificial viscosity: for an approaching pair (v.rhat < 0)
+//   pre + q_ab/(rho^2 Omega) = pre - (acs - beta v.rhat) v.rhat hqf = (av2 v.rhat + av1) v.rhat + pre,
+// two fused multiply-adds per side.
 struct __align__(16) FRec {
     double x, y, z, h;
     double vx, vy, vz, au;
     double pre, hqf, acs, P2;
     double rho, rh2, k0, k1;
     double k2, k3, k4, k5;
+    double av1, av2;
 };
-static_assert(sizeof(FRec) == 160, "FP64 force record");
+static_assert(sizeof(FRec) == 176, "FP64 force record");
 
 __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                              const double *__restrict__ z, const double *__restrict__ vx,
@@ -76,6 +80,8 @@ __global__ void k_force_prep(int64_t n, const double *__restrict__ x, const doub
         f.vx = vx[i]; f.vy = vy[i]; f.vz = vz[i]; f.au = fp.alpha_u * ui;
         f.pre = (gam - 1.0) * ui * qf; f.hqf = 0.5 * qf;
         f.acs = (alpha ? alpha[i] : fp.alpha_av) * sqrt(gam * (gam - 1.0) * ui);
+        f.av1 = -f.acs * f.hqf;
+        f.av2 = fp.beta_av * f.hqf;
         f.P2 = 2.0 * ((gam - 1.0) * r * ui);
         f.rho = r;
         const double fn = hinv * hinv * hinv * hinv * fp.kern_c;
@@ -114,6 +120,7 @@ __device__ __forceinline__ void load_rec(const FRec *p, FRec &o) {
         t = __ldg(q + 8); o.k2 = t.x; o.k3 = t.y;
         t = __ldg(q + 9); o.k4 = t.x; o.k5 = t.y;
     }
+    t = __ldg(q + 10); o.av1 = t.x; o.av2 = t.y;
 }
 
 // F_ab(h)/r of one side of a pair from its record (see FRec), r2 = r^2, rinv = 1/r, inside the
@@ -258,10 +265,9 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
             const double vdotr = vd * rinv;
             double Aa = A.pre, Ab = B.pre;
             if (__double_as_longlong(vdotr) < 0) {   // sign bit: approaching (-0 changes nothing below)
-                const double w = fp.beta_av * vdotr;   // = -beta |v.rhat|
-                Aa -= (A.acs - w) * vdotr * A.hqf;
-                Ab -= (B.acs - w) * vdotr * B.hqf;
-                vs = nonneg_max(vs, A.acs - w);
+                Aa = fma(fma(A.av2, vdotr, A.av1), vdotr, Aa);
+                Ab = fma(fma(B.av2, vdotr, B.av1), vdotr, Ab);
+                vs = nonneg_max(vs, fma(-fp.beta_av, vdotr, A.acs));   // alpha c_s + beta |v.rhat|
             }
             const double sc_ = Aa * Ga + Ab * Gb;
             axs -= sc_ * dx;
