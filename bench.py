@@ -48,8 +48,8 @@ FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan)
 TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
                    "paper_2503_09713_gb300/csrc/sph_internal.cuh")
 TRAFFIC = {
-    "k_forces_fp64": {"workload": "sedov128", "bytes": 1141351168 + 96429312, "src_sha256": "eff73214bbc897a6acc7090fc68a197a647ba93df20d014cceb3be95f7fc9695"},
-    "k_forces_mixed": {"workload": "sedov128", "bytes": 889846016 + 92917504, "src_sha256": "eff73214bbc897a6acc7090fc68a197a647ba93df20d014cceb3be95f7fc9695"},
+    "k_forces_fp64": {"workload": "sedov128", "bytes": 1183352832 + 99274752, "src_sha256": "8f828add51abc16facb1eeb59efd6a178c827c4b71388c651d6bb646e36c10e5"},
+    "k_forces_mixed": {"workload": "sedov128", "bytes": 889846016 + 92917504, "src_sha256": "8f828add51abc16facb1eeb59efd6a178c827c4b71388c651d6bb646e36c10e5"},
 }
 
 

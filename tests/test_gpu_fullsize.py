@@ -6,8 +6,9 @@
   oracle (uniform-grid candidates, OpenMP) for the tree, the converged state and one step;
   neighbour sets of sampled particles against brute force.
 * uniform 256^3 (16,777,216 particles): mixed precision against FP64 for every particle
-  (density <= 1e-5 relative, accelerations <= 1e-4 of max|a|), sampled particles of the FP64 run
-  against the oracle's definitions evaluated one by one.
+  (density <= 1e-5 relative, accelerations <= 1e-4 of max|a|), and 48 sampled particles of both
+  runs against the oracle's definitions evaluated one by one (FP64 at the FP64 tolerances, mixed at
+  the mixed ones).
 * Sedov 512^3 (134,217,728 particles): the same checks on the converged state, and sampled
   particles after one FP64 step.
 
@@ -148,20 +149,66 @@ def test_uniform256_mixed_against_fp64_and_sampled_oracle():
     amax = np.max(np.abs(np.stack([g64["ax"], g64["ay"], g64["az"]])))
     for k in ("ax", "ay", "az"):
         assert np.max(np.abs(g32[k] - g64[k])) < 1e-4 * amax
-    # sampled particles of the FP64 run against the definitions, evaluated one by one
+    # sampled particles of both runs against the definitions, evaluated one by one on the
+    # neighbourhood of the samples (exact: see _local): FP64 at the FP64 tolerances, mixed at the
+    # mixed ones (density 1e-5 relative, accelerations 1e-4 of max|a|)
     rng = np.random.default_rng(9)
-    idx = rng.integers(0, n, 6)
-    r = O.subset_forces(w["x"], w["y"], w["z"], w["vx"], w["vy"], w["vz"], w["u"], w["mass"], O.Params(), idx,
-                        3.0 * w["dx"])
+    idx = rng.choice(n, 48, replace=False)
+    h_hi = 2.0 * w["dx"]   # h is ~1.2 dx; a root above this bound raises in the oracle
+    cells = _CellIndex(w, 4.2 * h_hi)
+    rs = []
+    for a in idx:
+        sub, j = cells.local(a)
+        rs.append(O.subset_forces(*[sub[k] for k in ("x", "y", "z", "vx", "vy", "vz", "u")], w["mass"],
+                                  O.Params(), [j], h_hi))
+    r = {k: np.array([x[k][0] for x in rs]) for k in rs[0]}
     assert np.max(np.abs(g64["h"][idx] / r["h"] - 1)) < 1e-9
     for k in ("ax", "ay", "az"):
         assert np.max(np.abs(g64[k][idx] - r[k])) < 1e-8 * amax
+    rho_o = w["mass"] * (1.2 / r["h"]) ** 3
+    assert np.max(np.abs(g32["rho"][idx] / rho_o - 1)) < 1e-5
+    for k in ("ax", "ay", "az"):
+        assert np.max(np.abs(g32[k][idx] - r[k])) < 1e-4 * amax
 
 
 def _fetch(s, fields):
     """Selected fields of a device state, in the original particle order (host copies)."""
     ids = s.t["id"].cpu().numpy().view(np.uint32).astype(np.int64)
     return {f: to_orig(s.t[f].cpu().numpy(), ids) for f in fields}
+
+
+class _CellIndex:
+    """Particles of a periodic unit box binned into cells of side >= radius: the particles within
+    `radius` of one particle, as sub-arrays, from its 27 surrounding cells (see _local for why such
+    a neighbourhood gives the oracle's exact answer when radius is above 4 h_hi)."""
+
+    def __init__(self, st, radius):
+        self.st, self.r = st, radius
+        self.G = G = max(3, int(1.0 / radius))
+        self.c = [np.minimum((st[k] * G).astype(np.int64), G - 1) for k in ("x", "y", "z")]
+        key = (self.c[0] * G + self.c[1]) * G + self.c[2]
+        self.order = np.argsort(key, kind="stable")
+        self.skey = key[self.order]
+
+    def local(self, a):
+        G, st = self.G, self.st
+        ca = [int(c[a]) for c in self.c]
+        parts = []
+        for ox in (-1, 0, 1):
+            for oy in (-1, 0, 1):
+                for oz in (-1, 0, 1):
+                    key = (((ca[0] + ox) % G) * G + (ca[1] + oy) % G) * G + (ca[2] + oz) % G
+                    lo, hi = np.searchsorted(self.skey, [key, key + 1])
+                    parts.append(self.order[lo:hi])
+        sel = np.unique(np.concatenate(parts))
+        d2 = np.zeros(len(sel))
+        for k in ("x", "y", "z"):
+            d = np.abs(st[k][sel] - st[k][a])
+            d = np.minimum(d, 1.0 - d)
+            d2 += d * d
+        sel = sel[d2 < self.r * self.r]
+        sub = {k: np.ascontiguousarray(st[k][sel]) for k in ("x", "y", "z", "vx", "vy", "vz", "u")}
+        return sub, int(np.searchsorted(sel, a))
 
 
 def _local(st, idx, radius):
