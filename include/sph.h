@@ -258,7 +258,7 @@ int sph_get_launch(sph_ctx *ctx, sph_launch *out);
 int sph_set_launch(sph_ctx *ctx, const sph_launch *in);
 
 /* Autotuner of the launch shapes (no counterpart in the paper; the paper reports the optimum
- * reduction level of its own hardware, App. C, "around 10 particles per leaf").  Times A1-A9 on *s
+ * reduction level of its own hardware, App. C: about ten particles per leaf).  Times A1-A9 on *s
  * (device pointers, as sph_step) for each candidate: the reduction levels 1-7, then, one knob at a
  * time, the stage-2 warps per block {2, 4, 8} and the density, force and walk block sizes
  * {64, 128, 256}, two runs each with CUDA events (the faster counts), and keeps the fastest

@@ -59,7 +59,7 @@ def test_derivative_finite_difference(name, k):
 @pytest.mark.parametrize("name,k", [("M4", 0), ("M6", 2)])
 def test_mean_neighbour_number(name, k):
     """Uniform random particles at the density root: the mean number of neighbours inside R h is
-    close to 4/3 pi (R hfact)^3, the paper's "around 60" for M4 with hfact 1.2 (57.9) and 113 for
+    close to 4/3 pi (R hfact)^3: about 60 for M4 with hfact 1.2 (57.9), as the paper states, and 113 for
     M6 with hfact 1.0 (Sect. 4)."""
     rng = np.random.default_rng(17)
     n = 6000
