@@ -37,7 +37,7 @@ FLOP_DENS_CAND = 9           # separation, q^2
 FLOP_DENS_PAIR = 20          # sqrt, M4 value and two derivatives, the three sums
 # FP32 pair loop of the mixed path (an FMA counts 2; Kahan additions 4 each; the artificial
 # viscosity, evaluated only for approaching pairs, is not counted)
-FLOP_FORCE32_CAND = 16       # cell-relative separation, r^2, radius test
+FLOP_FORCE32_CAND = 10       # separation, r^2, radius test (the same count as the FP64 loop's)
 FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan), energy and
                              # conductivity (Kahan), divergence
 
@@ -48,8 +48,8 @@ FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan)
 TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
                    "paper_2503_09713_gb300/csrc/sph_internal.cuh")
 TRAFFIC = {
-    "k_forces_fp64": {"workload": "sedov128", "bytes": 1183352832 + 99274752, "src_sha256": "8f828add51abc16facb1eeb59efd6a178c827c4b71388c651d6bb646e36c10e5"},
-    "k_forces_mixed": {"workload": "sedov128", "bytes": 889846016 + 92917504, "src_sha256": "8f828add51abc16facb1eeb59efd6a178c827c4b71388c651d6bb646e36c10e5"},
+    "k_forces_fp64": {"workload": "sedov128", "bytes": 1183352832 + 99274752, "src_sha256": "0553bf72286062dbf95e3843835474eb82febe75d52c81c37dc032d359b40b82"},
+    "k_forces_mixed": {"workload": "sedov128", "bytes": 889846016 + 92917504, "src_sha256": "0553bf72286062dbf95e3843835474eb82febe75d52c81c37dc032d359b40b82"},
 }
 
 

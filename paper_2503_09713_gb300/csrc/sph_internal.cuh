@@ -15,7 +15,6 @@ namespace sph {
 constexpr int kMortonBits = 21;          // bits per axis; 63-bit codes (App. B)
 constexpr int kCodeBits = 3 * kMortonBits;
 constexpr int kGroup = 32;               // largest neighbour-search group (one warp)
-constexpr int kCellBits = 10;            // cell grid of the FP32 relative coordinates: 2^10 per axis
 constexpr int kStackDepth = 66;          // tree-walk stack (tree depth <= 63 for distinct 63-bit codes)
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kGatherBatch = 4;          // state fields reordered per gather pass (scratch: 4 x n_cap doubles)

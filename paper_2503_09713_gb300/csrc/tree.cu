@@ -95,7 +95,7 @@ __global__ void k_morton(int64_t n, const double *__restrict__ x, const double *
 
 // ====================================================================================== radix sort
 // LSD radix sort of (63-bit key, u32 value) pairs, 8 passes of 8-bit digits.  One kernel per pass
-// ranks a 4096-key tile in shared memory (warp multi-split with match.any, stable), obtains the
+// ranks a 2048-key tile (kSortTile) in shared memory (warp multi-split with match.any, stable), obtains the
 // tile's global digit offsets by decoupled look-back over earlier tiles, and writes each digit run
 // contiguously.
 constexpr int kRsThreads = 256;
