@@ -313,15 +313,14 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
         cur = r0.x;
         rend = r0.y;
     }
-    // ---- (1) tests, 32 candidates of the concatenated ranges per chunk
-    for (int64_t chunk = 0; chunk < nchunks; ++chunk) {
-        uint32_t *gch = gbase + (size_t)chunk * kChunkWords;   // [0, 32): masks, [32, 64): candidates
-        int64_t b = -1;   // this lane's candidate
-        int filled = 0;
-        while (filled < 32 && ci < ncand) {
-            const int take = (int)min((int64_t)(32 - filled), rend - cur);
-            if (lane >= filled && lane < filled + take) b = cur + (lane - filled);
-            filled += take;
+    // the lane's candidate of the next chunk (the next 32 of the concatenated ranges) and its record
+    auto fill = [&](int64_t &bn, int &fn) {
+        bn = -1;
+        fn = 0;
+        while (fn < 32 && ci < ncand) {
+            const int take = (int)min((int64_t)(32 - fn), rend - cur);
+            if (lane >= fn && lane < fn + take) bn = cur + (lane - fn);
+            fn += take;
             cur += take;
             if (cur == rend && ++ci < ncand) {
                 const uint2 r = cl[ci];
@@ -329,11 +328,27 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
                 rend = r.y;
             }
         }
+    };
+    int64_t b_next;
+    int f_next;
+    fill(b_next, f_next);
+    uint4 Q_next = b_next >= 0 ? qpos[b_next] : make_uint4(0u, 0u, 0u, 0u);
+    // ---- (1) tests, 32 candidates of the concatenated ranges per chunk; the next chunk's records
+    // are loaded while this one is tested
+    for (int64_t chunk = 0; chunk < nchunks; ++chunk) {
+        uint32_t *gch = gbase + (size_t)chunk * kChunkWords;   // [0, 32): masks, [32, 64): candidates
+        const int64_t b = b_next;   // this lane's candidate
+        const int filled = f_next;
+        const uint4 Qc = Q_next;
+        if (chunk + 1 < nchunks) {
+            fill(b_next, f_next);
+            Q_next = b_next >= 0 ? qpos[b_next] : make_uint4(0u, 0u, 0u, 0u);
+        }
         // compact: group-frame position and (s h_b)^2; otherwise the fixed-point position
         float4 P = make_float4(1e30f, 1e30f, 1e30f, 0.f);
         float hb = 0.f;
         if (b >= 0) {
-            const uint4 Q = qpos[b];
+            const uint4 Q = Qc;
             hb = __uint_as_float(Q.w);
             if (compact) {
                 float px, py, pz;
@@ -491,10 +506,16 @@ __global__ void __launch_bounds__(kS2MaxWarps * 32) k_stage2(
     const int64_t row = 4 * gsize;
     uint4 quad = make_uint4(0u, 0u, 0u, 0u);
     uint32_t k = 0;
+    // the next chunk's mask and candidates are loaded while the current one is expanded
+    uint32_t m_next = nchunks > 0 ? gbase[lane] : 0u, id_next = nchunks > 0 ? gbase[32 + lane] : 0u;
     for (int64_t chunk = 0; chunk < nchunks; ++chunk) {
-        const uint32_t *gch = gbase + (size_t)chunk * kChunkWords;
-        uint32_t m = gch[lane];
-        s_jj[lane] = (int)gch[32 + lane];   // the chunk's candidates (slots without a mask bit unused)
+        uint32_t m = m_next;
+        s_jj[lane] = (int)id_next;   // the chunk's candidates (slots without a mask bit unused)
+        if (chunk + 1 < nchunks) {
+            const uint32_t *nxt = gbase + (size_t)(chunk + 1) * kChunkWords;
+            m_next = nxt[lane];
+            id_next = nxt[32 + lane];
+        }
         __syncwarp();
         while (m) {
             const int jj = __ffs(m) - 1;
