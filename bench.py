@@ -48,8 +48,8 @@ FLOP_FORCE32_PAIR = 69       # rsqrt, two M4 gradients, v.rhat, momentum (Kahan)
 TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb300/csrc/physics.cuh",
                    "paper_2503_09713_gb300/csrc/sph_internal.cuh")
 TRAFFIC = {
-    "k_forces_fp64": {"workload": "sedov128", "bytes": 1183352832 + 99274752, "src_sha256": "0553bf72286062dbf95e3843835474eb82febe75d52c81c37dc032d359b40b82"},
-    "k_forces_mixed": {"workload": "sedov128", "bytes": 889846016 + 92917504, "src_sha256": "0553bf72286062dbf95e3843835474eb82febe75d52c81c37dc032d359b40b82"},
+    "k_forces_fp64": {"workload": "sedov128", "bytes": 1183352832 + 99274752, "src_sha256": "17092a40ea792687bf92f69ba16794e2e8a262bc8987bc20a471b684675a9ff9"},
+    "k_forces_mixed": {"workload": "sedov128", "bytes": 889846016 + 92917504, "src_sha256": "17092a40ea792687bf92f69ba16794e2e8a262bc8987bc20a471b684675a9ff9"},
 }
 
 

@@ -37,10 +37,11 @@ int ensure_tree(sph_ctx *c, int64_t L) {
     const int64_t cap = std::min(L + L / 4 + 64, c->n_cap);   // L <= n
     void **ptrs[] = {(void **)&c->lchild, (void **)&c->rchild, (void **)&c->endrange, (void **)&c->lflag,
                      (void **)&c->rflag, (void **)&c->child, (void **)&c->node_parent, (void **)&c->leaf_parent,
-                     (void **)&c->visit, (void **)&c->nodes, (void **)&c->nodesf};
+                     (void **)&c->visit, (void **)&c->nodes, (void **)&c->nodesf, (void **)&c->wnodes};
     const size_t bytes[] = {(size_t)cap * 4, (size_t)cap * 4, (size_t)cap * 4, (size_t)cap, (size_t)cap,
                             (size_t)cap * 8, (size_t)cap * 4, (size_t)cap * 4, (size_t)cap * 4,
-                            (size_t)cap * 2 * sizeof(Node), (size_t)cap * 2 * sizeof(NodeF)};
+                            (size_t)cap * 2 * sizeof(Node), (size_t)cap * 2 * sizeof(NodeF),
+                            (size_t)cap * sizeof(WNode)};
     c->l_cap = 0;
     int r = regrow(c, ptrs, bytes, sizeof(ptrs) / sizeof(ptrs[0]), "tree arrays");
     if (r) return r;
@@ -156,7 +157,7 @@ int alloc(sph_ctx *c, T **p, size_t count) {
 void free_all(sph_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->digit_hist, c->lookback, c->tile_ctr,
                     c->mask[0], c->mask[1], c->scan_tmp, c->leaf_first, c->mu_leaf, c->lchild, c->rchild,
-                    c->endrange, c->lflag, c->rflag, c->child, c->node_parent, c->leaf_parent, c->visit, c->nodes, c->nodesf,
+                    c->endrange, c->lflag, c->rflag, c->child, c->node_parent, c->leaf_parent, c->visit, c->nodes, c->nodesf, c->wnodes,
                     c->gather_tmp, c->id_tmp, c->qpos, c->h_base, c->gboxf, c->grp_chunks, c->chunk_off, c->masks, c->cand, c->cand_cnt, c->nb_cnt, c->nb_ptr,
                     c->grp_slots, c->grp_off, c->nb_ids, c->frec, c->m_v, c->m_t, c->m_r, c->a_new, c->dhdt, c->block_part, c->rerun,
                     c->hs_fields, c->hs_id, c->dscal, c->box_of, c->box_mass, c->box_gamma, c->box_root,

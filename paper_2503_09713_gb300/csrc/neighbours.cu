@@ -103,7 +103,7 @@ __device__ __forceinline__ float walk_radius(float s, float h1, float h2) {
 }
 
 __global__ void __launch_bounds__(256) k_walk(Groups gr, Count Gc, Count Lc, const NodeF *__restrict__ gboxf,
-                                             const NodeF *__restrict__ nodesf, const int32_t *__restrict__ child,
+                                             const NodeF *__restrict__ nodesf, const WNode *__restrict__ wnodes,
                                              const int64_t *__restrict__ leaf_first,
                                              const int32_t *__restrict__ box_root, float s, Geo geo,
                                              uint2 *__restrict__ cand, uint32_t *__restrict__ cand_cnt, int cap,
@@ -138,9 +138,9 @@ __global__ void __launch_bounds__(256) k_walk(Groups gr, Count Gc, Count Lc, con
                                       __fadd_rd(q.lo[2], sh[2][iz])};
                 const float qhi[3] = {__fadd_ru(q.hi[0], sh[0][ix]), __fadd_ru(q.hi[1], sh[1][iy]),
                                       __fadd_ru(q.hi[2], sh[2][iz])};
-                // Depth-first walk over hit nodes: a node's two children are loaded and tested
-                // together when the node is popped, and only hits are pushed (right, then left, so
-                // leaves come out in Morton order).
+                // Depth-first walk over hit nodes: a node's two children are loaded (one 64-byte
+                // record of their boxes and ids, WNode) and tested together when the node is popped,
+                // and only hits are pushed (right, then left, so leaves come out in Morton order).
                 auto hits = [&](const NodeF &nd) {
                     const float r = walk_radius(s, q.hmax, nd.hmax);
                     // squared distance between the two boxes, rounded down, against r^2 rounded up
@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(256) k_walk(Groups gr, Count Gc, Count Lc, con
                         push_leaf(out, cap, count, (uint32_t)leaf_first[j], (uint32_t)leaf_first[j + 1]);
                         continue;
                     }
-                    const int2 ch = *reinterpret_cast<const int2 *>(&child[2 * c]);
-                    const NodeF nl = load_nodef(&nodesf[ch.x]), nr = load_nodef(&nodesf[ch.y]);
+                    const NodeF nl = load_nodef(&wnodes[c].l), nr = load_nodef(&wnodes[c].r);
+                    const int2 ch = make_int2(__float_as_int(nl.pad), __float_as_int(nr.pad));
                     const bool hl = hits(nl), hr = hits(nr);
                     if (sp + 2 > kStackDepth) {
                         atomicOr(flags, kErrStack);
@@ -604,7 +604,7 @@ int neighbours_build(sph_ctx *c, const sph_state *s) {
     for (int attempt = 0;; attempt++) {
         if (!c->capturing) SPH_CUDA(c, cudaMemsetAsync(&c->dscal->flags, 0, sizeof(uint32_t), c->stream));
         k_walk<<<grid_for(G, c->launch.walk_block), c->launch.walk_block, 0, c->stream>>>(
-            gr, group_count(c), leaf_count(c), c->gboxf, c->nodesf, c->child, c->leaf_first, c->box_root, (float)sc,
+            gr, group_count(c), leaf_count(c), c->gboxf, c->nodesf, c->wnodes, c->leaf_first, c->box_root, (float)sc,
             geo, c->cand, c->cand_cnt, c->cand_cap, c->grp_chunks, &c->dscal->flags);
         SPH_LAUNCH_CHECK(c, "k_walk");
         int r = exclusive_scan_i64_dev(c, c->grp_chunks, c->chunk_off, &c->dscal->n_groups, G);

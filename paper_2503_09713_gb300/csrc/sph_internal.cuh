@@ -86,6 +86,12 @@ struct __align__(16) NodeF {
     float pad;
 };
 
+// Both children of an internal node as the walk tests them (64 bytes): their FP32 boxes, each child's
+// node id in its .pad (as int bits), so that a popped node costs one dependent load.
+struct __align__(16) WNode {
+    NodeF l, r;
+};
+
 __device__ __forceinline__ NodeF to_float_outward(const Node &b) {
     NodeF f;
     for (int k = 0; k < 3; k++) {
@@ -226,6 +232,7 @@ struct sph_ctx {
     uint32_t *visit = nullptr;         // [n_cap]
     sph::Node *nodes = nullptr;        // [2 n_cap]
     sph::NodeF *nodesf = nullptr;      // [2 n_cap] FP32 outward copy for the walk
+    sph::WNode *wnodes = nullptr;      // [n_cap] per internal node: both children for the walk
     int64_t n_leaves = 0;
     int64_t l_cap = 0;                 // capacity of the leaf- and node-indexed arrays (ensure_tree)
     bool tree_valid = false;

@@ -598,7 +598,8 @@ __device__ __forceinline__ void load_node(const Node *nd, Node &o) {
 __global__ void k_boxes(Count Lc, const int64_t *__restrict__ leaf_first, const double *__restrict__ x,
                         const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h,
                         const int32_t *__restrict__ child, const int32_t *__restrict__ node_parent,
-                        const int32_t *__restrict__ leaf_parent, uint32_t *visit, Node *nodes, NodeF *nodesf) {
+                        const int32_t *__restrict__ leaf_parent, uint32_t *visit, Node *nodes, NodeF *nodesf,
+                        WNode *wnodes) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t L = read_count(Lc, kAbortTree);
     if (j >= L) return;
@@ -631,8 +632,14 @@ __global__ void k_boxes(Count Lc, const int64_t *__restrict__ leaf_first, const 
         if (old == 0) return;
         __threadfence();
         Node l, r;
-        load_node(&nodes[child[2 * node]], l);
-        load_node(&nodes[child[2 * node + 1]], r);
+        const int32_t cl = child[2 * node], cr = child[2 * node + 1];
+        load_node(&nodes[cl], l);
+        load_node(&nodes[cr], r);
+        NodeF fl = to_float_outward(l), fr = to_float_outward(r);   // the walk's copy of both children
+        fl.pad = __int_as_float(cl);
+        fr.pad = __int_as_float(cr);
+        wnodes[node].l = fl;
+        wnodes[node].r = fr;
         Node m;
         for (int k = 0; k < 3; k++) {
             m.lo[k] = fmin(l.lo[k], r.lo[k]);
@@ -812,7 +819,7 @@ static int boxes(sph_ctx *c, const sph_state *s) {
     if (L > 1) SPH_CUDA(c, cudaMemsetAsync(c->visit, 0, (size_t)(L - 1) * sizeof(uint32_t), c->stream));
     k_boxes<<<grid_for(L, 128), 128, 0, c->stream>>>(leaf_count(c), c->leaf_first, s->x, s->y, s->z, s->h, c->child,
                                                      c->node_parent, c->leaf_parent, c->visit, c->nodes,
-                                                     c->nodesf);
+                                                     c->nodesf, c->wnodes);
     SPH_LAUNCH_CHECK(c, "k_boxes");
     return SPH_OK;
 }
