@@ -24,6 +24,15 @@ struct DensParams {
     const uint16_t *box_of;   // box of each particle (batch) or nullptr
 };
 
+// A positive normal float as a double, from its bits: exponent rebiased (127 -> 1023), mantissa
+// moved up by 29 bits.  Exact (IEEE 754 binary32 -> binary64) and on the integer pipe.
+__device__ __forceinline__ double widen_normal(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const unsigned long long d = ((unsigned long long)((u >> 23) + (1023u - 127u)) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
 constexpr int kDensQueue = 32;   // FP64 path: queued candidates per thread (8 bytes each in shared memory)
 
 // Sums over the neighbours of a at smoothing length h (kernel K):  sf = sum f(q),
@@ -102,9 +111,11 @@ __device__ __forceinline__ void density_sums(int64_t a, double ha, uint32_t cnt,
                 const float q2f = __uint_as_float(ec.y) * hinv2f;
                 const float qf = sqrtf(q2f);
                 // q = sqrt(q2) by one Newton-Raphson step from the FP32 root of the FP32 separation
-                // (relative error below 1e-13)
-                const double qd = (double)qf;
-                const double q = qf > 0.f ? fma(fma(-qd, qd, q2), (double)(0.5f / qf), qd) : sqrt(q2);
+                // (relative error below 1e-13); the two FP32 values are widened by their bits
+                // (exact for normal numbers, integer pipe)
+                const double q = qf >= 0x1p-126f ? fma(fma(-widen_normal(qf), widen_normal(qf), q2),
+                                                       widen_normal(0.5f / qf), widen_normal(qf))
+                                                 : sqrt(q2);
                 double f, df;
                 K::eval(q, f, df);
                 f0 += f;
