@@ -49,7 +49,7 @@ TRAFFIC_SOURCES = ("paper_2503_09713_gb300/csrc/forces.cu", "paper_2503_09713_gb
                    "paper_2503_09713_gb300/csrc/sph_internal.cuh")
 TRAFFIC = {
     "k_forces_fp64": {"workload": "sedov128", "bytes": 1183352832 + 99274752, "src_sha256": "17092a40ea792687bf92f69ba16794e2e8a262bc8987bc20a471b684675a9ff9"},
-    "k_forces_mixed": {"workload": "sedov128", "bytes": 889846016 + 92917504, "src_sha256": "17092a40ea792687bf92f69ba16794e2e8a262bc8987bc20a471b684675a9ff9"},
+    "k_forces_mixed": {"workload": "sedov128", "bytes": 889846016 + 92917504, "src_sha256": "ddf46fd8d25de4283dfdd47255f394b4b362b8da6f1fd6c2d020300b5a06b986"},
 }
 
 

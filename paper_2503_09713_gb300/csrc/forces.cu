@@ -136,6 +136,23 @@ __device__ __forceinline__ double grad_over_r(const FRec &R, double r2, double r
     }
 }
 
+// 1/sqrt(x) for 2^-125 <= x < 2^127 without FP32/FP64 conversion instructions (they issue on the
+// FP64 pipe, this loop's bound): x narrowed to FP32 by truncating its bits (relative error below
+// 2^-23), its FP32 reciprocal square root widened back by its bits (exact), then one Newton-Raphson
+// step y <- y + y (1 - x y^2) / 2, which squares the relative error (below 1e-13).
+__device__ __forceinline__ bool fp32_normal_range(double x) {
+    const uint32_t e = (uint32_t)((unsigned long long)__double_as_longlong(x) >> 52);   // x > 0: no sign bit
+    return e >= 1023u - 125u && e <= 1023u + 126u;
+}
+__device__ __forceinline__ double rsqrt_via_fp32(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t xf = (((uint32_t)(b >> 52) - (1023u - 127u)) << 23) | (uint32_t)((b >> 29) & 0x7fffffu);
+    const uint32_t u = __float_as_uint(rsqrtf(__uint_as_float(xf)));
+    const double y = __longlong_as_double((long long)(((unsigned long long)((u >> 23) + (1023u - 127u)) << 52) |
+                                                      ((unsigned long long)(u & 0x7fffffu) << 29)));
+    return fma(0.5 * y, fma(-x * y, y, 1.0), y);
+}
+
 struct ForceOut {
     double *ax, *ay, *az, *du, *vsig;
     double *dhdt;   // dh/dt = -h/(3 rho Omega) sum_b m v_ab . grad_a W_ab(h_a)  (Eq. rhoh with the SPH
@@ -258,7 +275,10 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
             const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
             if (!nonneg_lt(r2, nonneg_max(A.rh2, B.rh2))) continue;
             ++npair;
-            const double rinv = rsqrt(r2);
+            // the warp takes the FP32-seeded form when every active lane's r^2 is in its range
+            double rinv;
+            if (__all_sync(__activemask(), fp32_normal_range(r2))) rinv = rsqrt_via_fp32(r2);
+            else rinv = rsqrt(r2);
             // G = F_ab/r of both sides: F rhat = G (r_a - r_b), v_ab . rhat F = (v_ab . (r_a - r_b)) G
             const double Ga = grad_over_r<K>(A, r2, rinv), Gb = grad_over_r<K>(B, r2, rinv);
             const double vd = (A.vx - B.vx) * dx + (A.vy - B.vy) * dy + (A.vz - B.vz) * dz;
@@ -279,7 +299,11 @@ __global__ void __launch_bounds__(256) k_forces_fp64(int64_t n, const FRec *__re
             if (fp.alpha_u != 0.0) {
                 const double t = fabs(A.P2 - B.P2);   // 2 |P_a - P_b|; v_sig^u = sqrt(t / (rho_a + rho_b))
                 if (__double_as_longlong(t) > 0) {
-                    const double vsu = t * rsqrt(t * (A.rho + B.rho));
+                    const double xu = t * (A.rho + B.rho);
+                    double ru;
+                    if (__all_sync(__activemask(), fp32_normal_range(xu))) ru = rsqrt_via_fp32(xu);
+                    else ru = rsqrt(xu);
+                    const double vsu = t * ru;
                     // F_a hqf_a + F_b hqf_b = r (G_a hqf_a + G_b hqf_b)
                     dus += vsu * (A.au - B.au) * ((r2 * rinv) * (Ga * A.hqf + Gb * B.hqf));
                 }
